@@ -1,0 +1,233 @@
+"""CPU oracle for the HoneyComb hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's timed
+CPU-baseline leg may import this package.  The product path (the CUDA
+library and its binding) never does, and shares no code with it.
+
+The arithmetic lives in ``oracle.c`` (plain C, compiled with gcc into
+``oracle/_build``); this module only marshals numpy arrays.  Functions and
+the passages they follow:
+
+* ``coco_build``   -- the CoCo trie of a binary relation (Sec. 4, Fig.
+  "cocoindex"): V1 (distinct first values), O1 (run starts, O1[l1] = n), V2.
+* ``partition``    -- HyperCube partitioning of one relation (Sec. 4,
+  Example "partition"): R~, B, B^pref and the per-partition CoCo.
+* ``gj_count`` / ``gj_enumerate`` -- Generic Join of a full conjunctive
+  query of binary atoms (Eq. "full:cq", Sec. 2 "Generic Join Algorithm",
+  Sec. 5 intersection and level restriction).
+* ``tuple_cells``  -- the HyperCube cell of each output tuple (Sec. 5:
+  the outputs of different cells are disjoint).
+* ``share``        -- h_i(x) mod P_i, read as ((fmix32(x ^ seed) * P) >> 32).
+
+A query is ``(n_vars, atoms)`` with ``atoms`` a list of ``(var0, var1)``:
+the relation bound to atom j holds pairs whose column 0 is variable var0
+and column 1 is variable var1.  Output tuples list values in variable-id
+order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+_u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+_u64p = np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+
+OC_ECAP = 3
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` with gcc into ``oracle/_build/liboracle.so``."""
+    out_dir = os.path.join(_HERE, "_build")
+    so = os.path.join(out_dir, "liboracle.so")
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+        os.makedirs(out_dir, exist_ok=True)
+        tmp = so + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", src, "-o", tmp])
+        os.replace(tmp, so)
+    return so
+
+
+def _lib():
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    lib = ctypes.CDLL(build())
+    vp = ctypes.c_void_p
+    u64 = ctypes.c_uint64
+    lib.oc_fmix32.restype = ctypes.c_uint32
+    lib.oc_fmix32.argtypes = [ctypes.c_uint32]
+    lib.oc_share.restype = ctypes.c_uint32
+    lib.oc_share.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
+    lib.oc_has_duplicates.restype = ctypes.c_int
+    lib.oc_has_duplicates.argtypes = [vp, u64]
+    lib.oc_coco_build.restype = ctypes.c_int
+    lib.oc_coco_build.argtypes = [vp, u64, ctypes.c_int, _u32p, _u64p, _u32p, ctypes.POINTER(u64)]
+    lib.oc_partition.restype = ctypes.c_int
+    lib.oc_partition.argtypes = [vp, u64, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
+                                 ctypes.c_uint32, ctypes.c_uint32, _u32p, _u64p, _u64p, _u32p,
+                                 _u64p, _u64p, ctypes.POINTER(u64)]
+    lib.oc_gj_count.restype = ctypes.c_int
+    lib.oc_gj_count.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp), _u64p, _i32p, _i32p,
+                                _i32p, vp, u64, ctypes.c_int, ctypes.POINTER(u64),
+                                ctypes.POINTER(u64), vp, u64, ctypes.POINTER(u64)]
+    lib.oc_gj_enumerate.restype = ctypes.c_int
+    lib.oc_gj_enumerate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp), _u64p, _i32p,
+                                    _i32p, _i32p, vp, u64, vp, u64, ctypes.POINTER(u64)]
+    lib.oc_tuple_cells.restype = ctypes.c_int
+    lib.oc_tuple_cells.argtypes = [vp, u64, ctypes.c_int, _u32p, _u32p, _u32p]
+    _LIB = lib
+    return lib
+
+
+def _pairs(a) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.uint32))
+    if a.size == 0:
+        return np.zeros((0, 2), dtype=np.uint32)
+    if a.ndim != 2 or a.shape[1] != 2:
+        raise ValueError("a relation is an (n, 2) array of pairs")
+    return a
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise OracleError(f"{what} failed with code {rc}")
+
+
+def fmix32(x: int) -> int:
+    return int(_lib().oc_fmix32(int(x) & 0xFFFFFFFF))
+
+
+def share(x: int, seed: int, p: int) -> int:
+    """h(x) mod P read as (fmix32(x ^ seed) * P) >> 32."""
+    return int(_lib().oc_share(int(x) & 0xFFFFFFFF, int(seed) & 0xFFFFFFFF, int(p)))
+
+
+def has_duplicates(pairs) -> bool:
+    p = _pairs(pairs)
+    return bool(_lib().oc_has_duplicates(p.ctypes.data, p.shape[0]))
+
+
+def coco_build(pairs, attr_order: int = 0):
+    """(V1 uint32[l1], O1 uint64[l1+1], V2 uint32[n]) of the relation."""
+    p = _pairs(pairs)
+    n = p.shape[0]
+    v1 = np.zeros(max(n, 1), dtype=np.uint32)
+    o1 = np.zeros(n + 1, dtype=np.uint64)
+    v2 = np.zeros(max(n, 1), dtype=np.uint32)
+    l1 = ctypes.c_uint64(0)
+    _check(_lib().oc_coco_build(p.ctypes.data, n, int(attr_order), v1, o1, v2, ctypes.byref(l1)),
+           "coco_build")
+    l = l1.value
+    return v1[:l].copy(), o1[:l + 1].copy(), v2[:n].copy()
+
+
+def partition(pairs, attr_order: int, seed_a: int, pa: int, seed_b: int, pb: int) -> dict:
+    """Partitioned relation and per-partition CoCo (global offsets)."""
+    p = _pairs(pairs)
+    n = p.shape[0]
+    npart = pa * pb
+    rt = np.zeros(max(2 * n, 1), dtype=np.uint32)
+    hist = np.zeros(npart, dtype=np.uint64)
+    pref = np.zeros(npart + 1, dtype=np.uint64)
+    v1 = np.zeros(max(n, 1), dtype=np.uint32)
+    o1 = np.zeros(n + 1, dtype=np.uint64)
+    start = np.zeros(npart + 1, dtype=np.uint64)
+    l1 = ctypes.c_uint64(0)
+    _check(_lib().oc_partition(p.ctypes.data, n, int(attr_order), seed_a, pa, seed_b, pb, rt, hist,
+                               pref, v1, o1, start, ctypes.byref(l1)), "partition")
+    l = l1.value
+    return {"rt": rt[:2 * n].reshape(n, 2).copy(), "B": hist, "Bpref": pref, "V1": v1[:l].copy(),
+            "O1": o1[:l + 1].copy(), "lvl1_start": start}
+
+
+def _query_args(n_vars, atoms, rels, order):
+    na = len(atoms)
+    if len(rels) != na:
+        raise ValueError("one relation per atom")
+    rels = [_pairs(r) for r in rels]
+    ptrs = (ctypes.c_void_p * na)(*[r.ctypes.data if r.shape[0] else None for r in rels])
+    ns = np.array([r.shape[0] for r in rels], dtype=np.uint64)
+    v0 = np.array([a[0] for a in atoms], dtype=np.int32)
+    v1 = np.array([a[1] for a in atoms], dtype=np.int32)
+    od = np.array(list(range(n_vars)) if order is None else list(order), dtype=np.int32)
+    if od.shape[0] != n_vars:
+        raise ValueError("order must list every variable once")
+    return rels, ptrs, ns, v0, v1, od
+
+
+def _filter_arg(filt):
+    if filt is None:
+        return None, None, 0
+    f = np.ascontiguousarray(np.unique(np.asarray(filt, dtype=np.uint32)))
+    return f, (f.ctypes.data if f.shape[0] else None), f.shape[0]
+
+
+def gj_count(n_vars: int, atoms, rels, order=None, filt=None, nthreads: int = 1,
+             per_top: bool = False):
+    """Count of the query; returns (count, work, per_top_counts or None).
+
+    ``filt`` restricts the first loop's variable to the given values
+    (selection pushed into the atoms, Eq. "full:cq" remark on predicates).
+    ``per_top`` also returns the count for each loop-1 value (ascending).
+    """
+    rels, ptrs, ns, v0, v1, od = _query_args(n_vars, atoms, rels, order)
+    f, fptr, nf = _filter_arg(filt)
+    cnt, work, ntop = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+    lib = _lib()
+    if per_top:
+        _check(lib.oc_gj_count(n_vars, len(atoms), ptrs, ns, v0, v1, od, fptr, nf, 1,
+                               ctypes.byref(cnt), None, None, 0, ctypes.byref(ntop)), "gj_count")
+        buf = np.zeros(max(ntop.value, 1), dtype=np.uint64)
+        _check(lib.oc_gj_count(n_vars, len(atoms), ptrs, ns, v0, v1, od, fptr, nf, int(nthreads),
+                               ctypes.byref(cnt), ctypes.byref(work), buf.ctypes.data, buf.shape[0],
+                               ctypes.byref(ntop)), "gj_count")
+        return cnt.value, work.value, buf[:ntop.value].copy()
+    _check(lib.oc_gj_count(n_vars, len(atoms), ptrs, ns, v0, v1, od, fptr, nf, int(nthreads),
+                           ctypes.byref(cnt), ctypes.byref(work), None, 0, ctypes.byref(ntop)),
+           "gj_count")
+    return cnt.value, work.value, None
+
+
+def gj_enumerate(n_vars: int, atoms, rels, order=None, filt=None) -> np.ndarray:
+    """All output tuples, (count, n_vars) uint32 in variable-id order."""
+    rels, ptrs, ns, v0, v1, od = _query_args(n_vars, atoms, rels, order)
+    f, fptr, nf = _filter_arg(filt)
+    cnt, _, _ = gj_count(n_vars, atoms, rels, order, filt)
+    out = np.zeros(max(cnt, 1) * n_vars, dtype=np.uint32)
+    nout = ctypes.c_uint64(0)
+    _check(_lib().oc_gj_enumerate(n_vars, len(atoms), ptrs, ns, v0, v1, od, fptr, nf,
+                                  out.ctypes.data, max(cnt, 1), ctypes.byref(nout)), "gj_enumerate")
+    return out[:nout.value * n_vars].reshape(nout.value, n_vars).copy()
+
+
+def tuple_cells(tuples, seeds, shares) -> np.ndarray:
+    """Cell id of each tuple: mixed radix of (s_1..s_n) in variable-id order."""
+    t = np.ascontiguousarray(np.asarray(tuples, dtype=np.uint32))
+    nv = len(shares)
+    t = t.reshape(-1, nv)
+    out = np.zeros(max(t.shape[0], 1), dtype=np.uint32)
+    _check(_lib().oc_tuple_cells(t.ctypes.data if t.shape[0] else None, t.shape[0], nv,
+                                 np.asarray(seeds, dtype=np.uint32),
+                                 np.asarray(shares, dtype=np.uint32), out), "tuple_cells")
+    return out[:t.shape[0]].copy()
+
+
+# Query shapes of the paper's Table "Queries" (variables numbered X=0, Y=1,
+# Z=2, U=3, V=4 in the table's head order).
+TRIANGLE = (3, [(0, 1), (1, 2), (0, 2)])                     # Q1: R(X,Y) S(Y,Z) T(X,Z)
+FOUR_CYCLE = (4, [(0, 1), (0, 2), (1, 3), (2, 3)])           # Q2: R1(X,Y) R2(X,Z) R3(Y,U) R4(Z,U)
+FOUR_DIAMOND = (4, [(0, 1), (0, 2), (1, 3), (2, 3), (1, 2)])  # Q4
+FOUR_CLIQUE = (4, [(0, 1), (0, 2), (1, 3), (2, 3), (1, 2), (0, 3)])  # Q6
+TWO_TRIANGLE = (5, [(0, 1), (0, 2), (1, 2), (2, 3), (2, 4), (3, 4)])  # Q8
