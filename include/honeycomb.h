@@ -1,0 +1,231 @@
+/*
+ * honeycomb.h -- C ABI of the GB300 (sm_103a) HoneyComb join library.
+ *
+ * The library evaluates full conjunctive queries of binary atoms (Eq.
+ * "full:cq" of Wu & Suciu, "HoneyComb: A Parallel Worst-Case Optimal Join on
+ * Multicores") by Generic Join over CoCo indexes, with the variable domains
+ * split into HyperCube shares.  Three calls follow the paper's architecture
+ * (Sec. 3): hc_build_index (Preprocessor: sort + CoCo, Sec. 4),
+ * hc_choose_shares (Optimizer: cost model and plan decision, Sec. 5.2-5.3),
+ * hc_run_join (Preprocessor partitioning + Executor, Sec. 4-5).
+ *
+ * Conventions for every entry point:
+ *  - Device pointers ("d_" prefix) are CUDA device memory of the current
+ *    device; host pointers are ordinary memory.  `stream` is a cudaStream_t
+ *    passed as void* (NULL = the legacy default stream).  Work is enqueued on
+ *    that stream; where a call must wait for the GPU (to size an allocation or
+ *    to return a host value) it says so.
+ *  - Relations are sets of uint32 pairs stored as n rows of two uint32 values
+ *    (row-major, [n][2]).  Repeated rows are not allowed (Sec. 4 assumes a
+ *    unique relation when it drops the last offset array).
+ *  - Objects returned through an out-pointer (hc_index, hc_result) are owned
+ *    by the library and released with their _free call; inputs stay owned by
+ *    the caller and are never freed or modified.
+ *  - Every call returns an hc_status; HC_OK is 0.  On failure no output
+ *    object is returned and hc_last_error() describes the failure (a
+ *    thread-local string).  No call throws or aborts.
+ */
+#ifndef HONEYCOMB_H
+#define HONEYCOMB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HC_OK = 0,
+    HC_ERR_ARG = 1,        /* an argument violates the contract stated at the call    */
+    HC_ERR_OOM = 2,        /* device or host allocation failed                         */
+    HC_ERR_CUDA = 3,       /* a CUDA runtime call or kernel launch failed              */
+    HC_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up (result is invalid)   */
+    HC_ERR_CAPACITY = 5,   /* a size exceeds a fixed limit of the library              */
+    HC_ERR_DUPLICATE = 6,  /* the relation holds a repeated row (checking mode only)   */
+    HC_ERR_BUSY = 7        /* a serving queue or admission budget is full              */
+} hc_status;
+
+#define HC_MAX_VARS 8
+#define HC_MAX_ATOMS 8
+
+/* One binary atom R_j(X_var0, X_var1): column 0 of its relation holds the
+ * values of variable var0, column 1 those of var1 (var0 != var1). */
+typedef struct {
+    uint8_t var0;
+    uint8_t var1;
+} hc_atom;
+
+/* A full conjunctive query Q(X_0..X_{n_vars-1}) <- R_0(..) ^ ... (Eq.
+ * "full:cq").  Every variable must occur in some atom.  order[i] is the
+ * variable bound by loop i of Generic Join (Sec. 2); it must list each
+ * variable once.  Predicates are pushed into the atoms by the caller, as
+ * selections on their relations (Sec. 2). */
+typedef struct {
+    uint32_t n_vars;
+    uint32_t n_atoms;
+    hc_atom atoms[HC_MAX_ATOMS];
+    uint8_t order[HC_MAX_VARS];
+} hc_query;
+
+typedef struct hc_index hc_index;
+typedef struct hc_result hc_result;
+
+/* ------------------------------------------------------------ build_index
+ * CoCo index of one binary relation (Sec. 4, "Construction of CoCo"):
+ * the rows sorted lexicographically in attribute order `attr_order` (0: by
+ * column 0 then column 1; 1: by column 1 then column 0) by an LSD radix sort,
+ * then one run-boundary scan producing
+ *    V1[l1]   distinct first-attribute values, ascending          (uint32)
+ *    O1[l1+1] start of each value's run in V2, O1[l1] = n          (uint32)
+ *    V2[n]    second-attribute values, in sorted row order         (uint32)
+ * (the last level's offsets are dropped because the relation is a set).
+ *   d_pairs  device, [n][2] uint32, caller-owned, read only.
+ *   n        number of rows; 0 < n < 2^32 - 1 (HC_ERR_CAPACITY above).
+ *   out      receives the library-owned index (free with hc_index_free).
+ * Waits for the GPU once (to read the column maxima that size the sort).
+ * The rows must be distinct; with HC_BUILD_CHECK_DUPLICATES in `flags` a
+ * repeated row returns HC_ERR_DUPLICATE instead of an index. */
+#define HC_BUILD_CHECK_DUPLICATES 1u
+hc_status hc_build_index(const uint32_t* d_pairs, uint64_t n, uint32_t attr_order, uint32_t flags,
+                         void* stream, hc_index** out);
+hc_status hc_index_free(hc_index* index);
+
+/* Read-only view of an index's device arrays (valid until hc_index_free). */
+typedef struct {
+    uint64_t n;             /* rows                                            */
+    uint64_t l1;            /* distinct first-attribute values                 */
+    uint32_t attr_order;
+    uint32_t max_first;     /* largest first-attribute value (0 if n == 0)     */
+    uint32_t max_second;
+    const uint32_t* d_v1;   /* [l1]                                            */
+    const uint32_t* d_o1;   /* [l1+1]                                          */
+    const uint32_t* d_v2;   /* [n]                                             */
+    const uint64_t* d_keys; /* [n] sorted rows as (first << 32 | second)       */
+} hc_index_view;
+hc_status hc_index_get_view(const hc_index* index, hc_index_view* out);
+
+/* A statistics-only index: no device arrays, only the sizes the optimizer
+ * reads (n rows, l1 distinct first-attribute values, attribute order and the
+ * largest first / second values).  Host only, needs no GPU.  Accepted by
+ * hc_choose_shares; hc_run_join and hc_partition_index reject it with
+ * HC_ERR_ARG.  Free with hc_index_free.  Requires l1 <= n and l1 >= 1 when
+ * n >= 1. */
+hc_status hc_index_from_stats(uint64_t n, uint64_t l1, uint32_t attr_order, uint32_t max_first,
+                              uint32_t max_second, hc_index** out);
+
+/* ------------------------------------------------------- partition_index
+ * HyperCube partitioning of one indexed relation (Sec. 4, partitioning
+ * paragraphs and Example "partition"): a row (a, b) in the index's attribute
+ * order has partition identifiers s_a = share(a; seed_a, pa) and
+ * s_b = share(b; seed_b, pb), share(x; seed, P) = (fmix32(x ^ seed) * P) >> 32,
+ * and partition id pid = s_a * pb + s_b (lexicographic order, as B^pref).
+ * The result R~ holds every row exactly once (no replication), partitions
+ * concatenated in pid order, each sorted by (a, b) (a stable scatter of the
+ * sorted index), and one CoCo per partition:
+ *    keys[n]        R~ as (a << 32 | b)                                 (uint64)
+ *    bpref[np+1]    B^pref: start of partition p in R~; bpref[np] = n   (uint32)
+ *    v1[l1], o1[l1+1], v2[n]  per-partition CoCo levels concatenated;
+ *                   o1 entries are row positions in R~ (o1[l1] = n)    (uint32)
+ *    lvl1_start[np+1]  first level-1 entry of partition p in v1        (uint32)
+ * with np = pa * pb, 1 <= np <= 2^16.  Enqueued on `stream` without waiting.
+ * The partitioned relation is library-owned (hc_partitioned_free). */
+typedef struct hc_partitioned hc_partitioned;
+hc_status hc_partition_index(const hc_index* index, uint32_t seed_a, uint32_t pa, uint32_t seed_b,
+                             uint32_t pb, void* stream, hc_partitioned** out);
+typedef struct {
+    uint64_t n, l1, n_parts;
+    uint32_t pa, pb;
+    const uint64_t* d_keys;
+    const uint32_t* d_bpref;
+    const uint32_t* d_v1;
+    const uint32_t* d_o1;
+    const uint32_t* d_v2;
+    const uint32_t* d_lvl1_start;
+} hc_partitioned_view;
+/* Waits for the partitioning's stream (l1 is read back), then fills `out`. */
+hc_status hc_partitioned_get_view(hc_partitioned* p, hc_partitioned_view* out);
+hc_status hc_partitioned_free(hc_partitioned* p);
+
+/* ---------------------------------------------------------- choose_shares
+ * Shares P_i for each variable (Sec. 5.2 cost model, Lemma "cost-ub" and
+ * Eq. "total:cost"; Sec. 5.3 plan decision): among power-of-two share
+ * vectors with product P, drop those whose replicated cost exceeds twice the
+ * unpartitioned cost or that give some variable more shares than its domain
+ * supports (|Dom(X_i)| < 3 P_i ln P_i), then take the one of least evenness
+ * E = sum_i P_sigma(i) w(i), w(i) = max(1 - i/100, 3/4); ties go to the
+ * lexicographically smallest vector.  Host only; reads only the indexes'
+ * sizes.  idx[j] is the index bound to atom j.  P must be a power of two,
+ * 1 <= P <= 2^16.  shares_out[v] for v < n_vars, 1 elsewhere. */
+hc_status hc_choose_shares(const hc_query* q, const hc_index* const* idx, uint32_t P,
+                           uint32_t shares_out[HC_MAX_VARS]);
+
+/* Estimated cost of a plan (Sec. 5.2): level_cost[i] is the bound of Lemma
+ * "cost-ub" for loop i with all shares 1, and *replicated_cost is Eq.
+ * "total:cost" for the given shares (per variable id).  dom_out[v] is the
+ * domain size estimate of variable v used by the domain rule.  Host only;
+ * the same estimates drive hc_choose_shares. */
+hc_status hc_plan_cost(const hc_query* q, const hc_index* const* idx, const uint32_t shares[HC_MAX_VARS],
+                       double level_cost[HC_MAX_VARS], double dom_out[HC_MAX_VARS], double* replicated_cost);
+
+/* ------------------------------------------------------------- run_join */
+#define HC_MODE_COUNT 0u
+#define HC_MODE_MATERIALIZE 1u
+
+#define HC_FLAG_CELL_COUNTS 1u /* also return the count of each HyperCube cell        */
+#define HC_FLAG_STATS 2u       /* also return the intersection work counter           */
+
+typedef struct {
+    uint32_t shares[HC_MAX_VARS]; /* P_v per variable id (>= 1); their product = cells  */
+    uint32_t seeds[HC_MAX_VARS];  /* hash seed per variable id                          */
+    uint32_t mode;                /* HC_MODE_COUNT or HC_MODE_MATERIALIZE               */
+    uint32_t flags;               /* HC_FLAG_*                                          */
+    uint32_t item_grain;          /* loop-2 candidates per work item (0: default)       */
+    uint32_t block_threads;       /* threads per block of the join kernel (0: default)  */
+} hc_join_params;
+
+/* Generic Join of q over the indexes, one logical worker per HyperCube cell
+ * (Sec. 5, Listing C of Fig. "algo-comp").
+ *   idx[j]   index bound to atom j; its attr_order must sort the atom's
+ *            variables in loop order (Sec. 4: T(Z,X) under order X,Y,Z is
+ *            sorted by X first), else HC_ERR_ARG.
+ *   params   shares and hash seeds per variable; a variable value x goes to
+ *            share s = (fmix32(x ^ seed) * P) >> 32 (MurmurHash3 finaliser).
+ *            Atoms whose two variables both have one share are read in place;
+ *            the others are partitioned per call (Sec. 4).
+ *   out      library-owned result (hc_result_free).
+ * Count mode enqueues everything and returns without waiting; the count is
+ * read with hc_result_get (which waits).  Materialize mode waits once after
+ * its counting pass to size the output, then enqueues the emitting pass.
+ * Output tuples hold n_vars uint32 values in variable-id order, cell-major
+ * and in loop order's lexicographic order within a cell; the result is a set
+ * (no repeats) whatever the shares. */
+hc_status hc_run_join(const hc_query* q, const hc_index* const* idx, const hc_join_params* params,
+                      void* stream, hc_result** out);
+
+typedef struct {
+    uint64_t count;             /* |Q|                                                */
+    uint64_t n_tuples;          /* tuples in d_tuples (materialize), else 0           */
+    const uint32_t* d_tuples;   /* [n_tuples][n_vars], library-owned, or NULL         */
+    uint64_t n_cells;           /* product of the shares                              */
+    const uint64_t* d_cell_counts; /* [n_cells] with HC_FLAG_CELL_COUNTS, else NULL   */
+    uint64_t work;              /* with HC_FLAG_STATS: sum over loops and bindings of  */
+                                /* (number of lists) * (shortest list length), else 0 */
+    uint64_t n_items;           /* work items of the join kernel                      */
+    float ms_join_kernel;       /* device time of the join kernel(s), when measured   */
+} hc_result_view;
+/* Waits for the result's stream, then fills `out`. */
+hc_status hc_result_get(hc_result* r, hc_result_view* out);
+hc_status hc_result_free(hc_result* r);
+
+/* -------------------------------------------------------------- utilities */
+const char* hc_status_str(hc_status s);
+const char* hc_last_error(void);
+/* Library version and the compute capability it was built for (e.g. 103). */
+uint32_t hc_version(void);
+uint32_t hc_target_sm(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HONEYCOMB_H */

@@ -1,0 +1,322 @@
+"""GB300-native HoneyComb: Generic Join over CoCo indexes with HyperCube shares.
+
+Python binding of the C ABI (include/honeycomb.h).  The functions here only
+marshal arguments: every step of the join runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.
+
+    build_index(pairs, attr_order)            Sec. 4: radix sort + CoCo
+    choose_shares(query, indexes, P)          Sec. 5.2-5.3: cost model, plan decision
+    run_join(query, indexes, shares, ...)     Sec. 4-5: partitioning + Generic Join
+    partition_index(index, ...)               Sec. 4: HyperCube partitioning alone
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+from typing import Sequence
+
+import torch
+
+from . import _lib
+from ._lib import HoneycombError
+
+__all__ = ["Query", "Index", "Partitioned", "Result", "build_index", "choose_shares", "run_join",
+           "partition_index", "plan_cost", "HoneycombError", "TRIANGLE", "FOUR_CYCLE", "FOUR_DIAMOND", "FOUR_CLIQUE",
+           "TWO_TRIANGLE", "library_path"]
+
+
+def library_path() -> str:
+    return _lib.library_path()
+
+
+class _DeviceArray:
+    """__cuda_array_interface__ over library-owned device memory."""
+
+    def __init__(self, ptr: int, shape: tuple, typestr: str, owner):
+        self._owner = owner
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr or 0, True),
+                                         "version": 3, "strides": None}
+
+
+def _alias(ptr, shape, dtype: torch.dtype, owner) -> torch.Tensor:
+    """A torch tensor aliasing library memory (valid while `owner` lives)."""
+    n = 1
+    for s in shape:
+        n *= s
+    if n == 0 or not ptr:
+        return torch.empty(shape, dtype=dtype, device="cuda")
+    typestr = {torch.int32: "<i4", torch.int64: "<i8"}[dtype]
+    return torch.as_tensor(_DeviceArray(ptr, tuple(shape), typestr, owner), device="cuda")
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+@dataclass(frozen=True)
+class Query:
+    """Full conjunctive query of binary atoms (Eq. "full:cq").
+
+    ``atoms[j] = (var0, var1)``: column 0 of atom j's relation holds variable
+    var0, column 1 variable var1.  ``order`` is the Generic Join loop order
+    (default: variables 0, 1, ...).
+    """
+    n_vars: int
+    atoms: tuple
+    order: tuple | None = None
+
+    def loop_order(self) -> tuple:
+        return tuple(range(self.n_vars)) if self.order is None else tuple(self.order)
+
+    def with_order(self, order) -> "Query":
+        return Query(self.n_vars, self.atoms, tuple(order))
+
+    def attr_order(self, j: int) -> int:
+        """Attribute order an index needs for atom j under the loop order."""
+        rank = {v: i for i, v in enumerate(self.loop_order())}
+        a, b = self.atoms[j]
+        return 0 if rank[a] < rank[b] else 1
+
+    def _c(self) -> _lib.hc_query:
+        q = _lib.hc_query()
+        q.n_vars = self.n_vars
+        q.n_atoms = len(self.atoms)
+        for j, (a, b) in enumerate(self.atoms):
+            q.atoms[j].var0 = a
+            q.atoms[j].var1 = b
+        for i, v in enumerate(self.loop_order()):
+            q.order[i] = v
+        return q
+
+
+# Query shapes of the paper's Table "Queries", variables X=0, Y=1, Z=2, U=3, V=4.
+TRIANGLE = Query(3, ((0, 1), (1, 2), (0, 2)))
+FOUR_CYCLE = Query(4, ((0, 1), (0, 2), (1, 3), (2, 3)))
+FOUR_DIAMOND = Query(4, ((0, 1), (0, 2), (1, 3), (2, 3), (1, 2)))
+FOUR_CLIQUE = Query(4, ((0, 1), (0, 2), (1, 3), (2, 3), (1, 2), (0, 3)))
+TWO_TRIANGLE = Query(5, ((0, 1), (0, 2), (1, 2), (2, 3), (2, 4), (3, 4)))
+
+
+class Index:
+    """A CoCo index (library-owned device memory)."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+        v = _lib.hc_index_view()
+        _lib.check(_lib.load().hc_index_get_view(self._h, ctypes.byref(v)), "hc_index_get_view")
+        self.n, self.l1, self.attr_order = v.n, v.l1, v.attr_order
+        self.max_first, self.max_second = v.max_first, v.max_second
+        self._view = v
+
+    @classmethod
+    def from_stats(cls, n: int, l1: int, attr_order: int = 0, max_first: int = 0, max_second: int = 0) -> "Index":
+        """Statistics-only index for planning (no GPU, no data)."""
+        out = ctypes.c_void_p()
+        _lib.check(_lib.load().hc_index_from_stats(n, l1, attr_order, max_first, max_second, ctypes.byref(out)),
+                   "hc_index_from_stats")
+        return cls(out.value)
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("index already freed")
+        return self._h
+
+    def v1(self) -> torch.Tensor:
+        return _alias(self._view.d_v1, (self.l1,), torch.int32, self)
+
+    def o1(self) -> torch.Tensor:
+        return _alias(self._view.d_o1, (self.l1 + 1,), torch.int32, self)
+
+    def v2(self) -> torch.Tensor:
+        return _alias(self._view.d_v2, (self.n,), torch.int32, self)
+
+    def keys(self) -> torch.Tensor:
+        return _alias(self._view.d_keys, (self.n,), torch.int64, self)
+
+    def free(self) -> None:
+        if self._h is not None:
+            _lib.load().hc_index_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _check_pairs(pairs: torch.Tensor) -> torch.Tensor:
+    if not isinstance(pairs, torch.Tensor) or not pairs.is_cuda:
+        raise TypeError("pairs must be a CUDA tensor of shape (n, 2)")
+    if pairs.dtype not in (torch.int32, torch.uint32) or pairs.dim() != 2 or pairs.shape[1] != 2:
+        raise TypeError("pairs must be an (n, 2) int32/uint32 tensor")
+    return pairs.contiguous()
+
+
+def build_index(pairs: torch.Tensor, attr_order: int = 0, check_duplicates: bool = False, stream=None) -> Index:
+    """CoCo index of a relation given as an (n, 2) uint32 CUDA tensor."""
+    p = _check_pairs(pairs)
+    out = ctypes.c_void_p()
+    flags = _lib.HC_BUILD_CHECK_DUPLICATES if check_duplicates else 0
+    st = _lib.load().hc_build_index(ctypes.c_void_p(p.data_ptr() if p.numel() else 0), p.shape[0], attr_order,
+                                    flags, ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(out))
+    _lib.check(st, "hc_build_index")
+    return Index(out.value)
+
+
+class Partitioned:
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+        v = _lib.hc_partitioned_view()
+        _lib.check(_lib.load().hc_partitioned_get_view(self._h, ctypes.byref(v)), "hc_partitioned_get_view")
+        self.n, self.l1, self.n_parts, self.pa, self.pb = v.n, v.l1, v.n_parts, v.pa, v.pb
+        self._view = v
+
+    def keys(self):
+        return _alias(self._view.d_keys, (self.n,), torch.int64, self)
+
+    def bpref(self):
+        return _alias(self._view.d_bpref, (self.n_parts + 1,), torch.int32, self)
+
+    def v1(self):
+        return _alias(self._view.d_v1, (self.l1,), torch.int32, self)
+
+    def o1(self):
+        return _alias(self._view.d_o1, (self.l1 + 1,), torch.int32, self)
+
+    def v2(self):
+        return _alias(self._view.d_v2, (self.n,), torch.int32, self)
+
+    def lvl1_start(self):
+        return _alias(self._view.d_lvl1_start, (self.n_parts + 1,), torch.int32, self)
+
+    def free(self):
+        if self._h is not None:
+            _lib.load().hc_partitioned_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def partition_index(index: Index, seed_a: int, pa: int, seed_b: int, pb: int, stream=None) -> Partitioned:
+    out = ctypes.c_void_p()
+    st = _lib.load().hc_partition_index(index.handle, seed_a & 0xFFFFFFFF, pa, seed_b & 0xFFFFFFFF, pb,
+                                        ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(out))
+    _lib.check(st, "hc_partition_index")
+    return Partitioned(out.value)
+
+
+def _index_array(indexes: Sequence[Index]):
+    arr = (ctypes.c_void_p * len(indexes))(*[ix.handle.value for ix in indexes])
+    return ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), arr
+
+
+def choose_shares(query: Query, indexes: Sequence[Index], P: int = 1024) -> list[int]:
+    """Shares per variable id (Sec. 5.3 plan decision)."""
+    q = query._c()
+    ptr, keep = _index_array(indexes)
+    out = (ctypes.c_uint32 * _lib.HC_MAX_VARS)()
+    _lib.check(_lib.load().hc_choose_shares(ctypes.byref(q), ptr, P, out), "hc_choose_shares")
+    return [int(out[v]) for v in range(query.n_vars)]
+
+
+def plan_cost(query: Query, indexes: Sequence[Index], shares: Sequence[int]) -> dict:
+    """Estimated per-loop costs, domain sizes and replicated cost (Sec. 5.2)."""
+    q = query._c()
+    ptr, keep = _index_array(indexes)
+    sh = (ctypes.c_uint32 * _lib.HC_MAX_VARS)(*([int(x) for x in shares] + [1] * (_lib.HC_MAX_VARS - len(shares))))
+    lc = (ctypes.c_double * _lib.HC_MAX_VARS)()
+    dom = (ctypes.c_double * _lib.HC_MAX_VARS)()
+    rep = ctypes.c_double()
+    _lib.check(_lib.load().hc_plan_cost(ctypes.byref(q), ptr, sh, lc, dom, ctypes.byref(rep)), "hc_plan_cost")
+    n = query.n_vars
+    return {"level_cost": list(lc)[:n], "dom": list(dom)[:n], "replicated": rep.value}
+
+
+DEFAULT_SEEDS = (0x9E3779B9, 0x85EBCA6B, 0xC2B2AE35, 0x27D4EB2F, 0x165667B1, 0xD3A2646C, 0xFD7046C5, 0xB55A4F09)
+
+
+@dataclass
+class Result:
+    count: int
+    n_cells: int
+    work: int
+    n_items: int
+    tuples: torch.Tensor | None = None
+    cell_counts: torch.Tensor | None = None
+    _handle: object = field(default=None, repr=False)
+
+
+def run_join(query: Query, indexes: Sequence[Index], shares: Sequence[int] | None = None,
+             seeds: Sequence[int] | None = None, mode: str = "count", cell_counts: bool = False,
+             stats: bool = False, item_grain: int = 0, block_threads: int = 0, stream=None,
+             keep_device: bool = False) -> Result:
+    """Evaluate the query.  Tuples (materialize) come back as an
+    (count, n_vars) int32 CUDA tensor in variable-id order (a copy, unless
+    ``keep_device`` keeps an alias of library memory tied to the result)."""
+    if len(indexes) != len(query.atoms):
+        raise ValueError("one index per atom")
+    q = query._c()
+    ptr, keep = _index_array(indexes)
+    prm = _lib.hc_join_params()
+    sh = list(shares) if shares is not None else [1] * query.n_vars
+    sd = list(seeds) if seeds is not None else list(DEFAULT_SEEDS)
+    for v in range(_lib.HC_MAX_VARS):
+        prm.shares[v] = sh[v] if v < len(sh) else 1
+        prm.seeds[v] = (sd[v] if v < len(sd) else DEFAULT_SEEDS[v]) & 0xFFFFFFFF
+    if mode not in ("count", "materialize"):
+        raise ValueError("mode is 'count' or 'materialize'")
+    prm.mode = _lib.HC_MODE_COUNT if mode == "count" else _lib.HC_MODE_MATERIALIZE
+    prm.flags = (_lib.HC_FLAG_CELL_COUNTS if cell_counts else 0) | (_lib.HC_FLAG_STATS if stats else 0)
+    prm.item_grain = item_grain
+    prm.block_threads = block_threads
+    lib = _lib.load()
+    out = ctypes.c_void_p()
+    _lib.check(lib.hc_run_join(ctypes.byref(q), ptr, ctypes.byref(prm), ctypes.c_void_p(_stream_ptr(stream)),
+                               ctypes.byref(out)), "hc_run_join")
+    h = out.value
+    try:
+        v = _lib.hc_result_view()
+        _lib.check(lib.hc_result_get(ctypes.c_void_p(h), ctypes.byref(v)), "hc_result_get")
+        res = Result(count=v.count, n_cells=v.n_cells, work=v.work, n_items=v.n_items)
+        holder = _ResultHandle(h)
+        if v.d_tuples:
+            t = _alias(v.d_tuples, (v.n_tuples, query.n_vars), torch.int32, holder)
+            res.tuples = t if keep_device else t.clone()
+        if v.d_cell_counts:
+            c = _alias(v.d_cell_counts, (v.n_cells,), torch.int64, holder)
+            res.cell_counts = c if keep_device else c.clone()
+        if keep_device:
+            res._handle = holder
+        else:
+            torch.cuda.current_stream().synchronize()
+            holder.free()
+        return res
+    except Exception:
+        lib.hc_result_free(ctypes.c_void_p(h))
+        raise
+
+
+class _ResultHandle:
+    def __init__(self, h):
+        self.h = h
+
+    def free(self):
+        if self.h:
+            _lib.load().hc_result_free(ctypes.c_void_p(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -1,0 +1,212 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/honeycomb.h"
+
+namespace hc {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+hc_status fail(hc_status s, const std::string& msg);
+hc_status cuda_fail(cudaError_t e, const char* what);
+
+#define HC_CUDA_TRY(expr)                                  \
+    do {                                                   \
+        cudaError_t _e = (expr);                           \
+        if (_e != cudaSuccess) return ::hc::cuda_fail(_e, #expr); \
+    } while (0)
+
+#define HC_TRY(expr)                    \
+    do {                                \
+        hc_status _s = (expr);          \
+        if (_s != HC_OK) return _s;     \
+    } while (0)
+
+// ------------------------------------------------- device memory (stream-ordered)
+hc_status dev_alloc(void** p, size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+
+// Device-side error word: bit 0 = a bounded wait gave up.
+enum : uint32_t { DEV_ERR_TIMEOUT = 1u };
+
+// Library-wide per-device scratch holding the error word and work counters.
+struct DevScratch {
+    uint32_t* err;  // [1]
+};
+hc_status dev_scratch(DevScratch* out);
+
+// -------------------------------------------------------------- owned objects
+}  // namespace hc
+
+struct hc_index {
+    uint64_t n = 0, l1 = 0;
+    uint32_t attr_order = 0, max_first = 0, max_second = 0;
+    uint64_t* d_keys = nullptr;  // [n] sorted (first << 32 | second)
+    uint32_t* d_v1 = nullptr;    // [l1]
+    uint32_t* d_o1 = nullptr;    // [l1 + 1]
+    uint32_t* d_v2 = nullptr;    // [n]
+    bool stats_only = false;     // sizes only (planning), no device arrays
+};
+
+struct hc_partitioned {
+    uint64_t n = 0, l1 = 0, n_parts = 0;
+    uint32_t pa = 1, pb = 1, seed_a = 0, seed_b = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t* d_keys = nullptr;        // [n]
+    uint32_t* d_bpref = nullptr;       // [np + 1]
+    uint32_t* d_v1 = nullptr;          // [<= n]
+    uint32_t* d_o1 = nullptr;          // [<= n + 1]
+    uint32_t* d_v2 = nullptr;          // [n]
+    uint32_t* d_lvl1_start = nullptr;  // [np + 1]
+    uint32_t* d_l1 = nullptr;          // [1] device copy of l1
+    bool l1_known = false;
+};
+
+namespace hc {
+
+// --------------------------------------------------------------- device code
+#if defined(__CUDACC__)
+
+// MurmurHash3 32-bit finaliser (Appleby, 2011).
+__host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// Share of value x among P buckets: (fmix32(x ^ seed) * P) >> 32.
+__host__ __device__ __forceinline__ uint32_t share_of(uint32_t x, uint32_t seed, uint32_t P) {
+    return (uint32_t)(((uint64_t)fmix32(x ^ seed) * (uint64_t)P) >> 32);
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Decoupled look-back status word: 2 flag bits over a 62-bit value.
+constexpr uint64_t LB_AGG = 1ull << 62;
+constexpr uint64_t LB_INC = 2ull << 62;
+constexpr uint64_t LB_VAL = (1ull << 62) - 1;
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // a single wait gives up after 2 s
+
+// Exclusive prefix of tile `tile` for one counter, by decoupled look-back
+// (Merrill & Garland, 2016) over status[t * stride].  Predecessor tiles have
+// all started (tile ids are taken in launch order), so each wait ends unless
+// the device stalls; a wait longer than WAIT_LIMIT_NS sets DEV_ERR_TIMEOUT in
+// *err and returns what it has.
+__device__ __forceinline__ uint64_t lookback_prefix(uint64_t* status, uint32_t stride, uint32_t tile,
+                                                    uint32_t* err) {
+    uint64_t excl = 0;
+    int64_t t = (int64_t)tile - 1;
+    while (t >= 0) {
+        const uint64_t* p = status + (uint64_t)t * stride;
+        uint64_t w = ld_acquire(p);
+        if ((w & ~LB_VAL) == 0) {
+            uint64_t t0 = globaltimer_ns();
+            uint32_t spins = 0;
+            do {
+                if (++spins > 64) __nanosleep(64);
+                w = ld_acquire(p);
+                if ((w & ~LB_VAL) == 0 && globaltimer_ns() - t0 > WAIT_LIMIT_NS) {
+                    atomicOr(err, DEV_ERR_TIMEOUT);
+                    return excl;
+                }
+            } while ((w & ~LB_VAL) == 0);
+        }
+        excl += w & LB_VAL;
+        if (w & LB_INC) break;
+        --t;
+    }
+    return excl;
+}
+
+// Warp-wide inclusive scan (sum) of a 32-bit value.
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+    const uint32_t lane = lane_id();
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t u = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= (uint32_t)d) v += u;
+    }
+    return v;
+}
+__device__ __forceinline__ uint64_t warp_incl_scan64(uint64_t v) {
+    const uint32_t lane = lane_id();
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint64_t u = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= (uint32_t)d) v += u;
+    }
+    return v;
+}
+__device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+// First index in [lo, hi) of sorted a[] whose value is >= x (hi if none).
+template <typename P>
+__device__ __forceinline__ uint32_t lower_bound_u32(P a, uint32_t lo, uint32_t hi, uint32_t x) {
+    while (lo < hi) {
+        uint32_t mid = lo + ((hi - lo) >> 1);
+        if (a[mid] < x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+#endif  // __CUDACC__
+
+// --------------------------------------------------------------- host entry
+// Sorting and CoCo construction (hc_sort.cu).
+hc_status build_index_impl(const uint32_t* d_pairs, uint64_t n, uint32_t attr_order, uint32_t flags,
+                           cudaStream_t s, hc_index** out);
+hc_status partition_impl(const hc_index* idx, uint32_t seed_a, uint32_t pa, uint32_t seed_b,
+                         uint32_t pb, cudaStream_t s, hc_partitioned** out);
+void partitioned_release(hc_partitioned* p, cudaStream_t s);
+void index_release(hc_index* idx, cudaStream_t s);
+
+// Device-wide exclusive scan of counts into uint64 offsets; out[n] receives
+// the total.  n = min(n_max, *d_n) when d_n is given (a device-side count),
+// else n_max.  A timed-out look-back sets DEV_ERR_TIMEOUT in *d_err.
+// Temporary memory is stream-ordered.
+hc_status exclusive_scan_u32_to_u64(const uint32_t* d_in, uint64_t* d_out, uint64_t n_max, const uint32_t* d_n,
+                                    uint32_t* d_err, cudaStream_t s);
+hc_status exclusive_scan_u64(const uint64_t* d_in, uint64_t* d_out, uint64_t n_max, const uint32_t* d_n,
+                             uint32_t* d_err, cudaStream_t s);
+hc_status partitioned_sync(hc_partitioned* p);
+void result_release(hc_result* r);
+hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_join_params* prm, cudaStream_t s,
+                        hc_result** out);
+
+int num_sms();
+
+}  // namespace hc

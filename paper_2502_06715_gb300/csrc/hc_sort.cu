@@ -1,0 +1,679 @@
+// CoCo construction on the GPU (Sec. 4 "Construction of CoCo"): an LSD radix
+// sort of the rows packed as 64-bit keys (first << 32 | second), then a
+// single-pass run-boundary scan that writes the trie levels V1, O1, V2.
+// HyperCube partitioning (Sec. 4, partitioning paragraphs) reuses the same
+// radix pass with the partition id as the digit (a stable scatter of the
+// already sorted rows, so each partition stays sorted) and a segmented
+// run-boundary scan that builds one CoCo per partition.
+#include <algorithm>
+#include <vector>
+
+#include "hc_internal.cuh"
+
+namespace hc {
+
+namespace {
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_WARPS = SORT_THREADS / 32;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 4096 keys per tile
+constexpr int RADIX = 256;
+constexpr int MAX_PASSES = 8;
+
+// How a pass extracts its 8-bit digit: a byte of the key (mode 0), or a byte
+// of the key's HyperCube partition id (mode 1).
+struct DigitSpec {
+    uint32_t mode, shift;
+    uint32_t seed_a, pa, seed_b, pb;
+};
+
+__device__ __forceinline__ uint32_t partition_id(uint64_t key, uint32_t seed_a, uint32_t pa,
+                                                 uint32_t seed_b, uint32_t pb) {
+    return share_of((uint32_t)(key >> 32), seed_a, pa) * pb + share_of((uint32_t)key, seed_b, pb);
+}
+
+__device__ __forceinline__ uint32_t digit_of(uint64_t key, const DigitSpec& d) {
+    uint64_t v = d.mode == 0 ? key : (uint64_t)partition_id(key, d.seed_a, d.pa, d.seed_b, d.pb);
+    return (uint32_t)(v >> d.shift) & 0xFFu;
+}
+
+__device__ __forceinline__ uint64_t pack_row(const uint2* pairs, uint64_t i, uint32_t ao) {
+    uint2 r = pairs[i];
+    uint32_t a = ao ? r.y : r.x, b = ao ? r.x : r.y;
+    return ((uint64_t)a << 32) | b;
+}
+
+// Per-call control block in device memory.
+struct Ctl {
+    uint32_t err;
+    uint32_t dup;
+    uint32_t maxv[2];
+    uint32_t l1;
+    uint32_t pad;
+    uint32_t tile_counter[MAX_PASSES + 2];
+};
+
+// ------------------------------------------------------------ column maxima
+__global__ void colmax_kernel(const uint2* __restrict__ pairs, uint64_t n, Ctl* ctl) {
+    uint32_t m0 = 0, m1 = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint2 r = pairs[i];
+        m0 = max(m0, r.x);
+        m1 = max(m1, r.y);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        m0 = max(m0, __shfl_xor_sync(0xffffffffu, m0, d));
+        m1 = max(m1, __shfl_xor_sync(0xffffffffu, m1, d));
+    }
+    if (lane_id() == 0) {
+        atomicMax(&ctl->maxv[0], m0);
+        atomicMax(&ctl->maxv[1], m1);
+    }
+}
+
+// ------------------------------------------------------------- histograms
+// Digit histograms of every pass in one read of the input.
+template <bool FROM_PAIRS>
+__global__ void __launch_bounds__(SORT_THREADS) hist_kernel(const void* __restrict__ in, uint64_t n,
+                                                            uint32_t ao, const DigitSpec* __restrict__ ds,
+                                                            int npasses, uint32_t* __restrict__ ghist) {
+    __shared__ uint32_t sh[MAX_PASSES][RADIX];
+    __shared__ DigitSpec sds[MAX_PASSES];
+    for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) (&sh[0][0])[i] = 0;
+    if (threadIdx.x < npasses) sds[threadIdx.x] = ds[threadIdx.x];
+    __syncthreads();
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t k = FROM_PAIRS ? pack_row((const uint2*)in, i, ao) : ((const uint64_t*)in)[i];
+        for (int p = 0; p < npasses; ++p) atomicAdd(&sh[p][digit_of(k, sds[p])], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < npasses * RADIX; i += blockDim.x) {
+        uint32_t v = (&sh[0][0])[i];
+        if (v) atomicAdd(&ghist[i], v);
+    }
+}
+
+// Exclusive scan of each pass's 256 counters (one block of 256 per pass).
+__global__ void digit_scan_kernel(uint32_t* __restrict__ ghist) {
+    __shared__ uint32_t wsum[SORT_WARPS];
+    uint32_t* h = ghist + blockIdx.x * RADIX;
+    uint32_t v = h[threadIdx.x];
+    uint32_t inc = warp_incl_scan(v);
+    if (lane_id() == 31) wsum[threadIdx.x >> 5] = inc;
+    __syncthreads();
+    uint32_t add = 0;
+    for (uint32_t w = 0; w < (threadIdx.x >> 5); ++w) add += wsum[w];
+    __syncthreads();
+    h[threadIdx.x] = inc - v + add;
+}
+
+// --------------------------------------------------------- onesweep pass
+// One stable LSD pass over 8 bits.  Each tile ranks its keys per digit
+// (warp-private counters, __match_any_sync peers), gets its global digit
+// offsets by decoupled look-back over the tiles before it, stages the keys in
+// shared memory in digit order and writes each digit run contiguously.
+template <bool FROM_PAIRS>
+__global__ void __launch_bounds__(SORT_THREADS) onesweep_kernel(
+    const void* __restrict__ in, uint64_t* __restrict__ out, uint64_t n, uint32_t ao, DigitSpec ds,
+    const uint32_t* __restrict__ gbase, uint64_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
+    uint32_t* __restrict__ err) {
+    __shared__ uint64_t skeys[SORT_TILE];
+    __shared__ uint8_t sdig[SORT_TILE];
+    __shared__ uint32_t whist[SORT_WARPS][RADIX];
+    __shared__ uint32_t local_start[RADIX];
+    __shared__ uint64_t goff[RADIX];
+    __shared__ uint32_t wsum[SORT_WARPS];
+    __shared__ uint32_t s_tile;
+
+    const uint32_t tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+    for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_THREADS) (&whist[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t base = (uint64_t)tile * SORT_TILE;
+
+    uint64_t k[SORT_ITEMS];
+    uint32_t rank[SORT_ITEMS];
+    uint32_t dig[SORT_ITEMS];
+#pragma unroll
+    for (int j = 0; j < SORT_ITEMS; ++j) {
+        uint64_t i = base + (uint64_t)w * (SORT_ITEMS * 32) + (uint64_t)j * 32 + lane;
+        bool valid = i < n;
+        uint64_t key = 0;
+        if (valid) key = FROM_PAIRS ? pack_row((const uint2*)in, i, ao) : ((const uint64_t*)in)[i];
+        uint32_t d = valid ? digit_of(key, ds) : RADIX;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t leader = __ffs(peers) - 1;
+        uint32_t b = 0;
+        if (lane == leader && d < RADIX) {
+            b = whist[w][d];
+            whist[w][d] = b + __popc(peers);
+        }
+        b = __shfl_sync(0xffffffffu, b, leader);
+        k[j] = key;
+        dig[j] = d;
+        rank[j] = b + __popc(peers & lanemask_lt());
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // per digit: exclusive prefix over warps, tile total, look-back
+    const uint32_t d = tid;
+    uint32_t run = 0;
+#pragma unroll
+    for (int ww = 0; ww < SORT_WARPS; ++ww) {
+        uint32_t c = whist[ww][d];
+        whist[ww][d] = run;
+        run += c;
+    }
+    uint64_t* st = status + (uint64_t)tile * RADIX + d;
+    uint64_t excl = 0;
+    if (tile == 0) {
+        st_release(st, LB_INC | run);
+    } else {
+        st_release(st, LB_AGG | run);
+        excl = lookback_prefix(status + d, RADIX, tile, err);
+        st_release(st, LB_INC | (excl + run));
+    }
+    // tile-local digit starts (block exclusive scan of the tile totals)
+    uint32_t inc = warp_incl_scan(run);
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    uint32_t add = 0;
+    for (uint32_t q = 0; q < w; ++q) add += wsum[q];
+    const uint32_t lstart = inc - run + add;
+    local_start[d] = lstart;
+    goff[d] = (uint64_t)gbase[d] + excl - (uint64_t)lstart;
+    __syncthreads();
+
+#pragma unroll
+    for (int j = 0; j < SORT_ITEMS; ++j) {
+        if (dig[j] < RADIX) {
+            uint32_t pos = local_start[dig[j]] + whist[w][dig[j]] + rank[j];
+            skeys[pos] = k[j];
+            sdig[pos] = (uint8_t)dig[j];
+        }
+    }
+    __syncthreads();
+    const uint64_t remain = n - base;
+    const uint32_t tile_n = remain < (uint64_t)SORT_TILE ? (uint32_t)remain : (uint32_t)SORT_TILE;
+    for (uint32_t i = tid; i < tile_n; i += SORT_THREADS) out[goff[sdig[i]] + i] = skeys[i];
+}
+
+// Pack rows into keys without sorting (a relation with a single key value).
+__global__ void pack_kernel(const uint2* __restrict__ pairs, uint64_t* __restrict__ out, uint64_t n, uint32_t ao) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = pack_row(pairs, i, ao);
+}
+
+// ------------------------------------------------------ run-boundary scan
+// Single pass over the sorted keys.  Row i opens a level-1 entry when its
+// first attribute (or, with SEGMENTED, its partition id) differs from row
+// i-1.  Flags are counted with ballots, the tile's offset comes from a
+// decoupled look-back, and every flagged row writes V1[pos] = first value and
+// O1[pos] = i; every row writes V2[i] = second value.  The last tile writes
+// O1[l1] = n and l1.  Equal adjacent keys mark a duplicate row.
+template <bool SEGMENTED>
+__global__ void __launch_bounds__(SORT_THREADS) boundary_kernel(
+    const uint64_t* __restrict__ keys, uint64_t n, uint32_t seed_a, uint32_t pa, uint32_t seed_b,
+    uint32_t pb, uint32_t* __restrict__ v1, uint32_t* __restrict__ o1, uint32_t* __restrict__ v2,
+    uint64_t* __restrict__ status, uint32_t* __restrict__ tile_counter, Ctl* __restrict__ ctl) {
+    __shared__ uint32_t wsum[SORT_WARPS];
+    __shared__ uint64_t s_excl;
+    __shared__ uint32_t s_tile;
+    const uint32_t tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t base = (uint64_t)tile * SORT_TILE + (uint64_t)w * (SORT_ITEMS * 32);
+
+    uint64_t k[SORT_ITEMS];
+    uint32_t ball[SORT_ITEMS];
+    uint32_t wcount = 0;
+    bool dup = false;
+#pragma unroll
+    for (int j = 0; j < SORT_ITEMS; ++j) {
+        uint64_t i = base + (uint64_t)j * 32 + lane;
+        bool valid = i < n;
+        uint64_t key = valid ? keys[i] : 0;
+        uint64_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+        if (lane == 0 && valid && i > 0) prev = keys[i - 1];
+        bool flag = false;
+        if (valid) {
+            if (i == 0) {
+                flag = true;
+            } else if (SEGMENTED) {
+                flag = (prev >> 32) != (key >> 32) ||
+                       partition_id(prev, seed_a, pa, seed_b, pb) != partition_id(key, seed_a, pa, seed_b, pb);
+            } else {
+                flag = (prev >> 32) != (key >> 32);
+            }
+            dup |= i > 0 && prev == key;
+        }
+        ball[j] = __ballot_sync(0xffffffffu, flag);
+        wcount += __popc(ball[j]);
+        k[j] = key;
+    }
+    if (__any_sync(0xffffffffu, dup) && lane == 0) atomicOr(&ctl->dup, 1u);
+    if (lane == 0) wsum[w] = wcount;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t tot = 0;
+        for (int q = 0; q < SORT_WARPS; ++q) tot += wsum[q];
+        uint64_t* st = status + tile;
+        uint64_t excl = 0;
+        if (tile == 0) {
+            st_release(st, LB_INC | tot);
+        } else {
+            st_release(st, LB_AGG | tot);
+            excl = lookback_prefix(status, 1, tile, &ctl->err);
+            st_release(st, LB_INC | (excl + tot));
+        }
+        s_excl = excl;
+        uint64_t tile_end = (uint64_t)tile * SORT_TILE + SORT_TILE;
+        if (tile_end >= n) {  // the tile holding the last row closes the arrays
+            o1[excl + tot] = (uint32_t)n;
+            ctl->l1 = (uint32_t)(excl + tot);
+        }
+    }
+    __syncthreads();
+    uint64_t pos = s_excl;
+    for (uint32_t q = 0; q < w; ++q) pos += wsum[q];
+#pragma unroll
+    for (int j = 0; j < SORT_ITEMS; ++j) {
+        uint64_t i = base + (uint64_t)j * 32 + lane;
+        if (i < n) {
+            v2[i] = (uint32_t)k[j];
+            if (ball[j] >> lane & 1u) {
+                uint64_t p = pos + __popc(ball[j] & lanemask_lt());
+                v1[p] = (uint32_t)(k[j] >> 32);
+                o1[p] = (uint32_t)i;
+            }
+        }
+        pos += __popc(ball[j]);
+    }
+}
+
+// B^pref and the level-1 directory of a partitioned relation: partition p
+// starts at the first row whose partition id is >= p (ids ascend along R~),
+// and its level 1 at the first entry whose row offset is >= that start.
+__global__ void directory_kernel(const uint64_t* __restrict__ keys, uint64_t n, uint32_t seed_a,
+                                 uint32_t pa, uint32_t seed_b, uint32_t pb,
+                                 const uint32_t* __restrict__ o1, const Ctl* __restrict__ ctl,
+                                 uint32_t* __restrict__ bpref, uint32_t* __restrict__ lvl1_start) {
+    const uint32_t np = pa * pb;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p <= np; p += gridDim.x * blockDim.x) {
+        uint64_t lo = 0, hi = n;
+        while (lo < hi) {
+            uint64_t mid = lo + ((hi - lo) >> 1);
+            if (partition_id(keys[mid], seed_a, pa, seed_b, pb) < p)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        bpref[p] = (uint32_t)lo;
+        lvl1_start[p] = lower_bound_u32(o1, 0u, ctl->l1, (uint32_t)lo);
+    }
+}
+
+// ----------------------------------------------------------- device scan
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// Exclusive scan of in[0..n) into out[0..n), out[n] = total.  n is read from
+// *d_n when given (a count produced on the device), else n_max is used; the
+// grid covers n_max elements and tiles past n contribute nothing.
+template <typename T>
+__global__ void __launch_bounds__(SCAN_THREADS) scan_kernel(const T* __restrict__ in, uint64_t* __restrict__ out,
+                                                            uint64_t n_max, const uint32_t* __restrict__ d_n,
+                                                            uint64_t* __restrict__ status,
+                                                            uint32_t* __restrict__ tile_counter,
+                                                            uint32_t* __restrict__ err) {
+    __shared__ uint64_t wsum[SCAN_THREADS / 32];
+    __shared__ uint64_t s_excl;
+    __shared__ uint32_t s_tile;
+    const uint32_t tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+    const uint64_t n = d_n ? (n_max < (uint64_t)*d_n ? n_max : (uint64_t)*d_n) : n_max;
+    const uint64_t ntiles = (n_max + SCAN_TILE - 1) / SCAN_TILE;
+    if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t base = (uint64_t)tile * SCAN_TILE + (uint64_t)tid * SCAN_ITEMS;
+    uint64_t v[SCAN_ITEMS];
+    uint64_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        v[j] = base + j < n ? (uint64_t)in[base + j] : 0;
+        sum += v[j];
+    }
+    uint64_t inc = warp_incl_scan64(sum);
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (tid == 0) {
+        uint64_t tot = 0;
+        for (int q = 0; q < SCAN_THREADS / 32; ++q) tot += wsum[q];
+        uint64_t* st = status + tile;
+        uint64_t excl = 0;
+        if (tile == 0) {
+            st_release(st, LB_INC | tot);
+        } else {
+            st_release(st, LB_AGG | tot);
+            excl = lookback_prefix(status, 1, tile, err);
+            st_release(st, LB_INC | (excl + tot));
+        }
+        s_excl = excl;
+        const uint64_t last = ntiles ? (n / SCAN_TILE < ntiles - 1 ? n / SCAN_TILE : ntiles - 1) : 0;
+        if (tile == last) out[n] = excl + tot;
+    }
+    __syncthreads();
+    uint64_t run = s_excl + inc - sum;
+    for (uint32_t q = 0; q < w; ++q) run += wsum[q];
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        if (base + j < n) out[base + j] = run;
+        run += v[j];
+    }
+}
+
+int grid_for(uint64_t n, int threads, int per_sm) {
+    uint64_t want = (n + threads - 1) / threads;
+    uint64_t cap = (uint64_t)num_sms() * per_sm;
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, cap));
+}
+
+struct Tmp {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit Tmp(cudaStream_t st) : s(st) {}
+    ~Tmp() {
+        for (void* p : ptrs) dev_free(p, s);
+    }
+    template <typename T>
+    hc_status get(T** p, size_t count) {
+        void* v = nullptr;
+        HC_TRY(dev_alloc(&v, std::max<size_t>(count, 1) * sizeof(T), s));
+        ptrs.push_back(v);
+        *p = (T*)v;
+        return HC_OK;
+    }
+};
+
+hc_status check_ctl(const Ctl* d_ctl, cudaStream_t s, Ctl* h) {
+    HC_CUDA_TRY(cudaMemcpyAsync(h, d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    HC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h->err & DEV_ERR_TIMEOUT) return fail(HC_ERR_TIMEOUT, "a look-back wait in the sort gave up");
+    return HC_OK;
+}
+
+// Radix passes over the given digit specs; the sorted keys end in `dst`.
+hc_status radix_passes(const void* src, bool src_pairs, uint32_t ao, uint64_t n, const std::vector<DigitSpec>& specs,
+                       uint64_t* dst, Tmp& tmp, Ctl* d_ctl, cudaStream_t s) {
+    const int np = (int)specs.size();
+    if (np == 0) return fail(HC_ERR_ARG, "internal: no radix passes");
+    DigitSpec* d_specs;
+    uint32_t* d_hist;
+    HC_TRY(tmp.get(&d_specs, np));
+    HC_TRY(tmp.get(&d_hist, (size_t)np * RADIX));
+    HC_CUDA_TRY(cudaMemcpyAsync(d_specs, specs.data(), np * sizeof(DigitSpec), cudaMemcpyHostToDevice, s));
+    HC_CUDA_TRY(cudaMemsetAsync(d_hist, 0, (size_t)np * RADIX * sizeof(uint32_t), s));
+    const int hgrid = grid_for(n, SORT_THREADS * 8, 4);
+    if (src_pairs)
+        hist_kernel<true><<<hgrid, SORT_THREADS, 0, s>>>(src, n, ao, d_specs, np, d_hist);
+    else
+        hist_kernel<false><<<hgrid, SORT_THREADS, 0, s>>>(src, n, ao, d_specs, np, d_hist);
+    HC_CUDA_TRY(cudaGetLastError());
+    digit_scan_kernel<<<np, RADIX, 0, s>>>(d_hist);
+    HC_CUDA_TRY(cudaGetLastError());
+
+    const uint64_t ntiles = (n + SORT_TILE - 1) / SORT_TILE;
+    if (ntiles > 0xFFFFFFFFull) return fail(HC_ERR_CAPACITY, "too many sort tiles");
+    uint64_t* status;
+    uint64_t* alt = nullptr;
+    HC_TRY(tmp.get(&status, ntiles * RADIX));
+    if (np > 1 || !src_pairs) HC_TRY(tmp.get(&alt, n));
+    // ping-pong so that the last pass writes `dst`
+    uint64_t* bufs[2] = {dst, alt};
+    int cur = (np % 2 == 1) ? 0 : 1;  // buffer written by pass 0
+    const void* in = src;
+    for (int p = 0; p < np; ++p) {
+        uint64_t* outb = bufs[cur];
+        if (outb == nullptr) return fail(HC_ERR_ARG, "internal: radix buffer");
+        HC_CUDA_TRY(cudaMemsetAsync(status, 0, ntiles * RADIX * sizeof(uint64_t), s));
+        if (p == 0 && src_pairs)
+            onesweep_kernel<true><<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(
+                in, outb, n, ao, specs[p], d_hist + p * RADIX, status, &d_ctl->tile_counter[p], &d_ctl->err);
+        else
+            onesweep_kernel<false><<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(
+                in, outb, n, ao, specs[p], d_hist + p * RADIX, status, &d_ctl->tile_counter[p], &d_ctl->err);
+        HC_CUDA_TRY(cudaGetLastError());
+        in = outb;
+        cur ^= 1;
+    }
+    return HC_OK;
+}
+
+hc_status run_boundary(const uint64_t* keys, uint64_t n, bool segmented, uint32_t seed_a, uint32_t pa,
+                       uint32_t seed_b, uint32_t pb, uint32_t* v1, uint32_t* o1, uint32_t* v2, Tmp& tmp,
+                       Ctl* d_ctl, cudaStream_t s) {
+    const uint64_t ntiles = std::max<uint64_t>(1, (n + SORT_TILE - 1) / SORT_TILE);
+    uint64_t* status;
+    HC_TRY(tmp.get(&status, ntiles));
+    HC_CUDA_TRY(cudaMemsetAsync(status, 0, ntiles * sizeof(uint64_t), s));
+    uint32_t* tc = &d_ctl->tile_counter[MAX_PASSES];
+    if (segmented)
+        boundary_kernel<true><<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(keys, n, seed_a, pa, seed_b, pb, v1, o1, v2,
+                                                                         status, tc, d_ctl);
+    else
+        boundary_kernel<false><<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(keys, n, 0, 1, 0, 1, v1, o1, v2, status,
+                                                                          tc, d_ctl);
+    HC_CUDA_TRY(cudaGetLastError());
+    return HC_OK;
+}
+
+uint32_t bits_of(uint32_t v) { return v == 0 ? 0 : 32 - __builtin_clz(v); }
+
+}  // namespace
+
+void index_release(hc_index* idx, cudaStream_t s) {
+    if (!idx) return;
+    dev_free(idx->d_keys, s);
+    dev_free(idx->d_v1, s);
+    dev_free(idx->d_o1, s);
+    dev_free(idx->d_v2, s);
+    delete idx;
+}
+
+hc_status build_index_impl(const uint32_t* d_pairs, uint64_t n, uint32_t ao, uint32_t flags, cudaStream_t s,
+                           hc_index** out) {
+    if (!out) return fail(HC_ERR_ARG, "build_index: out is NULL");
+    *out = nullptr;
+    if (ao > 1) return fail(HC_ERR_ARG, "build_index: attr_order must be 0 or 1");
+    if (n > 0 && !d_pairs) return fail(HC_ERR_ARG, "build_index: d_pairs is NULL");
+    if (n >= 0xFFFFFFFFull) return fail(HC_ERR_CAPACITY, "build_index: n must be below 2^32 - 1");
+    hc_index* idx = new hc_index();
+    idx->n = n;
+    idx->attr_order = ao;
+    auto bail = [&](hc_status st) {
+        index_release(idx, s);
+        return st;
+    };
+    void* p;
+    if (dev_alloc(&p, std::max<uint64_t>(n, 1) * 8, s) != HC_OK) return bail(HC_ERR_OOM);
+    idx->d_keys = (uint64_t*)p;
+    if (dev_alloc(&p, std::max<uint64_t>(n, 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+    idx->d_v1 = (uint32_t*)p;
+    if (dev_alloc(&p, (n + 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+    idx->d_o1 = (uint32_t*)p;
+    if (dev_alloc(&p, std::max<uint64_t>(n, 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+    idx->d_v2 = (uint32_t*)p;
+
+    hc_status st;
+    {
+        Tmp tmp(s);
+        Ctl* d_ctl;
+        if ((st = tmp.get(&d_ctl, 1)) != HC_OK) return bail(st);
+        if (cudaMemsetAsync(d_ctl, 0, sizeof(Ctl), s) != cudaSuccess)
+            return bail(cuda_fail(cudaGetLastError(), "memset"));
+        if (n == 0) {
+            if (cudaMemsetAsync(idx->d_o1, 0, 4, s) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
+            *out = idx;
+            return HC_OK;
+        }
+        colmax_kernel<<<grid_for(n, 256, 4), 256, 0, s>>>((const uint2*)d_pairs, n, d_ctl);
+        if (cudaGetLastError() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "colmax_kernel"));
+        Ctl h;
+        if ((st = check_ctl(d_ctl, s, &h)) != HC_OK) return bail(st);
+        idx->max_first = ao ? h.maxv[1] : h.maxv[0];
+        idx->max_second = ao ? h.maxv[0] : h.maxv[1];
+        std::vector<DigitSpec> specs;
+        for (uint32_t b = 0; b < bits_of(idx->max_second); b += 8) specs.push_back({0, b, 0, 1, 0, 1});
+        for (uint32_t b = 0; b < bits_of(idx->max_first); b += 8) specs.push_back({0, 32 + b, 0, 1, 0, 1});
+        if (specs.empty()) {
+            pack_kernel<<<grid_for(n, 256, 4), 256, 0, s>>>((const uint2*)d_pairs, idx->d_keys, n, ao);
+            if (cudaGetLastError() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "pack_kernel"));
+        } else if ((st = radix_passes(d_pairs, true, ao, n, specs, idx->d_keys, tmp, d_ctl, s)) != HC_OK) {
+            return bail(st);
+        }
+        if ((st = run_boundary(idx->d_keys, n, false, 0, 1, 0, 1, idx->d_v1, idx->d_o1, idx->d_v2, tmp, d_ctl, s)) !=
+            HC_OK)
+            return bail(st);
+        if ((st = check_ctl(d_ctl, s, &h)) != HC_OK) return bail(st);
+        if ((flags & HC_BUILD_CHECK_DUPLICATES) && h.dup)
+            return bail(fail(HC_ERR_DUPLICATE, "build_index: the relation holds a repeated row"));
+        idx->l1 = h.l1;
+    }
+    *out = idx;
+    return HC_OK;
+}
+
+void partitioned_release(hc_partitioned* p, cudaStream_t s) {
+    if (!p) return;
+    dev_free(p->d_keys, s);
+    dev_free(p->d_bpref, s);
+    dev_free(p->d_v1, s);
+    dev_free(p->d_o1, s);
+    dev_free(p->d_v2, s);
+    dev_free(p->d_lvl1_start, s);
+    dev_free(p->d_l1, s);
+    delete p;
+}
+
+hc_status partition_impl(const hc_index* idx, uint32_t seed_a, uint32_t pa, uint32_t seed_b, uint32_t pb,
+                         cudaStream_t s, hc_partitioned** out) {
+    if (!out) return fail(HC_ERR_ARG, "partition: out is NULL");
+    *out = nullptr;
+    if (!idx) return fail(HC_ERR_ARG, "partition: index is NULL");
+    if (idx->stats_only) return fail(HC_ERR_ARG, "partition: a statistics-only index has no data");
+    if (pa == 0 || pb == 0 || (uint64_t)pa * pb > 65536ull)
+        return fail(HC_ERR_ARG, "partition: shares must be >= 1 with product <= 65536");
+    const uint64_t n = idx->n;
+    const uint32_t np = pa * pb;
+    hc_partitioned* part = new hc_partitioned();
+    part->n = n;
+    part->n_parts = np;
+    part->pa = pa;
+    part->pb = pb;
+    part->seed_a = seed_a;
+    part->seed_b = seed_b;
+    part->stream = s;
+    auto bail = [&](hc_status st) {
+        partitioned_release(part, s);
+        return st;
+    };
+    void* p;
+    if (dev_alloc(&p, std::max<uint64_t>(n, 1) * 8, s) != HC_OK) return bail(HC_ERR_OOM);
+    part->d_keys = (uint64_t*)p;
+    if (dev_alloc(&p, (uint64_t)(np + 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+    part->d_bpref = (uint32_t*)p;
+    if (dev_alloc(&p, std::max<uint64_t>(n, 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+    part->d_v1 = (uint32_t*)p;
+    if (dev_alloc(&p, (n + 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+    part->d_o1 = (uint32_t*)p;
+    if (dev_alloc(&p, std::max<uint64_t>(n, 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+    part->d_v2 = (uint32_t*)p;
+    if (dev_alloc(&p, (uint64_t)(np + 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+    part->d_lvl1_start = (uint32_t*)p;
+    if (dev_alloc(&p, sizeof(Ctl), s) != HC_OK) return bail(HC_ERR_OOM);
+    part->d_l1 = (uint32_t*)p;  // holds a Ctl; l1 is read from its field
+    Ctl* d_ctl = (Ctl*)p;
+    if (cudaMemsetAsync(d_ctl, 0, sizeof(Ctl), s) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
+
+    hc_status st;
+    {
+        Tmp tmp(s);
+        if (n == 0) {
+            if (cudaMemsetAsync(part->d_o1, 0, 4, s) != cudaSuccess ||
+                cudaMemsetAsync(part->d_bpref, 0, (np + 1) * 4, s) != cudaSuccess ||
+                cudaMemsetAsync(part->d_lvl1_start, 0, (np + 1) * 4, s) != cudaSuccess)
+                return bail(cuda_fail(cudaGetLastError(), "memset"));
+            part->l1_known = true;
+            *out = part;
+            return HC_OK;
+        }
+        if (np == 1) {
+            if (cudaMemcpyAsync(part->d_keys, idx->d_keys, n * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return bail(cuda_fail(cudaGetLastError(), "copy"));
+        } else {
+            std::vector<DigitSpec> specs;
+            for (uint32_t b = 0; b < bits_of(np - 1); b += 8) specs.push_back({1, b, seed_a, pa, seed_b, pb});
+            if ((st = radix_passes(idx->d_keys, false, 0, n, specs, part->d_keys, tmp, d_ctl, s)) != HC_OK)
+                return bail(st);
+        }
+        if ((st = run_boundary(part->d_keys, n, true, seed_a, pa, seed_b, pb, part->d_v1, part->d_o1, part->d_v2, tmp,
+                               d_ctl, s)) != HC_OK)
+            return bail(st);
+        directory_kernel<<<grid_for(np + 1, 128, 2), 128, 0, s>>>(part->d_keys, n, seed_a, pa, seed_b, pb, part->d_o1,
+                                                                  d_ctl, part->d_bpref, part->d_lvl1_start);
+        if (cudaGetLastError() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "directory_kernel"));
+    }
+    *out = part;
+    return HC_OK;
+}
+
+hc_status partitioned_sync(hc_partitioned* p) {
+    if (p->l1_known) return HC_OK;
+    Ctl h;
+    HC_CUDA_TRY(cudaMemcpyAsync(&h, p->d_l1, sizeof(Ctl), cudaMemcpyDeviceToHost, p->stream));
+    HC_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    if (h.err & DEV_ERR_TIMEOUT) return fail(HC_ERR_TIMEOUT, "a look-back wait in partitioning gave up");
+    p->l1 = h.l1;
+    p->l1_known = true;
+    return HC_OK;
+}
+
+const uint32_t* partitioned_l1_ptr(const hc_partitioned* p) { return &((const Ctl*)p->d_l1)->l1; }
+const uint32_t* partitioned_err_ptr(const hc_partitioned* p) { return &((const Ctl*)p->d_l1)->err; }
+
+template <typename T>
+hc_status exclusive_scan_impl(const T* d_in, uint64_t* d_out, uint64_t n_max, const uint32_t* d_n, uint32_t* d_err,
+                              cudaStream_t s) {
+    Tmp tmp(s);
+    const uint64_t ntiles = std::max<uint64_t>(1, (n_max + SCAN_TILE - 1) / SCAN_TILE);
+    if (ntiles > 0xFFFFFFFFull) return fail(HC_ERR_CAPACITY, "scan: too many tiles");
+    uint64_t* status;
+    uint32_t* ctr;
+    HC_TRY(tmp.get(&status, ntiles));
+    HC_TRY(tmp.get(&ctr, 1));
+    HC_CUDA_TRY(cudaMemsetAsync(status, 0, ntiles * sizeof(uint64_t), s));
+    HC_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t), s));
+    scan_kernel<T><<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(d_in, d_out, n_max, d_n, status, ctr, d_err);
+    HC_CUDA_TRY(cudaGetLastError());
+    return HC_OK;
+}
+
+hc_status exclusive_scan_u32_to_u64(const uint32_t* d_in, uint64_t* d_out, uint64_t n_max, const uint32_t* d_n,
+                                    uint32_t* d_err, cudaStream_t s) {
+    return exclusive_scan_impl<uint32_t>(d_in, d_out, n_max, d_n, d_err, s);
+}
+hc_status exclusive_scan_u64(const uint64_t* d_in, uint64_t* d_out, uint64_t n_max, const uint32_t* d_n,
+                             uint32_t* d_err, cudaStream_t s) {
+    return exclusive_scan_impl<uint64_t>(d_in, d_out, n_max, d_n, d_err, s);
+}
+
+}  // namespace hc

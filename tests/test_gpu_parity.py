@@ -1,0 +1,234 @@
+"""GPU parity against the CPU oracle through the C ABI (needs a GB300).
+
+Integer work throughout: every comparison is exact (bit-exact arrays,
+equal counts, equal sorted tuple sets).
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hc(cuda_device):
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2502_06715_gb300 as hc
+
+    return hc
+
+
+def dev(arr):
+    import torch
+
+    a = np.ascontiguousarray(np.asarray(arr, dtype=np.uint32).reshape(-1, 2))
+    return torch.from_numpy(a.view(np.int32)).cuda()
+
+
+def u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def sorted_rows(a):
+    a = np.asarray(a)
+    if a.shape[0] == 0:
+        return a
+    return a[np.lexsort(a.T[::-1])]
+
+
+# ------------------------------------------------------------------ CoCo build
+
+@pytest.mark.parametrize("n", [1, 2, 31, 100, 4095, 4096, 4097, 65537, 300_001])
+@pytest.mark.parametrize("ao", [0, 1])
+def test_build_index_matches_oracle(hc, n, ao):
+    rng = np.random.default_rng(n * 7 + ao)
+    hi = 1 << 22 if n > 1000 else 50
+    pairs = datagen.directed_set(rng.integers(0, hi, size=(int(n * 1.2) + 2, 2)).astype(np.uint32))[:n]
+    pairs = datagen.scatter_order(pairs, n)
+    ix = hc.build_index(dev(pairs), ao, check_duplicates=True)
+    v1, o1, v2 = oracle.coco_build(pairs, ao)
+    assert ix.n == pairs.shape[0] and ix.l1 == v1.shape[0]
+    assert np.array_equal(u32(ix.v1()), v1)
+    assert np.array_equal(u32(ix.o1()).astype(np.uint64), o1)
+    assert np.array_equal(u32(ix.v2()), v2)
+
+
+def test_build_index_full_uint32_range(hc):
+    """Values across all 32 bits: eight 8-bit passes."""
+    rng = np.random.default_rng(5)
+    raw = rng.integers(0, 2**32, size=(200_000, 2), dtype=np.uint64).astype(np.uint32)
+    raw[:10] = [[0xFFFFFFFF, 0xFFFFFFFF], [0, 0], [0xFFFFFFFF, 0], [0, 0xFFFFFFFF], [1, 2], [2, 1],
+                [0x80000000, 0x7FFFFFFF], [0x7FFFFFFF, 0x80000000], [5, 5], [6, 6]]
+    pairs = datagen.scatter_order(datagen.directed_set(raw), 3)
+    pairs = np.concatenate([pairs, np.array([[0, 0], [0xFFFFFFFF, 0xFFFFFFFF], [9, 9]], dtype=np.uint32)])
+    for ao in (0, 1):
+        ix = hc.build_index(dev(pairs), ao)
+        v1, o1, v2 = oracle.coco_build(pairs, ao)
+        assert np.array_equal(u32(ix.v1()), v1)
+        assert np.array_equal(u32(ix.o1()).astype(np.uint64), o1)
+        assert np.array_equal(u32(ix.v2()), v2)
+
+
+def test_build_index_single_key_value(hc):
+    """All rows equal in both columns but distinct (no radix pass needed)."""
+    pairs = np.array([[0, 0]], dtype=np.uint32)
+    ix = hc.build_index(dev(pairs), 0)
+    assert ix.l1 == 1 and u32(ix.o1()).tolist() == [0, 1] and u32(ix.v2()).tolist() == [0]
+
+
+def test_build_index_empty(hc):
+    import torch
+
+    ix = hc.build_index(torch.zeros((0, 2), dtype=torch.int32, device="cuda"), 0)
+    assert ix.n == 0 and ix.l1 == 0 and u32(ix.o1()).tolist() == [0]
+
+
+def test_build_index_rejects_duplicates(hc):
+    pairs = np.array([[1, 2], [3, 4], [1, 2]], dtype=np.uint32)
+    with pytest.raises(hc.HoneycombError) as e:
+        hc.build_index(dev(pairs), 0, check_duplicates=True)
+    assert e.value.status == 6
+    with pytest.raises(hc.HoneycombError) as e:
+        hc.build_index(dev(pairs), 2)
+    assert e.value.status == 1
+
+
+# ------------------------------------------------------------------ partitioning
+
+@pytest.mark.parametrize("shares", [(1, 1), (2, 3), (4, 4), (1, 16), (16, 1), (32, 32), (256, 256)])
+def test_partition_matches_oracle(hc, shares):
+    pa, pb = shares
+    sym = datagen.rmat_graph(12, 8, 4)
+    pairs = datagen.scatter_order(datagen.orient_lt(sym), 2)
+    for ao in (0, 1):
+        ix = hc.build_index(dev(pairs), ao)
+        part = hc.partition_index(ix, 1234, pa, 987654, pb)
+        ref = oracle.partition(pairs, ao, 1234, pa, 987654, pb)
+        keys = part.keys().cpu().numpy().view(np.uint64)
+        got_rt = np.stack([(keys >> np.uint64(32)).astype(np.uint32), (keys & np.uint64(0xFFFFFFFF)).astype(np.uint32)], 1)
+        assert np.array_equal(got_rt, ref["rt"])
+        assert np.array_equal(u32(part.bpref()).astype(np.uint64), ref["Bpref"])
+        assert part.l1 == ref["V1"].shape[0]
+        assert np.array_equal(u32(part.v1()), ref["V1"])
+        assert np.array_equal(u32(part.o1()).astype(np.uint64), ref["O1"])
+        assert np.array_equal(u32(part.v2()), ref["rt"][:, 1])
+        assert np.array_equal(u32(part.lvl1_start()).astype(np.uint64), ref["lvl1_start"])
+
+
+# ------------------------------------------------------------------ joins
+
+QUERIES = ["TRIANGLE", "FOUR_CYCLE", "FOUR_DIAMOND", "FOUR_CLIQUE", "TWO_TRIANGLE"]
+
+
+def _run(hc, q, rels, **kw):
+    """Index each atom's relation in the attr order its loop order needs."""
+    ixs = []
+    cache = {}
+    for j, r in enumerate(rels):
+        ao = q.attr_order(j)
+        key = (id(r), ao)
+        if key not in cache:
+            cache[key] = hc.build_index(dev(r), ao)
+        ixs.append(cache[key])
+    return hc.run_join(q, ixs, **kw)
+
+
+@pytest.mark.parametrize("qname", QUERIES)
+def test_counts_and_tuples_small_graphs(hc, qname):
+    q = getattr(hc, qname)
+    for seed in range(3):
+        sym = datagen.random_graph(40 + 10 * seed, 0.2, seed)
+        for rel in (sym, datagen.orient_lt(sym)):
+            rels = [rel] * len(q.atoms)
+            cnt, work, _ = oracle.gj_count(q.n_vars, list(q.atoms), rels)
+            r = _run(hc, q, rels, mode="materialize", stats=True)
+            assert r.count == cnt
+            assert r.work == work
+            ref = oracle.gj_enumerate(q.n_vars, list(q.atoms), rels)
+            assert np.array_equal(sorted_rows(u32(r.tuples)), sorted_rows(ref))
+
+
+@pytest.mark.parametrize("qname", QUERIES)
+def test_independent_random_relations(hc, qname):
+    """Different relations per atom, directed, with empty sub-lists."""
+    q = getattr(hc, qname)
+    rng = np.random.default_rng(11)
+    for case in range(4):
+        rels = [datagen.directed_set(rng.integers(0, 30, size=(300, 2)).astype(np.uint32)) for _ in q.atoms]
+        cnt, work, _ = oracle.gj_count(q.n_vars, list(q.atoms), rels)
+        r = _run(hc, q, rels, mode="count", stats=True)
+        assert r.count == cnt and r.work == work
+
+
+@pytest.mark.parametrize("qname", ["TRIANGLE", "FOUR_CYCLE", "FOUR_CLIQUE", "TWO_TRIANGLE"])
+def test_share_invariance_and_cell_counts(hc, qname):
+    """Sec. 5: cell outputs are disjoint and cover Q, whatever the shares."""
+    q = getattr(hc, qname)
+    sym = datagen.rmat_graph(9, 8, 21)
+    rel = datagen.orient_lt(sym) if qname != "FOUR_CYCLE" else sym
+    rels = [rel] * len(q.atoms)
+    ref = oracle.gj_enumerate(q.n_vars, list(q.atoms), rels)
+    seeds = [17, 29, 31, 37, 41]
+    rng = np.random.default_rng(1)
+    share_sets = [[1] * q.n_vars, [4] + [1] * (q.n_vars - 1), [2] * q.n_vars]
+    for _ in range(3):
+        share_sets.append([int(2 ** rng.integers(0, 4)) for _ in range(q.n_vars)])
+    for sh in share_sets:
+        r = _run(hc, q, rels, shares=sh, seeds=seeds, mode="materialize", cell_counts=True)
+        assert r.count == ref.shape[0], sh
+        assert np.array_equal(sorted_rows(u32(r.tuples)), sorted_rows(ref)), sh
+        cells = oracle.tuple_cells(ref, seeds[:q.n_vars], sh)
+        want = np.bincount(cells, minlength=int(np.prod(sh))).astype(np.uint64)
+        assert np.array_equal(r.cell_counts.cpu().numpy().view(np.uint64), want), sh
+
+
+@pytest.mark.parametrize("order", list(itertools.permutations(range(4)))[::3])
+def test_variable_orders_four_clique(hc, order):
+    q = hc.FOUR_CLIQUE.with_order(order)
+    sym = datagen.random_graph(36, 0.35, 4)
+    rels = [sym] * 6
+    cnt, _, _ = oracle.gj_count(4, list(q.atoms), rels, order=order)
+    assert _run(hc, q, rels, shares=[2, 1, 2, 1]).count == cnt
+
+
+@pytest.mark.parametrize("grain,threads", [(1, 32), (7, 64), (64, 128), (4096, 256), (32, 96)])
+def test_launch_shapes_agree(hc, grain, threads):
+    sym = datagen.rmat_graph(11, 8, 5)
+    ep = datagen.orient_lt(sym)
+    cnt, _, _ = oracle.gj_count(3, list(hc.TRIANGLE.atoms), [ep] * 3)
+    r = _run(hc, hc.TRIANGLE, [ep] * 3, item_grain=grain, block_threads=threads, shares=[4, 2, 1])
+    assert r.count == cnt
+
+
+def test_uniform_4096_vertices_32768_edges(hc):
+    """The oracle-sized triangle workload: x<y<z over a uniform graph."""
+    ep = datagen.uniform_graph(4096, 32768, seed=1)
+    cnt, work, _ = oracle.gj_count(3, list(hc.TRIANGLE.atoms), [ep] * 3)
+    r = _run(hc, hc.TRIANGLE, [ep] * 3, mode="materialize", stats=True)
+    assert r.count == cnt and r.work == work
+    ref = oracle.gj_enumerate(3, list(hc.TRIANGLE.atoms), [ep] * 3)
+    assert np.array_equal(sorted_rows(u32(r.tuples)), sorted_rows(ref))
+
+
+def test_empty_and_degenerate(hc):
+    empty = np.zeros((0, 2), dtype=np.uint32)
+    one = np.array([[0, 1]], dtype=np.uint32)
+    assert _run(hc, hc.TRIANGLE, [empty, empty, empty]).count == 0
+    assert _run(hc, hc.TRIANGLE, [one, empty, one]).count == 0
+    assert _run(hc, hc.TRIANGLE, [one, one, one], shares=[2, 2, 2]).count == 0
+    r = _run(hc, hc.TRIANGLE, [np.array([[0, 1]]), np.array([[1, 2]]), np.array([[0, 2]])], mode="materialize")
+    assert r.count == 1 and u32(r.tuples).tolist() == [[0, 1, 2]]
+
+
+def test_wrong_attr_order_rejected(hc):
+    ep = datagen.orient_lt(datagen.random_graph(20, 0.3, 1))
+    ix1 = hc.build_index(dev(ep), 1)
+    with pytest.raises(hc.HoneycombError) as e:
+        hc.run_join(hc.TRIANGLE, [ix1, ix1, ix1])
+    assert e.value.status == 1
