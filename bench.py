@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the HoneyComb hot path on a GB300.
+
+Workload (one "step" = the whole hot path on one batch of input already in
+HBM): the triangle query Q(x,y,z) = E(x,y), E(y,z), E(x,z) with x < y < z
+(the selection pushed into the relation: E+ = {(u,v) in E : u < v}) over an
+R-MAT graph of scale 22, edge factor 16, (a,b,c,d) = (.57,.19,.19,.05),
+scrambled ids, symmetrised, de-duplicated, self loops removed.  A step:
+  build_index(E+)        LSD radix sort + run-boundary scan (CoCo)
+  run_join(materialize)  HyperCube routing of every atom whose shares are
+                         not all 1, loop-1 intersection per cell, the
+                         persistent search kernel counting then emitting
+                         every output tuple.
+Metric: output tuples per second (|Q| / step time), whole job.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  The reference arm times the CPU oracle (the
+plain Generic Join used by the tests) on the host cores on a bounded sample
+of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "join output tuples/s (R-MAT triangle)"
+UNIT = "tuples/s"
+PROFILE_NOTE = os.path.join(ROOT, "profiles", "gj_search_kernel_rmat22.md")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scale", type=int, default=22)
+    ap.add_argument("--edge-factor", type=int, default=16)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--mode", choices=["materialize", "count"], default="materialize")
+    ap.add_argument("--shares", default="plan",
+                    help="'plan' (Sec. 5.3 decision at --P cells) or explicit, e.g. 32,32,1")
+    ap.add_argument("--P", type=int, default=1024)
+    ap.add_argument("--grain", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-frac", type=float, default=1.0 / 32,
+                    help="fraction of x values in the oracle's bounded sample")
+    return ap.parse_args()
+
+
+def workload_name(a) -> str:
+    return (f"triangle x<y<z, R-MAT scale {a.scale} ef {a.edge_factor} (a,b,c,d)=(.57,.19,.19,.05), "
+            f"scrambled, symmetrised, deduplicated; {a.mode}")
+
+
+def make_graph(a, rank: int, device: str | None):
+    import datagen
+
+    t = time.perf_counter()
+    sym = datagen.rmat_graph(a.scale, a.edge_factor, a.seed + rank, device=device)
+    ep = datagen.orient_lt(sym)
+    del sym
+    ep = datagen.scatter_order(ep, a.seed + rank)
+    return ep, time.perf_counter() - t
+
+
+def oracle_sample(ep, frac: float, seed: int):
+    """Rows of R, S, T a restricted triangle query can touch: x in a seeded
+    vertex subset F (R, T), and y in R[F] (S).  Exact: the count over these
+    rows is |{(x,y,z) in Q : x in F}|."""
+    import numpy as np
+
+    import datagen
+
+    nv = int(ep.max()) + 1
+    mask = datagen.vertex_sample_mask(nv, seed, frac)
+    rt = ep[mask[ep[:, 0]]]
+    ys = np.zeros(nv, dtype=bool)
+    ys[rt[:, 1]] = True
+    s = ep[ys[ep[:, 0]]]
+    return np.ascontiguousarray(rt), np.ascontiguousarray(s), np.nonzero(mask)[0].astype(np.uint32)
+
+
+def run_oracle_sample(ep, frac, seed):
+    import oracle
+
+    rt, s, f = oracle_sample(ep, frac, seed)
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    cnt, _, _ = oracle.gj_count(3, [(0, 1), (1, 2), (0, 2)], [rt, s, rt], filt=f, nthreads=cores)
+    dt = time.perf_counter() - t
+    desc = (f"triangles with x in a seeded {frac:.5f} vertex sample ({f.shape[0]} x values); oracle over the "
+            f"{rt.shape[0]} R/T rows and {s.shape[0]} S rows that sample touches (trie builds included), "
+            f"{cnt} tuples in {dt:.2f} s")
+    return cnt, dt, cores, desc
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        for line in out.strip().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, p[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def profiled_traffic():
+    """Per-launch DRAM bytes of the search kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    try:
+        text = open(PROFILE_NOTE).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
+    h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    if not m or not h:
+        return None
+    src = os.path.join(ROOT, "paper_2502_06715_gb300", "csrc", "hc_join.cu")
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != h.group(1):
+        return None
+    return int(m.group(1))
+
+
+def main():
+    a = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        return reference_arm(a, world, rank)
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2502_06715_gb300 as hc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    # independent problem per rank (weak scaling): seed + rank
+    ep, gen_s = make_graph(a, rank, device=f"cuda:{local}")
+    n = ep.shape[0]
+    d_pairs = torch.from_numpy(ep.view(np.int32)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    q = hc.TRIANGLE
+
+    # plan (host): shares per the paper's decision rule at P cells, or given
+    ix0 = hc.build_index(d_pairs, 0)
+    if a.shares == "plan":
+        shares = hc.choose_shares(q, [ix0] * 3, a.P)
+    else:
+        shares = [int(x) for x in a.shares.split(",")]
+    stats = hc.run_join(q, [ix0] * 3, shares=shares, stats=True, item_grain=a.grain, block_threads=a.threads)
+    work, expect = stats.work, stats.count
+    l1 = ix0.l1
+    ix0.free()
+    del stats
+
+    def step():
+        ix = hc.build_index(d_pairs, 0, stream=stream)
+        r = hc.run_join(q, [ix, ix, ix], shares=shares, mode=a.mode, keep_device=True, time_kernels=True,
+                        item_grain=a.grain, block_threads=a.threads, stream=stream)
+        ix.free()
+        return r
+
+    for _ in range(a.warmup):
+        r = step()
+        if r.count != expect:
+            raise SystemExit(f"count mismatch in warm-up: {r.count} != {expect}")
+        del r
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    launches0 = hc.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kern_ms, kern_launches = 0.0, 0
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(a.steps):
+        r = step()
+        kern_ms += r.ms_join_kernel
+        kern_launches += r.n_join_launches
+        count = r.count
+        del r
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = hc.kernel_launches() - launches0
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        c = torch.tensor([count], device=dev, dtype=torch.float64)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        total_tuples = float(c.item()) * a.steps
+    else:
+        total_tuples = float(count) * a.steps
+    ms_step = ms_total / a.steps
+    value = total_tuples / (ms_total / 1e3)
+
+    # roofline of the search kernel: algorithmic bytes per launch = 4 B per
+    # unit of the work counter (each element of the shortest list read once
+    # per list it is searched in), plus, for the emitting launch, the output
+    # tuples written (3 x 4 B each)
+    n_launch_per_step = 2 if a.mode == "materialize" else 1
+    out_bytes = 12.0 * count if a.mode == "materialize" else 0.0
+    alg_bytes = 4.0 * work + out_bytes / n_launch_per_step
+    avg_launch_s = (kern_ms / max(1, kern_launches)) / 1e3
+    peak, peak_kind = measured_hbm_peak()
+    achieved = alg_bytes / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": "gj_kernel (persistent search)", "achieved": round(achieved, 1),
+                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": profiled_traffic(), "alg_bytes_per_launch": alg_bytes,
+                "avg_launch_ms": round(avg_launch_s * 1e3, 3)}
+
+    e2e = None
+    if not a.no_e2e:
+        e2e = end_to_end(a, hc, ep, shares, q, dev, stream, expect)
+
+    cpu = None
+    if not a.no_cpu_baseline and rank == 0 and world == 1:
+        cnt, dt, cores, desc = run_oracle_sample(ep, a.cpu_frac, 12345)
+        cpu = {"value": cnt / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic (seeded R-MAT)",
+            "config": {"workload": workload_name(a), "scale": a.scale, "edge_factor": a.edge_factor,
+                       "rows_E+": n, "distinct_x": l1, "tuples": count, "shares": shares,
+                       "shares_from": a.shares if a.shares != "plan" else f"choose_shares(P={a.P})",
+                       "work_counter": work, "l2": "inputs larger than L2 (E+ is %.0f MB)" % (n * 8 / 1e6),
+                       "parallelism": f"replicas x{world}", "generate_s": round(gen_s, 1)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def end_to_end(a, hc, ep, shares, q, dev, stream, expect):
+    """Same metric through the public API from pinned HOST memory: the H2D
+    copy of E+, the build, the join and the D2H copy of the result (all
+    tuples in materialize mode, the count otherwise) are inside the timed
+    region."""
+    import numpy as np
+    import torch
+
+    host_in = torch.from_numpy(ep.view(np.int32)).pin_memory()
+    nvars = 3
+    host_out = None
+    if a.mode == "materialize":
+        host_out = torch.empty((expect, nvars), dtype=torch.int32, pin_memory=True)
+
+    def e2e_step():
+        d = host_in.to(dev, non_blocking=True)
+        ix = hc.build_index(d, 0, stream=stream)
+        r = hc.run_join(q, [ix, ix, ix], shares=shares, mode=a.mode, keep_device=True, item_grain=a.grain,
+                        block_threads=a.threads, stream=stream)
+        if host_out is not None:
+            host_out.copy_(r.tuples, non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+        c = r.count
+        ix.free()
+        del r, d
+        return c
+
+    for _ in range(max(1, min(2, a.warmup))):
+        e2e_step()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(a.steps):
+        c = e2e_step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    if c != expect:
+        raise SystemExit("end-to-end count mismatch")
+    return {"value": c * a.steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(host_in.numel() * 4),
+            "d2h_bytes_per_step": int(host_out.numel() * 4) if host_out is not None else 8,
+            "ms_per_step": dt / a.steps * 1e3}
+
+
+def reference_arm(a, world, rank):
+    """The oracle as it stands, on the host cores, over a bounded sample of
+    the same workload each step."""
+    if rank != 0:
+        return
+    ep, gen_s = make_graph(a, 0, device=None if os.environ.get("HC_GEN_CPU") else _maybe_cuda())
+    times, counts = [], []
+    desc, cores = "", 1
+    for i in range(a.warmup + a.steps):
+        cnt, dt, cores, desc = run_oracle_sample(ep, a.cpu_frac, 12345)
+        if i >= a.warmup:
+            times.append(dt)
+            counts.append(cnt)
+    total = sum(counts) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": total, "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded R-MAT)",
+            "config": {"workload": workload_name(a), "scale": a.scale, "edge_factor": a.edge_factor,
+                       "sample_frac": a.cpu_frac},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": desc, "value": total, "unit": UNIT},
+            "e2e": {"value": total, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _maybe_cuda():
+    try:
+        import torch
+
+        return "cuda:0" if torch.cuda.is_available() else None
+    except Exception:
+        return None
+
+
+if __name__ == "__main__":
+    main()

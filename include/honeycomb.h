@@ -174,6 +174,7 @@ hc_status hc_plan_cost(const hc_query* q, const hc_index* const* idx, const uint
 
 #define HC_FLAG_CELL_COUNTS 1u /* also return the count of each HyperCube cell        */
 #define HC_FLAG_STATS 2u       /* also return the intersection work counter           */
+#define HC_FLAG_TIME_KERNELS 4u /* time the search kernel launches with device events  */
 
 typedef struct {
     uint32_t shares[HC_MAX_VARS]; /* P_v per variable id (>= 1); their product = cells  */
@@ -212,7 +213,9 @@ typedef struct {
     uint64_t work;              /* with HC_FLAG_STATS: sum over loops and bindings of  */
                                 /* (number of lists) * (shortest list length), else 0 */
     uint64_t n_items;           /* work items of the join kernel                      */
-    float ms_join_kernel;       /* device time of the join kernel(s), when measured   */
+    float ms_join_kernel;       /* with HC_FLAG_TIME_KERNELS: device time of the search */
+                                /* kernel launches (CUDA events on the join's stream)  */
+    uint32_t n_join_launches;   /* search kernel launches (1 count, 2 materialize)      */
 } hc_result_view;
 /* Waits for the result's stream, then fills `out`. */
 hc_status hc_result_get(hc_result* r, hc_result_view* out);
@@ -223,6 +226,8 @@ const char* hc_status_str(hc_status s);
 const char* hc_last_error(void);
 /* Library version and the compute capability it was built for (e.g. 103). */
 uint32_t hc_version(void);
+/* Kernels this library has launched in this process so far (host counter). */
+uint64_t hc_kernel_launches(void);
 uint32_t hc_target_sm(void);
 
 #ifdef __cplusplus

@@ -22,11 +22,16 @@ from ._lib import HoneycombError
 
 __all__ = ["Query", "Index", "Partitioned", "Result", "build_index", "choose_shares", "run_join",
            "partition_index", "plan_cost", "HoneycombError", "TRIANGLE", "FOUR_CYCLE", "FOUR_DIAMOND", "FOUR_CLIQUE",
-           "TWO_TRIANGLE", "library_path"]
+           "TWO_TRIANGLE", "library_path", "kernel_launches"]
 
 
 def library_path() -> str:
     return _lib.library_path()
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process (host counter)."""
+    return int(_lib.load().hc_kernel_launches())
 
 
 class _DeviceArray:
@@ -34,7 +39,7 @@ class _DeviceArray:
 
     def __init__(self, ptr: int, shape: tuple, typestr: str, owner):
         self._owner = owner
-        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr or 0, True),
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr or 0, False),
                                          "version": 3, "strides": None}
 
 
@@ -251,6 +256,8 @@ class Result:
     n_cells: int
     work: int
     n_items: int
+    ms_join_kernel: float = 0.0
+    n_join_launches: int = 0
     tuples: torch.Tensor | None = None
     cell_counts: torch.Tensor | None = None
     _handle: object = field(default=None, repr=False)
@@ -259,7 +266,7 @@ class Result:
 def run_join(query: Query, indexes: Sequence[Index], shares: Sequence[int] | None = None,
              seeds: Sequence[int] | None = None, mode: str = "count", cell_counts: bool = False,
              stats: bool = False, item_grain: int = 0, block_threads: int = 0, stream=None,
-             keep_device: bool = False) -> Result:
+             keep_device: bool = False, time_kernels: bool = False) -> Result:
     """Evaluate the query.  Tuples (materialize) come back as an
     (count, n_vars) int32 CUDA tensor in variable-id order (a copy, unless
     ``keep_device`` keeps an alias of library memory tied to the result)."""
@@ -276,7 +283,8 @@ def run_join(query: Query, indexes: Sequence[Index], shares: Sequence[int] | Non
     if mode not in ("count", "materialize"):
         raise ValueError("mode is 'count' or 'materialize'")
     prm.mode = _lib.HC_MODE_COUNT if mode == "count" else _lib.HC_MODE_MATERIALIZE
-    prm.flags = (_lib.HC_FLAG_CELL_COUNTS if cell_counts else 0) | (_lib.HC_FLAG_STATS if stats else 0)
+    prm.flags = ((_lib.HC_FLAG_CELL_COUNTS if cell_counts else 0) | (_lib.HC_FLAG_STATS if stats else 0)
+                 | (_lib.HC_FLAG_TIME_KERNELS if time_kernels else 0))
     prm.item_grain = item_grain
     prm.block_threads = block_threads
     lib = _lib.load()
@@ -287,7 +295,8 @@ def run_join(query: Query, indexes: Sequence[Index], shares: Sequence[int] | Non
     try:
         v = _lib.hc_result_view()
         _lib.check(lib.hc_result_get(ctypes.c_void_p(h), ctypes.byref(v)), "hc_result_get")
-        res = Result(count=v.count, n_cells=v.n_cells, work=v.work, n_items=v.n_items)
+        res = Result(count=v.count, n_cells=v.n_cells, work=v.work, n_items=v.n_items,
+                     ms_join_kernel=v.ms_join_kernel, n_join_launches=v.n_join_launches)
         holder = _ResultHandle(h)
         if v.d_tuples:
             t = _alias(v.d_tuples, (v.n_tuples, query.n_vars), torch.int32, holder)

@@ -17,6 +17,7 @@ HC_MODE_COUNT = 0
 HC_MODE_MATERIALIZE = 1
 HC_FLAG_CELL_COUNTS = 1
 HC_FLAG_STATS = 2
+HC_FLAG_TIME_KERNELS = 4
 HC_BUILD_CHECK_DUPLICATES = 1
 
 STATUS = {0: "HC_OK", 1: "HC_ERR_ARG", 2: "HC_ERR_OOM", 3: "HC_ERR_CUDA", 4: "HC_ERR_TIMEOUT",
@@ -55,7 +56,8 @@ class hc_join_params(ctypes.Structure):
 class hc_result_view(ctypes.Structure):
     _fields_ = [("count", ctypes.c_uint64), ("n_tuples", ctypes.c_uint64), ("d_tuples", ctypes.c_void_p),
                 ("n_cells", ctypes.c_uint64), ("d_cell_counts", ctypes.c_void_p), ("work", ctypes.c_uint64),
-                ("n_items", ctypes.c_uint64), ("ms_join_kernel", ctypes.c_float)]
+                ("n_items", ctypes.c_uint64), ("ms_join_kernel", ctypes.c_float),
+                ("n_join_launches", ctypes.c_uint32)]
 
 
 # name -> (restype, argtypes)
@@ -84,6 +86,7 @@ SIGNATURES = {
     "hc_last_error": (ctypes.c_char_p, []),
     "hc_version": (ctypes.c_uint32, []),
     "hc_target_sm": (ctypes.c_uint32, []),
+    "hc_kernel_launches": (ctypes.c_uint64, []),
 }
 
 _LIB = None

@@ -3,6 +3,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <functional>
 #include <string>
 #include <vector>
@@ -12,6 +13,9 @@
 namespace hc {
 
 static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -353,6 +357,7 @@ const char* hc_status_str(hc_status s) {
 const char* hc_last_error(void) { return hc::g_last_error.c_str(); }
 
 uint32_t hc_version(void) { return 100; }
+uint64_t hc_kernel_launches(void) { return hc::g_launches.load(std::memory_order_relaxed); }
 uint32_t hc_target_sm(void) { return 103; }
 
 }  // extern "C"

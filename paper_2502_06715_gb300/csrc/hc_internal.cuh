@@ -27,6 +27,14 @@ hc_status cuda_fail(cudaError_t e, const char* what);
         if (_s != HC_OK) return _s;     \
     } while (0)
 
+// Every kernel launch of the library goes through launch_check(), which
+// counts it (hc_kernel_launches) and returns the launch error, if any.
+void note_launch();
+inline cudaError_t launch_check() {
+    note_launch();
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------- device memory (stream-ordered)
 hc_status dev_alloc(void** p, size_t bytes, cudaStream_t s);
 void dev_free(void* p, cudaStream_t s);

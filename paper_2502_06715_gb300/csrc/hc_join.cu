@@ -608,7 +608,7 @@ hc_status launch_gj(bool mat, const GjArgs& g, cudaStream_t s) {
         gj_kernel<NL, false><<<grid, g.threads, 0, s>>>(g.plan, g.e_cell, g.e_x, g.e_rng, g.uoff, g.grain, g.ctl,
                                                         g.pass, g.cell_counts, g.item_counts, g.item_base, g.out,
                                                         g.stats);
-    HC_CUDA_TRY(cudaGetLastError());
+    HC_CUDA_TRY(launch_check());
     return HC_OK;
 }
 
@@ -638,6 +638,8 @@ struct hc_result {
     bool done = false;
     hc::JoinCtl h_ctl{};
     std::vector<hc_partitioned*> parts;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int n_timed = 0;  // search launches bracketed by ev[2i], ev[2i+1]
 };
 
 namespace hc {
@@ -677,6 +679,8 @@ void result_release(hc_result* r) {
     dev_free(r->d_ctl, s);
     dev_free(r->d_cell_counts, s);
     dev_free(r->d_tuples, s);
+    for (auto& e : r->ev)
+        if (e) cudaEventDestroy(e);
     delete r;
 }
 
@@ -694,6 +698,14 @@ hc_status result_get(hc_result* R, hc_result_view* v) {
     v->d_cell_counts = R->d_cell_counts;
     v->work = R->h_ctl.work;
     v->n_items = R->n_items;
+    v->n_join_launches = R->materialized ? 2 : 1;
+    float total_ms = 0.f;
+    for (int i = 0; i < R->n_timed; ++i) {
+        float ms = 0.f;
+        HC_CUDA_TRY(cudaEventElapsedTime(&ms, R->ev[2 * i], R->ev[2 * i + 1]));
+        total_ms += ms;
+    }
+    v->ms_join_kernel = total_ms;
     return HC_OK;
 }
 
@@ -863,24 +875,38 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     const int tpb = 256;
     l0_count_kernel<<<(unsigned)std::min<uint64_t>((ncells + tpb - 1) / tpb, 4096), tpb, 0, s>>>(d_plan, cand, ctl,
                                                                                                  stats);
-    if (cudaGetLastError() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "l0_count_kernel"));
+    if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "l0_count_kernel"));
     if ((st = exclusive_scan_u32_to_u64(cand, candoff, ncells, nullptr, &ctl->err, s)) != HC_OK) return bail(st);
     const unsigned pgrid =
         (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((cand_bound + tpb - 1) / tpb, (uint64_t)num_sms() * 16));
     l0_probe_kernel<false><<<pgrid, tpb, 0, s>>>(d_plan, candoff, cand_bound, flags, nullptr, nullptr, nullptr, nullptr,
                                                  nullptr);
-    if (cudaGetLastError() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "l0_probe_kernel"));
+    if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "l0_probe_kernel"));
     if ((st = exclusive_scan_u32_to_u64(flags, flagoff, cand_bound, nullptr, &ctl->err, s)) != HC_OK) return bail(st);
     l0_probe_kernel<true><<<pgrid, tpb, 0, s>>>(d_plan, candoff, cand_bound, flags, flagoff, e_cell, e_x, e_rng, e_units);
-    if (cudaGetLastError() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "l0_probe_kernel"));
+    if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "l0_probe_kernel"));
     entries_total_kernel<<<1, 1, 0, s>>>(flagoff, candoff, (uint32_t)ncells, cand_bound, ctl);
-    if (cudaGetLastError() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "entries_total_kernel"));
+    if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "entries_total_kernel"));
     if ((st = exclusive_scan_u32_to_u64(e_units, uoff, cand_bound, &ctl->n_entries, &ctl->err, s)) != HC_OK)
         return bail(st);
 
     GjArgs g{d_plan, e_cell, e_x, e_rng, uoff, grain, ctl, 0, R->d_cell_counts, nullptr, nullptr, nullptr, stats, threads};
+    const bool timed = (prm->flags & HC_FLAG_TIME_KERNELS) != 0;
+    if (timed)
+        for (auto& e : R->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "cudaEventCreate"));
+    // one search launch, bracketed by events when timed
+    auto search = [&](bool mat) -> hc_status {
+        if (timed && cudaEventRecord(R->ev[2 * R->n_timed], s) != cudaSuccess) return cuda_fail(cudaGetLastError(), "event");
+        HC_TRY(launch_any(nv, mat, g, s));
+        if (timed) {
+            if (cudaEventRecord(R->ev[2 * R->n_timed + 1], s) != cudaSuccess) return cuda_fail(cudaGetLastError(), "event");
+            R->n_timed++;
+        }
+        return HC_OK;
+    };
     if (prm->mode == HC_MODE_COUNT) {
-        if ((st = launch_any(nv, false, g, s)) != HC_OK) return bail(st);
+        if ((st = search(false)) != HC_OK) return bail(st);
         *out = R;
         return HC_OK;
     }
@@ -896,7 +922,7 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     if ((st = tmp.get(&item_counts, nitems)) != HC_OK) return bail(st);
     if ((st = tmp.get(&item_base, nitems + 1)) != HC_OK) return bail(st);
     g.item_counts = item_counts;
-    if ((st = launch_any(nv, false, g, s)) != HC_OK) return bail(st);
+    if ((st = search(false)) != HC_OK) return bail(st);
     if ((st = exclusive_scan_u64(item_counts, item_base, nitems, nullptr, &ctl->err, s)) != HC_OK) return bail(st);
     uint64_t total = 0;
     if (cudaMemcpyAsync(&total, item_base + nitems, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -912,7 +938,7 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     g.item_base = item_base;
     g.out = R->d_tuples;
     g.cell_counts = nullptr;
-    if ((st = launch_any(nv, true, g, s)) != HC_OK) return bail(st);
+    if ((st = search(true)) != HC_OK) return bail(st);
     R->n_tuples = total;
     R->materialized = true;
     *out = R;

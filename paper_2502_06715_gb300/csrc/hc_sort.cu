@@ -427,9 +427,9 @@ hc_status radix_passes(const void* src, bool src_pairs, uint32_t ao, uint64_t n,
         hist_kernel<true><<<hgrid, SORT_THREADS, 0, s>>>(src, n, ao, d_specs, np, d_hist);
     else
         hist_kernel<false><<<hgrid, SORT_THREADS, 0, s>>>(src, n, ao, d_specs, np, d_hist);
-    HC_CUDA_TRY(cudaGetLastError());
+    HC_CUDA_TRY(launch_check());
     digit_scan_kernel<<<np, RADIX, 0, s>>>(d_hist);
-    HC_CUDA_TRY(cudaGetLastError());
+    HC_CUDA_TRY(launch_check());
 
     const uint64_t ntiles = (n + SORT_TILE - 1) / SORT_TILE;
     if (ntiles > 0xFFFFFFFFull) return fail(HC_ERR_CAPACITY, "too many sort tiles");
@@ -451,7 +451,7 @@ hc_status radix_passes(const void* src, bool src_pairs, uint32_t ao, uint64_t n,
         else
             onesweep_kernel<false><<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(
                 in, outb, n, ao, specs[p], d_hist + p * RADIX, status, &d_ctl->tile_counter[p], &d_ctl->err);
-        HC_CUDA_TRY(cudaGetLastError());
+        HC_CUDA_TRY(launch_check());
         in = outb;
         cur ^= 1;
     }
@@ -472,7 +472,7 @@ hc_status run_boundary(const uint64_t* keys, uint64_t n, bool segmented, uint32_
     else
         boundary_kernel<false><<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(keys, n, 0, 1, 0, 1, v1, o1, v2, status,
                                                                           tc, d_ctl);
-    HC_CUDA_TRY(cudaGetLastError());
+    HC_CUDA_TRY(launch_check());
     return HC_OK;
 }
 
@@ -526,7 +526,7 @@ hc_status build_index_impl(const uint32_t* d_pairs, uint64_t n, uint32_t ao, uin
             return HC_OK;
         }
         colmax_kernel<<<grid_for(n, 256, 4), 256, 0, s>>>((const uint2*)d_pairs, n, d_ctl);
-        if (cudaGetLastError() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "colmax_kernel"));
+        if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "colmax_kernel"));
         Ctl h;
         if ((st = check_ctl(d_ctl, s, &h)) != HC_OK) return bail(st);
         idx->max_first = ao ? h.maxv[1] : h.maxv[0];
@@ -536,7 +536,7 @@ hc_status build_index_impl(const uint32_t* d_pairs, uint64_t n, uint32_t ao, uin
         for (uint32_t b = 0; b < bits_of(idx->max_first); b += 8) specs.push_back({0, 32 + b, 0, 1, 0, 1});
         if (specs.empty()) {
             pack_kernel<<<grid_for(n, 256, 4), 256, 0, s>>>((const uint2*)d_pairs, idx->d_keys, n, ao);
-            if (cudaGetLastError() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "pack_kernel"));
+            if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "pack_kernel"));
         } else if ((st = radix_passes(d_pairs, true, ao, n, specs, idx->d_keys, tmp, d_ctl, s)) != HC_OK) {
             return bail(st);
         }
@@ -630,7 +630,7 @@ hc_status partition_impl(const hc_index* idx, uint32_t seed_a, uint32_t pa, uint
             return bail(st);
         directory_kernel<<<grid_for(np + 1, 128, 2), 128, 0, s>>>(part->d_keys, n, seed_a, pa, seed_b, pb, part->d_o1,
                                                                   d_ctl, part->d_bpref, part->d_lvl1_start);
-        if (cudaGetLastError() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "directory_kernel"));
+        if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "directory_kernel"));
     }
     *out = part;
     return HC_OK;
@@ -663,7 +663,7 @@ hc_status exclusive_scan_impl(const T* d_in, uint64_t* d_out, uint64_t n_max, co
     HC_CUDA_TRY(cudaMemsetAsync(status, 0, ntiles * sizeof(uint64_t), s));
     HC_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t), s));
     scan_kernel<T><<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(d_in, d_out, n_max, d_n, status, ctr, d_err);
-    HC_CUDA_TRY(cudaGetLastError());
+    HC_CUDA_TRY(launch_check());
     return HC_OK;
 }
 

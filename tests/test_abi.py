@@ -22,7 +22,7 @@ def _declared():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"\b(?:hc_status|const char\s*\*|uint32_t)\s+(hc_\w+)\s*\(", text):
+        for m in re.finditer(r"\b(?:hc_status|const char\s*\*|uint32_t|uint64_t)\s+(hc_\w+)\s*\(", text):
             names.add(m.group(1))
     return names
 
