@@ -114,6 +114,31 @@ hc_status hc_index_get_view(const hc_index* index, hc_index_view* out);
 hc_status hc_index_from_stats(uint64_t n, uint64_t l1, uint32_t attr_order, uint32_t max_first,
                               uint32_t max_second, hc_index** out);
 
+/* --------------------------------------------------- coco_levels_noalloc
+ * The CoCo levels V1, O1, V2 (as hc_build_index writes them) of rows that
+ * the caller has already sorted, computed without allocating any memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot let the library allocate device memory -- services whose device
+ * memory is all reserved up front by another allocator, and request paths
+ * that must not call an allocator at all.
+ *   d_sorted_keys  device, [n] rows as (first << 32 | second), ascending.
+ *   n              rows; at most 16,777,216 (2^24), else HC_ERR_CAPACITY
+ *                  before any device work.
+ *   d_v1 [n], d_o1 [n + 1], d_v2 [n]   device outputs, caller-owned.
+ *   d_info [2]     device output: d_info[0] = l1 (the number of V1
+ *                  entries), d_info[1] = flags: bit 0 set when a bounded
+ *                  look-back wait gave up (the outputs are then invalid),
+ *                  bit 1 set when two adjacent rows are equal (not a set).
+ * Enqueued on `stream` without waiting.  Calls no cudaMalloc, cudaFree or
+ * other allocating routine; the kernel's scratch is one fixed array of
+ * 32,832 bytes inside the library, held by every GPU that loads it until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (once per device), so make it before any stream capture.  All
+ * calls share the array and each call clears what it reads: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race. */
+hc_status hc_coco_levels_noalloc(const uint64_t* d_sorted_keys, uint64_t n, uint32_t* d_v1, uint32_t* d_o1,
+                                 uint32_t* d_v2, uint32_t* d_info, void* stream);
+
 /* ------------------------------------------------------- partition_index
  * HyperCube partitioning of one indexed relation (Sec. 4, partitioning
  * paragraphs and Example "partition"): a row (a, b) in the index's attribute

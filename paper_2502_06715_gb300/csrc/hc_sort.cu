@@ -6,6 +6,8 @@
 // already sorted rows, so each partition stays sorted) and a segmented
 // run-boundary scan that builds one CoCo per partition.
 #include <algorithm>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "hc_internal.cuh"
@@ -677,3 +679,93 @@ hc_status exclusive_scan_u64(const uint64_t* d_in, uint64_t* d_out, uint64_t n_m
 }
 
 }  // namespace hc
+
+namespace hc {
+namespace {
+__global__ void noalloc_info_kernel(const Ctl* __restrict__ ctl, uint32_t* __restrict__ info) {
+    info[0] = ctl->l1;
+    info[1] = (ctl->err & DEV_ERR_TIMEOUT ? 1u : 0u) | (ctl->dup ? 2u : 0u);
+}
+}  // namespace
+}  // namespace hc
+
+// ---------------------------------------------------------------------------
+// Allocation-free CoCo level build (hc_coco_levels_noalloc).
+//
+// Some callers cannot let this library allocate device memory: services
+// whose device memory is entirely reserved up front by another allocator
+// (a library-side cudaMalloc would fail or fragment that reservation), and
+// request paths that forbid any allocation so that their latency never
+// includes an allocator call.  For them this entry point runs the same
+// run-boundary kernel as hc_build_index on keys the caller has already
+// sorted, writing only into the caller's buffers.  The kernel's look-back
+// scratch lives in the fixed array below, which every GPU that loads this
+// library holds until the process exits.
+namespace hc {
+namespace {
+
+constexpr uint32_t NOALLOC_MAX_TILES = 4096;  // 4096 tiles of 4096 rows
+constexpr uint64_t NOALLOC_MAX_ROWS = (uint64_t)NOALLOC_MAX_TILES * SORT_TILE;  // 16,777,216 rows
+// NOALLOC_MAX_TILES look-back words, then one control block (8 words).
+constexpr uint32_t NOALLOC_WORDS = NOALLOC_MAX_TILES + 8;
+static_assert(sizeof(Ctl) <= 8 * sizeof(uint64_t), "control block must fit the scratch tail");
+
+static __device__ __align__(256) uint64_t g_noalloc_scratch[NOALLOC_WORDS];
+
+// Device address of g_noalloc_scratch for each device, looked up once per
+// device with that device current.  In host code the array's name is only a
+// host-side stand-in, never a device address, so kernels always receive the
+// looked-up pointer.
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256] = {};
+
+hc_status noalloc_scratch(uint64_t** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 256) return fail(HC_ERR_CAPACITY, "coco_levels_noalloc: device ordinal above 255");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_addr[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = (uint64_t*)g_noalloc_addr[dev];
+    return HC_OK;
+}
+
+}  // namespace
+}  // namespace hc
+
+extern "C" hc_status hc_coco_levels_noalloc(const uint64_t* d_sorted_keys, uint64_t n, uint32_t* d_v1,
+                                            uint32_t* d_o1, uint32_t* d_v2, uint32_t* d_info, void* stream) {
+    using namespace hc;
+    if (n > NOALLOC_MAX_ROWS)
+        return fail(HC_ERR_CAPACITY, "coco_levels_noalloc: n = " + std::to_string(n) + " rows exceeds the fixed " +
+                                         "scratch limit of " + std::to_string(NOALLOC_MAX_ROWS) + " rows");
+    if (!d_o1 || !d_info || (n > 0 && (!d_sorted_keys || !d_v1 || !d_v2)))
+        return fail(HC_ERR_ARG, "coco_levels_noalloc: NULL buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t* scratch = nullptr;
+    HC_TRY(noalloc_scratch(&scratch));
+    Ctl* ctl = (Ctl*)(scratch + NOALLOC_MAX_TILES);
+    const uint64_t ntiles = n == 0 ? 0 : (n + SORT_TILE - 1) / SORT_TILE;
+    // the scratch keeps the previous call's words: clear the status words
+    // this call reads and the control block
+    if (ntiles > 0) HC_CUDA_TRY(cudaMemsetAsync(scratch, 0, ntiles * sizeof(uint64_t), s));
+    HC_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+    if (n == 0) {
+        HC_CUDA_TRY(cudaMemsetAsync(d_o1, 0, sizeof(uint32_t), s));
+    } else {
+        boundary_kernel<false><<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(d_sorted_keys, n, 0, 1, 0, 1, d_v1, d_o1,
+                                                                          d_v2, scratch, &ctl->tile_counter[MAX_PASSES],
+                                                                          ctl);
+        HC_CUDA_TRY(launch_check());
+    }
+    // d_info[0] = l1, d_info[1] = flags: bit 0 a look-back wait gave up,
+    // bit 1 two adjacent rows are equal
+    noalloc_info_kernel<<<1, 1, 0, s>>>(ctl, d_info);
+    HC_CUDA_TRY(launch_check());
+    return HC_OK;
+}
