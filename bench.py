@@ -55,6 +55,9 @@ def parse_args():
     ap.add_argument("--P", type=int, default=1024)
     ap.add_argument("--grain", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--capacity", default="plan",
+                    help="materialize output pool: 'plan' = 1.25 x the planning run's count (one pass), "
+                         "'0' = counting pass + emitting pass")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-frac", type=float, default=1.0 / 32,
@@ -218,10 +221,12 @@ def main():
     ix0.free()
     del stats
 
+    capacity = int(1.25 * expect) + 1 if a.capacity == "plan" else int(a.capacity)
+
     def step():
         ix = hc.build_index(d_pairs, 0, stream=stream)
         r = hc.run_join(q, [ix, ix, ix], shares=shares, mode=a.mode, keep_device=True, time_kernels=True,
-                        item_grain=a.grain, block_threads=a.threads, stream=stream)
+                        item_grain=a.grain, block_threads=a.threads, stream=stream, out_capacity=capacity)
         ix.free()
         return r
 
@@ -266,7 +271,7 @@ def main():
     # unit of the work counter (each element of the shortest list read once
     # per list it is searched in), plus, for the emitting launch, the output
     # tuples written (3 x 4 B each)
-    n_launch_per_step = 2 if a.mode == "materialize" else 1
+    n_launch_per_step = kern_launches / a.steps
     out_bytes = 12.0 * count if a.mode == "materialize" else 0.0
     alg_bytes = 4.0 * work + out_bytes / n_launch_per_step
     avg_launch_s = (kern_ms / max(1, kern_launches)) / 1e3
@@ -279,7 +284,7 @@ def main():
 
     e2e = None
     if not a.no_e2e:
-        e2e = end_to_end(a, hc, ep, shares, q, dev, stream, expect)
+        e2e = end_to_end(a, hc, ep, shares, q, dev, stream, expect, capacity)
 
     cpu = None
     if not a.no_cpu_baseline and rank == 0 and world == 1:
@@ -294,6 +299,8 @@ def main():
             "config": {"workload": workload_name(a), "scale": a.scale, "edge_factor": a.edge_factor,
                        "rows_E+": n, "distinct_x": l1, "tuples": count, "shares": shares,
                        "shares_from": a.shares if a.shares != "plan" else f"choose_shares(P={a.P})",
+                       "out_capacity": capacity if a.mode == "materialize" else None,
+                       "search_launches_per_step": n_launch_per_step,
                        "work_counter": work, "l2": "inputs larger than L2 (E+ is %.0f MB)" % (n * 8 / 1e6),
                        "parallelism": f"replicas x{world}", "generate_s": round(gen_s, 1)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
@@ -303,7 +310,7 @@ def main():
         dist.destroy_process_group()
 
 
-def end_to_end(a, hc, ep, shares, q, dev, stream, expect):
+def end_to_end(a, hc, ep, shares, q, dev, stream, expect, capacity):
     """Same metric through the public API from pinned HOST memory: the H2D
     copy of E+, the build, the join and the D2H copy of the result (all
     tuples in materialize mode, the count otherwise) are inside the timed
@@ -321,7 +328,7 @@ def end_to_end(a, hc, ep, shares, q, dev, stream, expect):
         d = host_in.to(dev, non_blocking=True)
         ix = hc.build_index(d, 0, stream=stream)
         r = hc.run_join(q, [ix, ix, ix], shares=shares, mode=a.mode, keep_device=True, item_grain=a.grain,
-                        block_threads=a.threads, stream=stream)
+                        block_threads=a.threads, stream=stream, out_capacity=capacity)
         if host_out is not None:
             host_out.copy_(r.tuples, non_blocking=True)
         torch.cuda.current_stream(dev).synchronize()

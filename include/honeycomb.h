@@ -207,7 +207,17 @@ typedef struct {
     uint32_t mode;                /* HC_MODE_COUNT or HC_MODE_MATERIALIZE               */
     uint32_t flags;               /* HC_FLAG_*                                          */
     uint32_t item_grain;          /* loop-2 candidates per work item (0: default)       */
-    uint32_t block_threads;       /* threads per block of the join kernel (0: default)  */
+    uint32_t block_threads;       /* threads per block of the search kernel, a multiple */
+                                  /* of 32 up to 128 (0: default 128)                   */
+    uint32_t merge_min;           /* last loop: two lists both at least this long ...   */
+    uint32_t merge_ratio;         /* ... and within this length ratio are intersected    */
+                                  /* by a warp block merge, others by binary search      */
+                                  /* (0: defaults 32 and 4; 0xFFFFFFFF: never merge)     */
+    uint64_t out_capacity;        /* materialize: 0 runs a counting pass, then an        */
+                                  /* emitting pass (tuples cell-major, in a fixed order); */
+                                  /* > 0 runs one pass writing into an output pool of    */
+                                  /* about this many tuples (order not fixed), and falls */
+                                  /* back to the emitting pass if the pool overflows     */
 } hc_join_params;
 
 /* Generic Join of q over the indexes, one logical worker per HyperCube cell
@@ -221,11 +231,10 @@ typedef struct {
  *            the others are partitioned per call (Sec. 4).
  *   out      library-owned result (hc_result_free).
  * Count mode enqueues everything and returns without waiting; the count is
- * read with hc_result_get (which waits).  Materialize mode waits once after
- * its counting pass to size the output, then enqueues the emitting pass.
- * Output tuples hold n_vars uint32 values in variable-id order, cell-major
- * and in loop order's lexicographic order within a cell; the result is a set
- * (no repeats) whatever the shares. */
+ * read with hc_result_get (which waits).  Materialize mode waits for the
+ * device to size its output (see out_capacity).  Output tuples hold n_vars
+ * uint32 values in variable-id order; the result is a set (no repeats)
+ * whatever the shares. */
 hc_status hc_run_join(const hc_query* q, const hc_index* const* idx, const hc_join_params* params,
                       void* stream, hc_result** out);
 
@@ -240,7 +249,7 @@ typedef struct {
     uint64_t n_items;           /* work items of the join kernel                      */
     float ms_join_kernel;       /* with HC_FLAG_TIME_KERNELS: device time of the search */
                                 /* kernel launches (CUDA events on the join's stream)  */
-    uint32_t n_join_launches;   /* search kernel launches (1 count, 2 materialize)      */
+    uint32_t n_join_launches;   /* search kernel launches of this join (1 or 2)         */
 } hc_result_view;
 /* Waits for the result's stream, then fills `out`. */
 hc_status hc_result_get(hc_result* r, hc_result_view* out);

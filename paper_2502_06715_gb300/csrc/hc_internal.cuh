@@ -179,16 +179,19 @@ __device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
 }
 
 // First index in [lo, hi) of sorted a[] whose value is >= x (hi if none).
+// Branch-free halving: each step keeps the upper half when its first
+// element is still below x.
 template <typename P>
 __device__ __forceinline__ uint32_t lower_bound_u32(P a, uint32_t lo, uint32_t hi, uint32_t x) {
-    while (lo < hi) {
-        uint32_t mid = lo + ((hi - lo) >> 1);
-        if (a[mid] < x)
-            lo = mid + 1;
-        else
-            hi = mid;
+    uint32_t len = hi - lo;
+    if (len == 0) return lo;
+    uint32_t base = lo;
+    while (len > 1) {
+        const uint32_t half = len >> 1;
+        base = a[base + half] < x ? base + half : base;
+        len -= half;
     }
-    return lo;
+    return base + (a[base] < x ? 1u : 0u);
 }
 
 #endif  // __CUDACC__

@@ -50,6 +50,15 @@ struct DPlan {
     int src_top[HC_MAX_VARS][MAXSRC];
     int nopen[HC_MAX_VARS];
     int var_of_level[HC_MAX_VARS];
+    // per loop and source: 1 when the list depends only on the loop-1
+    // binding (a top-level list, or the sub-list of an atom loop 1 opens);
+    // otherwise the loop f that opens the atom and its slot there
+    int src_ec[HC_MAX_VARS][MAXSRC];
+    int src_f[HC_MAX_VARS][MAXSRC];
+    int src_slot[HC_MAX_VARS][MAXSRC];
+    // last loop: a parent whose two lists are both >= merge_min long and
+    // within merge_ratio of each other takes the block-merge path
+    uint32_t merge_min, merge_ratio;
 };
 
 struct JoinCtl {
@@ -59,7 +68,14 @@ struct JoinCtl {
     uint64_t total;      // |Q|
     uint64_t work;       // work counter (stats)
     uint64_t n_items;
+    uint32_t chunk_ctr;  // output chunks handed out (single-pass materialize)
+    uint32_t overflow;   // 1 when the output pool ran out of chunks
 };
+
+// Single-pass materialize: each warp writes its tuples into chunks of
+// OUT_CHUNK tuples taken from an output pool with one atomic per chunk.
+constexpr uint32_t OUT_CHUNK = 2048;
+constexpr uint32_t NO_CHUNK = 0xFFFFFFFFu;
 
 __device__ __forceinline__ void load_plan(DPlan& dst, const DPlan* __restrict__ src) {
     const uint32_t* s = (const uint32_t*)src;
@@ -212,68 +228,103 @@ __global__ void entries_total_kernel(const uint64_t* __restrict__ flagoff, const
 }
 
 // ---------------------------------------------------------- search loops
-// Bindings of the batches of loops 2.. (index = loop), one per lane.
-struct Frame {
-    uint32_t val[HC_MAX_VARS];
-    uint32_t par[HC_MAX_VARS];
-    uint32_t olo[HC_MAX_VARS][MAXOPEN];
-    uint32_t ohi[HC_MAX_VARS][MAXOPEN];
+// Shapes are compiled per (NL loops, S lists per loop, O atoms opened per
+// loop) so that per-lane state stays in registers.
+
+// The loop-1 binding a work item is under (lane-uniform): the value, its
+// cell, and for every later loop the ranges of its lists that depend only on
+// this binding (top-level lists of the cell's partitions, and sub-lists of
+// atoms opened by loop 1).
+template <int NL, int S>
+struct Entry {
+    uint32_t cell, x;
+    uint32_t lo[NL][S], hi[NL][S];
+    uint32_t k0, k1;      // the work item's subrange of loop 1's shortest list
+    uint32_t best1, len1;  // that list (source index) and its full length
 };
 
-// The loop-1 binding a work item is under (lane-uniform).
-struct EntryCtx {
-    uint32_t cell, x;
-    uint32_t r0lo[MAXOPEN], r0hi[MAXOPEN];          // atoms opened by loop 1
-    uint32_t tlo[HC_MAX_ATOMS], thi[HC_MAX_ATOMS];  // partition top-level range per atom
+// Batch bindings of loops 1..NL-2 (index = loop), one per lane.
+template <int NL, int O>
+struct Frame {
+    uint32_t val[NL];
+    uint32_t par[NL];
+    uint32_t olo[NL][O];
+    uint32_t ohi[NL][O];
 };
 
 struct Acc {
     uint64_t count;    // matches at the last loop (lane-uniform)
     uint64_t work;     // per-lane work counter
-    uint64_t out_pos;  // next output slot (materialize)
+    uint64_t out_pos;  // next output slot (two-pass materialize)
     uint32_t* out;
     int stats;
+    // single-pass materialize (pool != 0): the warp's current chunk and fill
+    int pool;
+    uint32_t chunk, fill, n_chunks;
+    uint32_t* chunk_fill;
+    JoinCtl* ctl;
 };
+
+// Output slot of the lane holding rank r among the k = popc(ball) matches
+// of this round (all lanes call).  Two-pass mode: consecutive slots from
+// out_pos.  Pool mode: the rest of the warp's chunk, then a new chunk; a slot
+// of ~0 means the pool is exhausted and the tuple is not written.
+__device__ __forceinline__ uint64_t out_reserve(Acc& A, uint32_t ball) {
+    const uint32_t r = __popc(ball & lanemask_lt());
+    const uint32_t k = __popc(ball);
+    if (!A.pool) {
+        const uint64_t slot = A.out_pos + r;
+        A.out_pos += k;
+        return slot;
+    }
+    if (k == 0) return ~0ull;
+    const uint32_t room = OUT_CHUNK - A.fill;
+    uint64_t slot;
+    if (k <= room) {
+        slot = A.chunk == NO_CHUNK ? ~0ull : (uint64_t)A.chunk * OUT_CHUNK + A.fill + r;
+        A.fill += k;
+        return slot;
+    }
+    uint32_t nc = 0;
+    if (lane_id() == 0) {
+        if (A.chunk != NO_CHUNK) A.chunk_fill[A.chunk] = OUT_CHUNK;
+        nc = atomicAdd(&A.ctl->chunk_ctr, 1u);
+        if (nc >= A.n_chunks) atomicOr(&A.ctl->overflow, 1u);
+    }
+    nc = __shfl_sync(0xffffffffu, nc, 0);
+    if (nc >= A.n_chunks) nc = NO_CHUNK;
+    if (r < room)
+        slot = A.chunk == NO_CHUNK ? ~0ull : (uint64_t)A.chunk * OUT_CHUNK + A.fill + r;
+    else
+        slot = nc == NO_CHUNK ? ~0ull : (uint64_t)nc * OUT_CHUNK + (r - room);
+    A.chunk = nc;
+    A.fill = k - room;
+    return slot;
+}
 
 // Position of the r-th (0-based) set bit of m (r < popc(m)).
 __device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t r) {
     uint32_t pos = 0;
 #pragma unroll
     for (uint32_t w = 16; w >= 1; w >>= 1) {
-        uint32_t c = __popc(m & ((1u << (pos + w)) - 1u));  // set bits below pos + w
+        const uint32_t c = __popc(m & ((1u << (pos + w)) - 1u));  // set bits below pos + w
         if (c <= r) pos += w;
     }
     return pos;
 }
 
 // Range of source q of loop L for the binding of loop L-1 held by lane
-// `lane_of` (every lane calls with its own lane_of; all lanes take part).
-template <int L>
-__device__ __forceinline__ void src_range(const DPlan& P, const Frame& F, const EntryCtx& E, int q, uint32_t lane_of,
-                                          uint32_t& lo, uint32_t& hi) {
-    const int j = P.src_atom[L][q];
-    const DAtom& a = P.atom[j];
-    lo = 0;
-    hi = 0;
-    if (P.src_top[L][q]) {
-#pragma unroll
-        for (int jj = 0; jj < HC_MAX_ATOMS; ++jj)
-            if (jj == j) {
-                lo = E.tlo[jj];
-                hi = E.thi[jj];
-            }
+// `lane_of` (all lanes call together: ranges of atoms opened by loops >= 1
+// are fetched from the holder of the opening binding by shuffles).
+template <int L, int NL, int S, int O>
+__device__ __forceinline__ void src_range(const DPlan& P, const Frame<NL, O>& F, const Entry<NL, S>& E, int q,
+                                          uint32_t lane_of, uint32_t& lo, uint32_t& hi) {
+    if (P.src_ec[L][q]) {
+        lo = E.lo[L][q];
+        hi = E.hi[L][q];
         return;
     }
-    const int f = a.lev_first, s = a.slot;
-    if (f == 0) {
-#pragma unroll
-        for (int ss = 0; ss < MAXOPEN; ++ss)
-            if (ss == s) {
-                lo = E.r0lo[ss];
-                hi = E.r0hi[ss];
-            }
-        return;
-    }
+    const int f = P.src_f[L][q], s = P.src_slot[L][q];
     uint32_t anc = lane_of;  // ancestor at loop f of the loop L-1 binding
 #pragma unroll
     for (int g = L - 1; g >= 1; --g)
@@ -282,7 +333,7 @@ __device__ __forceinline__ void src_range(const DPlan& P, const Frame& F, const 
 #pragma unroll
     for (int g = 1; g < L; ++g)
 #pragma unroll
-        for (int ss = 0; ss < MAXOPEN; ++ss)
+        for (int ss = 0; ss < O; ++ss)
             if (g == f && ss == s) {
                 mylo = F.olo[g][ss];
                 myhi = F.ohi[g][ss];
@@ -297,15 +348,16 @@ __device__ __forceinline__ const uint32_t* src_list(const DPlan& P, int L, int q
 }
 
 // Search candidate v (element kpos of source `best`) in the other lists of
-// loop L.  A top-level list that holds v opens its atom: the o1 range of v's
-// position is the atom's sub-list for the next loops.
-template <int L>
-__device__ __forceinline__ bool probe(const DPlan& P, int best, const uint32_t (&rlo)[MAXSRC],
-                                      const uint32_t (&rhi)[MAXSRC], uint32_t kpos, uint32_t v, bool active,
-                                      uint32_t (&nlo)[MAXOPEN], uint32_t (&nhi)[MAXOPEN]) {
+// loop L ("search(V, x)", Sec. 5: first position >= x, by binary search).  A
+// top-level list holding v opens its atom: the o1 range at v's position is
+// the atom's sub-list for later loops (Sec. 5 level restriction).
+template <int L, int S, int O>
+__device__ __forceinline__ bool probe(const DPlan& P, int best, const uint32_t (&rlo)[S], const uint32_t (&rhi)[S],
+                                      uint32_t kpos, uint32_t v, bool active, uint32_t (&nlo)[O],
+                                      uint32_t (&nhi)[O]) {
     bool ok = active;
 #pragma unroll
-    for (int q = 0; q < MAXSRC; ++q) {
+    for (int q = 0; q < S; ++q) {
         if (q < P.nsrc[L]) {
             const uint32_t* list = src_list(P, L, q);
             uint32_t p = kpos;
@@ -313,7 +365,7 @@ __device__ __forceinline__ bool probe(const DPlan& P, int best, const uint32_t (
                 p = ok ? lower_bound_u32(list, rlo[q], rhi[q], v) : rhi[q];
                 ok = ok && p < rhi[q] && list[p] == v;
             }
-            if (q < MAXOPEN && P.src_top[L][q] && ok) {
+            if (q < O && P.src_top[L][q] && ok) {  // top sources come first, slot == q
                 const DAtom& a = P.atom[P.src_atom[L][q]];
                 nlo[q] = a.o1[p];
                 nhi[q] = a.o1[p + 1];
@@ -323,40 +375,138 @@ __device__ __forceinline__ bool probe(const DPlan& P, int best, const uint32_t (
     return ok;
 }
 
-template <int L, int NL, bool MAT>
-__device__ __forceinline__ void run_level(const DPlan& P, Frame& F, const EntryCtx& E, Acc& A, uint32_t nb);
+// Values bound by loops 1..L-1 for the binding of loop L-1 held by lane
+// `parent` (all lanes call together).
+template <int L, int NL, int O>
+__device__ __forceinline__ void prefix_values(const Frame<NL, O>& F, uint32_t parent, uint32_t (&vals)[NL]) {
+    uint32_t anc = parent;
+#pragma unroll
+    for (int g = L - 1; g >= 1; --g) {
+        vals[g] = __shfl_sync(0xffffffffu, F.val[g], anc);
+        anc = __shfl_sync(0xffffffffu, F.par[g], anc);
+    }
+}
 
-// Last loop: count the matches, or write them as output tuples.
-template <int L, int NL, bool MAT>
-__device__ __forceinline__ void finish_round(const DPlan& P, const Frame& F, const EntryCtx& E, Acc& A, bool ok,
-                                             uint32_t v, uint32_t parent) {
+template <int L, int NL>
+__device__ __forceinline__ void write_tuple(const DPlan& P, uint32_t* o, uint32_t x, const uint32_t (&vals)[NL],
+                                            uint32_t v) {
+    o[P.var_of_level[L]] = v;
+    o[P.var_of_level[0]] = x;
+#pragma unroll
+    for (int g = L - 1; g >= 1; --g) o[P.var_of_level[g]] = vals[g];
+}
+
+template <int L, int NL, int S, int O, bool MAT>
+__device__ __forceinline__ void run_level(const DPlan& P, Frame<NL, O>& F, const Entry<NL, S>& E, Acc& A,
+                                          uint32_t nb);
+
+// Last loop, flattened path: count the round's matches, or write them.
+template <int L, int NL, int S, int O, bool MAT>
+__device__ __forceinline__ void finish_round(const DPlan& P, const Frame<NL, O>& F, const Entry<NL, S>& E, Acc& A,
+                                             bool ok, uint32_t v, uint32_t parent) {
     const uint32_t ball = __ballot_sync(0xffffffffu, ok);
     if constexpr (MAT) {
-        uint32_t vals[HC_MAX_VARS];
-        uint32_t anc = parent;
-#pragma unroll
-        for (int g = L - 1; g >= 1; --g) {
-            vals[g] = __shfl_sync(0xffffffffu, F.val[g], anc);
-            anc = __shfl_sync(0xffffffffu, F.par[g], anc);
-        }
-        if (ok) {
-            const uint64_t slot = A.out_pos + __popc(ball & lanemask_lt());
-            uint32_t* o = A.out + slot * (uint64_t)P.nv;
-            o[P.var_of_level[L]] = v;
-            o[P.var_of_level[0]] = E.x;
-#pragma unroll
-            for (int g = L - 1; g >= 1; --g) o[P.var_of_level[g]] = vals[g];
-        }
+        uint32_t vals[NL];
+        prefix_values<L, NL, O>(F, parent, vals);
+        const uint64_t slot = out_reserve(A, ball);
+        if (ok && slot != ~0ull) write_tuple<L, NL>(P, A.out + slot * (uint64_t)P.nv, E.x, vals, v);
     }
     A.count += __popc(ball);
-    A.out_pos += __popc(ball);
+}
+
+// Last loop, merge-path for one parent whose two lists are long and of
+// similar length.  The longer list B is cut into 32 equal chunks, one per
+// lane; each lane finds the matching range of the shorter list A by two
+// binary searches (the A values in [B[j0], B[j1]) ) and walks both ranges as
+// a sequential merge, so an equal pair is met by exactly one lane (the lane
+// owning its B position).  Count mode walks lanes independently; materialize
+// mode steps the lanes together and writes each step's matches in lane order.
+template <int L, int NL, int S, int O, bool MAT>
+__device__ __forceinline__ void merge_pair(const DPlan& P, const Entry<NL, S>& E, Acc& A, const uint32_t* la,
+                                           uint32_t a0, uint32_t a1, const uint32_t* lb, uint32_t b0, uint32_t b1,
+                                           const uint32_t (&vals)[NL]) {
+    const uint32_t lane = lane_id();
+    if (a1 - a0 > b1 - b0) {  // B is the longer list
+        const uint32_t* t = la;
+        la = lb;
+        lb = t;
+        uint32_t u = a0;
+        a0 = b0;
+        b0 = u;
+        u = a1;
+        a1 = b1;
+        b1 = u;
+    }
+    const uint32_t n = b1 - b0;
+    const uint32_t j0 = b0 + (uint32_t)(((uint64_t)n * lane) >> 5);
+    const uint32_t j1 = b0 + (uint32_t)(((uint64_t)n * (lane + 1)) >> 5);
+    uint32_t i = a1, i1 = a1;
+    if (j0 < j1) {
+        i = lower_bound_u32(la, a0, a1, lb[j0]);
+        i1 = j1 < b1 ? lower_bound_u32(la, i, a1, lb[j1]) : a1;
+    }
+    uint32_t j = j0;
+    if constexpr (!MAT) {
+        uint32_t cnt = 0;
+        if (i < i1 && j < j1) {
+            uint32_t x = la[i], y = lb[j];
+            for (;;) {
+                if (x < y) {
+                    if (++i >= i1) break;
+                    x = la[i];
+                } else if (y < x) {
+                    if (++j >= j1) break;
+                    y = lb[j];
+                } else {
+                    ++cnt;
+                    if (++i >= i1 || ++j >= j1) break;
+                    x = la[i];
+                    y = lb[j];
+                }
+            }
+        }
+        A.count += __reduce_add_sync(0xffffffffu, cnt);
+    } else {
+        bool live = i < i1 && j < j1;
+        uint32_t x = live ? la[i] : 0, y = live ? lb[j] : 0;
+        while (__any_sync(0xffffffffu, live)) {
+            bool m = false;
+            uint32_t mv = 0;
+            if (live) {
+                if (x < y) {
+                    if (++i >= i1)
+                        live = false;
+                    else
+                        x = la[i];
+                } else if (y < x) {
+                    if (++j >= j1)
+                        live = false;
+                    else
+                        y = lb[j];
+                } else {
+                    m = true;
+                    mv = x;
+                    if (++i >= i1 || ++j >= j1) {
+                        live = false;
+                    } else {
+                        x = la[i];
+                        y = lb[j];
+                    }
+                }
+            }
+            const uint32_t ball = __ballot_sync(0xffffffffu, m);
+            const uint64_t slot = out_reserve(A, ball);
+            if (m && slot != ~0ull) write_tuple<L, NL>(P, A.out + slot * (uint64_t)P.nv, E.x, vals, mv);
+            A.count += __popc(ball);
+        }
+    }
 }
 
 // Compact this round's matches into the batch of loop L and descend.
-template <int L, int NL, bool MAT>
-__device__ __forceinline__ void descend(const DPlan& P, Frame& F, const EntryCtx& E, Acc& A, bool ok, uint32_t v,
-                                        uint32_t parent, const uint32_t (&nlo)[MAXOPEN],
-                                        const uint32_t (&nhi)[MAXOPEN]) {
+template <int L, int NL, int S, int O, bool MAT>
+__device__ __forceinline__ void descend(const DPlan& P, Frame<NL, O>& F, const Entry<NL, S>& E, Acc& A, bool ok,
+                                        uint32_t v, uint32_t parent, const uint32_t (&nlo)[O],
+                                        const uint32_t (&nhi)[O]) {
     const uint32_t ball = __ballot_sync(0xffffffffu, ok);
     const uint32_t nnew = __popc(ball);
     if (nnew == 0) return;
@@ -365,27 +515,30 @@ __device__ __forceinline__ void descend(const DPlan& P, Frame& F, const EntryCtx
     F.val[L] = __shfl_sync(0xffffffffu, v, src);
     F.par[L] = __shfl_sync(0xffffffffu, parent, src);
 #pragma unroll
-    for (int s = 0; s < MAXOPEN; ++s) {
+    for (int s = 0; s < O; ++s) {
         F.olo[L][s] = __shfl_sync(0xffffffffu, nlo[s], src);
         F.ohi[L][s] = __shfl_sync(0xffffffffu, nhi[s], src);
     }
-    run_level<L + 1, NL, MAT>(P, F, E, A, nnew);
+    run_level<L + 1, NL, S, O, MAT>(P, F, E, A, nnew);
 }
 
-// Loop L >= 2 (index): the parents are the nb bindings of loop L-1 held by
-// lanes 0..nb-1; their candidates are flattened over the lanes, 32 a round.
-template <int L, int NL, bool MAT>
-__device__ __forceinline__ void run_level(const DPlan& P, Frame& F, const EntryCtx& E, Acc& A, uint32_t nb) {
+// Loop L >= 1 (index): the parents are the nb bindings of loop L-1 held by
+// lanes 0..nb-1 (for L == 1 the entry itself, nb == 1, candidates limited to
+// the work item's subrange via E.lo/hi of its shortest list); their
+// candidates are flattened over the lanes, 32 a round.
+template <int L, int NL, int S, int O, bool MAT>
+__device__ __forceinline__ void run_level(const DPlan& P, Frame<NL, O>& F, const Entry<NL, S>& E, Acc& A,
+                                          uint32_t nb) {
     if constexpr (L < NL) {
         const uint32_t lane = lane_id();
         const int ns = P.nsrc[L];
-        uint32_t mlo[MAXSRC], mhi[MAXSRC];
+        uint32_t mlo[S], mhi[S];
         uint32_t best = 0, bestlen = 0xFFFFFFFFu;
 #pragma unroll
-        for (int q = 0; q < MAXSRC; ++q) {
+        for (int q = 0; q < S; ++q) {
             mlo[q] = mhi[q] = 0;
             if (q < ns) {
-                src_range<L>(P, F, E, q, lane < nb ? lane : 0, mlo[q], mhi[q]);
+                src_range<L, NL, S, O>(P, F, E, q, lane < nb ? lane : 0, mlo[q], mhi[q]);
                 const uint32_t len = mhi[q] - mlo[q];
                 if (len < bestlen) {
                     bestlen = len;
@@ -393,8 +546,33 @@ __device__ __forceinline__ void run_level(const DPlan& P, Frame& F, const EntryC
                 }
             }
         }
-        const uint32_t cnt = lane < nb ? bestlen : 0;
-        if (A.stats) A.work += (uint64_t)ns * cnt;
+        if constexpr (L == 1) {
+            // loop 1 of a work item: its subrange [k0, k1) of the entry's shortest list
+            best = E.best1;
+            bestlen = E.k1 - E.k0;
+#pragma unroll
+            for (int q = 0; q < S; ++q)
+                if (q == (int)best) {
+                    const uint32_t base = mlo[q];
+                    mlo[q] = base + E.k0;
+                    mhi[q] = base + E.k1;
+                }
+        }
+        bool merge_class = false;
+        if constexpr (L == NL - 1 && S >= 2) {
+            if (ns == 2 && lane < nb) {
+                const uint32_t l0 = mhi[0] - mlo[0], l1 = mhi[1] - mlo[1];
+                const uint32_t mn = min(l0, l1), mx = max(l0, l1);
+                merge_class = mn >= P.merge_min && (uint64_t)mx <= (uint64_t)P.merge_ratio * mn;
+            }
+        }
+        const uint32_t cnt = (lane < nb && !merge_class) ? bestlen : 0;
+        if (A.stats && lane < nb) {
+            if (L > 1)
+                A.work += (uint64_t)ns * bestlen;
+            else if (E.k0 == 0)
+                A.work += (uint64_t)ns * E.len1;  // once per loop-1 binding
+        }
         const uint32_t incl = warp_incl_scan(cnt);
         const uint32_t excl = incl - cnt;
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
@@ -402,89 +580,50 @@ __device__ __forceinline__ void run_level(const DPlan& P, Frame& F, const EntryC
             const uint32_t t = t0 + lane;
             const bool active = t < total;
             uint32_t p = 0;  // parent of candidate t: the last lane p < nb with excl_p <= t
+            if (nb > 1) {
 #pragma unroll
-            for (uint32_t step = 16; step >= 1; step >>= 1) {
-                const uint32_t c = p + step;
-                const uint32_t ex = __shfl_sync(0xffffffffu, excl, c & 31u);
-                if (c < nb && ex <= t) p = c;
+                for (uint32_t step = 16; step >= 1; step >>= 1) {
+                    const uint32_t c = p + step;
+                    const uint32_t ex = __shfl_sync(0xffffffffu, excl, c & 31u);
+                    if (c < nb && ex <= t) p = c;
+                }
             }
             const uint32_t k = t - __shfl_sync(0xffffffffu, excl, p);
             const uint32_t pbest = __shfl_sync(0xffffffffu, best, p);
-            uint32_t rlo[MAXSRC], rhi[MAXSRC];
+            uint32_t rlo[S], rhi[S];
 #pragma unroll
-            for (int q = 0; q < MAXSRC; ++q) {
+            for (int q = 0; q < S; ++q) {
                 rlo[q] = __shfl_sync(0xffffffffu, mlo[q], p);
                 rhi[q] = __shfl_sync(0xffffffffu, mhi[q], p);
             }
             uint32_t v = 0, kpos = 0;
 #pragma unroll
-            for (int q = 0; q < MAXSRC; ++q)
+            for (int q = 0; q < S; ++q)
                 if (q == (int)pbest && active) {
                     kpos = rlo[q] + k;
                     v = src_list(P, L, q)[kpos];
                 }
-            uint32_t nlo[MAXOPEN] = {0, 0, 0, 0}, nhi[MAXOPEN] = {0, 0, 0, 0};
-            const bool ok = probe<L>(P, (int)pbest, rlo, rhi, kpos, v, active, nlo, nhi);
+            uint32_t nlo[O], nhi[O];
+#pragma unroll
+            for (int s = 0; s < O; ++s) nlo[s] = nhi[s] = 0;
+            const bool ok = probe<L, S, O>(P, (int)pbest, rlo, rhi, kpos, v, active, nlo, nhi);
             if constexpr (L == NL - 1)
-                finish_round<L, NL, MAT>(P, F, E, A, ok, v, p);
+                finish_round<L, NL, S, O, MAT>(P, F, E, A, ok, v, p);
             else
-                descend<L, NL, MAT>(P, F, E, A, ok, v, p, nlo, nhi);
+                descend<L, NL, S, O, MAT>(P, F, E, A, ok, v, p, nlo, nhi);
         }
-    }
-}
-
-// Loop 2 (index 1) of one entry, candidates [k0, k1) of its shortest list.
-template <int NL, bool MAT>
-__device__ __forceinline__ void run_entry(const DPlan& P, Frame& F, const EntryCtx& E, Acc& A, uint32_t k0,
-                                          uint32_t k1) {
-    const uint32_t lane = lane_id();
-    const int ns = P.nsrc[1];
-    uint32_t rlo[MAXSRC], rhi[MAXSRC];
-    uint32_t best = 0, bestlen = 0xFFFFFFFFu;
-#pragma unroll
-    for (int q = 0; q < MAXSRC; ++q) {
-        rlo[q] = rhi[q] = 0;
-        if (q < ns) {
-            const int j = P.src_atom[1][q];
-            const DAtom& a = P.atom[j];
-            if (P.src_top[1][q]) {
-#pragma unroll
-                for (int jj = 0; jj < HC_MAX_ATOMS; ++jj)
-                    if (jj == j) {
-                        rlo[q] = E.tlo[jj];
-                        rhi[q] = E.thi[jj];
-                    }
-            } else {
-#pragma unroll
-                for (int s = 0; s < MAXOPEN; ++s)
-                    if (s == a.slot) {
-                        rlo[q] = E.r0lo[s];
-                        rhi[q] = E.r0hi[s];
-                    }
-            }
-            if (rhi[q] - rlo[q] < bestlen) {
-                bestlen = rhi[q] - rlo[q];
-                best = q;
+        if constexpr (L == NL - 1 && S >= 2) {
+            uint32_t mball = __ballot_sync(0xffffffffu, merge_class);
+            while (mball) {
+                const uint32_t p = __ffs(mball) - 1;
+                mball &= mball - 1;
+                const uint32_t a0 = __shfl_sync(0xffffffffu, mlo[0], p), a1 = __shfl_sync(0xffffffffu, mhi[0], p);
+                const uint32_t b0 = __shfl_sync(0xffffffffu, mlo[1], p), b1 = __shfl_sync(0xffffffffu, mhi[1], p);
+                uint32_t vals[NL];
+                if constexpr (MAT) prefix_values<L, NL, O>(F, p, vals);
+                merge_pair<L, NL, S, O, MAT>(P, E, A, src_list(P, L, 0), a0, a1, src_list(P, L, 1), b0, b1, vals);
             }
         }
-    }
-    if (A.stats && k0 == 0 && lane == 0) A.work += (uint64_t)ns * bestlen;
-    for (uint32_t t0 = k0; t0 < k1; t0 += 32) {
-        const uint32_t k = t0 + lane;
-        const bool active = k < k1;
-        uint32_t v = 0, kpos = 0;
-#pragma unroll
-        for (int q = 0; q < MAXSRC; ++q)
-            if (q == (int)best && active) {
-                kpos = rlo[q] + k;
-                v = src_list(P, 1, q)[kpos];
-            }
-        uint32_t nlo[MAXOPEN] = {0, 0, 0, 0}, nhi[MAXOPEN] = {0, 0, 0, 0};
-        const bool ok = probe<1>(P, (int)best, rlo, rhi, kpos, v, active, nlo, nhi);
-        if constexpr (NL == 2)
-            finish_round<1, NL, MAT>(P, F, E, A, ok, v, 0);
-        else
-            descend<1, NL, MAT>(P, F, E, A, ok, v, 0, nlo, nhi);
     }
 }
 
@@ -492,27 +631,34 @@ __device__ __forceinline__ void run_entry(const DPlan& P, Frame& F, const EntryC
 // [i*grain, (i+1)*grain) of the concatenation of all entries' candidates.
 // pass 0 counts (and, with item_counts, records each item's count); pass 1
 // writes tuples at item_base[item].
-template <int NL, bool MAT>
-__global__ void __launch_bounds__(256) gj_kernel(const DPlan* __restrict__ gP, const uint32_t* __restrict__ e_cell,
-                                                 const uint32_t* __restrict__ e_x, const uint32_t* __restrict__ e_rng,
-                                                 const uint64_t* __restrict__ uoff, uint32_t grain, JoinCtl* ctl,
-                                                 int pass, uint64_t* __restrict__ cell_counts,
-                                                 uint64_t* __restrict__ item_counts,
-                                                 const uint64_t* __restrict__ item_base, uint32_t* __restrict__ out,
-                                                 int stats) {
+template <int NL, int S, int O, bool MAT>
+__global__ void __launch_bounds__(128, 8) gj_kernel(const DPlan* __restrict__ gP, const uint32_t* __restrict__ e_cell,
+                                                    const uint32_t* __restrict__ e_x,
+                                                    const uint32_t* __restrict__ e_rng,
+                                                    const uint64_t* __restrict__ uoff, uint32_t grain, JoinCtl* ctl,
+                                                    int pass, uint64_t* __restrict__ cell_counts,
+                                                    uint64_t* __restrict__ item_counts,
+                                                    const uint64_t* __restrict__ item_base, uint32_t* __restrict__ out,
+                                                    int stats, uint32_t* __restrict__ chunk_fill, uint32_t n_chunks) {
     __shared__ DPlan P;
     load_plan(P, gP);
     const uint32_t lane = lane_id();
     const uint32_t E_n = ctl->n_entries;
     const uint64_t U = uoff[E_n];
     const uint64_t nitems = (U + grain - 1) / grain;
-    Frame F;
+    Frame<NL, O> F;
     Acc A;
     A.count = 0;
     A.work = 0;
     A.out_pos = 0;
     A.out = out;
     A.stats = stats && pass == 0;
+    A.pool = MAT && pass == 0;  // single pass: count and write into pool chunks
+    A.chunk = NO_CHUNK;
+    A.fill = OUT_CHUNK;
+    A.n_chunks = n_chunks;
+    A.chunk_fill = chunk_fill;
+    A.ctl = ctl;
     uint64_t total = 0;
     for (;;) {
         uint32_t item = 0;
@@ -530,7 +676,7 @@ __global__ void __launch_bounds__(256) gj_kernel(const DPlan* __restrict__ gP, c
                 hi = mid;
         }
         uint32_t e = lo;
-        A.out_pos = MAT ? item_base[item] : 0;
+        A.out_pos = (MAT && !A.pool) ? item_base[item] : 0;
         uint64_t item_count = 0;
         while (u0 < u1 && e < E_n) {
             const uint64_t eb = uoff[e], ee = uoff[e + 1];
@@ -540,21 +686,49 @@ __global__ void __launch_bounds__(256) gj_kernel(const DPlan* __restrict__ gP, c
             }
             const uint32_t k0 = (uint32_t)(u0 - eb);
             const uint32_t k1 = (uint32_t)(min(u1, ee) - eb);
-            EntryCtx E;
+            Entry<NL, S> E;
             E.cell = e_cell[e];
             E.x = e_x[e];
+            uint32_t r0lo[MAXOPEN], r0hi[MAXOPEN];
 #pragma unroll
             for (int s = 0; s < MAXOPEN; ++s) {
-                E.r0lo[s] = e_rng[(uint64_t)e * (2 * MAXOPEN) + 2 * s];
-                E.r0hi[s] = e_rng[(uint64_t)e * (2 * MAXOPEN) + 2 * s + 1];
+                r0lo[s] = s < P.nopen[0] ? e_rng[(uint64_t)e * (2 * MAXOPEN) + 2 * s] : 0;
+                r0hi[s] = s < P.nopen[0] ? e_rng[(uint64_t)e * (2 * MAXOPEN) + 2 * s + 1] : 0;
             }
 #pragma unroll
-            for (int j = 0; j < HC_MAX_ATOMS; ++j) {
-                E.tlo[j] = E.thi[j] = 0;
-                if (j < P.natoms && P.atom[j].lev_first >= 1) top_range(P.atom[j], E.cell, E.tlo[j], E.thi[j]);
+            for (int L = 1; L < NL; ++L)
+#pragma unroll
+                for (int q = 0; q < S; ++q) {
+                    E.lo[L][q] = E.hi[L][q] = 0;
+                    if (q < P.nsrc[L] && P.src_ec[L][q]) {
+                        const DAtom& a = P.atom[P.src_atom[L][q]];
+                        if (P.src_top[L][q]) {
+                            top_range(a, E.cell, E.lo[L][q], E.hi[L][q]);
+                        } else {
+#pragma unroll
+                            for (int s = 0; s < MAXOPEN; ++s)
+                                if (s == a.slot) {
+                                    E.lo[L][q] = r0lo[s];
+                                    E.hi[L][q] = r0hi[s];
+                                }
+                        }
+                    }
+                }
+            {
+                uint32_t best = 0, bestlen = 0xFFFFFFFFu;
+#pragma unroll
+                for (int q = 0; q < S; ++q)
+                    if (q < P.nsrc[1] && E.hi[1][q] - E.lo[1][q] < bestlen) {
+                        bestlen = E.hi[1][q] - E.lo[1][q];
+                        best = q;
+                    }
+                E.k0 = k0;
+                E.k1 = k1;
+                E.best1 = best;
+                E.len1 = bestlen;
             }
             const uint64_t before = A.count;
-            run_entry<NL, MAT>(P, F, E, A, k0, k1);
+            run_level<1, NL, S, O, MAT>(P, F, E, A, 1);
             const uint64_t got = A.count - before;
             if (pass == 0 && cell_counts && got && lane == 0)
                 atomicAdd((unsigned long long*)&cell_counts[E.cell], (unsigned long long)got);
@@ -566,17 +740,31 @@ __global__ void __launch_bounds__(256) gj_kernel(const DPlan* __restrict__ gP, c
         total += item_count;
     }
     if (pass == 0 && lane == 0 && total) atomicAdd((unsigned long long*)&ctl->total, (unsigned long long)total);
+    if (A.pool && lane == 0 && A.chunk != NO_CHUNK) chunk_fill[A.chunk] = A.fill;
     if (A.stats) {
         const uint64_t w = warp_sum64(A.work);
         if (lane == 0 && w) atomicAdd((unsigned long long*)&ctl->work, (unsigned long long)w);
     }
 }
 
-// A query with one loop per variable has at least two loops; NL = 2..5 are
-// instantiated.
-template <int NL>
+// Single-pass materialize: concatenate the filled part of each used pool
+// chunk at its offset in the output.
+__global__ void gather_chunks_kernel(const uint32_t* __restrict__ pool, const uint32_t* __restrict__ chunk_fill,
+                                     const uint64_t* __restrict__ chunk_off, uint32_t n_used, uint32_t nv,
+                                     uint32_t* __restrict__ out) {
+    for (uint32_t c = blockIdx.x; c < n_used; c += gridDim.x) {
+        const uint64_t words = (uint64_t)chunk_fill[c] * nv;
+        const uint32_t* src = pool + (uint64_t)c * OUT_CHUNK * nv;
+        uint32_t* dst = out + chunk_off[c] * nv;
+        for (uint64_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+    }
+}
+
+// Search kernels are compiled for NL = 2..5 loops and for S (lists per
+// loop) and O (atoms opened per loop) of 2 or 4.
+template <int NL, int S, int O>
 int gj_grid(bool mat, int threads) {
-    const void* kern = mat ? (const void*)gj_kernel<NL, true> : (const void*)gj_kernel<NL, false>;
+    const void* kern = mat ? (const void*)gj_kernel<NL, S, O, true> : (const void*)gj_kernel<NL, S, O, false>;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0) != cudaSuccess || per_sm < 1)
         per_sm = 1;
@@ -596,28 +784,56 @@ struct GjArgs {
     uint32_t* out;
     int stats;
     int threads;
+    uint32_t* chunk_fill;
+    uint32_t n_chunks;
 };
 
-template <int NL>
+template <int NL, int S, int O>
 hc_status launch_gj(bool mat, const GjArgs& g, cudaStream_t s) {
-    const int grid = gj_grid<NL>(mat, g.threads);
+    const int grid = gj_grid<NL, S, O>(mat, g.threads);
     if (mat)
-        gj_kernel<NL, true><<<grid, g.threads, 0, s>>>(g.plan, g.e_cell, g.e_x, g.e_rng, g.uoff, g.grain, g.ctl, g.pass,
-                                                       g.cell_counts, g.item_counts, g.item_base, g.out, g.stats);
+        gj_kernel<NL, S, O, true><<<grid, g.threads, 0, s>>>(g.plan, g.e_cell, g.e_x, g.e_rng, g.uoff, g.grain, g.ctl,
+                                                             g.pass, g.cell_counts, g.item_counts, g.item_base, g.out,
+                                                             g.stats, g.chunk_fill, g.n_chunks);
     else
-        gj_kernel<NL, false><<<grid, g.threads, 0, s>>>(g.plan, g.e_cell, g.e_x, g.e_rng, g.uoff, g.grain, g.ctl,
-                                                        g.pass, g.cell_counts, g.item_counts, g.item_base, g.out,
-                                                        g.stats);
+        gj_kernel<NL, S, O, false><<<grid, g.threads, 0, s>>>(g.plan, g.e_cell, g.e_x, g.e_rng, g.uoff, g.grain,
+                                                              g.ctl, g.pass, g.cell_counts, g.item_counts, g.item_base,
+                                                              g.out, g.stats, g.chunk_fill, g.n_chunks);
     HC_CUDA_TRY(launch_check());
     return HC_OK;
 }
 
-hc_status launch_any(int nl, bool mat, const GjArgs& g, cudaStream_t s) {
+template <int NL>
+hc_status launch_nl(int S, int O, bool mat, const GjArgs& g, cudaStream_t s) {
+    if (S <= 2 && O <= 2) return launch_gj<NL, 2, 2>(mat, g, s);
+    if (S <= 2) return launch_gj<NL, 2, 4>(mat, g, s);
+    if (O <= 2) return launch_gj<NL, 4, 2>(mat, g, s);
+    return launch_gj<NL, 4, 4>(mat, g, s);
+}
+
+template <int NL>
+int gj_grid_nl(int S, int O, bool mat, int threads) {
+    if (S <= 2 && O <= 2) return gj_grid<NL, 2, 2>(mat, threads);
+    if (S <= 2) return gj_grid<NL, 2, 4>(mat, threads);
+    if (O <= 2) return gj_grid<NL, 4, 2>(mat, threads);
+    return gj_grid<NL, 4, 4>(mat, threads);
+}
+
+int gj_grid_any(int nl, int S, int O, bool mat, int threads) {
     switch (nl) {
-        case 2: return launch_gj<2>(mat, g, s);
-        case 3: return launch_gj<3>(mat, g, s);
-        case 4: return launch_gj<4>(mat, g, s);
-        case 5: return launch_gj<5>(mat, g, s);
+        case 2: return gj_grid_nl<2>(S, O, mat, threads);
+        case 3: return gj_grid_nl<3>(S, O, mat, threads);
+        case 4: return gj_grid_nl<4>(S, O, mat, threads);
+        default: return gj_grid_nl<5>(S, O, mat, threads);
+    }
+}
+
+hc_status launch_any(int nl, int S, int O, bool mat, const GjArgs& g, cudaStream_t s) {
+    switch (nl) {
+        case 2: return launch_nl<2>(S, O, mat, g, s);
+        case 3: return launch_nl<3>(S, O, mat, g, s);
+        case 4: return launch_nl<4>(S, O, mat, g, s);
+        case 5: return launch_nl<5>(S, O, mat, g, s);
         default: return fail(HC_ERR_CAPACITY, "run_join: queries of 2 to 5 variables are built in");
     }
 }
@@ -639,7 +855,8 @@ struct hc_result {
     hc::JoinCtl h_ctl{};
     std::vector<hc_partitioned*> parts;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    int n_timed = 0;  // search launches bracketed by ev[2i], ev[2i+1]
+    int n_timed = 0;   // search launches bracketed by ev[2i], ev[2i+1]
+    int n_search = 0;  // search launches of this join
 };
 
 namespace hc {
@@ -698,7 +915,7 @@ hc_status result_get(hc_result* R, hc_result_view* v) {
     v->d_cell_counts = R->d_cell_counts;
     v->work = R->h_ctl.work;
     v->n_items = R->n_items;
-    v->n_join_launches = R->materialized ? 2 : 1;
+    v->n_join_launches = (uint32_t)R->n_search;
     float total_ms = 0.f;
     for (int i = 0; i < R->n_timed; ++i) {
         float ms = 0.f;
@@ -753,8 +970,8 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     }
     const uint32_t grain = prm->item_grain ? prm->item_grain : 64;
     const int threads = prm->block_threads ? (int)prm->block_threads : 128;
-    if (threads % 32 != 0 || threads < 32 || threads > 256)
-        return fail(HC_ERR_ARG, "run_join: block_threads must be a multiple of 32 in [32, 256]");
+    if (threads % 32 != 0 || threads < 32 || threads > 128)
+        return fail(HC_ERR_ARG, "run_join: block_threads must be a multiple of 32 in [32, 128]");
 
     hc_result* R = new hc_result();
     R->stream = s;
@@ -826,6 +1043,19 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
             }
         }
     }
+    int shape_s = 2, shape_o = 2;
+    for (int L = 0; L < nv; ++L) {
+        shape_s = std::max(shape_s, P.nsrc[L]);
+        if (L >= 1) shape_o = std::max(shape_o, P.nopen[L]);
+        for (int q = 0; q < P.nsrc[L]; ++q) {
+            const DAtom& a = P.atom[P.src_atom[L][q]];
+            P.src_ec[L][q] = (P.src_top[L][q] || a.lev_first == 0) ? 1 : 0;
+            P.src_f[L][q] = a.lev_first;
+            P.src_slot[L][q] = a.slot;
+        }
+    }
+    P.merge_min = prm->merge_min ? prm->merge_min : 32;
+    P.merge_ratio = prm->merge_ratio ? prm->merge_ratio : 4;
     // loop-1 candidates are bounded by any loop-1 atom's rows times the
     // number of cells that read each of its partitions
     uint64_t cand_bound = UINT64_MAX;
@@ -890,7 +1120,8 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     if ((st = exclusive_scan_u32_to_u64(e_units, uoff, cand_bound, &ctl->n_entries, &ctl->err, s)) != HC_OK)
         return bail(st);
 
-    GjArgs g{d_plan, e_cell, e_x, e_rng, uoff, grain, ctl, 0, R->d_cell_counts, nullptr, nullptr, nullptr, stats, threads};
+    GjArgs g{d_plan, e_cell, e_x,     e_rng,   uoff,    grain,   ctl, 0, R->d_cell_counts,
+             nullptr, nullptr, nullptr, stats, threads, nullptr, 0};
     const bool timed = (prm->flags & HC_FLAG_TIME_KERNELS) != 0;
     if (timed)
         for (auto& e : R->ev)
@@ -898,7 +1129,8 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     // one search launch, bracketed by events when timed
     auto search = [&](bool mat) -> hc_status {
         if (timed && cudaEventRecord(R->ev[2 * R->n_timed], s) != cudaSuccess) return cuda_fail(cudaGetLastError(), "event");
-        HC_TRY(launch_any(nv, mat, g, s));
+        HC_TRY(launch_any(nv, shape_s, shape_o, mat, g, s));
+        R->n_search++;
         if (timed) {
             if (cudaEventRecord(R->ev[2 * R->n_timed + 1], s) != cudaSuccess) return cuda_fail(cudaGetLastError(), "event");
             R->n_timed++;
@@ -922,18 +1154,63 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     if ((st = tmp.get(&item_counts, nitems)) != HC_OK) return bail(st);
     if ((st = tmp.get(&item_base, nitems + 1)) != HC_OK) return bail(st);
     g.item_counts = item_counts;
-    if ((st = search(false)) != HC_OK) return bail(st);
-    if ((st = exclusive_scan_u64(item_counts, item_base, nitems, nullptr, &ctl->err, s)) != HC_OK) return bail(st);
     uint64_t total = 0;
-    if (cudaMemcpyAsync(&total, item_base + nitems, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return bail(cuda_fail(cudaGetLastError(), "read total"));
-    {
+    bool written = false;
+    if (prm->out_capacity > 0) {
+        // single pass into pool chunks; the slack covers every warp's last,
+        // partly filled chunk
+        const uint64_t warps = (uint64_t)gj_grid_any(nv, shape_s, shape_o, true, threads) * (threads / 32);
+        const uint64_t n_chunks64 = (prm->out_capacity + OUT_CHUNK - 1) / OUT_CHUNK + warps;
+        if (n_chunks64 >= 0xFFFFFFFFull) return bail(fail(HC_ERR_CAPACITY, "run_join: out_capacity too large"));
+        const uint32_t n_chunks = (uint32_t)n_chunks64;
+        uint32_t *pool, *chunk_fill;
+        uint64_t* chunk_off;
+        if ((st = tmp.get(&pool, (size_t)n_chunks * OUT_CHUNK * nv)) != HC_OK) return bail(st);
+        if ((st = tmp.get(&chunk_fill, n_chunks)) != HC_OK) return bail(st);
+        if ((st = tmp.get(&chunk_off, (size_t)n_chunks + 1)) != HC_OK) return bail(st);
+        g.out = pool;
+        g.chunk_fill = chunk_fill;
+        g.n_chunks = n_chunks;
+        if ((st = search(true)) != HC_OK) return bail(st);
+        if ((st = read_ctl(R)) != HC_OK) return bail(st);
+        total = R->h_ctl.total;
+        if (!R->h_ctl.overflow) {
+            const uint32_t n_used = std::min<uint32_t>(R->h_ctl.chunk_ctr, n_chunks);
+            if ((st = exclusive_scan_u32_to_u64(chunk_fill, chunk_off, n_used, nullptr, &ctl->err, s)) != HC_OK)
+                return bail(st);
+            void* p;
+            if (dev_alloc(&p, std::max<uint64_t>(total, 1) * nv * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+            R->d_tuples = (uint32_t*)p;
+            if (n_used > 0) {
+                gather_chunks_kernel<<<std::min<uint32_t>(n_used, (uint32_t)num_sms() * 16), 256, 0, s>>>(
+                    pool, chunk_fill, chunk_off, n_used, (uint32_t)nv, R->d_tuples);
+                if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "gather_chunks_kernel"));
+            }
+            written = true;
+        }
+        // on overflow the item counts of the single pass place the tuples of a
+        // second, deterministic emitting pass
+    } else {
+        if ((st = search(false)) != HC_OK) return bail(st);
+    }
+    if (!written) {
+        if ((st = exclusive_scan_u64(item_counts, item_base, nitems, nullptr, &ctl->err, s)) != HC_OK) return bail(st);
+        if (cudaMemcpyAsync(&total, item_base + nitems, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return bail(cuda_fail(cudaGetLastError(), "read total"));
         void* p;
         if (dev_alloc(&p, std::max<uint64_t>(total, 1) * nv * 4, s) != HC_OK) return bail(HC_ERR_OOM);
         R->d_tuples = (uint32_t*)p;
     }
+    if (written) {
+        R->n_tuples = total;
+        R->materialized = true;
+        *out = R;
+        return HC_OK;
+    }
     g.pass = 1;
+    g.chunk_fill = nullptr;
+    g.n_chunks = 0;
     g.item_counts = nullptr;
     g.item_base = item_base;
     g.out = R->d_tuples;

@@ -147,11 +147,12 @@ def test_counts_and_tuples_small_graphs(hc, qname):
         for rel in (sym, datagen.orient_lt(sym)):
             rels = [rel] * len(q.atoms)
             cnt, work, _ = oracle.gj_count(q.n_vars, list(q.atoms), rels)
-            r = _run(hc, q, rels, mode="materialize", stats=True)
-            assert r.count == cnt
-            assert r.work == work
             ref = oracle.gj_enumerate(q.n_vars, list(q.atoms), rels)
-            assert np.array_equal(sorted_rows(u32(r.tuples)), sorted_rows(ref))
+            for mmin, mratio in ((0, 0), (1, 1 << 30), (0xFFFFFFFF, 1)):
+                r = _run(hc, q, rels, mode="materialize", stats=True, merge_min=mmin, merge_ratio=mratio)
+                assert r.count == cnt
+                assert r.work == work
+                assert np.array_equal(sorted_rows(u32(r.tuples)), sorted_rows(ref))
 
 
 @pytest.mark.parametrize("qname", QUERIES)
@@ -197,13 +198,36 @@ def test_variable_orders_four_clique(hc, order):
     assert _run(hc, q, rels, shares=[2, 1, 2, 1]).count == cnt
 
 
-@pytest.mark.parametrize("grain,threads", [(1, 32), (7, 64), (64, 128), (4096, 256), (32, 96)])
+@pytest.mark.parametrize("grain,threads", [(1, 32), (7, 64), (64, 128), (4096, 128), (32, 96)])
 def test_launch_shapes_agree(hc, grain, threads):
     sym = datagen.rmat_graph(11, 8, 5)
     ep = datagen.orient_lt(sym)
     cnt, _, _ = oracle.gj_count(3, list(hc.TRIANGLE.atoms), [ep] * 3)
     r = _run(hc, hc.TRIANGLE, [ep] * 3, item_grain=grain, block_threads=threads, shares=[4, 2, 1])
     assert r.count == cnt
+    # the last loop's two strategies give the same result: never merge, merge
+    # whenever both lists are non-empty, and in between
+    for mmin, mratio in ((0xFFFFFFFF, 1), (1, 1 << 30), (8, 2)):
+        r = _run(hc, hc.TRIANGLE, [ep] * 3, item_grain=grain, block_threads=threads, merge_min=mmin,
+                 merge_ratio=mratio, mode="materialize")
+        assert r.count == cnt
+
+
+@pytest.mark.parametrize("qname", ["TRIANGLE", "FOUR_CYCLE", "FOUR_CLIQUE"])
+def test_single_pass_materialize(hc, qname):
+    """Pool output: enough room (one pass), and far too little (overflow, then
+    the counted items place a second, deterministic pass)."""
+    q = getattr(hc, qname)
+    sym = datagen.rmat_graph(10, 8, 6)
+    rel = datagen.orient_lt(sym) if qname != "FOUR_CYCLE" else sym
+    rels = [rel] * len(q.atoms)
+    ref = oracle.gj_enumerate(q.n_vars, list(q.atoms), rels)
+    for cap in (ref.shape[0] + 1, 10 ** 9, 1):
+        for sh in ([1] * q.n_vars, [2] * q.n_vars):
+            r = _run(hc, q, rels, mode="materialize", out_capacity=cap, shares=sh, cell_counts=True)
+            assert r.count == ref.shape[0]
+            assert np.array_equal(sorted_rows(u32(r.tuples)), sorted_rows(ref)), (cap, sh)
+            assert int(r.cell_counts.sum()) == ref.shape[0]
 
 
 def test_uniform_4096_vertices_32768_edges(hc):
