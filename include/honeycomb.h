@@ -213,6 +213,9 @@ typedef struct {
     uint32_t merge_ratio;         /* ... and within this length ratio are intersected    */
                                   /* by a warp block merge, others by binary search      */
                                   /* (0: defaults 32 and 4; 0xFFFFFFFF: never merge)     */
+    uint32_t slice_grain;         /* 4+ loops: loop-3 candidates per work slice of a     */
+                                  /* loop-2 binding (0: default 256; 0xFFFFFFFF: none)   */
+    uint32_t reserved0;           /* must be 0                                           */
     uint64_t out_capacity;        /* materialize: 0 runs a counting pass, then an        */
                                   /* emitting pass (tuples cell-major, in a fixed order); */
                                   /* > 0 runs one pass writing into an output pool of    */

@@ -267,7 +267,7 @@ def run_join(query: Query, indexes: Sequence[Index], shares: Sequence[int] | Non
              seeds: Sequence[int] | None = None, mode: str = "count", cell_counts: bool = False,
              stats: bool = False, item_grain: int = 0, block_threads: int = 0, stream=None,
              keep_device: bool = False, time_kernels: bool = False, merge_min: int = 0,
-             merge_ratio: int = 0, out_capacity: int = 0) -> Result:
+             merge_ratio: int = 0, out_capacity: int = 0, slice_grain: int = 0) -> Result:
     """Evaluate the query.  Tuples (materialize) come back as an
     (count, n_vars) int32 CUDA tensor in variable-id order (a copy, unless
     ``keep_device`` keeps an alias of library memory tied to the result)."""
@@ -291,6 +291,7 @@ def run_join(query: Query, indexes: Sequence[Index], shares: Sequence[int] | Non
     prm.merge_min = merge_min & 0xFFFFFFFF
     prm.merge_ratio = merge_ratio & 0xFFFFFFFF
     prm.out_capacity = int(out_capacity)
+    prm.slice_grain = slice_grain & 0xFFFFFFFF
     lib = _lib.load()
     out = ctypes.c_void_p()
     _lib.check(lib.hc_run_join(ctypes.byref(q), ptr, ctypes.byref(prm), ctypes.c_void_p(_stream_ptr(stream)),

@@ -59,6 +59,10 @@ struct DPlan {
     // last loop: a parent whose two lists are both >= merge_min long and
     // within merge_ratio of each other takes the block-merge path
     uint32_t merge_min, merge_ratio;
+    // queries of 4+ loops: an entry whose loop-3 lists (those fixed by the
+    // entry) exceed slice_grain is cut into slices of about that many loop-3
+    // candidates per loop-2 candidate (0: no slicing)
+    uint32_t slice_grain;
 };
 
 struct JoinCtl {
@@ -128,7 +132,8 @@ template <bool WRITE>
 __global__ void l0_probe_kernel(const DPlan* __restrict__ gP, const uint64_t* __restrict__ candoff, uint64_t tmax,
                                 uint32_t* __restrict__ flags, const uint64_t* __restrict__ flagoff,
                                 uint32_t* __restrict__ e_cell, uint32_t* __restrict__ e_x,
-                                uint32_t* __restrict__ e_rng, uint32_t* __restrict__ e_units) {
+                                uint32_t* __restrict__ e_rng, uint64_t* __restrict__ e_units,
+                                uint32_t* __restrict__ e_split) {
     __shared__ DPlan P;
     load_plan(P, gP);
     const uint64_t T = min(tmax, candoff[P.ncells]);
@@ -217,7 +222,29 @@ __global__ void l0_probe_kernel(const DPlan* __restrict__ gP, const uint64_t* __
                 m = min(m, len);
             }
         }
-        e_units[e] = m;
+        // work units of the entry: loop-2 candidates, each cut into slices of
+        // its loop-3 candidates when the entry fixes a long loop-3 list
+        uint32_t split = 1;
+        if (P.nlev >= 4 && P.slice_grain > 0) {
+            uint32_t w = 0xFFFFFFFFu;
+            for (int q = 0; q < P.nsrc[2]; ++q) {
+                const DAtom& a = P.atom[P.src_atom[2][q]];
+                uint32_t len = 0xFFFFFFFFu;
+                if (P.src_top[2][q]) {
+                    uint32_t l0, l1;
+                    top_range(a, c, l0, l1);
+                    len = l1 - l0;
+                } else if (a.lev_first == 0) {
+#pragma unroll
+                    for (int s = 0; s < MAXOPEN; ++s)
+                        if (s == a.slot) len = rhi[s] - rlo[s];
+                }
+                w = min(w, len);
+            }
+            if (w != 0xFFFFFFFFu) split = max(1u, (w + P.slice_grain - 1) / P.slice_grain);
+        }
+        e_units[e] = (uint64_t)m * split;
+        e_split[e] = split;
     }
 }
 
@@ -238,9 +265,11 @@ __global__ void entries_total_kernel(const uint64_t* __restrict__ flagoff, const
 template <int NL, int S>
 struct Entry {
     uint32_t cell, x;
-    uint32_t lo[NL][S], hi[NL][S];
+    uint32_t (*lo)[S];  // [NL][S] in the warp's shared memory (lane-uniform)
+    uint32_t (*hi)[S];
     uint32_t k0, k1;      // the work item's subrange of loop 1's shortest list
     uint32_t best1, len1;  // that list (source index) and its full length
+    uint32_t j0, j1, ns;   // slices [j0, j1) of ns of the loop-2 binding's loop-3 candidates
 };
 
 // Batch bindings of loops 1..NL-2 (index = loop), one per lane.
@@ -446,57 +475,32 @@ __device__ __forceinline__ void merge_pair(const DPlan& P, const Entry<NL, S>& E
         i1 = j1 < b1 ? lower_bound_u32(la, i, a1, lb[j1]) : a1;
     }
     uint32_t j = j0;
+    // branch-free merge step: both heads are compared, the equal pair is
+    // counted, and each side advances when its head is not the larger one
     if constexpr (!MAT) {
         uint32_t cnt = 0;
-        if (i < i1 && j < j1) {
-            uint32_t x = la[i], y = lb[j];
-            for (;;) {
-                if (x < y) {
-                    if (++i >= i1) break;
-                    x = la[i];
-                } else if (y < x) {
-                    if (++j >= j1) break;
-                    y = lb[j];
-                } else {
-                    ++cnt;
-                    if (++i >= i1 || ++j >= j1) break;
-                    x = la[i];
-                    y = lb[j];
-                }
-            }
+        while (i < i1 && j < j1) {
+            const uint32_t x = la[i], y = lb[j];
+            cnt += x == y ? 1u : 0u;
+            i += x <= y ? 1u : 0u;
+            j += y <= x ? 1u : 0u;
         }
         A.count += __reduce_add_sync(0xffffffffu, cnt);
     } else {
-        bool live = i < i1 && j < j1;
-        uint32_t x = live ? la[i] : 0, y = live ? lb[j] : 0;
-        while (__any_sync(0xffffffffu, live)) {
-            bool m = false;
-            uint32_t mv = 0;
+        for (;;) {
+            const bool live = i < i1 && j < j1;
+            if (!__any_sync(0xffffffffu, live)) break;
+            uint32_t x = 0, y = 1;
             if (live) {
-                if (x < y) {
-                    if (++i >= i1)
-                        live = false;
-                    else
-                        x = la[i];
-                } else if (y < x) {
-                    if (++j >= j1)
-                        live = false;
-                    else
-                        y = lb[j];
-                } else {
-                    m = true;
-                    mv = x;
-                    if (++i >= i1 || ++j >= j1) {
-                        live = false;
-                    } else {
-                        x = la[i];
-                        y = lb[j];
-                    }
-                }
+                x = la[i];
+                y = lb[j];
+                i += x <= y ? 1u : 0u;
+                j += y <= x ? 1u : 0u;
             }
+            const bool m = live && x == y;
             const uint32_t ball = __ballot_sync(0xffffffffu, m);
             const uint64_t slot = out_reserve(A, ball);
-            if (m && slot != ~0ull) write_tuple<L, NL>(P, A.out + slot * (uint64_t)P.nv, E.x, vals, mv);
+            if (m && slot != ~0ull) write_tuple<L, NL>(P, A.out + slot * (uint64_t)P.nv, E.x, vals, x);
             A.count += __popc(ball);
         }
     }
@@ -558,6 +562,18 @@ __device__ __forceinline__ void run_level(const DPlan& P, Frame<NL, O>& F, const
                     mhi[q] = base + E.k1;
                 }
         }
+        if constexpr (L == 2 && NL >= 4) {
+            // a sliced work unit: one loop-2 binding (lane 0), slices [j0, j1)
+            if (E.ns > 1 && lane == 0 && nb == 1) {
+#pragma unroll
+                for (int q = 0; q < S; ++q)
+                    if (q == (int)best) {
+                        const uint32_t base = mlo[q];
+                        mlo[q] = base + (uint32_t)(((uint64_t)bestlen * E.j0) / E.ns);
+                        mhi[q] = base + (uint32_t)(((uint64_t)bestlen * E.j1) / E.ns);
+                    }
+            }
+        }
         bool merge_class = false;
         if constexpr (L == NL - 1 && S >= 2) {
             if (ns == 2 && lane < nb) {
@@ -566,13 +582,20 @@ __device__ __forceinline__ void run_level(const DPlan& P, Frame<NL, O>& F, const
                 merge_class = mn >= P.merge_min && (uint64_t)mx <= (uint64_t)P.merge_ratio * mn;
             }
         }
-        const uint32_t cnt = (lane < nb && !merge_class) ? bestlen : 0;
         if (A.stats && lane < nb) {
-            if (L > 1)
-                A.work += (uint64_t)ns * bestlen;
-            else if (E.k0 == 0)
+            if (L > 2 || (L == 2 && E.j0 == 0))
+                A.work += (uint64_t)ns * bestlen;  // once per binding, before slicing
+            else if (L == 1 && E.k0 == 0 && E.j0 == 0)
                 A.work += (uint64_t)ns * E.len1;  // once per loop-1 binding
         }
+        if constexpr (L == 2 && NL >= 4) {
+            if (E.ns > 1 && lane == 0 && nb == 1) {
+#pragma unroll
+                for (int q = 0; q < S; ++q)
+                    if (q == (int)best) bestlen = mhi[q] - mlo[q];
+            }
+        }
+        const uint32_t cnt = (lane < nb && !merge_class) ? bestlen : 0;
         const uint32_t incl = warp_incl_scan(cnt);
         const uint32_t excl = incl - cnt;
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
@@ -632,15 +655,17 @@ __device__ __forceinline__ void run_level(const DPlan& P, Frame<NL, O>& F, const
 // pass 0 counts (and, with item_counts, records each item's count); pass 1
 // writes tuples at item_base[item].
 template <int NL, int S, int O, bool MAT>
-__global__ void __launch_bounds__(128, 8) gj_kernel(const DPlan* __restrict__ gP, const uint32_t* __restrict__ e_cell,
+__global__ void __launch_bounds__(128, (NL <= 3 ? 8 : 6)) gj_kernel(const DPlan* __restrict__ gP, const uint32_t* __restrict__ e_cell,
                                                     const uint32_t* __restrict__ e_x,
                                                     const uint32_t* __restrict__ e_rng,
+                                                    const uint32_t* __restrict__ e_split,
                                                     const uint64_t* __restrict__ uoff, uint32_t grain, JoinCtl* ctl,
                                                     int pass, uint64_t* __restrict__ cell_counts,
                                                     uint64_t* __restrict__ item_counts,
                                                     const uint64_t* __restrict__ item_base, uint32_t* __restrict__ out,
                                                     int stats, uint32_t* __restrict__ chunk_fill, uint32_t n_chunks) {
     __shared__ DPlan P;
+    __shared__ uint32_t s_elo[4][NL][S], s_ehi[4][NL][S];  // per warp (blocks of <= 128 threads)
     load_plan(P, gP);
     const uint32_t lane = lane_id();
     const uint32_t E_n = ctl->n_entries;
@@ -684,9 +709,11 @@ __global__ void __launch_bounds__(128, 8) gj_kernel(const DPlan* __restrict__ gP
                 ++e;
                 continue;
             }
-            const uint32_t k0 = (uint32_t)(u0 - eb);
-            const uint32_t k1 = (uint32_t)(min(u1, ee) - eb);
+            const uint64_t ku0 = u0 - eb, ku1 = min(u1, ee) - eb;
             Entry<NL, S> E;
+            E.lo = s_elo[threadIdx.x >> 5];
+            E.hi = s_ehi[threadIdx.x >> 5];
+            __syncwarp();  // the previous entry's ranges are no longer read
             E.cell = e_cell[e];
             E.x = e_x[e];
             uint32_t r0lo[MAXOPEN], r0hi[MAXOPEN];
@@ -695,45 +722,65 @@ __global__ void __launch_bounds__(128, 8) gj_kernel(const DPlan* __restrict__ gP
                 r0lo[s] = s < P.nopen[0] ? e_rng[(uint64_t)e * (2 * MAXOPEN) + 2 * s] : 0;
                 r0hi[s] = s < P.nopen[0] ? e_rng[(uint64_t)e * (2 * MAXOPEN) + 2 * s + 1] : 0;
             }
+            uint32_t best1 = 0, len1 = 0xFFFFFFFFu;
 #pragma unroll
             for (int L = 1; L < NL; ++L)
 #pragma unroll
                 for (int q = 0; q < S; ++q) {
-                    E.lo[L][q] = E.hi[L][q] = 0;
+                    uint32_t lo = 0, hi = 0;
                     if (q < P.nsrc[L] && P.src_ec[L][q]) {
                         const DAtom& a = P.atom[P.src_atom[L][q]];
                         if (P.src_top[L][q]) {
-                            top_range(a, E.cell, E.lo[L][q], E.hi[L][q]);
+                            top_range(a, E.cell, lo, hi);
                         } else {
 #pragma unroll
                             for (int s = 0; s < MAXOPEN; ++s)
                                 if (s == a.slot) {
-                                    E.lo[L][q] = r0lo[s];
-                                    E.hi[L][q] = r0hi[s];
+                                    lo = r0lo[s];
+                                    hi = r0hi[s];
                                 }
                         }
                     }
-                }
-            {
-                uint32_t best = 0, bestlen = 0xFFFFFFFFu;
-#pragma unroll
-                for (int q = 0; q < S; ++q)
-                    if (q < P.nsrc[1] && E.hi[1][q] - E.lo[1][q] < bestlen) {
-                        bestlen = E.hi[1][q] - E.lo[1][q];
-                        best = q;
+                    if (L == 1 && q < P.nsrc[1] && hi - lo < len1) {
+                        len1 = hi - lo;
+                        best1 = q;
                     }
-                E.k0 = k0;
-                E.k1 = k1;
-                E.best1 = best;
-                E.len1 = bestlen;
-            }
+                    if (lane == 0) {
+                        E.lo[L][q] = lo;
+                        E.hi[L][q] = hi;
+                    }
+                }
+            __syncwarp();
+            E.best1 = best1;
+            E.len1 = len1;
             const uint64_t before = A.count;
-            run_level<1, NL, S, O, MAT>(P, F, E, A, 1);
+            const uint32_t split = e_split[e];
+            // units are (loop-2 candidate k, slice j) pairs, k-major; an
+            // unsliced entry (split 1) is one call over its candidate range
+            for (uint64_t u = ku0; u < ku1;) {
+                if (split == 1) {
+                    E.k0 = (uint32_t)u;
+                    E.k1 = (uint32_t)ku1;
+                    E.j0 = 0;
+                    E.j1 = 1;
+                    u = ku1;
+                } else {
+                    const uint32_t j0 = (uint32_t)(u % split);
+                    const uint64_t jend = j0 + (ku1 - u);
+                    E.k0 = (uint32_t)(u / split);
+                    E.k1 = E.k0 + 1;
+                    E.j0 = j0;
+                    E.j1 = jend < split ? (uint32_t)jend : split;
+                    u += E.j1 - j0;
+                }
+                E.ns = split;
+                run_level<1, NL, S, O, MAT>(P, F, E, A, 1);
+            }
             const uint64_t got = A.count - before;
             if (pass == 0 && cell_counts && got && lane == 0)
                 atomicAdd((unsigned long long*)&cell_counts[E.cell], (unsigned long long)got);
             item_count += got;
-            u0 = eb + k1;
+            u0 = eb + ku1;
             ++e;
         }
         if (pass == 0 && item_counts && lane == 0) item_counts[item] = item_count;
@@ -773,7 +820,7 @@ int gj_grid(bool mat, int threads) {
 
 struct GjArgs {
     const DPlan* plan;
-    const uint32_t *e_cell, *e_x, *e_rng;
+    const uint32_t *e_cell, *e_x, *e_rng, *e_split;
     const uint64_t* uoff;
     uint32_t grain;
     JoinCtl* ctl;
@@ -792,11 +839,13 @@ template <int NL, int S, int O>
 hc_status launch_gj(bool mat, const GjArgs& g, cudaStream_t s) {
     const int grid = gj_grid<NL, S, O>(mat, g.threads);
     if (mat)
-        gj_kernel<NL, S, O, true><<<grid, g.threads, 0, s>>>(g.plan, g.e_cell, g.e_x, g.e_rng, g.uoff, g.grain, g.ctl,
+        gj_kernel<NL, S, O, true><<<grid, g.threads, 0, s>>>(g.plan, g.e_cell, g.e_x, g.e_rng, g.e_split, g.uoff,
+                                                             g.grain, g.ctl,
                                                              g.pass, g.cell_counts, g.item_counts, g.item_base, g.out,
                                                              g.stats, g.chunk_fill, g.n_chunks);
     else
-        gj_kernel<NL, S, O, false><<<grid, g.threads, 0, s>>>(g.plan, g.e_cell, g.e_x, g.e_rng, g.uoff, g.grain,
+        gj_kernel<NL, S, O, false><<<grid, g.threads, 0, s>>>(g.plan, g.e_cell, g.e_x, g.e_rng, g.e_split, g.uoff,
+                                                              g.grain,
                                                               g.ctl, g.pass, g.cell_counts, g.item_counts, g.item_base,
                                                               g.out, g.stats, g.chunk_fill, g.n_chunks);
     HC_CUDA_TRY(launch_check());
@@ -1056,6 +1105,7 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     }
     P.merge_min = prm->merge_min ? prm->merge_min : 32;
     P.merge_ratio = prm->merge_ratio ? prm->merge_ratio : 4;
+    P.slice_grain = prm->slice_grain == 0xFFFFFFFFu ? 0 : (prm->slice_grain ? prm->slice_grain : 256);
     // loop-1 candidates are bounded by any loop-1 atom's rows times the
     // number of cells that read each of its partitions
     uint64_t cand_bound = UINT64_MAX;
@@ -1086,8 +1136,8 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
 
     Scratch tmp(s);
     DPlan* d_plan;
-    uint32_t *cand, *flags, *e_cell, *e_x, *e_rng, *e_units;
-    uint64_t *candoff, *flagoff, *uoff;
+    uint32_t *cand, *flags, *e_cell, *e_x, *e_rng, *e_split;
+    uint64_t *candoff, *flagoff, *uoff, *e_units;
     hc_status st;
     if ((st = tmp.get(&d_plan, 1)) != HC_OK) return bail(st);
     if (cudaMemcpyAsync(d_plan, &P, sizeof(DPlan), cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -1100,6 +1150,7 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     if ((st = tmp.get(&e_x, cand_bound)) != HC_OK) return bail(st);
     if ((st = tmp.get(&e_rng, cand_bound * 2 * MAXOPEN)) != HC_OK) return bail(st);
     if ((st = tmp.get(&e_units, cand_bound)) != HC_OK) return bail(st);
+    if ((st = tmp.get(&e_split, cand_bound)) != HC_OK) return bail(st);
     if ((st = tmp.get(&uoff, cand_bound + 1)) != HC_OK) return bail(st);
 
     const int tpb = 256;
@@ -1110,17 +1161,18 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     const unsigned pgrid =
         (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((cand_bound + tpb - 1) / tpb, (uint64_t)num_sms() * 16));
     l0_probe_kernel<false><<<pgrid, tpb, 0, s>>>(d_plan, candoff, cand_bound, flags, nullptr, nullptr, nullptr, nullptr,
-                                                 nullptr);
+                                                 nullptr, nullptr);
     if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "l0_probe_kernel"));
     if ((st = exclusive_scan_u32_to_u64(flags, flagoff, cand_bound, nullptr, &ctl->err, s)) != HC_OK) return bail(st);
-    l0_probe_kernel<true><<<pgrid, tpb, 0, s>>>(d_plan, candoff, cand_bound, flags, flagoff, e_cell, e_x, e_rng, e_units);
+    l0_probe_kernel<true><<<pgrid, tpb, 0, s>>>(d_plan, candoff, cand_bound, flags, flagoff, e_cell, e_x, e_rng, e_units,
+                                                e_split);
     if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "l0_probe_kernel"));
     entries_total_kernel<<<1, 1, 0, s>>>(flagoff, candoff, (uint32_t)ncells, cand_bound, ctl);
     if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "entries_total_kernel"));
-    if ((st = exclusive_scan_u32_to_u64(e_units, uoff, cand_bound, &ctl->n_entries, &ctl->err, s)) != HC_OK)
+    if ((st = exclusive_scan_u64(e_units, uoff, cand_bound, &ctl->n_entries, &ctl->err, s)) != HC_OK)
         return bail(st);
 
-    GjArgs g{d_plan, e_cell, e_x,     e_rng,   uoff,    grain,   ctl, 0, R->d_cell_counts,
+    GjArgs g{d_plan,  e_cell,  e_x,     e_rng, e_split, uoff,    grain,   ctl, 0, R->d_cell_counts,
              nullptr, nullptr, nullptr, stats, threads, nullptr, 0};
     const bool timed = (prm->flags & HC_FLAG_TIME_KERNELS) != 0;
     if (timed)
