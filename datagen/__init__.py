@@ -265,6 +265,37 @@ def induced_subgraph(pairs: np.ndarray, n_vertices: int, seed_q: int, target_edg
     return np.ascontiguousarray(pairs[sel]), f
 
 
+MERSENNE31 = (1 << 31) - 1
+
+
+def vertex_keys(n_vertices: int, seed_q: int) -> np.ndarray:
+    """Seeded vertex keys k(v) = (A v + B) mod (2^31 - 1), A, B from the seed.
+
+    Exact in int64 for v < 2^31 (A v < 2^62), so numpy and torch agree.
+    """
+    r = _rng(seed_q)
+    a = int(r.integers(1, MERSENNE31))
+    b = int(r.integers(0, MERSENNE31))
+    v = np.arange(n_vertices, dtype=np.int64)
+    return (v * a + b) % MERSENNE31
+
+
+def induced_by_key(pairs: np.ndarray, n_vertices: int, seed_q: int, target_edges: int) -> np.ndarray:
+    """Induced subgraph on {v : k(v) < t} with t chosen for ~target_edges.
+
+    An edge survives iff max(k(u), k(v)) < t, so t is the target-th smallest
+    edge key plus one: exactly target_edges edges (fewer if the graph has
+    fewer).  Returns the surviving pairs in input order.
+    """
+    k = vertex_keys(n_vertices, seed_q)
+    ek = np.maximum(k[pairs[:, 0]], k[pairs[:, 1]])
+    m = pairs.shape[0]
+    if target_edges >= m:
+        return np.ascontiguousarray(pairs)
+    t = np.partition(ek, target_edges - 1)[target_edges - 1] + 1
+    return np.ascontiguousarray(pairs[ek < t])
+
+
 def complete_graph(n: int) -> np.ndarray:
     """All pairs (u, v), u != v, of K_n (symmetric)."""
     u, v = np.meshgrid(np.arange(n, dtype=np.uint32), np.arange(n, dtype=np.uint32), indexing="ij")

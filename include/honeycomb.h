@@ -49,8 +49,13 @@ typedef enum {
 #define HC_MAX_VARS 8
 #define HC_MAX_ATOMS 8
 
-/* One binary atom R_j(X_var0, X_var1): column 0 of its relation holds the
- * values of variable var0, column 1 those of var1 (var0 != var1). */
+/* One atom R_j(X_var0, X_var1): column 0 of its relation holds the values
+ * of variable var0, column 1 those of var1 (var0 != var1).  With var1 =
+ * HC_UNARY the atom is unary, R_j(X_var0): the set of column-0 values of its
+ * relation (an index with attr_order 0; column 1 is ignored).  Unary atoms
+ * express a selection pushed into the query (Sec. 2), e.g. restricting a
+ * variable to a vertex subset. */
+#define HC_UNARY 0xFFu
 typedef struct {
     uint8_t var0;
     uint8_t var1;
@@ -257,6 +262,30 @@ typedef struct {
 /* Waits for the result's stream, then fills `out`. */
 hc_status hc_result_get(hc_result* r, hc_result_view* out);
 hc_status hc_result_free(hc_result* r);
+
+/* ---------------------------------------------------------------- batches
+ * Many count-mode joins in one persistent search launch (the paper's
+ * scheduler runs its P logical workers by work stealing, Sec. 3
+ * "Allocator"; here the work items of all queries form one space handed out
+ * by one atomic counter, so warps move on to whichever query still has work).
+ *   qs[n], prm[n]  the queries and their parameters (mode must be COUNT);
+ *   idx_flat       the indexes of query 0's atoms, then query 1's, ...;
+ *   n              1..65536 queries of 3 or 4 variables, of at most two
+ *                  shapes (lists and atoms per loop) per batch.
+ * hc_batch_create plans every query, partitions atoms whose shares need it
+ * and allocates the batch's device memory (waits for the GPU once).
+ * hc_batch_launch enqueues the loop-1 passes of all queries and the one
+ * search launch, without waiting.  hc_batch_capture records that work once
+ * as a CUDA graph on `stream` (a created, non-default stream); later
+ * hc_batch_launch calls replay the graph.  hc_batch_counts waits for the
+ * last launch and writes counts[n].  The indexes must outlive the batch. */
+typedef struct hc_batch hc_batch;
+hc_status hc_batch_create(const hc_query* qs, const hc_index* const* idx_flat, const hc_join_params* prm, uint32_t n,
+                          void* stream, hc_batch** out);
+hc_status hc_batch_launch(hc_batch* b, void* stream);
+hc_status hc_batch_capture(hc_batch* b, void* stream);
+hc_status hc_batch_counts(hc_batch* b, uint64_t* counts);
+hc_status hc_batch_free(hc_batch* b);
 
 /* -------------------------------------------------------------- utilities */
 const char* hc_status_str(hc_status s);

@@ -21,8 +21,8 @@ the passages they follow:
 
 A query is ``(n_vars, atoms)`` with ``atoms`` a list of ``(var0, var1)``:
 the relation bound to atom j holds pairs whose column 0 is variable var0
-and column 1 is variable var1.  Output tuples list values in variable-id
-order.
+and column 1 is variable var1; ``var1 = -1`` makes a unary atom over column
+0 (the set of its values).  Output tuples list values in variable-id order.
 """
 from __future__ import annotations
 

@@ -48,7 +48,7 @@
 #include <string.h>
 
 #define OC_MAXV 8
-#define OC_MAXA 8
+#define OC_MAXA 16
 
 enum { OC_OK = 0, OC_EARG = 1, OC_ENOMEM = 2, OC_ECAP = 3 };
 
@@ -374,16 +374,18 @@ static int plan_build(int nv, int na, const uint32_t *const *pairs, const uint64
     }
     int covered[OC_MAXV] = {0};
     for (int j = 0; j < na; ++j) {
-        if (var0[j] < 0 || var0[j] >= nv || var1[j] < 0 || var1[j] >= nv || var0[j] == var1[j])
+        /* var1 = -1: a unary atom R_j(X_var0) over column 0 of its relation */
+        if (var0[j] < 0 || var0[j] >= nv || var1[j] < -1 || var1[j] >= nv || var0[j] == var1[j])
             return OC_EARG;
-        covered[var0[j]] = covered[var1[j]] = 1;
+        covered[var0[j]] = 1;
+        if (var1[j] >= 0) covered[var1[j]] = 1;
     }
     for (int v = 0; v < nv; ++v)
         if (!covered[v]) return OC_EARG; /* every variable occurs in some atom */
     for (int j = 0; j < na; ++j) {
-        int swap = p->rank[var1[j]] < p->rank[var0[j]];
+        int swap = var1[j] >= 0 && p->rank[var1[j]] < p->rank[var0[j]];
         p->first[j] = swap ? var1[j] : var0[j];
-        p->second[j] = swap ? var0[j] : var1[j];
+        p->second[j] = var1[j] < 0 ? -1 : (swap ? var0[j] : var1[j]);
         int rc = build_trie(pairs[j], n[j], swap, &p->trie[j]);
         if (rc) return rc;
     }

@@ -22,7 +22,7 @@ from ._lib import HoneycombError
 
 __all__ = ["Query", "Index", "Partitioned", "Result", "build_index", "choose_shares", "run_join",
            "partition_index", "plan_cost", "HoneycombError", "TRIANGLE", "FOUR_CYCLE", "FOUR_DIAMOND", "FOUR_CLIQUE",
-           "TWO_TRIANGLE", "library_path", "kernel_launches"]
+           "TWO_TRIANGLE", "library_path", "kernel_launches", "Batch"]
 
 
 def library_path() -> str:
@@ -67,8 +67,9 @@ class Query:
     """Full conjunctive query of binary atoms (Eq. "full:cq").
 
     ``atoms[j] = (var0, var1)``: column 0 of atom j's relation holds variable
-    var0, column 1 variable var1.  ``order`` is the Generic Join loop order
-    (default: variables 0, 1, ...).
+    var0, column 1 variable var1; ``var1 = None`` (or -1) makes a unary atom
+    over column 0.  ``order`` is the Generic Join loop order (default:
+    variables 0, 1, ...).
     """
     n_vars: int
     atoms: tuple
@@ -84,7 +85,12 @@ class Query:
         """Attribute order an index needs for atom j under the loop order."""
         rank = {v: i for i, v in enumerate(self.loop_order())}
         a, b = self.atoms[j]
+        if b is None or b < 0:
+            return 0
         return 0 if rank[a] < rank[b] else 1
+
+    def with_atoms(self, extra) -> "Query":
+        return Query(self.n_vars, tuple(self.atoms) + tuple(extra), self.order)
 
     def _c(self) -> _lib.hc_query:
         q = _lib.hc_query()
@@ -92,7 +98,7 @@ class Query:
         q.n_atoms = len(self.atoms)
         for j, (a, b) in enumerate(self.atoms):
             q.atoms[j].var0 = a
-            q.atoms[j].var1 = b
+            q.atoms[j].var1 = 0xFF if (b is None or b < 0) else b
         for i, v in enumerate(self.loop_order()):
             q.order[i] = v
         return q
@@ -318,6 +324,77 @@ def run_join(query: Query, indexes: Sequence[Index], shares: Sequence[int] | Non
     except Exception:
         lib.hc_result_free(ctypes.c_void_p(h))
         raise
+
+
+def _params(query: Query, shares=None, seeds=None, item_grain=0, block_threads=0, merge_min=0, merge_ratio=0,
+            slice_grain=0, mode="count", flags=0, out_capacity=0) -> _lib.hc_join_params:
+    prm = _lib.hc_join_params()
+    sh = list(shares) if shares is not None else [1] * query.n_vars
+    sd = list(seeds) if seeds is not None else list(DEFAULT_SEEDS)
+    for v in range(_lib.HC_MAX_VARS):
+        prm.shares[v] = sh[v] if v < len(sh) else 1
+        prm.seeds[v] = (sd[v] if v < len(sd) else DEFAULT_SEEDS[v]) & 0xFFFFFFFF
+    prm.mode = _lib.HC_MODE_COUNT if mode == "count" else _lib.HC_MODE_MATERIALIZE
+    prm.flags = flags
+    prm.item_grain = item_grain
+    prm.block_threads = block_threads
+    prm.merge_min = merge_min & 0xFFFFFFFF
+    prm.merge_ratio = merge_ratio & 0xFFFFFFFF
+    prm.slice_grain = slice_grain & 0xFFFFFFFF
+    prm.out_capacity = int(out_capacity)
+    return prm
+
+
+class Batch:
+    """Many count-mode joins in one persistent search launch.
+
+    ``queries[i]`` runs over ``indexes[i]`` (one index per atom) with the
+    keyword options ``options[i]`` (shares, seeds, item_grain, merge_min,
+    merge_ratio, slice_grain).  ``launch`` enqueues the batch; after
+    ``capture(stream)`` launches replay a CUDA graph.  ``counts`` waits.
+    """
+
+    def __init__(self, queries, indexes, options=None, stream=None):
+        n = len(queries)
+        if n == 0 or len(indexes) != n:
+            raise ValueError("one index list per query")
+        options = options or [{}] * n
+        self._keep = list(indexes)
+        qarr = (_lib.hc_query * n)(*[q._c() for q in queries])
+        flat = [ix.handle.value for lst in indexes for ix in lst]
+        for q, lst in zip(queries, indexes):
+            if len(lst) != len(q.atoms):
+                raise ValueError("one index per atom")
+        iarr = (ctypes.c_void_p * len(flat))(*flat)
+        parr = (_lib.hc_join_params * n)(*[_params(q, **o) for q, o in zip(queries, options)])
+        out = ctypes.c_void_p()
+        _lib.check(_lib.load().hc_batch_create(qarr, ctypes.cast(iarr, ctypes.POINTER(ctypes.c_void_p)), parr, n,
+                                               ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(out)),
+                   "hc_batch_create")
+        self._h = out
+        self.n = n
+
+    def launch(self, stream=None) -> None:
+        _lib.check(_lib.load().hc_batch_launch(self._h, ctypes.c_void_p(_stream_ptr(stream))), "hc_batch_launch")
+
+    def capture(self, stream) -> None:
+        _lib.check(_lib.load().hc_batch_capture(self._h, ctypes.c_void_p(_stream_ptr(stream))), "hc_batch_capture")
+
+    def counts(self) -> list[int]:
+        out = (ctypes.c_uint64 * self.n)()
+        _lib.check(_lib.load().hc_batch_counts(self._h, out), "hc_batch_counts")
+        return [int(x) for x in out]
+
+    def free(self) -> None:
+        if self._h is not None:
+            _lib.load().hc_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 class _ResultHandle:

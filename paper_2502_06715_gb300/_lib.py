@@ -85,6 +85,13 @@ SIGNATURES = {
                                    ctypes.POINTER(ctypes.c_void_p)]),
     "hc_result_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hc_result_view)]),
     "hc_result_free": (ctypes.c_int, [ctypes.c_void_p]),
+    "hc_batch_create": (ctypes.c_int, [ctypes.POINTER(hc_query), ctypes.POINTER(ctypes.c_void_p),
+                                       ctypes.POINTER(hc_join_params), ctypes.c_uint32, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "hc_batch_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hc_batch_capture": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hc_batch_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "hc_batch_free": (ctypes.c_int, [ctypes.c_void_p]),
     "hc_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "hc_last_error": (ctypes.c_char_p, []),
     "hc_version": (ctypes.c_uint32, []),

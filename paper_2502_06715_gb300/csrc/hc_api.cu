@@ -96,9 +96,10 @@ static void level_costs(const hc_query* q, const int* rank, const AtomStat* st, 
         for (int j = 0; j < na; ++j) {
             int a = q->atoms[j].var0, b = q->atoms[j].var1;
             if (a != v && b != v) continue;
+            const bool unary = b == (int)HC_UNARY;
             const int other = a == v ? b : a;
-            const bool top = rank[other] > i;  // v is the atom's first variable in loop order
-            const int first = rank[a] < rank[b] ? a : b;
+            const bool top = unary || rank[other] > i;  // v is the atom's first variable in loop order
+            const int first = (unary || rank[a] < rank[b]) ? a : b;
             const double fd = first == a ? st[j].col0_distinct : st[j].col1_distinct;
             const double len = top ? fd : st[j].rows / std::max(1.0, fd);
             smin = std::min(smin, len);
@@ -136,7 +137,8 @@ static hc_status plan_inputs(const hc_query* q, const hc_index* const* idx, int*
     for (int j = 0; j < na; ++j) {
         if (!idx[j]) return fail(HC_ERR_ARG, "plan: missing index");
         int a = q->atoms[j].var0, b = q->atoms[j].var1;
-        if (a >= nv || b >= nv || a == b) return fail(HC_ERR_ARG, "plan: bad atom");
+        const bool unary = b == (int)HC_UNARY;
+        if (a >= nv || (b >= nv && !unary) || a == b) return fail(HC_ERR_ARG, "plan: bad atom");
         const hc_index* ix = idx[j];
         // the index knows the distinct count of its own first attribute; the
         // other attribute's is bounded by its largest value + 1 and by the rows
@@ -148,7 +150,7 @@ static hc_status plan_inputs(const hc_query* q, const hc_index* const* idx, int*
         st[j].col0_distinct = d_col0;
         st[j].col1_distinct = d_col1;
         dom[a] = std::min(dom[a], d_col0);
-        dom[b] = std::min(dom[b], d_col1);
+        if (!unary) dom[b] = std::min(dom[b], d_col1);
     }
     for (int v = 0; v < nv; ++v)
         if (!(dom[v] < INFINITY)) return fail(HC_ERR_ARG, "plan: a variable occurs in no atom");
@@ -334,6 +336,18 @@ hc_status hc_run_join(const hc_query* q, const hc_index* const* idx, const hc_jo
 }
 
 hc_status hc_result_get(hc_result* r, hc_result_view* out) { return hc::result_get(r, out); }
+
+hc_status hc_batch_create(const hc_query* qs, const hc_index* const* idx_flat, const hc_join_params* prm, uint32_t n,
+                          void* stream, hc_batch** out) {
+    return hc::batch_create(qs, idx_flat, prm, n, (cudaStream_t)stream, out);
+}
+hc_status hc_batch_launch(hc_batch* b, void* stream) { return hc::batch_launch(b, (cudaStream_t)stream); }
+hc_status hc_batch_capture(hc_batch* b, void* stream) { return hc::batch_capture(b, (cudaStream_t)stream); }
+hc_status hc_batch_counts(hc_batch* b, uint64_t* counts) { return hc::batch_counts(b, counts); }
+hc_status hc_batch_free(hc_batch* b) {
+    hc::batch_release(b);
+    return HC_OK;
+}
 
 hc_status hc_result_free(hc_result* r) {
     hc::result_release(r);

@@ -650,10 +650,118 @@ __device__ __forceinline__ void run_level(const DPlan& P, Frame<NL, O>& F, const
     }
 }
 
-// Persistent search kernel.  Work item i covers loop-2 candidates
-// [i*grain, (i+1)*grain) of the concatenation of all entries' candidates.
-// pass 0 counts (and, with item_counts, records each item's count); pass 1
-// writes tuples at item_base[item].
+// One work item: units [item*grain, (item+1)*grain) of the concatenation of
+// all entries' units (a unit is a loop-2 candidate, or a slice of one for
+// deep queries).  Returns the item's count; cell counts are added when
+// requested.  elo/ehi are the warp's shared-memory rows for entry ranges.
+template <int NL, int S, int O, bool MAT>
+__device__ __forceinline__ uint64_t search_item(const DPlan& P, Frame<NL, O>& F, Acc& A, uint32_t (*elo)[S],
+                                                uint32_t (*ehi)[S], uint64_t item, uint32_t grain, uint32_t E_n,
+                                                uint64_t U, const uint32_t* __restrict__ e_cell,
+                                                const uint32_t* __restrict__ e_x, const uint32_t* __restrict__ e_rng,
+                                                const uint32_t* __restrict__ e_split,
+                                                const uint64_t* __restrict__ uoff, uint64_t* __restrict__ cell_counts,
+                                                int pass) {
+    const uint32_t lane = lane_id();
+    uint64_t u0 = item * grain;
+    const uint64_t u1 = min(U, u0 + grain);
+    uint32_t lo = 0, hi = E_n;  // last entry e with uoff[e] <= u0
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (uoff[mid] <= u0)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    uint32_t e = lo;
+    uint64_t item_count = 0;
+    while (u0 < u1 && e < E_n) {
+        const uint64_t eb = uoff[e], ee = uoff[e + 1];
+        if (ee <= u0) {
+            ++e;
+            continue;
+        }
+        const uint64_t ku0 = u0 - eb, ku1 = min(u1, ee) - eb;
+        Entry<NL, S> E;
+        E.lo = elo;
+        E.hi = ehi;
+        __syncwarp();  // the previous entry's ranges are no longer read
+        E.cell = e_cell[e];
+        E.x = e_x[e];
+        uint32_t r0lo[MAXOPEN], r0hi[MAXOPEN];
+#pragma unroll
+        for (int s = 0; s < MAXOPEN; ++s) {
+            r0lo[s] = s < P.nopen[0] ? e_rng[(uint64_t)e * (2 * MAXOPEN) + 2 * s] : 0;
+            r0hi[s] = s < P.nopen[0] ? e_rng[(uint64_t)e * (2 * MAXOPEN) + 2 * s + 1] : 0;
+        }
+        uint32_t best1 = 0, len1 = 0xFFFFFFFFu;
+#pragma unroll
+        for (int L = 1; L < NL; ++L)
+#pragma unroll
+            for (int q = 0; q < S; ++q) {
+                uint32_t lo2 = 0, hi2 = 0;
+                if (q < P.nsrc[L] && P.src_ec[L][q]) {
+                    const DAtom& a = P.atom[P.src_atom[L][q]];
+                    if (P.src_top[L][q]) {
+                        top_range(a, E.cell, lo2, hi2);
+                    } else {
+#pragma unroll
+                        for (int s = 0; s < MAXOPEN; ++s)
+                            if (s == a.slot) {
+                                lo2 = r0lo[s];
+                                hi2 = r0hi[s];
+                            }
+                    }
+                }
+                if (L == 1 && q < P.nsrc[1] && hi2 - lo2 < len1) {
+                    len1 = hi2 - lo2;
+                    best1 = q;
+                }
+                if (lane == 0) {
+                    E.lo[L][q] = lo2;
+                    E.hi[L][q] = hi2;
+                }
+            }
+        __syncwarp();
+        E.best1 = best1;
+        E.len1 = len1;
+        const uint64_t before = A.count;
+        const uint32_t split = e_split[e];
+        // units are (loop-2 candidate k, slice j) pairs, k-major; an
+        // unsliced entry (split 1) is one call over its candidate range
+        for (uint64_t u = ku0; u < ku1;) {
+            if (split == 1) {
+                E.k0 = (uint32_t)u;
+                E.k1 = (uint32_t)ku1;
+                E.j0 = 0;
+                E.j1 = 1;
+                u = ku1;
+            } else {
+                const uint32_t j0 = (uint32_t)(u % split);
+                const uint64_t jend = j0 + (ku1 - u);
+                E.k0 = (uint32_t)(u / split);
+                E.k1 = E.k0 + 1;
+                E.j0 = j0;
+                E.j1 = jend < split ? (uint32_t)jend : split;
+                u += E.j1 - j0;
+            }
+            E.ns = split;
+            run_level<1, NL, S, O, MAT>(P, F, E, A, 1);
+        }
+        const uint64_t got = A.count - before;
+        if (pass == 0 && cell_counts && got && lane == 0)
+            atomicAdd((unsigned long long*)&cell_counts[E.cell], (unsigned long long)got);
+        item_count += got;
+        u0 = eb + ku1;
+        ++e;
+    }
+    return item_count;
+}
+
+// Persistent search kernel of one query.  Warps take work items from an
+// atomic counter.  pass 0 counts (and, with item_counts, records each item's
+// count; materialize writes into pool chunks); pass 1 writes tuples at
+// item_base[item].
 template <int NL, int S, int O, bool MAT>
 __global__ void __launch_bounds__(128, (NL <= 3 ? 8 : 6)) gj_kernel(const DPlan* __restrict__ gP, const uint32_t* __restrict__ e_cell,
                                                     const uint32_t* __restrict__ e_x,
@@ -690,99 +798,10 @@ __global__ void __launch_bounds__(128, (NL <= 3 ? 8 : 6)) gj_kernel(const DPlan*
         if (lane == 0) item = atomicAdd(&ctl->item_ctr[pass], 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= nitems) break;
-        uint64_t u0 = (uint64_t)item * grain;
-        const uint64_t u1 = min(U, u0 + grain);
-        uint32_t lo = 0, hi = E_n;  // last entry e with uoff[e] <= u0
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (uoff[mid] <= u0)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        uint32_t e = lo;
         A.out_pos = (MAT && !A.pool) ? item_base[item] : 0;
-        uint64_t item_count = 0;
-        while (u0 < u1 && e < E_n) {
-            const uint64_t eb = uoff[e], ee = uoff[e + 1];
-            if (ee <= u0) {
-                ++e;
-                continue;
-            }
-            const uint64_t ku0 = u0 - eb, ku1 = min(u1, ee) - eb;
-            Entry<NL, S> E;
-            E.lo = s_elo[threadIdx.x >> 5];
-            E.hi = s_ehi[threadIdx.x >> 5];
-            __syncwarp();  // the previous entry's ranges are no longer read
-            E.cell = e_cell[e];
-            E.x = e_x[e];
-            uint32_t r0lo[MAXOPEN], r0hi[MAXOPEN];
-#pragma unroll
-            for (int s = 0; s < MAXOPEN; ++s) {
-                r0lo[s] = s < P.nopen[0] ? e_rng[(uint64_t)e * (2 * MAXOPEN) + 2 * s] : 0;
-                r0hi[s] = s < P.nopen[0] ? e_rng[(uint64_t)e * (2 * MAXOPEN) + 2 * s + 1] : 0;
-            }
-            uint32_t best1 = 0, len1 = 0xFFFFFFFFu;
-#pragma unroll
-            for (int L = 1; L < NL; ++L)
-#pragma unroll
-                for (int q = 0; q < S; ++q) {
-                    uint32_t lo = 0, hi = 0;
-                    if (q < P.nsrc[L] && P.src_ec[L][q]) {
-                        const DAtom& a = P.atom[P.src_atom[L][q]];
-                        if (P.src_top[L][q]) {
-                            top_range(a, E.cell, lo, hi);
-                        } else {
-#pragma unroll
-                            for (int s = 0; s < MAXOPEN; ++s)
-                                if (s == a.slot) {
-                                    lo = r0lo[s];
-                                    hi = r0hi[s];
-                                }
-                        }
-                    }
-                    if (L == 1 && q < P.nsrc[1] && hi - lo < len1) {
-                        len1 = hi - lo;
-                        best1 = q;
-                    }
-                    if (lane == 0) {
-                        E.lo[L][q] = lo;
-                        E.hi[L][q] = hi;
-                    }
-                }
-            __syncwarp();
-            E.best1 = best1;
-            E.len1 = len1;
-            const uint64_t before = A.count;
-            const uint32_t split = e_split[e];
-            // units are (loop-2 candidate k, slice j) pairs, k-major; an
-            // unsliced entry (split 1) is one call over its candidate range
-            for (uint64_t u = ku0; u < ku1;) {
-                if (split == 1) {
-                    E.k0 = (uint32_t)u;
-                    E.k1 = (uint32_t)ku1;
-                    E.j0 = 0;
-                    E.j1 = 1;
-                    u = ku1;
-                } else {
-                    const uint32_t j0 = (uint32_t)(u % split);
-                    const uint64_t jend = j0 + (ku1 - u);
-                    E.k0 = (uint32_t)(u / split);
-                    E.k1 = E.k0 + 1;
-                    E.j0 = j0;
-                    E.j1 = jend < split ? (uint32_t)jend : split;
-                    u += E.j1 - j0;
-                }
-                E.ns = split;
-                run_level<1, NL, S, O, MAT>(P, F, E, A, 1);
-            }
-            const uint64_t got = A.count - before;
-            if (pass == 0 && cell_counts && got && lane == 0)
-                atomicAdd((unsigned long long*)&cell_counts[E.cell], (unsigned long long)got);
-            item_count += got;
-            u0 = eb + ku1;
-            ++e;
-        }
+        const uint64_t item_count =
+            search_item<NL, S, O, MAT>(P, F, A, s_elo[threadIdx.x >> 5], s_ehi[threadIdx.x >> 5], item, grain, E_n, U,
+                                       e_cell, e_x, e_rng, e_split, uoff, cell_counts, pass);
         if (pass == 0 && item_counts && lane == 0) item_counts[item] = item_count;
         total += item_count;
     }
@@ -791,6 +810,95 @@ __global__ void __launch_bounds__(128, (NL <= 3 ? 8 : 6)) gj_kernel(const DPlan*
     if (A.stats) {
         const uint64_t w = warp_sum64(A.work);
         if (lane == 0 && w) atomicAdd((unsigned long long*)&ctl->work, (unsigned long long)w);
+    }
+}
+
+// ------------------------------------------------------------ batched launch
+// Many queries in one persistent launch (count mode).  Each query keeps its
+// own plan, entries and unit offsets; the work items of all queries form one
+// space (item_off: prefix of the per-query item counts) handed out by one
+// atomic counter, so warps move on to whichever query still has work.  A
+// warp keeps the plan of the query it is working on in shared memory.
+struct BQuery {
+    const DPlan* plan;
+    const uint32_t *e_cell, *e_x, *e_rng, *e_split;
+    const uint64_t* uoff;
+    JoinCtl* ctl;
+    uint32_t grain;
+    uint32_t shape;  // 0: the kernel's first shape, 1: its second
+};
+
+__global__ void batch_items_kernel(const BQuery* __restrict__ qs, uint32_t n, uint64_t* __restrict__ items) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const BQuery& b = qs[i];
+        const uint64_t U = b.uoff[b.ctl->n_entries];
+        items[i] = (U + b.grain - 1) / b.grain;
+    }
+}
+
+template <int NLA, int SA, int OA, int NLB, int SB, int OB>
+__global__ void __launch_bounds__(128, ((NLA <= 3 && NLB <= 3) ? 8 : 6))
+    gj_batch_kernel(const BQuery* __restrict__ qs, uint32_t n, const uint64_t* __restrict__ item_off,
+                    uint32_t* __restrict__ ctr) {
+    constexpr int NLM = NLA > NLB ? NLA : NLB;
+    constexpr int SM = SA > SB ? SA : SB;
+    __shared__ DPlan wplan[4];
+    __shared__ uint32_t s_e[4][2 * NLM * SM];
+    const uint32_t w = threadIdx.x >> 5, lane = lane_id();
+    const uint64_t total_items = item_off[n];
+    uint32_t cur = 0xFFFFFFFFu;
+    Acc A;
+    A.count = 0;
+    A.work = 0;
+    A.out_pos = 0;
+    A.out = nullptr;
+    A.stats = 0;
+    A.pool = 0;
+    A.chunk = NO_CHUNK;
+    A.fill = OUT_CHUNK;
+    A.n_chunks = 0;
+    A.chunk_fill = nullptr;
+    A.ctl = nullptr;
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(ctr, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= total_items) break;
+        uint32_t lo = 0, hi = n;  // query holding item it: last q with item_off[q] <= it
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (item_off[mid] <= it)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const uint32_t q = lo;
+        const BQuery& b = qs[q];
+        if (q != cur) {
+            __syncwarp();
+            const uint32_t* src = (const uint32_t*)b.plan;
+            uint32_t* dst = (uint32_t*)&wplan[w];
+            for (uint32_t i = lane; i < sizeof(DPlan) / 4; i += 32) dst[i] = src[i];
+            __syncwarp();
+            cur = q;
+        }
+        const DPlan& P = wplan[w];
+        const uint32_t E_n = b.ctl->n_entries;
+        const uint64_t U = b.uoff[E_n];
+        const uint64_t local = it - item_off[q];
+        uint64_t c;
+        if (b.shape == 0) {
+            Frame<NLA, OA> F;
+            c = search_item<NLA, SA, OA, false>(P, F, A, (uint32_t(*)[SA])s_e[w], (uint32_t(*)[SA])(s_e[w] + NLA * SA),
+                                                local, b.grain, E_n, U, b.e_cell, b.e_x, b.e_rng, b.e_split, b.uoff,
+                                                nullptr, 0);
+        } else {
+            Frame<NLB, OB> F;
+            c = search_item<NLB, SB, OB, false>(P, F, A, (uint32_t(*)[SB])s_e[w], (uint32_t(*)[SB])(s_e[w] + NLB * SB),
+                                                local, b.grain, E_n, U, b.e_cell, b.e_x, b.e_rng, b.e_split, b.uoff,
+                                                nullptr, 0);
+        }
+        if (lane == 0 && c) atomicAdd((unsigned long long*)&b.ctl->total, (unsigned long long)c);
     }
 }
 
@@ -975,11 +1083,25 @@ hc_status result_get(hc_result* R, hc_result_view* v) {
     return HC_OK;
 }
 
-hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_join_params* prm, cudaStream_t s,
-                        hc_result** out) {
-    if (!out) return fail(HC_ERR_ARG, "run_join: out is NULL");
-    *out = nullptr;
-    if (!q || !idx || !prm) return fail(HC_ERR_ARG, "run_join: NULL argument");
+// ------------------------------------------------------------ query plans
+// Host-side plan of one query: validation, loop order, the lists of every
+// loop, and the atoms it partitions (enqueued on `s`, owned by the caller).
+struct QueryPlan {
+    DPlan P;
+    int nv = 0, shape_s = 2, shape_o = 2, threads = 128, stats = 0;
+    uint32_t grain = 64;
+    uint64_t ncells = 1, cand_bound = 1;
+    std::vector<hc_partitioned*> parts;
+};
+
+static void release_parts(std::vector<hc_partitioned*>& parts, cudaStream_t s) {
+    for (auto* p : parts) partitioned_release(p, s);
+    parts.clear();
+}
+
+hc_status plan_query(const hc_query* q, const hc_index* const* idx, const hc_join_params* prm, cudaStream_t s,
+                     QueryPlan* out) {
+    if (!q || !idx || !prm || !out) return fail(HC_ERR_ARG, "run_join: NULL argument");
     const int nv = (int)q->n_vars, na = (int)q->n_atoms;
     if (nv < 2 || nv > HC_MAX_VARS || na < 1 || na > HC_MAX_ATOMS)
         return fail(HC_ERR_ARG, "run_join: need 2..8 variables and 1..8 atoms");
@@ -996,10 +1118,12 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     bool covered[HC_MAX_VARS] = {false};
     for (int j = 0; j < na; ++j) {
         const int a = q->atoms[j].var0, b = q->atoms[j].var1;
-        if (a >= nv || b >= nv || a == b) return fail(HC_ERR_ARG, "run_join: atom variables out of range or equal");
+        if (a >= nv || (b >= nv && b != (int)HC_UNARY) || a == b)
+            return fail(HC_ERR_ARG, "run_join: atom variables out of range or equal");
         if (!idx[j]) return fail(HC_ERR_ARG, "run_join: missing index for an atom");
         if (idx[j]->stats_only) return fail(HC_ERR_ARG, "run_join: a statistics-only index has no data");
-        covered[a] = covered[b] = true;
+        covered[a] = true;
+        if (b != (int)HC_UNARY) covered[b] = true;
     }
     for (int v = 0; v < nv; ++v)
         if (!covered[v]) return fail(HC_ERR_ARG, "run_join: a variable occurs in no atom");
@@ -1017,43 +1141,42 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
             st *= prm->shares[v];
         }
     }
-    const uint32_t grain = prm->item_grain ? prm->item_grain : 64;
-    const int threads = prm->block_threads ? (int)prm->block_threads : 128;
-    if (threads % 32 != 0 || threads < 32 || threads > 128)
+    out->grain = prm->item_grain ? prm->item_grain : 64;
+    out->threads = prm->block_threads ? (int)prm->block_threads : 128;
+    if (out->threads % 32 != 0 || out->threads < 32 || out->threads > 128)
         return fail(HC_ERR_ARG, "run_join: block_threads must be a multiple of 32 in [32, 128]");
+    out->nv = nv;
+    out->ncells = ncells;
+    out->stats = (prm->flags & HC_FLAG_STATS) ? 1 : 0;
 
-    hc_result* R = new hc_result();
-    R->stream = s;
-    R->n_vars = nv;
-    R->n_cells = ncells;
-    auto bail = [&](hc_status st) {
-        result_release(R);
-        return st;
-    };
-
-    DPlan P;
+    DPlan& P = out->P;
     memset(&P, 0, sizeof(P));
     P.nlev = nv;
     P.natoms = na;
     P.nv = nv;
     P.ncells = (uint32_t)ncells;
     for (int i = 0; i < nv; ++i) P.var_of_level[i] = q->order[i];
+    auto bail = [&](hc_status st) {
+        release_parts(out->parts, s);
+        return st;
+    };
     for (int j = 0; j < na; ++j) {
         const hc_index* ix = idx[j];
         const int a = q->atoms[j].var0, b = q->atoms[j].var1;
-        const int first = rank[a] < rank[b] ? a : b, second = first == a ? b : a;
-        const uint32_t need_ao = rank[a] < rank[b] ? 0u : 1u;
+        const bool unary = b == (int)HC_UNARY;
+        const int first = (unary || rank[a] < rank[b]) ? a : b, second = unary ? -1 : (first == a ? b : a);
+        const uint32_t need_ao = (unary || rank[a] < rank[b]) ? 0u : 1u;
         if (ix->attr_order != need_ao)
             return bail(fail(HC_ERR_ARG, "run_join: an index's attr_order does not sort its atom in loop order"));
         DAtom& d = P.atom[j];
-        const uint32_t pa = prm->shares[first], pb = prm->shares[second];
+        const uint32_t pa = prm->shares[first], pb = unary ? 1u : prm->shares[second];
         d.pb = pb;
         d.stride_f = (uint32_t)stride[first];
         d.share_f = pa;
-        d.stride_s = (uint32_t)stride[second];
+        d.stride_s = unary ? 1u : (uint32_t)stride[second];
         d.share_s = pb;
         d.lev_first = rank[first];
-        d.lev_second = rank[second];
+        d.lev_second = unary ? -1 : rank[second];
         if ((uint64_t)pa * pb == 1) {
             d.v1 = ix->d_v1;
             d.o1 = ix->d_o1;
@@ -1062,9 +1185,10 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
             d.l1_whole = (uint32_t)ix->l1;
         } else {
             hc_partitioned* part = nullptr;
-            const hc_status st = partition_impl(ix, prm->seeds[first], pa, prm->seeds[second], pb, s, &part);
+            const hc_status st =
+                partition_impl(ix, prm->seeds[first], pa, unary ? 0u : prm->seeds[second], pb, s, &part);
             if (st != HC_OK) return bail(st);
-            R->parts.push_back(part);
+            out->parts.push_back(part);
             d.v1 = part->d_v1;
             d.o1 = part->d_o1;
             d.v2 = part->d_v2;
@@ -1092,15 +1216,14 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
             }
         }
     }
-    int shape_s = 2, shape_o = 2;
     for (int L = 0; L < nv; ++L) {
-        shape_s = std::max(shape_s, P.nsrc[L]);
-        if (L >= 1) shape_o = std::max(shape_o, P.nopen[L]);
-        for (int q = 0; q < P.nsrc[L]; ++q) {
-            const DAtom& a = P.atom[P.src_atom[L][q]];
-            P.src_ec[L][q] = (P.src_top[L][q] || a.lev_first == 0) ? 1 : 0;
-            P.src_f[L][q] = a.lev_first;
-            P.src_slot[L][q] = a.slot;
+        out->shape_s = std::max(out->shape_s, P.nsrc[L]);
+        if (L >= 1) out->shape_o = std::max(out->shape_o, P.nopen[L]);
+        for (int qq = 0; qq < P.nsrc[L]; ++qq) {
+            const DAtom& a = P.atom[P.src_atom[L][qq]];
+            P.src_ec[L][qq] = (P.src_top[L][qq] || a.lev_first == 0) ? 1 : 0;
+            P.src_f[L][qq] = a.lev_first;
+            P.src_slot[L][qq] = a.slot;
         }
     }
     P.merge_min = prm->merge_min ? prm->merge_min : 32;
@@ -1118,7 +1241,87 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     }
     cand_bound = std::max<uint64_t>(cand_bound, 1);
     if (cand_bound >= 0xFFFFFFFFull) return bail(fail(HC_ERR_CAPACITY, "run_join: too many loop-1 candidates"));
+    out->cand_bound = cand_bound;
+    return HC_OK;
+}
 
+// Device buffers of one query's loop-1 pass.  The first group is needed by
+// the search; the second only during the loop-1 pass.
+struct Level1 {
+    DPlan* d_plan = nullptr;
+    uint32_t *e_cell = nullptr, *e_x = nullptr, *e_rng = nullptr, *e_split = nullptr;
+    uint64_t* uoff = nullptr;
+    uint32_t *cand = nullptr, *flags = nullptr;
+    uint64_t *candoff = nullptr, *flagoff = nullptr, *e_units = nullptr;
+};
+
+template <class Alloc>
+hc_status alloc_level1_keep(const QueryPlan& qp, Alloc& a, Level1* L) {
+    const uint64_t cb = qp.cand_bound;
+    HC_TRY(a.get(&L->d_plan, 1));
+    HC_TRY(a.get(&L->e_cell, cb));
+    HC_TRY(a.get(&L->e_x, cb));
+    HC_TRY(a.get(&L->e_rng, cb * 2 * MAXOPEN));
+    HC_TRY(a.get(&L->e_split, cb));
+    HC_TRY(a.get(&L->uoff, cb + 1));
+    return HC_OK;
+}
+
+template <class Alloc>
+hc_status alloc_level1_temp(const QueryPlan& qp, Alloc& a, Level1* L) {
+    const uint64_t cb = qp.cand_bound;
+    HC_TRY(a.get(&L->cand, qp.ncells));
+    HC_TRY(a.get(&L->candoff, qp.ncells + 1));
+    HC_TRY(a.get(&L->flags, cb));
+    HC_TRY(a.get(&L->flagoff, cb + 1));
+    HC_TRY(a.get(&L->e_units, cb));
+    return HC_OK;
+}
+
+// Loop 1 of every cell (enqueued, no host waits): candidates per cell, the
+// flat probe, compaction into entries and the entries' unit offsets.  The
+// plan must already be in L.d_plan.
+hc_status enqueue_level1(const QueryPlan& qp, const Level1& L, JoinCtl* ctl, cudaStream_t s) {
+    const int tpb = 256;
+    const uint64_t ncells = qp.ncells, cb = qp.cand_bound;
+    l0_count_kernel<<<(unsigned)std::min<uint64_t>((ncells + tpb - 1) / tpb, 4096), tpb, 0, s>>>(L.d_plan, L.cand, ctl,
+                                                                                                 qp.stats);
+    if (cudaError_t le = launch_check()) return cuda_fail(le, "l0_count_kernel");
+    HC_TRY(exclusive_scan_u32_to_u64(L.cand, L.candoff, ncells, nullptr, &ctl->err, s));
+    const unsigned pgrid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((cb + tpb - 1) / tpb, (uint64_t)num_sms() * 16));
+    l0_probe_kernel<false><<<pgrid, tpb, 0, s>>>(L.d_plan, L.candoff, cb, L.flags, nullptr, nullptr, nullptr, nullptr,
+                                                 nullptr, nullptr);
+    if (cudaError_t le = launch_check()) return cuda_fail(le, "l0_probe_kernel");
+    HC_TRY(exclusive_scan_u32_to_u64(L.flags, L.flagoff, cb, nullptr, &ctl->err, s));
+    l0_probe_kernel<true><<<pgrid, tpb, 0, s>>>(L.d_plan, L.candoff, cb, L.flags, L.flagoff, L.e_cell, L.e_x, L.e_rng,
+                                                L.e_units, L.e_split);
+    if (cudaError_t le = launch_check()) return cuda_fail(le, "l0_probe_kernel");
+    entries_total_kernel<<<1, 1, 0, s>>>(L.flagoff, L.candoff, (uint32_t)ncells, cb, ctl);
+    if (cudaError_t le = launch_check()) return cuda_fail(le, "entries_total_kernel");
+    HC_TRY(exclusive_scan_u64(L.e_units, L.uoff, cb, &ctl->n_entries, &ctl->err, s));
+    return HC_OK;
+}
+
+hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_join_params* prm, cudaStream_t s,
+                        hc_result** out) {
+    if (!out) return fail(HC_ERR_ARG, "run_join: out is NULL");
+    *out = nullptr;
+    QueryPlan qp;
+    HC_TRY(plan_query(q, idx, prm, s, &qp));
+    const int nv = qp.nv, shape_s = qp.shape_s, shape_o = qp.shape_o, threads = qp.threads, stats = qp.stats;
+    const uint32_t grain = qp.grain;
+    const uint64_t ncells = qp.ncells;
+
+    hc_result* R = new hc_result();
+    R->stream = s;
+    R->n_vars = nv;
+    R->n_cells = ncells;
+    R->parts = qp.parts;
+    qp.parts.clear();
+    auto bail = [&](hc_status st) {
+        result_release(R);
+        return st;
+    };
     {
         void* p;
         if (dev_alloc(&p, sizeof(JoinCtl), s) != HC_OK) return bail(HC_ERR_OOM);
@@ -1126,7 +1329,6 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     }
     JoinCtl* ctl = R->d_ctl;
     if (cudaMemsetAsync(ctl, 0, sizeof(JoinCtl), s) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
-    const int stats = (prm->flags & HC_FLAG_STATS) ? 1 : 0;
     if (prm->flags & HC_FLAG_CELL_COUNTS) {
         void* p;
         if (dev_alloc(&p, ncells * 8, s) != HC_OK) return bail(HC_ERR_OOM);
@@ -1135,45 +1337,17 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     }
 
     Scratch tmp(s);
-    DPlan* d_plan;
-    uint32_t *cand, *flags, *e_cell, *e_x, *e_rng, *e_split;
-    uint64_t *candoff, *flagoff, *uoff, *e_units;
+    Level1 L;
     hc_status st;
-    if ((st = tmp.get(&d_plan, 1)) != HC_OK) return bail(st);
-    if (cudaMemcpyAsync(d_plan, &P, sizeof(DPlan), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    if ((st = alloc_level1_keep(qp, tmp, &L)) != HC_OK) return bail(st);
+    if ((st = alloc_level1_temp(qp, tmp, &L)) != HC_OK) return bail(st);
+    if (cudaMemcpyAsync(L.d_plan, &qp.P, sizeof(DPlan), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return bail(cuda_fail(cudaGetLastError(), "plan copy"));
-    if ((st = tmp.get(&cand, ncells)) != HC_OK) return bail(st);
-    if ((st = tmp.get(&candoff, ncells + 1)) != HC_OK) return bail(st);
-    if ((st = tmp.get(&flags, cand_bound)) != HC_OK) return bail(st);
-    if ((st = tmp.get(&flagoff, cand_bound + 1)) != HC_OK) return bail(st);
-    if ((st = tmp.get(&e_cell, cand_bound)) != HC_OK) return bail(st);
-    if ((st = tmp.get(&e_x, cand_bound)) != HC_OK) return bail(st);
-    if ((st = tmp.get(&e_rng, cand_bound * 2 * MAXOPEN)) != HC_OK) return bail(st);
-    if ((st = tmp.get(&e_units, cand_bound)) != HC_OK) return bail(st);
-    if ((st = tmp.get(&e_split, cand_bound)) != HC_OK) return bail(st);
-    if ((st = tmp.get(&uoff, cand_bound + 1)) != HC_OK) return bail(st);
+    if ((st = enqueue_level1(qp, L, ctl, s)) != HC_OK) return bail(st);
+    const uint64_t* uoff = L.uoff;
 
-    const int tpb = 256;
-    l0_count_kernel<<<(unsigned)std::min<uint64_t>((ncells + tpb - 1) / tpb, 4096), tpb, 0, s>>>(d_plan, cand, ctl,
-                                                                                                 stats);
-    if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "l0_count_kernel"));
-    if ((st = exclusive_scan_u32_to_u64(cand, candoff, ncells, nullptr, &ctl->err, s)) != HC_OK) return bail(st);
-    const unsigned pgrid =
-        (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((cand_bound + tpb - 1) / tpb, (uint64_t)num_sms() * 16));
-    l0_probe_kernel<false><<<pgrid, tpb, 0, s>>>(d_plan, candoff, cand_bound, flags, nullptr, nullptr, nullptr, nullptr,
-                                                 nullptr, nullptr);
-    if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "l0_probe_kernel"));
-    if ((st = exclusive_scan_u32_to_u64(flags, flagoff, cand_bound, nullptr, &ctl->err, s)) != HC_OK) return bail(st);
-    l0_probe_kernel<true><<<pgrid, tpb, 0, s>>>(d_plan, candoff, cand_bound, flags, flagoff, e_cell, e_x, e_rng, e_units,
-                                                e_split);
-    if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "l0_probe_kernel"));
-    entries_total_kernel<<<1, 1, 0, s>>>(flagoff, candoff, (uint32_t)ncells, cand_bound, ctl);
-    if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "entries_total_kernel"));
-    if ((st = exclusive_scan_u64(e_units, uoff, cand_bound, &ctl->n_entries, &ctl->err, s)) != HC_OK)
-        return bail(st);
-
-    GjArgs g{d_plan,  e_cell,  e_x,     e_rng, e_split, uoff,    grain,   ctl, 0, R->d_cell_counts,
-             nullptr, nullptr, nullptr, stats, threads, nullptr, 0};
+    GjArgs g{L.d_plan, L.e_cell, L.e_x,   L.e_rng, L.e_split, uoff,    grain,   ctl, 0, R->d_cell_counts,
+             nullptr,  nullptr,  nullptr, stats,   threads,   nullptr, 0};
     const bool timed = (prm->flags & HC_FLAG_TIME_KERNELS) != 0;
     if (timed)
         for (auto& e : R->ev)
@@ -1271,6 +1445,221 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     R->n_tuples = total;
     R->materialized = true;
     *out = R;
+    return HC_OK;
+}
+
+// -------------------------------------------------------------- batches
+// Shape classes of the batched kernel: (loops, lists per loop, atoms opened
+// per loop) rounded up to the instantiated widths.
+enum ShapeClass { SC_T = 0, SC_T4 = 1, SC_C = 2, SC_K = 3, SC_NONE = 4 };
+
+static int shape_class(const QueryPlan& qp) {
+    const bool wide = qp.shape_s > 2 || qp.shape_o > 2;
+    if (qp.nv == 3) return wide ? SC_T4 : SC_T;
+    if (qp.nv == 4) return wide ? SC_K : SC_C;
+    return SC_NONE;
+}
+
+template <int NLA, int SA, int OA, int NLB, int SB, int OB>
+hc_status launch_batch_kernel(const BQuery* q, uint32_t n, const uint64_t* item_off, uint32_t* ctr, cudaStream_t s) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_batch_kernel<NLA, SA, OA, NLB, SB, OB>, 128, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    gj_batch_kernel<NLA, SA, OA, NLB, SB, OB><<<per_sm * num_sms(), 128, 0, s>>>(q, n, item_off, ctr);
+    HC_CUDA_TRY(launch_check());
+    return HC_OK;
+}
+
+// (a, b) with a <= b; the kernel's shape 0 is class a, shape 1 class b.
+static hc_status launch_batch_pair(int a, int b, const BQuery* q, uint32_t n, const uint64_t* item_off, uint32_t* ctr,
+                                   cudaStream_t s) {
+    switch (a * 8 + b) {
+        case SC_T * 8 + SC_T: return launch_batch_kernel<3, 2, 2, 3, 2, 2>(q, n, item_off, ctr, s);
+        case SC_T4 * 8 + SC_T4: return launch_batch_kernel<3, 4, 4, 3, 4, 4>(q, n, item_off, ctr, s);
+        case SC_C * 8 + SC_C: return launch_batch_kernel<4, 2, 2, 4, 2, 2>(q, n, item_off, ctr, s);
+        case SC_K * 8 + SC_K: return launch_batch_kernel<4, 4, 4, 4, 4, 4>(q, n, item_off, ctr, s);
+        case SC_T * 8 + SC_K: return launch_batch_kernel<3, 2, 2, 4, 4, 4>(q, n, item_off, ctr, s);
+        case SC_T * 8 + SC_C: return launch_batch_kernel<3, 2, 2, 4, 2, 2>(q, n, item_off, ctr, s);
+        case SC_C * 8 + SC_K: return launch_batch_kernel<4, 2, 2, 4, 4, 4>(q, n, item_off, ctr, s);
+        case SC_T4 * 8 + SC_K: return launch_batch_kernel<3, 4, 4, 4, 4, 4>(q, n, item_off, ctr, s);
+        default: return fail(HC_ERR_CAPACITY, "batch: this pair of query shapes is not built in");
+    }
+}
+
+// Owned device memory with plain (non stream-ordered) allocation, so that a
+// captured graph can replay the batch for as long as the batch lives.
+struct OwnedAlloc {
+    std::vector<void*>* list;
+    template <typename T>
+    hc_status get(T** p, size_t count) {
+        void* v = nullptr;
+        cudaError_t e = cudaMalloc(&v, std::max<size_t>(count, 1) * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HC_ERR_OOM, "batch: device allocation failed");
+        }
+        list->push_back(v);
+        *p = (T*)v;
+        return HC_OK;
+    }
+};
+
+}  // namespace hc
+
+struct hc_batch {
+    uint32_t n = 0;
+    std::vector<hc::QueryPlan> plans;
+    std::vector<hc::Level1> l1;
+    std::vector<void*> mem;
+    hc::JoinCtl* d_ctl = nullptr;
+    hc::BQuery* d_q = nullptr;
+    uint64_t* d_items = nullptr;
+    uint64_t* d_item_off = nullptr;
+    uint32_t* d_ctr = nullptr;
+    hc::Level1 temp;  // loop-1 temporaries shared by the queries (sized by the largest)
+    int class_a = 0, class_b = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace hc {
+
+void batch_release(hc_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaDeviceSynchronize();
+    for (auto& qp : b->plans) release_parts(qp.parts, nullptr);
+    for (void* p : b->mem) cudaFree(p);
+    delete b;
+}
+
+hc_status batch_create(const hc_query* qs, const hc_index* const* idx_flat, const hc_join_params* prm, uint32_t n,
+                       cudaStream_t s, hc_batch** out) {
+    if (!out) return fail(HC_ERR_ARG, "batch: out is NULL");
+    *out = nullptr;
+    if (!qs || !idx_flat || !prm || n == 0 || n > 65536) return fail(HC_ERR_ARG, "batch: need 1..65536 queries");
+    hc_batch* B = new hc_batch();
+    B->n = n;
+    B->plans.resize(n);
+    B->l1.resize(n);
+    auto bail = [&](hc_status st) {
+        batch_release(B);
+        return st;
+    };
+    OwnedAlloc A{&B->mem};
+    size_t off = 0;
+    int classes[2] = {-1, -1};
+    uint64_t max_cb = 1, max_cells = 1;
+    std::vector<BQuery> hq(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        if (prm[i].mode != HC_MODE_COUNT) return bail(fail(HC_ERR_ARG, "batch: queries run in count mode"));
+        hc_status st = plan_query(&qs[i], idx_flat + off, &prm[i], s, &B->plans[i]);
+        if (st != HC_OK) return bail(st);
+        off += qs[i].n_atoms;
+        const int c = shape_class(B->plans[i]);
+        if (c == SC_NONE) return bail(fail(HC_ERR_CAPACITY, "batch: queries of 3 or 4 variables are built in"));
+        if (classes[0] < 0 || classes[0] == c)
+            classes[0] = c;
+        else if (classes[1] < 0 || classes[1] == c)
+            classes[1] = c;
+        else
+            return bail(fail(HC_ERR_CAPACITY, "batch: at most two query shapes per batch"));
+        if ((st = alloc_level1_keep(B->plans[i], A, &B->l1[i])) != HC_OK) return bail(st);
+        max_cb = std::max(max_cb, B->plans[i].cand_bound);
+        max_cells = std::max(max_cells, B->plans[i].ncells);
+        if (cudaMemcpy(B->l1[i].d_plan, &B->plans[i].P, sizeof(DPlan), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(cuda_fail(cudaGetLastError(), "batch plan copy"));
+    }
+    if (classes[1] < 0) classes[1] = classes[0];
+    B->class_a = std::min(classes[0], classes[1]);
+    B->class_b = std::max(classes[0], classes[1]);
+    {
+        QueryPlan big;
+        big.cand_bound = max_cb;
+        big.ncells = max_cells;
+        hc_status st = alloc_level1_temp(big, A, &B->temp);
+        if (st != HC_OK) return bail(st);
+    }
+    hc_status st;
+    if ((st = A.get(&B->d_ctl, n)) != HC_OK || (st = A.get(&B->d_q, n)) != HC_OK ||
+        (st = A.get(&B->d_items, n)) != HC_OK || (st = A.get(&B->d_item_off, (size_t)n + 1)) != HC_OK ||
+        (st = A.get(&B->d_ctr, 1)) != HC_OK)
+        return bail(st);
+    for (uint32_t i = 0; i < n; ++i) {
+        const Level1& L = B->l1[i];
+        hq[i] = BQuery{L.d_plan, L.e_cell, L.e_x, L.e_rng, L.e_split, L.uoff, B->d_ctl + i, B->plans[i].grain,
+                       (uint32_t)(shape_class(B->plans[i]) == B->class_a ? 0 : 1)};
+    }
+    if (cudaMemcpy(B->d_q, hq.data(), n * sizeof(BQuery), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "batch table copy"));
+    if (cudaStreamSynchronize(s) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "batch partition sync"));
+    *out = B;
+    return HC_OK;
+}
+
+static hc_status batch_enqueue(hc_batch* B, cudaStream_t s) {
+    HC_CUDA_TRY(cudaMemsetAsync(B->d_ctl, 0, B->n * sizeof(JoinCtl), s));
+    HC_CUDA_TRY(cudaMemsetAsync(B->d_ctr, 0, sizeof(uint32_t), s));
+    for (uint32_t i = 0; i < B->n; ++i) {
+        Level1 L = B->l1[i];
+        L.cand = B->temp.cand;
+        L.candoff = B->temp.candoff;
+        L.flags = B->temp.flags;
+        L.flagoff = B->temp.flagoff;
+        L.e_units = B->temp.e_units;
+        HC_TRY(enqueue_level1(B->plans[i], L, B->d_ctl + i, s));
+    }
+    batch_items_kernel<<<(B->n + 255) / 256, 256, 0, s>>>(B->d_q, B->n, B->d_items);
+    HC_CUDA_TRY(launch_check());
+    HC_TRY(exclusive_scan_u64(B->d_items, B->d_item_off, B->n, nullptr, &B->d_ctl[0].err, s));
+    return launch_batch_pair(B->class_a, B->class_b, B->d_q, B->n, B->d_item_off, B->d_ctr, s);
+}
+
+hc_status batch_launch(hc_batch* B, cudaStream_t s) {
+    if (!B) return fail(HC_ERR_ARG, "batch: NULL");
+    B->last_stream = s;
+    if (B->exec) {
+        HC_CUDA_TRY(cudaGraphLaunch(B->exec, s));
+        return HC_OK;
+    }
+    return batch_enqueue(B, s);
+}
+
+hc_status batch_capture(hc_batch* B, cudaStream_t s) {
+    if (!B) return fail(HC_ERR_ARG, "batch: NULL");
+    if (s == nullptr) return fail(HC_ERR_ARG, "batch: graph capture needs a created (non-default) stream");
+    if (B->exec) return HC_OK;
+    HC_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    hc_status st = batch_enqueue(B, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != HC_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&B->exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    B->graph = g;
+    return HC_OK;
+}
+
+hc_status batch_counts(hc_batch* B, uint64_t* counts) {
+    if (!B || !counts) return fail(HC_ERR_ARG, "batch: NULL argument");
+    std::vector<JoinCtl> h(B->n);
+    HC_CUDA_TRY(cudaStreamSynchronize(B->last_stream));
+    HC_CUDA_TRY(cudaMemcpy(h.data(), B->d_ctl, B->n * sizeof(JoinCtl), cudaMemcpyDeviceToHost));
+    for (uint32_t i = 0; i < B->n; ++i) {
+        if (h[i].err & DEV_ERR_TIMEOUT) return fail(HC_ERR_TIMEOUT, "batch: a bounded device wait gave up");
+        counts[i] = h[i].total;
+    }
     return HC_OK;
 }
 

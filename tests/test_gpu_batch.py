@@ -1,0 +1,72 @@
+"""Batched persistent launch against separate launches and the oracle (GPU)."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hc(cuda_device):
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2502_06715_gb300 as hc
+
+    return hc
+
+
+def dev(arr):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(arr, dtype=np.uint32).view(np.int32)).cuda()
+
+
+def _queries(hc, n, seed):
+    """Triangle / 4-clique queries (50/50) on induced subgraphs of one R-MAT graph."""
+    sym = datagen.rmat_graph(12, 8, seed)
+    ep = datagen.orient_lt(sym)
+    rng = np.random.default_rng(seed)
+    nv = int(sym.max()) + 1
+    qs, rels = [], []
+    for i in range(n):
+        sub = datagen.induced_by_key(ep, nv, 1000 + i, int(rng.integers(200, 3000)))
+        q = hc.TRIANGLE if rng.random() < 0.5 else hc.FOUR_CLIQUE
+        qs.append(q)
+        rels.append(sub)
+    return qs, rels
+
+
+@pytest.mark.parametrize("n", [1, 7, 40])
+def test_batch_matches_separate_and_oracle(hc, n):
+    import torch
+
+    qs, rels = _queries(hc, n, 3 + n)
+    idx = [hc.build_index(dev(r), 0) for r in rels]
+    lists = [[ix] * len(q.atoms) for q, ix in zip(qs, idx)]
+    opts = [{"shares": [2] + [1] * (q.n_vars - 1) if i % 3 == 0 else None} for i, q in enumerate(qs)]
+    want = [oracle.gj_count(q.n_vars, list(q.atoms), [r] * len(q.atoms))[0] for q, r in zip(qs, rels)]
+    sep = [hc.run_join(q, l, **{k: v for k, v in o.items() if v is not None}).count for q, l, o in zip(qs, lists, opts)]
+    assert sep == want
+    b = hc.Batch(qs, lists, opts)
+    b.launch()
+    assert b.counts() == want
+    # record once as a CUDA graph, then replay twice
+    s = torch.cuda.Stream()
+    b.capture(s)
+    for _ in range(2):
+        b.launch(s)
+        assert b.counts() == want
+    b.free()
+
+
+def test_batch_rejects_three_shapes(hc):
+    sym = datagen.random_graph(30, 0.3, 1)
+    ep = datagen.orient_lt(sym)
+    ix = hc.build_index(dev(ep), 0)
+    ixs = hc.build_index(dev(sym), 0)
+    qs = [hc.TRIANGLE, hc.FOUR_CLIQUE, hc.FOUR_CYCLE]
+    with pytest.raises(hc.HoneycombError):
+        hc.Batch(qs, [[ix] * 3, [ix] * 6, [ixs] * 4])

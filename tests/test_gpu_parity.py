@@ -230,6 +230,29 @@ def test_single_pass_materialize(hc, qname):
             assert int(r.cell_counts.sum()) == ref.shape[0]
 
 
+@pytest.mark.parametrize("qname", ["TRIANGLE", "FOUR_CYCLE", "FOUR_CLIQUE"])
+def test_unary_atoms(hc, qname):
+    """Unary atoms restrict variables to value sets (selections pushed into
+    the query), with and without shares."""
+    q = getattr(hc, qname)
+    sym = datagen.rmat_graph(10, 8, 8)
+    rel = datagen.orient_lt(sym) if qname != "FOUR_CYCLE" else sym
+    rng = np.random.default_rng(3)
+    for case in range(4):
+        extra, rels = [], [rel] * len(q.atoms)
+        nun = 1 if qname == "FOUR_CLIQUE" else 2
+        for v in rng.choice(q.n_vars, size=nun, replace=False):
+            vals = np.unique(rng.integers(0, 1024, size=300)).astype(np.uint32)
+            extra.append(((int(v), -1), np.stack([vals, np.zeros_like(vals)], 1)))
+        q2 = q.with_atoms([e[0] for e in extra])
+        r2 = rels + [e[1] for e in extra]
+        ref = oracle.gj_enumerate(q.n_vars, list(q2.atoms), r2)
+        for sh in ([1] * q.n_vars, [2] * q.n_vars):
+            r = _run(hc, q2, r2, shares=sh, mode="materialize")
+            assert r.count == ref.shape[0]
+            assert np.array_equal(sorted_rows(u32(r.tuples)), sorted_rows(ref))
+
+
 def test_uniform_4096_vertices_32768_edges(hc):
     """The oracle-sized triangle workload: x<y<z over a uniform graph."""
     ep = datagen.uniform_graph(4096, 32768, seed=1)

@@ -50,6 +50,14 @@ def brute_force(n_vars, atoms, rels, dom):
     """All tuples of dom^n_vars satisfying every atom (indicator product)."""
     t = np.ones((dom,) * n_vars, dtype=bool)
     for (v0, v1), r in zip(atoms, rels):
+        if v1 < 0:  # unary atom: the set of column-0 values
+            u = np.zeros(dom, dtype=bool)
+            if len(r):
+                u[r[:, 0]] = True
+            shape = [1] * n_vars
+            shape[v0] = dom
+            t &= u.reshape(shape)
+            continue
         a = np.zeros((dom, dom), dtype=bool)
         if len(r):
             a[r[:, 0], r[:, 1]] = True
@@ -152,6 +160,36 @@ def test_brute_force_random_relations(name):
         assert cnt == expect.shape[0], (name, case)
         got = oracle.gj_enumerate(n_vars, atoms, rels)
         assert np.array_equal(_sorted_rows(got), _sorted_rows(expect)), (name, case)
+
+
+@pytest.mark.parametrize("name", ["triangle", "four_cycle", "four_clique"])
+def test_brute_force_with_unary_atoms(name):
+    """Unary atoms F(X_v) restrict a variable to a set of values."""
+    n_vars, atoms = QUERIES[name]
+    rng = np.random.default_rng(17)
+    dom = 7
+    for case in range(20):
+        rels = [np.argwhere(rng.random((dom, dom)) < 0.6).astype(np.uint32) for _ in atoms]
+        extra = []
+        for v in rng.choice(n_vars, size=int(rng.integers(1, n_vars + 1)), replace=False):
+            vals = np.unique(rng.integers(0, dom, size=int(rng.integers(0, dom + 1)))).astype(np.uint32)
+            extra.append(((int(v), -1), np.stack([vals, np.zeros_like(vals)], 1)))
+        a2 = list(atoms) + [e[0] for e in extra]
+        r2 = rels + [e[1] for e in extra]
+        expect = brute_force(n_vars, a2, r2, dom)
+        assert oracle.gj_count(n_vars, a2, r2)[0] == expect.shape[0]
+        got = oracle.gj_enumerate(n_vars, a2, r2)
+        assert np.array_equal(_sorted_rows(got), _sorted_rows(expect))
+
+
+def test_unary_first_variable_equals_filter():
+    sym = datagen.random_graph(60, 0.2, 3)
+    ep = datagen.orient_lt(sym)
+    f = np.array([3, 7, 11, 20, 41, 59], dtype=np.uint32)
+    unary = np.stack([f, np.zeros_like(f)], 1)
+    a = oracle.gj_count(3, list(oracle.TRIANGLE[1]) + [(0, -1)], [ep, ep, ep, unary])[0]
+    b = oracle.gj_count(3, list(oracle.TRIANGLE[1]), [ep, ep, ep], filt=f)[0]
+    assert a == b
 
 
 def test_brute_force_empty_and_degenerate():
