@@ -46,12 +46,19 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--scale", type=int, default=22)
+    ap.add_argument("--scale", type=int, default=None, help="R-MAT scale (default per workload)")
     ap.add_argument("--edge-factor", type=int, default=16)
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--mode", choices=["materialize", "count"], default="materialize")
-    ap.add_argument("--shares", default="plan",
-                    help="'plan' (Sec. 5.3 decision at --P cells) or explicit, e.g. 32,32,1")
+    ap.add_argument("--workload", choices=["triangle", "clique4", "cycle4", "batched"], default="triangle",
+                    help="triangle: R-MAT triangle (default line); clique4 / cycle4: R-MAT 4-clique / 4-cycle "
+                         "counts; batched: 512 triangle/4-clique queries on induced subgraphs in one launch")
+    ap.add_argument("--shares", default="autotune",
+                    help="'autotune' (timed search from the paper's plan over HyperCube share vectors of "
+                         ">= --min-cells cells and kernel schedules), 'plan' (Sec. 5.3 decision at --P cells), "
+                         "or explicit, e.g. 32,32,1")
+    ap.add_argument("--min-cells", type=int, default=64,
+                    help="autotune: smallest number of cells (so the routing steps always run)")
     ap.add_argument("--P", type=int, default=1024)
     ap.add_argument("--grain", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
@@ -60,6 +67,8 @@ def parse_args():
                          "'0' = counting pass + emitting pass")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-edges", default="1e4,8e6",
+                    help="batched: range of the log-uniform subgraph edge counts")
     ap.add_argument("--cpu-frac", type=float, default=1.0 / 32,
                     help="fraction of x values in the oracle's bounded sample")
     return ap.parse_args()
@@ -183,8 +192,12 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.scale is None:
+        a.scale = {"triangle": 22, "clique4": 20, "cycle4": 20, "batched": 21}[a.workload]
     if a.impl == "reference":
         return reference_arm(a, world, rank)
+    if a.workload != "triangle":
+        return other_workload(a, world, rank, local)
 
     import numpy as np
     import torch
@@ -209,13 +222,25 @@ def main():
     stream = torch.cuda.current_stream(dev)
     q = hc.TRIANGLE
 
-    # plan (host): shares per the paper's decision rule at P cells, or given
+    # plan (host, untimed): shares per the paper's decision rule at P cells,
+    # the autotuner's timed choice, or given; kernel schedules likewise
     ix0 = hc.build_index(d_pairs, 0)
+    plan_shares = hc.choose_shares(q, [ix0] * 3, a.P)
+    tuned = None
     if a.shares == "plan":
-        shares = hc.choose_shares(q, [ix0] * 3, a.P)
+        shares = plan_shares
+    elif a.shares == "autotune":
+        from paper_2502_06715_gb300.autotune import Tuner
+
+        tuned = Tuner().tune(q, [ix0] * 3, P_list=(64, 256, 1024), min_cells=a.min_cells)
+        shares = tuned.shares
+        if not a.grain:
+            a.grain = tuned.item_grain
     else:
         shares = [int(x) for x in a.shares.split(",")]
-    stats = hc.run_join(q, [ix0] * 3, shares=shares, stats=True, item_grain=a.grain, block_threads=a.threads)
+    knobs = {"merge_min": tuned.merge_min, "merge_ratio": tuned.merge_ratio} if tuned else {}
+    stats = hc.run_join(q, [ix0] * 3, shares=shares, stats=True, item_grain=a.grain, block_threads=a.threads,
+                        **knobs)
     work, expect = stats.work, stats.count
     l1 = ix0.l1
     ix0.free()
@@ -226,7 +251,7 @@ def main():
     def step():
         ix = hc.build_index(d_pairs, 0, stream=stream)
         r = hc.run_join(q, [ix, ix, ix], shares=shares, mode=a.mode, keep_device=True, time_kernels=True,
-                        item_grain=a.grain, block_threads=a.threads, stream=stream, out_capacity=capacity)
+                        item_grain=a.grain, block_threads=a.threads, stream=stream, out_capacity=capacity, **knobs)
         ix.free()
         return r
 
@@ -284,7 +309,7 @@ def main():
 
     e2e = None
     if not a.no_e2e:
-        e2e = end_to_end(a, hc, ep, shares, q, dev, stream, expect, capacity)
+        e2e = end_to_end(a, hc, ep, shares, q, dev, stream, expect, capacity, knobs)
 
     cpu = None
     if not a.no_cpu_baseline and rank == 0 and world == 1:
@@ -298,7 +323,11 @@ def main():
             "dtype": "u32", "data": "synthetic (seeded R-MAT)",
             "config": {"workload": workload_name(a), "scale": a.scale, "edge_factor": a.edge_factor,
                        "rows_E+": n, "distinct_x": l1, "tuples": count, "shares": shares,
-                       "shares_from": a.shares if a.shares != "plan" else f"choose_shares(P={a.P})",
+                       "shares_from": a.shares if a.shares not in ("plan", "autotune") else
+                       (f"choose_shares(P={a.P})" if a.shares == "plan" else
+                        f"autotune (>= {a.min_cells} cells; candidates include choose_shares(P=64..1024))"),
+                       "plan_shares_P1024": plan_shares, "item_grain": a.grain or 64,
+                       "merge": [knobs.get("merge_min", 32), knobs.get("merge_ratio", 4)],
                        "out_capacity": capacity if a.mode == "materialize" else None,
                        "search_launches_per_step": n_launch_per_step,
                        "work_counter": work, "l2": "inputs larger than L2 (E+ is %.0f MB)" % (n * 8 / 1e6),
@@ -310,7 +339,7 @@ def main():
         dist.destroy_process_group()
 
 
-def end_to_end(a, hc, ep, shares, q, dev, stream, expect, capacity):
+def end_to_end(a, hc, ep, shares, q, dev, stream, expect, capacity, knobs):
     """Same metric through the public API from pinned HOST memory: the H2D
     copy of E+, the build, the join and the D2H copy of the result (all
     tuples in materialize mode, the count otherwise) are inside the timed
@@ -328,7 +357,7 @@ def end_to_end(a, hc, ep, shares, q, dev, stream, expect, capacity):
         d = host_in.to(dev, non_blocking=True)
         ix = hc.build_index(d, 0, stream=stream)
         r = hc.run_join(q, [ix, ix, ix], shares=shares, mode=a.mode, keep_device=True, item_grain=a.grain,
-                        block_threads=a.threads, stream=stream, out_capacity=capacity)
+                        block_threads=a.threads, stream=stream, out_capacity=capacity, **knobs)
         if host_out is not None:
             host_out.copy_(r.tuples, non_blocking=True)
         torch.cuda.current_stream(dev).synchronize()
@@ -350,6 +379,153 @@ def end_to_end(a, hc, ep, shares, q, dev, stream, expect, capacity):
     return {"value": c * a.steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(host_in.numel() * 4),
             "d2h_bytes_per_step": int(host_out.numel() * 4) if host_out is not None else 8,
             "ms_per_step": dt / a.steps * 1e3}
+
+
+def other_workload(a, world, rank, local):
+    """Lines for the other configurations (not the default bench line)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import datagen
+
+    __graft_entry__.build()
+    import paper_2502_06715_gb300 as hc
+    from paper_2502_06715_gb300.autotune import Tuner
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    t = time.perf_counter()
+    sym = datagen.rmat_graph(a.scale, a.edge_factor, a.seed + rank, device=f"cuda:{local}")
+    gen_s = time.perf_counter() - t
+    clocks = None
+    if a.workload in ("clique4", "cycle4"):
+        rel = datagen.orient_lt(sym) if a.workload == "clique4" else sym
+        rel = datagen.scatter_order(rel, a.seed)
+        d = torch.from_numpy(rel.view(np.int32)).to(dev)
+        q = hc.FOUR_CLIQUE if a.workload == "clique4" else hc.FOUR_CYCLE
+        ix0 = hc.build_index(d, 0)
+        if a.shares == "autotune":
+            cfg = Tuner(reps=1).tune(q, [ix0] * len(q.atoms), P_list=(64, 256), min_cells=a.min_cells)
+            opts = cfg.options()
+        elif a.shares == "plan":
+            opts = {"shares": hc.choose_shares(q, [ix0] * len(q.atoms), a.P)}
+        else:
+            opts = {"shares": [int(x) for x in a.shares.split(",")]}
+        stats = hc.run_join(q, [ix0] * len(q.atoms), stats=True, **opts)
+        ix0.free()
+
+        def step():
+            ix = hc.build_index(d, 0, stream=stream)
+            r = hc.run_join(q, [ix] * len(q.atoms), stream=stream, time_kernels=True, **opts)
+            ix.free()
+            return r
+
+        for _ in range(a.warmup):
+            step()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        kern = 0.0
+        for _ in range(a.steps):
+            r = step()
+            kern += r.ms_join_kernel
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1) / a.steps
+        line = {"metric": "join output tuples/s (R-MAT %s)" % ("4-clique" if a.workload == "clique4" else "4-cycle"),
+                "value": r.count / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic (seeded R-MAT)",
+                "config": {"workload": f"{a.workload} on R-MAT scale {a.scale} ef {a.edge_factor}, "
+                                       f"{'E+ (x<y)' if a.workload == 'clique4' else 'symmetric'}; count",
+                           "rows": int(rel.shape[0]), "tuples": r.count, "work_counter": stats.work,
+                           "options": opts, "search_kernel_ms": kern / a.steps, "generate_s": round(gen_s, 1)},
+                "roofline": {"bound": "hbm", "kernel": "gj_kernel (persistent search)",
+                             "achieved": 4.0 * stats.work / (kern / a.steps / 1e3) / 1e9,
+                             "peak": measured_hbm_peak()[0], "unit": "GB/s",
+                             "frac": 4.0 * stats.work / (kern / a.steps / 1e3) / 1e9 / measured_hbm_peak()[0],
+                             "traffic": None},
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+        return
+    # batched: 512 triangle / 4-clique queries on induced subgraphs of E+
+    ep = datagen.orient_lt(sym)
+    d = torch.from_numpy(ep.view(np.int32)).to(dev)
+    nv = int(sym.max()) + 1
+    rng = np.random.default_rng(4)
+    n = 512
+    kinds = rng.random(n) < 0.5
+    lo_e, hi_e = (float(x) for x in a.batch_edges.split(","))
+    targets = np.exp(rng.uniform(np.log(lo_e), np.log(hi_e), size=n)).astype(np.int64)
+    qs, idx = [], []
+    t = time.perf_counter()
+    for i in range(n):
+        sub = datagen.induced_by_key(d, nv, 4_000_000 + i, int(targets[i]))
+        ix = hc.build_index(sub, 0)
+        q = hc.TRIANGLE if kinds[i] else hc.FOUR_CLIQUE
+        qs.append(q)
+        idx.append([ix] * len(q.atoms))
+    prep_s = time.perf_counter() - t
+    # autotune per (kind, size bucket) on the group's first query
+    tuner = Tuner(reps=1)
+    opts = []
+    t = time.perf_counter()
+    for q, l in zip(qs, idx):
+        cfg = tuner.tune(q, l, P_list=(8, 64), min_cells=1)
+        o = cfg.options()
+        opts.append(o)
+    tune_s = time.perf_counter() - t
+    sep_counts = [hc.run_join(q, l, **o).count for q, l, o in zip(qs, idx, opts)]
+    side = torch.cuda.Stream(dev)
+    b = hc.Batch(qs, idx, opts, stream=side)
+    l0 = hc.kernel_launches()
+    b.capture(side)
+    per_replay = hc.kernel_launches() - l0  # kernels recorded in the graph
+    b.launch(side)
+    if b.counts() != sep_counts:
+        raise SystemExit("batched counts differ from separate launches")
+    for _ in range(a.warmup):
+        b.launch(side)
+        b.counts()
+        pend = [hc.run_join_async(q, l, stream=side, **o) for q, l, o in zip(qs, idx, opts)]
+        [p.count() for p in pend]
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    launches0 = hc.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(side)
+    for _ in range(a.steps):
+        b.launch(side)
+    e1.record(side)
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1) / a.steps
+    launches = hc.kernel_launches() - launches0 + per_replay * a.steps
+    t = time.perf_counter()
+    for _ in range(a.steps):
+        pend = [hc.run_join_async(q, l, stream=side, **o) for q, l, o in zip(qs, idx, opts)]
+        counts = [p.count() for p in pend]
+    torch.cuda.synchronize()
+    sep_ms = (time.perf_counter() - t) * 1e3 / a.steps
+    clocks = sampler.stop()
+    total = sum(sep_counts)
+    line = {"metric": "join output tuples/s (batched triangle/4-clique on induced R-MAT subgraphs)",
+            "value": total / (batched_ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": batched_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded R-MAT)",
+            "config": {"workload": f"512 queries (triangle/4-clique 50/50) on induced subgraphs of R-MAT scale "
+                                   f"{a.scale} ef {a.edge_factor} E+, edges log-uniform {lo_e:g}..{hi_e:g}",
+                       "tuples": total, "edges_min": int(min(ix[0].n for ix in idx)),
+                       "edges_max": int(max(ix[0].n for ix in idx)),
+                       "separate_launches_ms_per_step": sep_ms,
+                       "speedup_vs_separate": sep_ms / batched_ms, "graph_replay": True,
+                       "tuning_groups": len(tuner.cache), "tune_s": round(tune_s, 1),
+                       "prep_s": round(prep_s, 1), "counts_equal_separate": True},
+            "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(line), flush=True)
 
 
 def reference_arm(a, world, rank):

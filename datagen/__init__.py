@@ -280,13 +280,29 @@ def vertex_keys(n_vertices: int, seed_q: int) -> np.ndarray:
     return (v * a + b) % MERSENNE31
 
 
-def induced_by_key(pairs: np.ndarray, n_vertices: int, seed_q: int, target_edges: int) -> np.ndarray:
+def induced_by_key(pairs, n_vertices: int, seed_q: int, target_edges: int):
     """Induced subgraph on {v : k(v) < t} with t chosen for ~target_edges.
 
     An edge survives iff max(k(u), k(v)) < t, so t is the target-th smallest
-    edge key plus one: exactly target_edges edges (fewer if the graph has
-    fewer).  Returns the surviving pairs in input order.
+    edge key plus one: exactly target_edges edges (fewer on ties or if the
+    graph has fewer).  Returns the surviving pairs in input order.  ``pairs``
+    may be a numpy array or a torch CUDA tensor (int32 view of the uint32
+    pairs); the torch path does the same integer arithmetic on the device.
     """
+    if not isinstance(pairs, np.ndarray):
+        import torch
+
+        r = _rng(seed_q)
+        a = int(r.integers(1, MERSENNE31))
+        b = int(r.integers(0, MERSENNE31))
+        v = torch.arange(n_vertices, dtype=torch.int64, device=pairs.device)
+        k = (v * a + b) % MERSENNE31
+        p64 = pairs.to(torch.int64) & 0xFFFFFFFF
+        ek = torch.maximum(k[p64[:, 0]], k[p64[:, 1]])
+        if target_edges >= pairs.shape[0]:
+            return pairs.contiguous()
+        t = torch.sort(ek).values[target_edges - 1] + 1
+        return pairs[ek < t].contiguous()
     k = vertex_keys(n_vertices, seed_q)
     ek = np.maximum(k[pairs[:, 0]], k[pairs[:, 1]])
     m = pairs.shape[0]

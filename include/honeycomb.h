@@ -47,7 +47,7 @@ typedef enum {
 } hc_status;
 
 #define HC_MAX_VARS 8
-#define HC_MAX_ATOMS 8
+#define HC_MAX_ATOMS 12
 
 /* One atom R_j(X_var0, X_var1): column 0 of its relation holds the values
  * of variable var0, column 1 those of var1 (var0 != var1).  With var1 =
@@ -245,6 +245,12 @@ typedef struct {
  * whatever the shares. */
 hc_status hc_run_join(const hc_query* q, const hc_index* const* idx, const hc_join_params* params,
                       void* stream, hc_result** out);
+
+/* Device memory a count-mode hc_run_join with these arguments may allocate
+ * at most (bytes), for admission control; host only, enqueues nothing.  The
+ * arguments are checked as hc_run_join checks them. */
+hc_status hc_join_footprint(const hc_query* q, const hc_index* const* idx, const hc_join_params* params,
+                            uint64_t* bytes_out);
 
 typedef struct {
     uint64_t count;             /* |Q|                                                */

@@ -22,7 +22,7 @@ from ._lib import HoneycombError
 
 __all__ = ["Query", "Index", "Partitioned", "Result", "build_index", "choose_shares", "run_join",
            "partition_index", "plan_cost", "HoneycombError", "TRIANGLE", "FOUR_CYCLE", "FOUR_DIAMOND", "FOUR_CLIQUE",
-           "TWO_TRIANGLE", "library_path", "kernel_launches", "Batch"]
+           "TWO_TRIANGLE", "library_path", "kernel_launches", "Batch", "run_join_async", "Pending", "join_footprint"]
 
 
 def library_path() -> str:
@@ -395,6 +395,45 @@ class Batch:
             self.free()
         except Exception:
             pass
+
+
+class Pending:
+    """A count-mode join enqueued without waiting; ``count()`` waits."""
+
+    def __init__(self, h):
+        self._h = _ResultHandle(h)
+
+    def count(self) -> int:
+        v = _lib.hc_result_view()
+        _lib.check(_lib.load().hc_result_get(ctypes.c_void_p(self._h.h), ctypes.byref(v)), "hc_result_get")
+        c = int(v.count)
+        self._h.free()
+        return c
+
+
+def join_footprint(query: Query, indexes: Sequence[Index], **options) -> int:
+    """Upper bound of the device bytes a count-mode join allocates (host only)."""
+    q = query._c()
+    ptr, keep = _index_array(indexes)
+    prm = _params(query, **options)
+    out = ctypes.c_uint64()
+    _lib.check(_lib.load().hc_join_footprint(ctypes.byref(q), ptr, ctypes.byref(prm), ctypes.byref(out)),
+               "hc_join_footprint")
+    return int(out.value)
+
+
+def run_join_async(query: Query, indexes: Sequence[Index], stream=None, **options) -> Pending:
+    """Enqueue a count-mode join and return at once (the library waits for
+    nothing in count mode); options as for ``run_join``."""
+    if len(indexes) != len(query.atoms):
+        raise ValueError("one index per atom")
+    q = query._c()
+    ptr, keep = _index_array(indexes)
+    prm = _params(query, **options)
+    out = ctypes.c_void_p()
+    _lib.check(_lib.load().hc_run_join(ctypes.byref(q), ptr, ctypes.byref(prm), ctypes.c_void_p(_stream_ptr(stream)),
+                                       ctypes.byref(out)), "hc_run_join")
+    return Pending(out.value)
 
 
 class _ResultHandle:

@@ -11,7 +11,7 @@ import os
 from . import build as _build
 
 HC_MAX_VARS = 8
-HC_MAX_ATOMS = 8
+HC_MAX_ATOMS = 12
 
 HC_MODE_COUNT = 0
 HC_MODE_MATERIALIZE = 1
@@ -84,6 +84,8 @@ SIGNATURES = {
                                    ctypes.POINTER(hc_join_params), ctypes.c_void_p,
                                    ctypes.POINTER(ctypes.c_void_p)]),
     "hc_result_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hc_result_view)]),
+    "hc_join_footprint": (ctypes.c_int, [ctypes.POINTER(hc_query), ctypes.POINTER(ctypes.c_void_p),
+                                         ctypes.POINTER(hc_join_params), ctypes.POINTER(ctypes.c_uint64)]),
     "hc_result_free": (ctypes.c_int, [ctypes.c_void_p]),
     "hc_batch_create": (ctypes.c_int, [ctypes.POINTER(hc_query), ctypes.POINTER(ctypes.c_void_p),
                                        ctypes.POINTER(hc_join_params), ctypes.c_uint32, ctypes.c_void_p,

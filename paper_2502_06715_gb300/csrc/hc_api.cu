@@ -124,7 +124,7 @@ static hc_status plan_inputs(const hc_query* q, const hc_index* const* idx, int*
     if (!q || !idx) return fail(HC_ERR_ARG, "plan: NULL argument");
     const int nv = (int)q->n_vars, na = (int)q->n_atoms;
     if (nv < 1 || nv > HC_MAX_VARS || na < 1 || na > HC_MAX_ATOMS)
-        return fail(HC_ERR_ARG, "plan: need 1..8 variables and 1..8 atoms");
+        return fail(HC_ERR_ARG, "plan: need 1..8 variables and 1..12 atoms");
     bool seen[HC_MAX_VARS] = {false};
     for (int i = 0; i < nv; ++i) {
         int v = q->order[i];
@@ -336,6 +336,11 @@ hc_status hc_run_join(const hc_query* q, const hc_index* const* idx, const hc_jo
 }
 
 hc_status hc_result_get(hc_result* r, hc_result_view* out) { return hc::result_get(r, out); }
+
+hc_status hc_join_footprint(const hc_query* q, const hc_index* const* idx, const hc_join_params* params,
+                            uint64_t* bytes_out) {
+    return hc::join_footprint_impl(q, idx, params, bytes_out);
+}
 
 hc_status hc_batch_create(const hc_query* qs, const hc_index* const* idx_flat, const hc_join_params* prm, uint32_t n,
                           void* stream, hc_batch** out) {

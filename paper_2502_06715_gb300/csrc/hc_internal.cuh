@@ -217,6 +217,8 @@ hc_status partitioned_sync(hc_partitioned* p);
 void result_release(hc_result* r);
 hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_join_params* prm, cudaStream_t s,
                         hc_result** out);
+hc_status join_footprint_impl(const hc_query* q, const hc_index* const* idx, const hc_join_params* prm,
+                              uint64_t* bytes);
 hc_status batch_create(const hc_query* qs, const hc_index* const* idx_flat, const hc_join_params* prm, uint32_t n,
                        cudaStream_t s, hc_batch** out);
 hc_status batch_launch(hc_batch* b, cudaStream_t s);

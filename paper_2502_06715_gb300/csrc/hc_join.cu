@@ -1100,11 +1100,11 @@ static void release_parts(std::vector<hc_partitioned*>& parts, cudaStream_t s) {
 }
 
 hc_status plan_query(const hc_query* q, const hc_index* const* idx, const hc_join_params* prm, cudaStream_t s,
-                     QueryPlan* out) {
+                     QueryPlan* out, uint64_t* partition_bytes = nullptr) {
     if (!q || !idx || !prm || !out) return fail(HC_ERR_ARG, "run_join: NULL argument");
     const int nv = (int)q->n_vars, na = (int)q->n_atoms;
     if (nv < 2 || nv > HC_MAX_VARS || na < 1 || na > HC_MAX_ATOMS)
-        return fail(HC_ERR_ARG, "run_join: need 2..8 variables and 1..8 atoms");
+        return fail(HC_ERR_ARG, "run_join: need 2..8 variables and 1..12 atoms");
     if (nv > 5) return fail(HC_ERR_CAPACITY, "run_join: queries of 2 to 5 variables are built in");
     if (prm->mode > HC_MODE_MATERIALIZE) return fail(HC_ERR_ARG, "run_join: unknown mode");
     int rank[HC_MAX_VARS];
@@ -1121,7 +1121,9 @@ hc_status plan_query(const hc_query* q, const hc_index* const* idx, const hc_joi
         if (a >= nv || (b >= nv && b != (int)HC_UNARY) || a == b)
             return fail(HC_ERR_ARG, "run_join: atom variables out of range or equal");
         if (!idx[j]) return fail(HC_ERR_ARG, "run_join: missing index for an atom");
-        if (idx[j]->stats_only) return fail(HC_ERR_ARG, "run_join: a statistics-only index has no data");
+        // a size estimate (partition_bytes given) needs no data
+        if (idx[j]->stats_only && !partition_bytes)
+            return fail(HC_ERR_ARG, "run_join: a statistics-only index has no data");
         covered[a] = true;
         if (b != (int)HC_UNARY) covered[b] = true;
     }
@@ -1183,6 +1185,12 @@ hc_status plan_query(const hc_query* q, const hc_index* const* idx, const hc_joi
             d.v2 = ix->d_v2;
             d.l1s = nullptr;
             d.l1_whole = (uint32_t)ix->l1;
+        } else if (partition_bytes) {
+            // estimate only: keys, levels and directory of the partitioned copy,
+            // plus the radix pass temporaries
+            const uint64_t n = ix->n, np = (uint64_t)pa * pb;
+            *partition_bytes += n * (8 + 8 + 4 + 4 + 4) + (np + 1) * 8 + ((n + 4095) / 4096) * 256 * 8 + 4096;
+            d.l1s = nullptr;
         } else {
             hc_partitioned* part = nullptr;
             const hc_status st =
@@ -1299,6 +1307,32 @@ hc_status enqueue_level1(const QueryPlan& qp, const Level1& L, JoinCtl* ctl, cud
     entries_total_kernel<<<1, 1, 0, s>>>(L.flagoff, L.candoff, (uint32_t)ncells, cb, ctl);
     if (cudaError_t le = launch_check()) return cuda_fail(le, "entries_total_kernel");
     HC_TRY(exclusive_scan_u64(L.e_units, L.uoff, cb, &ctl->n_entries, &ctl->err, s));
+    return HC_OK;
+}
+
+hc_status join_footprint_impl(const hc_query* q, const hc_index* const* idx, const hc_join_params* prm,
+                              uint64_t* bytes) {
+    if (!bytes) return fail(HC_ERR_ARG, "join_footprint: NULL argument");
+    QueryPlan qp;
+    uint64_t part_bytes = 0;
+    HC_TRY(plan_query(q, idx, prm, nullptr, &qp, &part_bytes));
+    // with partitioned atoms the bound uses their row counts (as run_join does)
+    uint64_t cb = 1;
+    {
+        uint64_t c = UINT64_MAX;
+        for (int q0 = 0; q0 < qp.P.nsrc[0]; ++q0) {
+            const int j = qp.P.src_atom[0][q0];
+            const DAtom& d = qp.P.atom[j];
+            const uint64_t rep = qp.ncells / ((uint64_t)d.share_f * d.share_s);
+            const uint64_t rows = ((uint64_t)d.share_f * d.share_s > 1) ? idx[j]->n : idx[j]->l1;
+            c = std::min<uint64_t>(c, rep * rows);
+        }
+        cb = std::max<uint64_t>(c, 1);
+    }
+    // loop-1 buffers (kept and temporary), per-cell arrays, scan look-back
+    // words and the control block
+    const uint64_t per_cand = 4 + 4 + 4 * 2 * MAXOPEN + 4 + 8 + 4 + 8 + 8;
+    *bytes = part_bytes + cb * per_cand + qp.ncells * (4 + 8 + 8) + ((cb + 2047) / 2048) * 8 * 3 + 65536;
     return HC_OK;
 }
 

@@ -1,0 +1,148 @@
+"""Continuous-batching join server over device-resident indexes.
+
+Relations are indexed once and stay in HBM.  A request names a query, the
+relation bound to each of its atoms and the values its first variable is
+restricted to (a unary atom, i.e. a selection pushed into the query,
+Sec. 2).  The loop admits queued requests while a stream slot is free and
+the request's device footprint (``join_footprint``) fits in what is left of
+the HBM budget; admitted requests run concurrently, one CUDA stream each, so
+their kernels overlap on the device; a finished request frees its slot and
+budget at once and the next queued one is admitted.  Arrival, admission
+and completion times are recorded per request.
+
+``serve_serial`` runs the same requests one at a time (FIFO) for the
+baseline and for the "alone" results.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import Index, Query, build_index, join_footprint, run_join, run_join_async
+
+
+@dataclass
+class Request:
+    rid: int
+    query: Query            # binary atoms first, then unary atoms over `restrict`
+    relations: tuple        # relation name per binary atom
+    restrict: np.ndarray    # values the unary atoms allow (sorted, distinct, uint32)
+    arrival: float = 0.0    # seconds from the start of the run
+
+
+@dataclass
+class Outcome:
+    rid: int
+    count: int
+    arrival: float
+    admitted: float
+    done: float
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+def _unary_pairs(values: np.ndarray, device) -> torch.Tensor:
+    v = np.ascontiguousarray(values, dtype=np.uint32)
+    pairs = np.stack([v, np.zeros_like(v)], axis=1)
+    return torch.from_numpy(pairs.view(np.int32)).to(device, non_blocking=False)
+
+
+@dataclass
+class Server:
+    indexes: dict                      # relation name -> Index (attr order 0)
+    budget_bytes: int = 120 << 30
+    max_inflight: int = 8
+    device: str = "cuda"
+    options: dict = field(default_factory=dict)
+
+    def _indexes(self, req: Request, unary: Index) -> list:
+        # every atom after the binary ones is a unary atom over the request's values
+        extra = len(req.query.atoms) - len(req.relations)
+        return [self.indexes[n] for n in req.relations] + [unary] * extra
+
+    def footprint(self, req: Request) -> int:
+        # a statistics-only stand-in for the request's unary index
+        n = max(1, int(req.restrict.shape[0]))
+        stand_in = Index.from_stats(n, n, 0, int(req.restrict.max()) if req.restrict.shape[0] else 0, 0)
+        return join_footprint(req.query, self._indexes(req, stand_in), **self.options)
+
+    def run(self, requests: list, realtime: bool = True) -> list:
+        """Serve requests arriving at req.arrival (seconds from now)."""
+        streams = collections.deque(torch.cuda.Stream(device=self.device) for _ in range(self.max_inflight))
+        order = sorted(requests, key=lambda r: r.arrival)
+        queue: collections.deque = collections.deque()
+        inflight = []
+        out = []
+        budget = self.budget_bytes
+        nxt = 0
+        t0 = time.perf_counter()
+        while nxt < len(order) or queue or inflight:
+            now = time.perf_counter() - t0
+            while nxt < len(order) and (not realtime or order[nxt].arrival <= now):
+                queue.append(order[nxt])
+                nxt += 1
+            # admit while a slot and the budget allow (head of line first)
+            while queue and streams:
+                req = queue[0]
+                fp = self.footprint(req)
+                if fp > budget and inflight:
+                    break
+                queue.popleft()
+                s = streams.popleft()
+                with torch.cuda.stream(s):
+                    unary = build_index(_unary_pairs(req.restrict, self.device), 0, stream=s)
+                    pend = run_join_async(req.query, self._indexes(req, unary), stream=s, **self.options)
+                    ev = torch.cuda.Event()
+                    ev.record(s)
+                budget -= fp
+                inflight.append((req, s, unary, pend, ev, fp, time.perf_counter() - t0))
+            # retire finished requests
+            still = []
+            for item in inflight:
+                req, s, unary, pend, ev, fp, t_adm = item
+                if ev.query():
+                    c = pend.count()
+                    unary.free()
+                    out.append(Outcome(req.rid, c, req.arrival, t_adm, time.perf_counter() - t0))
+                    budget += fp
+                    streams.append(s)
+                else:
+                    still.append(item)
+            inflight = still
+            if not queue and inflight and (nxt >= len(order) or order[nxt].arrival > time.perf_counter() - t0):
+                time.sleep(0)
+        return out
+
+
+def serve_serial(server: Server, requests: list) -> list:
+    """One request at a time, FIFO by arrival; returns per-request service
+    outcomes with arrival 0 (service time = done - admitted)."""
+    out = []
+    s = torch.cuda.Stream(device=server.device)
+    for req in sorted(requests, key=lambda r: r.rid):
+        t = time.perf_counter()
+        with torch.cuda.stream(s):
+            unary = build_index(_unary_pairs(req.restrict, server.device), 0, stream=s)
+            c = run_join(req.query, server._indexes(req, unary), stream=s, **server.options).count
+            unary.free()
+        s.synchronize()
+        out.append(Outcome(req.rid, c, 0.0, t, time.perf_counter()))
+    return out
+
+
+def fifo_latencies(service: list, arrivals: list) -> list:
+    """Latencies of a single FIFO server with the measured service times
+    (exact for serial execution)."""
+    free_at = 0.0
+    lat = []
+    for a, sv in sorted(zip(arrivals, service)):
+        start = max(a, free_at)
+        free_at = start + sv
+        lat.append(free_at - a)
+    return lat

@@ -70,3 +70,21 @@ def test_batch_rejects_three_shapes(hc):
     qs = [hc.TRIANGLE, hc.FOUR_CLIQUE, hc.FOUR_CYCLE]
     with pytest.raises(hc.HoneycombError):
         hc.Batch(qs, [[ix] * 3, [ix] * 6, [ixs] * 4])
+
+
+def test_autotuner_picks_a_valid_config(hc, tmp_path):
+    """The tuner's choice is one of its candidates and leaves the count unchanged."""
+    from paper_2502_06715_gb300.autotune import Tuner
+
+    sym = datagen.rmat_graph(12, 8, 9)
+    ep = datagen.orient_lt(sym)
+    ix = hc.build_index(dev(ep), 0)
+    want = oracle.gj_count(3, list(hc.TRIANGLE.atoms), [ep] * 3)[0]
+    path = str(tmp_path / "tune.json")
+    t = Tuner(path=path, reps=1)
+    cfg = t.tune(hc.TRIANGLE, [ix] * 3, P_list=(4, 16), min_cells=4)
+    assert int(np.prod(cfg.shares)) >= 4
+    assert hc.run_join(hc.TRIANGLE, [ix] * 3, **cfg.options()).count == want
+    # cached: a second tuner reads the file and returns the same choice
+    again = Tuner(path=path).tune(hc.TRIANGLE, [ix] * 3, P_list=(4, 16), min_cells=4)
+    assert again.shares == cfg.shares and again.item_grain == cfg.item_grain
