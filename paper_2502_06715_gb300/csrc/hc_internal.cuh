@@ -181,6 +181,9 @@ __device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
 // First index in [lo, hi) of sorted a[] whose value is >= x (hi if none).
 // Branch-free halving: each step keeps the upper half when its first
 // element is still below x.
+__device__ __forceinline__ uint32_t load_ro(const uint32_t* p) { return __ldg(p); }
+__device__ __forceinline__ uint32_t load_ro(uint32_t* p) { return *p; }
+
 template <typename P>
 __device__ __forceinline__ uint32_t lower_bound_u32(P a, uint32_t lo, uint32_t hi, uint32_t x) {
     uint32_t len = hi - lo;
@@ -188,10 +191,10 @@ __device__ __forceinline__ uint32_t lower_bound_u32(P a, uint32_t lo, uint32_t h
     uint32_t base = lo;
     while (len > 1) {
         const uint32_t half = len >> 1;
-        base = a[base + half] < x ? base + half : base;
+        base = load_ro(a + base + half) < x ? base + half : base;
         len -= half;
     }
-    return base + (a[base] < x ? 1u : 0u);
+    return base + (load_ro(a + base) < x ? 1u : 0u);
 }
 
 #endif  // __CUDACC__

@@ -478,12 +478,26 @@ __device__ __forceinline__ void merge_pair(const DPlan& P, const Entry<NL, S>& E
     // branch-free merge step: both heads are compared, the equal pair is
     // counted, and each side advances when its head is not the larger one
     if constexpr (!MAT) {
+        // software-pipelined: the heads x, y and the next elements xn, yn are
+        // in registers; each step issues the loads two positions ahead, so
+        // a step waits on no load issued in the same step
         uint32_t cnt = 0;
-        while (i < i1 && j < j1) {
-            const uint32_t x = la[i], y = lb[j];
-            cnt += x == y ? 1u : 0u;
-            i += x <= y ? 1u : 0u;
-            j += y <= x ? 1u : 0u;
+        if (i < i1 && j < j1) {
+            uint32_t x = __ldg(la + i), y = __ldg(lb + j);
+            uint32_t xn = __ldg(la + min(i + 1, i1 - 1)), yn = __ldg(lb + min(j + 1, j1 - 1));
+            for (;;) {
+                cnt += x == y ? 1u : 0u;
+                const bool ax = x <= y, ay = y <= x;
+                i += ax ? 1u : 0u;
+                j += ay ? 1u : 0u;
+                if (i >= i1 || j >= j1) break;
+                const uint32_t xnn = __ldg(la + min(i + 1, i1 - 1));
+                const uint32_t ynn = __ldg(lb + min(j + 1, j1 - 1));
+                x = ax ? xn : x;
+                xn = ax ? xnn : xn;
+                y = ay ? yn : y;
+                yn = ay ? ynn : yn;
+            }
         }
         A.count += __reduce_add_sync(0xffffffffu, cnt);
     } else {
