@@ -107,12 +107,15 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     return t;
 }
 
-__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+// Look-back status words carry their value in the same 64-bit word as the
+// flags, so plain relaxed (coherent, unordered) accesses at GPU scope suffice:
+// no other memory is read on the strength of a flag.
+__device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
     uint64_t v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -122,33 +125,43 @@ constexpr uint64_t LB_INC = 2ull << 62;
 constexpr uint64_t LB_VAL = (1ull << 62) - 1;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // a single wait gives up after 2 s
 
-// Exclusive prefix of tile `tile` for one counter, by decoupled look-back
-// (Merrill & Garland, 2016) over status[t * stride].  Predecessor tiles have
-// all started (tile ids are taken in launch order), so each wait ends unless
-// the device stalls; a wait longer than WAIT_LIMIT_NS sets DEV_ERR_TIMEOUT in
-// *err and returns what it has.
-__device__ __forceinline__ uint64_t lookback_prefix(uint64_t* status, uint32_t stride, uint32_t tile,
-                                                    uint32_t* err) {
+__device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+// Exclusive prefix of tile `tile` by decoupled look-back (Merrill & Garland,
+// 2016) over one status word per tile, by a whole warp: lane q reads the word
+// of tile top - q, so each round covers 32 predecessors; the round sums the
+// values up to the nearest inclusive word and stops there.  Tile ids are
+// taken in launch order, so every predecessor has started and each wait
+// ends unless the device stalls; a wait longer than WAIT_LIMIT_NS sets
+// DEV_ERR_TIMEOUT in *err and returns what it has.  All 32 lanes call it and
+// all get the result.
+__device__ __forceinline__ uint64_t warp_lookback(const uint64_t* status, uint32_t tile, uint32_t* err) {
+    const uint32_t lane = threadIdx.x & 31u;
     uint64_t excl = 0;
-    int64_t t = (int64_t)tile - 1;
-    while (t >= 0) {
-        const uint64_t* p = status + (uint64_t)t * stride;
-        uint64_t w = ld_acquire(p);
-        if ((w & ~LB_VAL) == 0) {
-            uint64_t t0 = globaltimer_ns();
-            uint32_t spins = 0;
-            do {
-                if (++spins > 64) __nanosleep(64);
-                w = ld_acquire(p);
-                if ((w & ~LB_VAL) == 0 && globaltimer_ns() - t0 > WAIT_LIMIT_NS) {
-                    atomicOr(err, DEV_ERR_TIMEOUT);
-                    return excl;
-                }
-            } while ((w & ~LB_VAL) == 0);
+    int64_t top = (int64_t)tile - 1;
+    const uint64_t t0 = globaltimer_ns();
+    while (top >= 0) {
+        const int64_t t = top - (int64_t)lane;
+        uint64_t x = t >= 0 ? ld_relaxed(status + t) : LB_INC;  // before tile 0: an inclusive zero
+        for (uint32_t spins = 0;; ++spins) {
+            const bool ready = (x & ~LB_VAL) != 0;
+            if (__all_sync(0xffffffffu, ready)) break;
+            if (__any_sync(0xffffffffu, globaltimer_ns() - t0 > WAIT_LIMIT_NS)) {
+                if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+                return excl;
+            }
+            if (spins > 16) __nanosleep(32);
+            if (!ready) x = ld_relaxed(status + t);
         }
-        excl += w & LB_VAL;
-        if (w & LB_INC) break;
-        --t;
+        const uint32_t incm = __ballot_sync(0xffffffffu, (x & LB_INC) != 0);
+        const uint32_t upto = incm ? (uint32_t)__ffs(incm) - 1u : 31u;
+        excl += warp_sum64(lane <= upto ? (x & LB_VAL) : 0);
+        if (incm) break;
+        top -= 32;
     }
     return excl;
 }
@@ -172,12 +185,6 @@ __device__ __forceinline__ uint64_t warp_incl_scan64(uint64_t v) {
     }
     return v;
 }
-__device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-    return v;
-}
-
 // First index in [lo, hi) of sorted a[] whose value is >= x (hi if none).
 // Branch-free halving: each step keeps the upper half when its first
 // element is still below x.

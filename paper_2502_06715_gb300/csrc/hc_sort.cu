@@ -114,96 +114,175 @@ __global__ void digit_scan_kernel(uint32_t* __restrict__ ghist) {
 }
 
 // --------------------------------------------------------- onesweep pass
-// One stable LSD pass over 8 bits.  Each tile ranks its keys per digit
-// (warp-private counters, __match_any_sync peers), gets its global digit
-// offsets by decoupled look-back over the tiles before it, stages the keys in
-// shared memory in digit order and writes each digit run contiguously.
-template <bool FROM_PAIRS>
-__global__ void __launch_bounds__(SORT_THREADS) onesweep_kernel(
-    const void* __restrict__ in, uint64_t* __restrict__ out, uint64_t n, uint32_t ao, DigitSpec ds,
+// One stable LSD pass over 8 bits (Adinets & Merrill's single-pass "onesweep"
+// structure).  A tile of PASS_TILE keys is loaded into registers, every key is
+// ranked among the equal digits before it in its warp, the warps' digit
+// counts are scanned into the tile's digit runs, and the tile's global digit
+// offsets come from a decoupled look-back over the tiles before it.  The keys
+// are staged in shared memory in digit order and each digit run is written
+// contiguously.  Row counts are below 2^32, so offsets are 32-bit.
+//
+// Ranking: lanes holding the same digit find each other through a per-warp,
+// per-digit word in shared memory that each lane ORs its lane bit into; the
+// group's highest lane advances the warp's digit counter by the group size.
+// Ranks follow (item, lane) order, which is the tile's row order, so the
+// pass is stable.
+constexpr int PASS_THREADS = 256;
+constexpr int PASS_WARPS = PASS_THREADS / 32;
+constexpr int PASS_ITEMS = 24;
+constexpr int PASS_TILE = PASS_THREADS * PASS_ITEMS;  // 6144 keys per tile
+constexpr int PASS_LOOKBACK = 8;                      // status words read per look-back round
+
+enum : int { SRC_KEYS = 0, SRC_PAIRS = 1 };
+enum : int { DIGIT_BYTE = 0, DIGIT_PARTITION = 1 };
+
+template <int DIG>
+__device__ __forceinline__ uint32_t pass_digit(uint64_t key, const DigitSpec& d) {
+    if (DIG == DIGIT_BYTE) return (uint32_t)(key >> d.shift) & 0xFFu;
+    return (partition_id(key, d.seed_a, d.pa, d.seed_b, d.pb) >> d.shift) & 0xFFu;
+}
+
+// Exclusive prefix of one digit's count over the tiles before `tile`:
+// status[t * RADIX] holds tile t's word for this digit.  Each round reads
+// PASS_LOOKBACK words at once and stops at the nearest inclusive one.
+__device__ __forceinline__ uint64_t digit_lookback(const uint64_t* status, uint32_t tile, uint32_t* err) {
+    uint64_t excl = 0;
+    int64_t t = (int64_t)tile - 1;
+    while (t >= 0) {
+        uint64_t wv[PASS_LOOKBACK];
+#pragma unroll
+        for (int q = 0; q < PASS_LOOKBACK; ++q)
+            wv[q] = (t - q >= 0) ? ld_relaxed(status + (uint64_t)(t - q) * RADIX) : LB_INC;
+        bool done = false;
+#pragma unroll
+        for (int q = 0; q < PASS_LOOKBACK; ++q) {
+            if (done) continue;
+            uint64_t x = wv[q];
+            if ((x & ~LB_VAL) == 0) {
+                const uint64_t* p = status + (uint64_t)(t - q) * RADIX;
+                const uint64_t t0 = globaltimer_ns();
+                uint32_t spins = 0;
+                do {
+                    if (++spins > 16) __nanosleep(32);
+                    x = ld_relaxed(p);
+                    if ((x & ~LB_VAL) == 0 && globaltimer_ns() - t0 > WAIT_LIMIT_NS) {
+                        atomicOr(err, DEV_ERR_TIMEOUT);
+                        return excl;
+                    }
+                } while ((x & ~LB_VAL) == 0);
+            }
+            excl += x & LB_VAL;
+            done = (x & LB_INC) != 0;
+        }
+        if (done) break;
+        t -= PASS_LOOKBACK;
+    }
+    return excl;
+}
+
+template <int SRC, int DIG>
+__global__ void __launch_bounds__(PASS_THREADS, 2) onesweep_kernel(
+    const void* __restrict__ in, uint64_t* __restrict__ out, uint32_t n, uint32_t ao, DigitSpec ds,
     const uint32_t* __restrict__ gbase, uint64_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
     uint32_t* __restrict__ err) {
-    __shared__ uint64_t skeys[SORT_TILE];
-    __shared__ uint8_t sdig[SORT_TILE];
-    __shared__ uint32_t whist[SORT_WARPS][RADIX];
-    __shared__ uint32_t local_start[RADIX];
-    __shared__ uint64_t goff[RADIX];
-    __shared__ uint32_t wsum[SORT_WARPS];
+    constexpr bool KEEP_DIGITS = DIG == DIGIT_PARTITION;  // hashing twice costs more than a byte of smem
+    __shared__ uint64_t skeys[PASS_TILE];
+    __shared__ uint8_t sdig[KEEP_DIGITS ? PASS_TILE : 1];
+    __shared__ uint32_t whist[PASS_WARPS][RADIX];  // per-warp digit counters, later run starts
+    __shared__ uint32_t peers_word[PASS_WARPS][RADIX];
+    __shared__ uint32_t goff[RADIX];
+    __shared__ uint32_t wsum[PASS_WARPS];
     __shared__ uint32_t s_tile;
 
     const uint32_t tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
-    for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_THREADS) (&whist[0][0])[i] = 0;
+    for (int i = tid; i < PASS_WARPS * RADIX; i += PASS_THREADS) {
+        (&whist[0][0])[i] = 0;
+        (&peers_word[0][0])[i] = 0;
+    }
     __syncthreads();
     const uint32_t tile = s_tile;
-    const uint64_t base = (uint64_t)tile * SORT_TILE;
+    const uint32_t base = tile * (uint32_t)PASS_TILE;
+    const uint32_t wb = base + w * (PASS_ITEMS * 32) + lane;  // row of item 0 of this lane
+    const bool full = n - base >= (uint32_t)PASS_TILE;
 
-    uint64_t k[SORT_ITEMS];
-    uint32_t rank[SORT_ITEMS];
-    uint32_t dig[SORT_ITEMS];
+    // all loads first, so that they are in flight together
+    uint64_t k[PASS_ITEMS];
 #pragma unroll
-    for (int j = 0; j < SORT_ITEMS; ++j) {
-        uint64_t i = base + (uint64_t)w * (SORT_ITEMS * 32) + (uint64_t)j * 32 + lane;
-        bool valid = i < n;
-        uint64_t key = 0;
-        if (valid) key = FROM_PAIRS ? pack_row((const uint2*)in, i, ao) : ((const uint64_t*)in)[i];
-        uint32_t d = valid ? digit_of(key, ds) : RADIX;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t leader = __ffs(peers) - 1;
-        uint32_t b = 0;
-        if (lane == leader && d < RADIX) {
+    for (int j = 0; j < PASS_ITEMS; ++j) {
+        const uint32_t i = wb + j * 32;
+        k[j] = 0;
+        if (full || i < n) k[j] = SRC == SRC_PAIRS ? pack_row((const uint2*)in, i, ao) : ((const uint64_t*)in)[i];
+    }
+
+    const uint32_t lt = lanemask_lt();
+    uint32_t rp[PASS_ITEMS];  // rank among the warp's equal digits | digit << 16 (digit RADIX: no row)
+#pragma unroll
+    for (int j = 0; j < PASS_ITEMS; ++j) {
+        const bool valid = full || wb + j * 32 < n;
+        const uint32_t d = valid ? pass_digit<DIG>(k[j], ds) : RADIX;
+        uint32_t peers = 0, b = 0;
+        if (valid) atomicOr(&peers_word[w][d], 1u << lane);
+        __syncwarp();
+        if (valid) peers = peers_word[w][d];
+        __syncwarp();
+        const uint32_t below = __popc(peers & lt);
+        if (valid && (peers >> lane) == 1u) {  // highest lane of the group
             b = whist[w][d];
-            whist[w][d] = b + __popc(peers);
+            whist[w][d] = b + below + 1u;
+            peers_word[w][d] = 0;
         }
-        b = __shfl_sync(0xffffffffu, b, leader);
-        k[j] = key;
-        dig[j] = d;
-        rank[j] = b + __popc(peers & lanemask_lt());
+        b = __shfl_sync(0xffffffffu, b, valid ? 31u - __clz(peers) : lane);
+        rp[j] = (b + below) | (d << 16);
         __syncwarp();
     }
     __syncthreads();
 
-    // per digit: exclusive prefix over warps, tile total, look-back
+    // per digit (one per thread): warp prefix, tile total, aggregate published
     const uint32_t d = tid;
     uint32_t run = 0;
 #pragma unroll
-    for (int ww = 0; ww < SORT_WARPS; ++ww) {
-        uint32_t c = whist[ww][d];
-        whist[ww][d] = run;
+    for (int q = 0; q < PASS_WARPS; ++q) {
+        const uint32_t c = whist[q][d];
+        whist[q][d] = run;
         run += c;
     }
     uint64_t* st = status + (uint64_t)tile * RADIX + d;
-    uint64_t excl = 0;
-    if (tile == 0) {
-        st_release(st, LB_INC | run);
-    } else {
-        st_release(st, LB_AGG | run);
-        excl = lookback_prefix(status + d, RADIX, tile, err);
-        st_release(st, LB_INC | (excl + run));
-    }
-    // tile-local digit starts (block exclusive scan of the tile totals)
-    uint32_t inc = warp_incl_scan(run);
+    st_relaxed(st, (tile == 0 ? LB_INC : LB_AGG) | run);
+    const uint32_t inc = warp_incl_scan(run);
     if (lane == 31) wsum[w] = inc;
     __syncthreads();
-    uint32_t add = 0;
-    for (uint32_t q = 0; q < w; ++q) add += wsum[q];
-    const uint32_t lstart = inc - run + add;
-    local_start[d] = lstart;
-    goff[d] = (uint64_t)gbase[d] + excl - (uint64_t)lstart;
+    uint32_t lstart = inc - run;
+#pragma unroll
+    for (uint32_t q = 0; q < (uint32_t)PASS_WARPS; ++q) lstart += q < w ? wsum[q] : 0u;
+#pragma unroll
+    for (int q = 0; q < PASS_WARPS; ++q) whist[q][d] += lstart;
     __syncthreads();
 
+    // stage the tile in digit order (keys leave the registers before the look-back)
 #pragma unroll
-    for (int j = 0; j < SORT_ITEMS; ++j) {
-        if (dig[j] < RADIX) {
-            uint32_t pos = local_start[dig[j]] + whist[w][dig[j]] + rank[j];
+    for (int j = 0; j < PASS_ITEMS; ++j) {
+        const uint32_t dg = rp[j] >> 16;
+        if (full || dg < RADIX) {
+            const uint32_t pos = whist[w][dg] + (rp[j] & 0xFFFFu);
             skeys[pos] = k[j];
-            sdig[pos] = (uint8_t)dig[j];
+            if (KEEP_DIGITS) sdig[pos] = (uint8_t)dg;
         }
     }
+    uint64_t excl = 0;
+    if (tile != 0) {
+        excl = digit_lookback(status + d, tile, err);
+        st_relaxed(st, LB_INC | (excl + run));
+    }
+    goff[d] = gbase[d] + (uint32_t)excl - lstart;  // mod 2^32; goff + row is below n
     __syncthreads();
-    const uint64_t remain = n - base;
-    const uint32_t tile_n = remain < (uint64_t)SORT_TILE ? (uint32_t)remain : (uint32_t)SORT_TILE;
-    for (uint32_t i = tid; i < tile_n; i += SORT_THREADS) out[goff[sdig[i]] + i] = skeys[i];
+
+    const uint32_t tile_n = full ? (uint32_t)PASS_TILE : n - base;
+    for (uint32_t i = tid; i < tile_n; i += PASS_THREADS) {
+        const uint64_t key = skeys[i];
+        const uint32_t dg = KEEP_DIGITS ? sdig[i] : pass_digit<DIG>(key, ds);
+        out[goff[dg] + i] = key;
+    }
 }
 
 // Pack rows into keys without sorting (a relation with a single key value).
@@ -217,11 +296,14 @@ __global__ void pack_kernel(const uint2* __restrict__ pairs, uint64_t* __restric
 // Single pass over the sorted keys.  Row i opens a level-1 entry when its
 // first attribute (or, with SEGMENTED, its partition id) differs from row
 // i-1.  Flags are counted with ballots, the tile's offset comes from a
-// decoupled look-back, and every flagged row writes V1[pos] = first value and
-// O1[pos] = i; every row writes V2[i] = second value.  The last tile writes
-// O1[l1] = n and l1.  Equal adjacent keys mark a duplicate row.
+// decoupled look-back (one warp reads 32 predecessors per round), and every
+// flagged row writes V1[pos] = first value and O1[pos] = i; every row writes
+// V2[i] = second value.  The last tile writes O1[l1] = n and l1.  Equal
+// adjacent keys mark a duplicate row.  Rows are warp-striped: item j of lane
+// q of warp w is row tile * SORT_TILE + w * 32 * SORT_ITEMS + 32 j + q, so
+// row i-1 of a lane-0 row is lane 31's row of the previous item.
 template <bool SEGMENTED>
-__global__ void __launch_bounds__(SORT_THREADS) boundary_kernel(
+__global__ void __launch_bounds__(SORT_THREADS, 3) boundary_kernel(
     const uint64_t* __restrict__ keys, uint64_t n, uint32_t seed_a, uint32_t pa, uint32_t seed_b,
     uint32_t pb, uint32_t* __restrict__ v1, uint32_t* __restrict__ o1, uint32_t* __restrict__ v2,
     uint64_t* __restrict__ status, uint32_t* __restrict__ tile_counter, Ctl* __restrict__ ctl) {
@@ -233,54 +315,67 @@ __global__ void __launch_bounds__(SORT_THREADS) boundary_kernel(
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint64_t base = (uint64_t)tile * SORT_TILE + (uint64_t)w * (SORT_ITEMS * 32);
+    const bool full = base + SORT_ITEMS * 32 <= n;
 
     uint64_t k[SORT_ITEMS];
+#pragma unroll
+    for (int j = 0; j < SORT_ITEMS; ++j) {
+        const uint64_t i = base + (uint64_t)j * 32 + lane;
+        k[j] = (full || i < n) ? keys[i] : 0;
+    }
+    // the row before the warp's first row
+    uint64_t carry = (lane == 0 && base > 0 && base < n) ? keys[base - 1] : 0;
+    auto pid = [&](uint64_t key) { return partition_id(key, seed_a, pa, seed_b, pb); };
+    uint32_t carry_pid = SEGMENTED && lane == 0 && base > 0 && base < n ? pid(carry) : 0;
+
     uint32_t ball[SORT_ITEMS];
     uint32_t wcount = 0;
     bool dup = false;
 #pragma unroll
     for (int j = 0; j < SORT_ITEMS; ++j) {
-        uint64_t i = base + (uint64_t)j * 32 + lane;
-        bool valid = i < n;
-        uint64_t key = valid ? keys[i] : 0;
-        uint64_t prev = __shfl_up_sync(0xffffffffu, key, 1);
-        if (lane == 0 && valid && i > 0) prev = keys[i - 1];
+        const uint64_t i = base + (uint64_t)j * 32 + lane;
+        const bool valid = full || i < n;
+        const uint32_t my_pid = SEGMENTED ? pid(k[j]) : 0;
+        uint64_t prev = __shfl_up_sync(0xffffffffu, k[j], 1);
+        uint32_t prev_pid = SEGMENTED ? __shfl_up_sync(0xffffffffu, my_pid, 1) : 0;
+        if (lane == 0) {
+            prev = carry;
+            prev_pid = carry_pid;
+        }
         bool flag = false;
         if (valid) {
-            if (i == 0) {
-                flag = true;
-            } else if (SEGMENTED) {
-                flag = (prev >> 32) != (key >> 32) ||
-                       partition_id(prev, seed_a, pa, seed_b, pb) != partition_id(key, seed_a, pa, seed_b, pb);
-            } else {
-                flag = (prev >> 32) != (key >> 32);
-            }
-            dup |= i > 0 && prev == key;
+            flag = i == 0 || (prev >> 32) != (k[j] >> 32) || (SEGMENTED && prev_pid != my_pid);
+            dup |= i > 0 && prev == k[j];
         }
         ball[j] = __ballot_sync(0xffffffffu, flag);
         wcount += __popc(ball[j]);
-        k[j] = key;
+        // lane 31's row precedes lane 0's row of the next item
+        const uint64_t last = __shfl_sync(0xffffffffu, k[j], 31);
+        const uint32_t last_pid = SEGMENTED ? __shfl_sync(0xffffffffu, my_pid, 31) : 0;
+        if (lane == 0) {
+            carry = last;
+            carry_pid = last_pid;
+        }
     }
     if (__any_sync(0xffffffffu, dup) && lane == 0) atomicOr(&ctl->dup, 1u);
     if (lane == 0) wsum[w] = wcount;
     __syncthreads();
-    if (tid == 0) {
-        uint32_t tot = 0;
-        for (int q = 0; q < SORT_WARPS; ++q) tot += wsum[q];
+    if (w == 0) {
+        const uint32_t tot = warp_sum64(lane < (uint32_t)SORT_WARPS ? wsum[lane] : 0u);
         uint64_t* st = status + tile;
+        if (lane == 0) st_relaxed(st, (tile == 0 ? LB_INC : LB_AGG) | tot);
         uint64_t excl = 0;
-        if (tile == 0) {
-            st_release(st, LB_INC | tot);
-        } else {
-            st_release(st, LB_AGG | tot);
-            excl = lookback_prefix(status, 1, tile, &ctl->err);
-            st_release(st, LB_INC | (excl + tot));
+        if (tile != 0) {
+            excl = warp_lookback(status, tile, &ctl->err);
+            if (lane == 0) st_relaxed(st, LB_INC | (excl + tot));
         }
-        s_excl = excl;
-        uint64_t tile_end = (uint64_t)tile * SORT_TILE + SORT_TILE;
-        if (tile_end >= n) {  // the tile holding the last row closes the arrays
-            o1[excl + tot] = (uint32_t)n;
-            ctl->l1 = (uint32_t)(excl + tot);
+        if (lane == 0) {
+            s_excl = excl;
+            const uint64_t tile_end = (uint64_t)tile * SORT_TILE + SORT_TILE;
+            if (tile_end >= n) {  // the tile holding the last row closes the arrays
+                o1[excl + tot] = (uint32_t)n;
+                ctl->l1 = (uint32_t)(excl + tot);
+            }
         }
     }
     __syncthreads();
@@ -288,11 +383,11 @@ __global__ void __launch_bounds__(SORT_THREADS) boundary_kernel(
     for (uint32_t q = 0; q < w; ++q) pos += wsum[q];
 #pragma unroll
     for (int j = 0; j < SORT_ITEMS; ++j) {
-        uint64_t i = base + (uint64_t)j * 32 + lane;
-        if (i < n) {
+        const uint64_t i = base + (uint64_t)j * 32 + lane;
+        if (full || i < n) {
             v2[i] = (uint32_t)k[j];
             if (ball[j] >> lane & 1u) {
-                uint64_t p = pos + __popc(ball[j] & lanemask_lt());
+                const uint64_t p = pos + __popc(ball[j] & lanemask_lt());
                 v1[p] = (uint32_t)(k[j] >> 32);
                 o1[p] = (uint32_t)i;
             }
@@ -330,8 +425,11 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 // Exclusive scan of in[0..n) into out[0..n), out[n] = total.  n is read from
 // *d_n when given (a count produced on the device), else n_max is used; the
-// grid covers n_max elements and tiles past n contribute nothing.
-template <typename T>
+// grid covers n_max elements and tiles past n contribute nothing.  Thread t
+// of a tile owns SCAN_ITEMS consecutive elements; with VEC (both arrays
+// 16-byte aligned) a full tile moves them as 16-byte vectors.  The tile
+// offset comes from a warp-wide decoupled look-back.
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(SCAN_THREADS) scan_kernel(const T* __restrict__ in, uint64_t* __restrict__ out,
                                                             uint64_t n_max, const uint32_t* __restrict__ d_n,
                                                             uint64_t* __restrict__ status,
@@ -347,39 +445,66 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_kernel(const T* __restrict_
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint64_t base = (uint64_t)tile * SCAN_TILE + (uint64_t)tid * SCAN_ITEMS;
+    const bool full = (uint64_t)(tile + 1) * SCAN_TILE <= n;
     uint64_t v[SCAN_ITEMS];
+    if (VEC && full) {
+        constexpr int PER = 16 / sizeof(T);
+#pragma unroll
+        for (int q = 0; q < SCAN_ITEMS / PER; ++q) {
+            const uint4 u = reinterpret_cast<const uint4*>(in + base)[q];
+            if (sizeof(T) == 4) {
+                v[q * 4 + 0] = u.x;
+                v[q * 4 + 1] = u.y;
+                v[q * 4 + 2] = u.z;
+                v[q * 4 + 3] = u.w;
+            } else {
+                v[q * 2 + 0] = ((uint64_t)u.y << 32) | u.x;
+                v[q * 2 + 1] = ((uint64_t)u.w << 32) | u.z;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; ++j) v[j] = base + j < n ? (uint64_t)in[base + j] : 0;
+    }
     uint64_t sum = 0;
 #pragma unroll
-    for (int j = 0; j < SCAN_ITEMS; ++j) {
-        v[j] = base + j < n ? (uint64_t)in[base + j] : 0;
-        sum += v[j];
-    }
-    uint64_t inc = warp_incl_scan64(sum);
+    for (int j = 0; j < SCAN_ITEMS; ++j) sum += v[j];
+    const uint64_t inc = warp_incl_scan64(sum);
     if (lane == 31) wsum[w] = inc;
     __syncthreads();
-    if (tid == 0) {
-        uint64_t tot = 0;
-        for (int q = 0; q < SCAN_THREADS / 32; ++q) tot += wsum[q];
+    if (w == 0) {
+        const uint64_t tot = warp_sum64(lane < (uint32_t)(SCAN_THREADS / 32) ? wsum[lane] : 0);
         uint64_t* st = status + tile;
+        if (lane == 0) st_relaxed(st, (tile == 0 ? LB_INC : LB_AGG) | tot);
         uint64_t excl = 0;
-        if (tile == 0) {
-            st_release(st, LB_INC | tot);
-        } else {
-            st_release(st, LB_AGG | tot);
-            excl = lookback_prefix(status, 1, tile, err);
-            st_release(st, LB_INC | (excl + tot));
+        if (tile != 0) {
+            excl = warp_lookback(status, tile, err);
+            if (lane == 0) st_relaxed(st, LB_INC | (excl + tot));
         }
-        s_excl = excl;
-        const uint64_t last = ntiles ? (n / SCAN_TILE < ntiles - 1 ? n / SCAN_TILE : ntiles - 1) : 0;
-        if (tile == last) out[n] = excl + tot;
+        if (lane == 0) {
+            s_excl = excl;
+            const uint64_t last = ntiles ? (n / SCAN_TILE < ntiles - 1 ? n / SCAN_TILE : ntiles - 1) : 0;
+            if (tile == last) out[n] = excl + tot;
+        }
     }
     __syncthreads();
     uint64_t run = s_excl + inc - sum;
     for (uint32_t q = 0; q < w; ++q) run += wsum[q];
+    if (VEC && full) {
 #pragma unroll
-    for (int j = 0; j < SCAN_ITEMS; ++j) {
-        if (base + j < n) out[base + j] = run;
-        run += v[j];
+        for (int q = 0; q < SCAN_ITEMS / 2; ++q) {
+            const uint64_t a = run;
+            const uint64_t b = run + v[2 * q];
+            run = b + v[2 * q + 1];
+            reinterpret_cast<uint4*>(out + base)[q] =
+                make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; ++j) {
+            if (base + j < n) out[base + j] = run;
+            run += v[j];
+        }
     }
 }
 
@@ -433,8 +558,8 @@ hc_status radix_passes(const void* src, bool src_pairs, uint32_t ao, uint64_t n,
     digit_scan_kernel<<<np, RADIX, 0, s>>>(d_hist);
     HC_CUDA_TRY(launch_check());
 
-    const uint64_t ntiles = (n + SORT_TILE - 1) / SORT_TILE;
-    if (ntiles > 0xFFFFFFFFull) return fail(HC_ERR_CAPACITY, "too many sort tiles");
+    if (n >= 0xFFFFFFFFull) return fail(HC_ERR_CAPACITY, "radix sort: n must be below 2^32 - 1");
+    const uint64_t ntiles = (n + PASS_TILE - 1) / PASS_TILE;
     uint64_t* status;
     uint64_t* alt = nullptr;
     HC_TRY(tmp.get(&status, ntiles * RADIX));
@@ -443,16 +568,18 @@ hc_status radix_passes(const void* src, bool src_pairs, uint32_t ao, uint64_t n,
     uint64_t* bufs[2] = {dst, alt};
     int cur = (np % 2 == 1) ? 0 : 1;  // buffer written by pass 0
     const void* in = src;
+    const uint32_t n32 = (uint32_t)n;
     for (int p = 0; p < np; ++p) {
         uint64_t* outb = bufs[cur];
         if (outb == nullptr) return fail(HC_ERR_ARG, "internal: radix buffer");
+        const bool from_pairs = p == 0 && src_pairs;
+        if (from_pairs && specs[p].mode != 0) return fail(HC_ERR_ARG, "internal: partition digits of raw pairs");
         HC_CUDA_TRY(cudaMemsetAsync(status, 0, ntiles * RADIX * sizeof(uint64_t), s));
-        if (p == 0 && src_pairs)
-            onesweep_kernel<true><<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(
-                in, outb, n, ao, specs[p], d_hist + p * RADIX, status, &d_ctl->tile_counter[p], &d_ctl->err);
-        else
-            onesweep_kernel<false><<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(
-                in, outb, n, ao, specs[p], d_hist + p * RADIX, status, &d_ctl->tile_counter[p], &d_ctl->err);
+        auto* kern = from_pairs              ? onesweep_kernel<SRC_PAIRS, DIGIT_BYTE>
+                     : specs[p].mode == 0 ? onesweep_kernel<SRC_KEYS, DIGIT_BYTE>
+                                          : onesweep_kernel<SRC_KEYS, DIGIT_PARTITION>;
+        kern<<<(unsigned)ntiles, PASS_THREADS, 0, s>>>(in, outb, n32, ao, specs[p], d_hist + p * RADIX, status,
+                                                       &d_ctl->tile_counter[p], &d_ctl->err);
         HC_CUDA_TRY(launch_check());
         in = outb;
         cur ^= 1;
@@ -664,7 +791,10 @@ hc_status exclusive_scan_impl(const T* d_in, uint64_t* d_out, uint64_t n_max, co
     HC_TRY(tmp.get(&ctr, 1));
     HC_CUDA_TRY(cudaMemsetAsync(status, 0, ntiles * sizeof(uint64_t), s));
     HC_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t), s));
-    scan_kernel<T><<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(d_in, d_out, n_max, d_n, status, ctr, d_err);
+    if ((((uintptr_t)d_in | (uintptr_t)d_out) & 15u) == 0)
+        scan_kernel<T, true><<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(d_in, d_out, n_max, d_n, status, ctr, d_err);
+    else
+        scan_kernel<T, false><<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(d_in, d_out, n_max, d_n, status, ctr, d_err);
     HC_CUDA_TRY(launch_check());
     return HC_OK;
 }
