@@ -38,6 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "join output tuples/s (R-MAT triangle)"
 UNIT = "tuples/s"
 PROFILE_NOTE = os.path.join(ROOT, "profiles", "gj_search_kernel_rmat22.md")
+BUILD_PROFILE_NOTE = os.path.join(ROOT, "profiles", "radix_pass_rmat22_build.md")
 
 
 def parse_args():
@@ -50,9 +51,11 @@ def parse_args():
     ap.add_argument("--edge-factor", type=int, default=16)
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--mode", choices=["materialize", "count"], default="materialize")
-    ap.add_argument("--workload", choices=["triangle", "clique4", "cycle4", "batched", "serve"], default="triangle",
+    ap.add_argument("--workload", choices=["triangle", "clique4", "cycle4", "batched", "serve", "build"],
+                    default="triangle",
                     help="triangle: R-MAT triangle (default line); clique4 / cycle4: R-MAT 4-clique / 4-cycle "
-                         "counts; batched: 512 triangle/4-clique queries on induced subgraphs in one launch")
+                         "counts; batched: 512 triangle/4-clique queries on induced subgraphs in one launch; "
+                         "serve: continuous-batching server; build: CoCo index build of R-MAT E+")
     ap.add_argument("--shares", default="autotune",
                     help="'autotune' (timed search from the paper's plan over HyperCube share vectors of "
                          ">= --min-cells cells and kernel schedules), 'plan' (Sec. 5.3 decision at --P cells), "
@@ -135,6 +138,15 @@ class ClockSampler:
                                          stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+        # nvidia-smi's start-up stalls the GPU for up to a second or so:
+        # start timing only once it has produced its first sample
+        self.first = []
+        if self.proc is not None:
+            import select
+
+            ready, _, _ = select.select([self.proc.stdout], [], [], 15.0)
+            if ready:
+                self.first.append(self.proc.stdout.readline())
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -146,7 +158,11 @@ class ClockSampler:
             self.proc.kill()
             out, _ = self.proc.communicate()
         sm, mx, reasons = [], [], set()
-        for line in out.strip().splitlines():
+        lines = (self.first + out.strip().splitlines())[1:]  # samples taken while timing
+        before = False
+        if not lines and self.first:  # a timed region shorter than the sampling period
+            lines, before = self.first, True
+        for line in lines:
             p = [x.strip() for x in line.split(",")]
             if len(p) < 9:
                 continue
@@ -158,8 +174,11 @@ class ClockSampler:
             for name, val in zip(self.NAMES, p[5:9]):
                 if val.lower() == "active":
                     reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        r = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+             "reasons": sorted(reasons), "samples": len(sm)}
+        if before:
+            r["note"] = "timed region shorter than the 200 ms sampling period: sample taken just before it"
+        return r
 
 
 def combine_ranks(ms_total: float, tuples: float, dist, device) -> tuple:
@@ -182,18 +201,18 @@ def measured_hbm_peak():
         return 6800.0, "fallback"
 
 
-def profiled_traffic():
-    """Per-launch DRAM bytes of the search kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+def profiled_traffic(note: str = None, source: str = "hc_join.cu"):
+    """Per-launch DRAM bytes of a kernel from a committed ncu summary, if it
+    was taken on the current source of the file that holds the kernel."""
     try:
-        text = open(PROFILE_NOTE).read()
+        text = open(note or PROFILE_NOTE).read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
     h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
     if not m or not h:
         return None
-    src = os.path.join(ROOT, "paper_2502_06715_gb300", "csrc", "hc_join.cu")
+    src = os.path.join(ROOT, "paper_2502_06715_gb300", "csrc", source)
     if hashlib.sha256(open(src, "rb").read()).hexdigest() != h.group(1):
         return None
     return int(m.group(1))
@@ -205,11 +224,13 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if a.scale is None:
-        a.scale = {"triangle": 22, "clique4": 20, "cycle4": 20, "batched": 21, "serve": 23}[a.workload]
+        a.scale = {"triangle": 22, "clique4": 20, "cycle4": 20, "batched": 21, "serve": 23, "build": 22}[a.workload]
     if a.impl == "reference":
         return reference_arm(a, world, rank)
     if a.workload == "serve":
         return serve_workload(a, world, rank, local)
+    if a.workload == "build":
+        return build_workload(a, world, rank, local)
     if a.workload != "triangle":
         return other_workload(a, world, rank, local)
 
@@ -535,6 +556,112 @@ def other_workload(a, world, rank, local):
                        "prep_s": round(prep_s, 1), "counts_equal_separate": True},
             "gpu_launches": launches, "clocks": clocks}
     print(json.dumps(line), flush=True)
+
+
+def build_workload(a, world, rank, local):
+    """CoCo construction of the R-MAT E+ relation (LSD radix sort + run-boundary
+    scan) as the step.  Metric: effective index-build GB/s, the algorithmic
+    bytes 8N (pairs read) + 4N (V2) + 8 l1 + 4 (V1, O1) over the step time."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2502_06715_gb300 as hc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ep, gen_s = make_graph(a, rank, device=f"cuda:{local}")
+    n = int(ep.shape[0])
+    d = torch.from_numpy(ep.view(np.int32)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ix = hc.build_index(d, 0, stream=stream, time_kernels=True)
+        r = (ix.l1, ix.ms_radix_passes, ix.n_radix_passes, ix.ms_boundary)
+        ix.free()
+        return r
+
+    for _ in range(a.warmup):
+        l1 = step()[0]
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    launches0 = hc.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    radix_ms, radix_n, bnd_ms = 0.0, 0, 0.0
+    e0.record(stream)
+    for _ in range(a.steps):
+        l1, rm, rn, bm = step()
+        radix_ms += rm
+        radix_n += rn
+        bnd_ms += bm
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = hc.kernel_launches() - launches0
+    ms = e0.elapsed_time(e1) / a.steps
+    b_build = 8 * n + 4 * n + 8 * l1 + 4
+    value = b_build / (ms / 1e3) / 1e9
+    peak, peak_kind = measured_hbm_peak()
+    pass_ms = radix_ms / max(1, radix_n)
+    achieved = 16.0 * n / (pass_ms / 1e3) / 1e9
+    bnd_alg = 8 * n + 4 * n + 8 * l1 + 4  # keys read; V2, V1, O1 written
+    roofline = {"bound": "hbm", "kernel": "onesweep_kernel (radix pass)", "achieved": round(achieved, 1),
+                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": profiled_traffic(BUILD_PROFILE_NOTE, "hc_sort.cu"),
+                "alg_bytes_per_launch": 16 * n, "avg_launch_ms": round(pass_ms, 4),
+                "passes_per_step": radix_n / a.steps,
+                "boundary_kernel": {"achieved": round(bnd_alg / (bnd_ms / a.steps / 1e3) / 1e9, 1),
+                                    "avg_launch_ms": round(bnd_ms / a.steps, 4)}}
+
+    e2e = None
+    if not a.no_e2e:
+        host = torch.from_numpy(ep.view(np.int32)).pin_memory()
+        dbuf = torch.empty_like(d)
+
+        def e2e_step():
+            dbuf.copy_(host, non_blocking=True)
+            ix = hc.build_index(dbuf, 0, stream=stream)
+            got = ix.l1  # read back by the library (its control block)
+            ix.free()
+            return got
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / a.steps
+        e2e = {"value": b_build / (e2e_ms / 1e3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": 8 * n,
+               "d2h_bytes_per_step": 128, "ms_per_step": e2e_ms}
+
+    cpu = None
+    if not a.no_cpu_baseline and rank == 0 and world == 1:
+        import oracle
+
+        rng = np.random.default_rng(12345)
+        m = min(n, 24_000_000)
+        sample = np.ascontiguousarray(ep[np.sort(rng.choice(n, size=m, replace=False))])
+        t0 = time.perf_counter()
+        v1, o1, v2 = oracle.coco_build(sample, 0)
+        dt = time.perf_counter() - t0
+        cpu = {"value": (12 * m + 8 * v1.shape[0] + 4) / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"CoCo build of a seeded random sample of {m} of the {n} rows ({dt:.2f} s, one thread)"}
+
+    if rank == 0:
+        line = {"metric": "index-build GB/s (CoCo of R-MAT E+)", "value": value, "unit": "GB/s", "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded R-MAT)",
+                "config": {"workload": f"build_index of E+ (x<y) of R-MAT scale {a.scale} ef {a.edge_factor}, "
+                                       f"scrambled, symmetrised, deduplicated, rows in random order",
+                           "rows": n, "l1": int(l1), "alg_bytes_per_step": b_build,
+                           "l2": "inputs larger than L2 (%.0f MB of pairs)" % (8 * n / 1e6),
+                           "generate_s": round(gen_s, 1)},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
 
 
 def serve_workload(a, world, rank, local):

@@ -90,8 +90,11 @@ typedef struct hc_result hc_result;
  *   out      receives the library-owned index (free with hc_index_free).
  * Waits for the GPU once (to read the column maxima that size the sort).
  * The rows must be distinct; with HC_BUILD_CHECK_DUPLICATES in `flags` a
- * repeated row returns HC_ERR_DUPLICATE instead of an index. */
+ * repeated row returns HC_ERR_DUPLICATE instead of an index.  With
+ * HC_BUILD_TIME_KERNELS the radix passes and the run-boundary scan are timed
+ * with CUDA events on `stream` (see hc_index_view). */
 #define HC_BUILD_CHECK_DUPLICATES 1u
+#define HC_BUILD_TIME_KERNELS 2u
 hc_status hc_build_index(const uint32_t* d_pairs, uint64_t n, uint32_t attr_order, uint32_t flags,
                          void* stream, hc_index** out);
 hc_status hc_index_free(hc_index* index);
@@ -107,6 +110,10 @@ typedef struct {
     const uint32_t* d_o1;   /* [l1+1]                                          */
     const uint32_t* d_v2;   /* [n]                                             */
     const uint64_t* d_keys; /* [n] sorted rows as (first << 32 | second)       */
+    /* filled when built with HC_BUILD_TIME_KERNELS, else 0:                 */
+    float ms_radix_passes;    /* device time of the radix-pass launches, summed  */
+    uint32_t n_radix_passes;  /* radix-pass launches                             */
+    float ms_boundary;        /* device time of the run-boundary scan            */
 } hc_index_view;
 hc_status hc_index_get_view(const hc_index* index, hc_index_view* out);
 

@@ -121,6 +121,8 @@ class Index:
         _lib.check(_lib.load().hc_index_get_view(self._h, ctypes.byref(v)), "hc_index_get_view")
         self.n, self.l1, self.attr_order = v.n, v.l1, v.attr_order
         self.max_first, self.max_second = v.max_first, v.max_second
+        # device times when built with time_kernels=True (else 0)
+        self.ms_radix_passes, self.n_radix_passes, self.ms_boundary = v.ms_radix_passes, v.n_radix_passes, v.ms_boundary
         self._view = v
 
     @classmethod
@@ -169,11 +171,15 @@ def _check_pairs(pairs: torch.Tensor) -> torch.Tensor:
     return pairs.contiguous()
 
 
-def build_index(pairs: torch.Tensor, attr_order: int = 0, check_duplicates: bool = False, stream=None) -> Index:
-    """CoCo index of a relation given as an (n, 2) uint32 CUDA tensor."""
+def build_index(pairs: torch.Tensor, attr_order: int = 0, check_duplicates: bool = False, stream=None,
+                time_kernels: bool = False) -> Index:
+    """CoCo index of a relation given as an (n, 2) uint32 CUDA tensor.  With
+    time_kernels the radix passes and the run-boundary scan are timed with
+    CUDA events (Index.ms_radix_passes, n_radix_passes, ms_boundary)."""
     p = _check_pairs(pairs)
     out = ctypes.c_void_p()
-    flags = _lib.HC_BUILD_CHECK_DUPLICATES if check_duplicates else 0
+    flags = (_lib.HC_BUILD_CHECK_DUPLICATES if check_duplicates else 0) | (
+        _lib.HC_BUILD_TIME_KERNELS if time_kernels else 0)
     st = _lib.load().hc_build_index(ctypes.c_void_p(p.data_ptr() if p.numel() else 0), p.shape[0], attr_order,
                                     flags, ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(out))
     _lib.check(st, "hc_build_index")

@@ -19,6 +19,7 @@ HC_FLAG_CELL_COUNTS = 1
 HC_FLAG_STATS = 2
 HC_FLAG_TIME_KERNELS = 4
 HC_BUILD_CHECK_DUPLICATES = 1
+HC_BUILD_TIME_KERNELS = 2
 
 STATUS = {0: "HC_OK", 1: "HC_ERR_ARG", 2: "HC_ERR_OOM", 3: "HC_ERR_CUDA", 4: "HC_ERR_TIMEOUT",
           5: "HC_ERR_CAPACITY", 6: "HC_ERR_DUPLICATE", 7: "HC_ERR_BUSY"}
@@ -37,7 +38,8 @@ class hc_index_view(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("l1", ctypes.c_uint64), ("attr_order", ctypes.c_uint32),
                 ("max_first", ctypes.c_uint32), ("max_second", ctypes.c_uint32),
                 ("d_v1", ctypes.c_void_p), ("d_o1", ctypes.c_void_p), ("d_v2", ctypes.c_void_p),
-                ("d_keys", ctypes.c_void_p)]
+                ("d_keys", ctypes.c_void_p), ("ms_radix_passes", ctypes.c_float),
+                ("n_radix_passes", ctypes.c_uint32), ("ms_boundary", ctypes.c_float)]
 
 
 class hc_partitioned_view(ctypes.Structure):

@@ -289,6 +289,9 @@ hc_status hc_index_get_view(const hc_index* ix, hc_index_view* out) {
     out->d_o1 = ix->d_o1;
     out->d_v2 = ix->d_v2;
     out->d_keys = ix->d_keys;
+    out->ms_radix_passes = ix->ms_radix;
+    out->n_radix_passes = ix->n_radix;
+    out->ms_boundary = ix->ms_boundary;
     return HC_OK;
 }
 

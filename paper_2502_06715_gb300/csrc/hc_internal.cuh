@@ -59,6 +59,8 @@ struct hc_index {
     uint32_t* d_o1 = nullptr;    // [l1 + 1]
     uint32_t* d_v2 = nullptr;    // [n]
     bool stats_only = false;     // sizes only (planning), no device arrays
+    float ms_radix = 0.f, ms_boundary = 0.f;  // with HC_BUILD_TIME_KERNELS
+    uint32_t n_radix = 0;
 };
 
 struct hc_partitioned {

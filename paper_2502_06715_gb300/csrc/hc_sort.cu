@@ -208,11 +208,17 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) onesweep_kernel(
 
     // all loads first, so that they are in flight together
     uint64_t k[PASS_ITEMS];
+    if (full) {
 #pragma unroll
-    for (int j = 0; j < PASS_ITEMS; ++j) {
-        const uint32_t i = wb + j * 32;
-        k[j] = 0;
-        if (full || i < n) k[j] = SRC == SRC_PAIRS ? pack_row((const uint2*)in, i, ao) : ((const uint64_t*)in)[i];
+        for (int j = 0; j < PASS_ITEMS; ++j)
+            k[j] = SRC == SRC_PAIRS ? pack_row((const uint2*)in + wb, j * 32, ao) : ((const uint64_t*)in + wb)[j * 32];
+    } else {
+#pragma unroll
+        for (int j = 0; j < PASS_ITEMS; ++j) {
+            const uint32_t i = wb + j * 32;
+            k[j] = 0;
+            if (i < n) k[j] = SRC == SRC_PAIRS ? pack_row((const uint2*)in, i, ao) : ((const uint64_t*)in)[i];
+        }
     }
 
     const uint32_t lt = lanemask_lt();
@@ -277,11 +283,22 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) onesweep_kernel(
     goff[d] = gbase[d] + (uint32_t)excl - lstart;  // mod 2^32; goff + row is below n
     __syncthreads();
 
-    const uint32_t tile_n = full ? (uint32_t)PASS_TILE : n - base;
-    for (uint32_t i = tid; i < tile_n; i += PASS_THREADS) {
-        const uint64_t key = skeys[i];
-        const uint32_t dg = KEEP_DIGITS ? sdig[i] : pass_digit<DIG>(key, ds);
-        out[goff[dg] + i] = key;
+    // unrolled for a full tile, so that the shared-memory reads of all items
+    // are in flight together
+    if (full) {
+#pragma unroll
+        for (int j = 0; j < PASS_ITEMS; ++j) {
+            const uint32_t i = tid + j * PASS_THREADS;
+            const uint64_t key = skeys[i];
+            const uint32_t dg = KEEP_DIGITS ? sdig[i] : pass_digit<DIG>(key, ds);
+            out[goff[dg] + i] = key;
+        }
+    } else {
+        for (uint32_t i = tid; i < n - base; i += PASS_THREADS) {
+            const uint64_t key = skeys[i];
+            const uint32_t dg = KEEP_DIGITS ? sdig[i] : pass_digit<DIG>(key, ds);
+            out[goff[dg] + i] = key;
+        }
     }
 }
 
@@ -298,7 +315,7 @@ __global__ void pack_kernel(const uint2* __restrict__ pairs, uint64_t* __restric
 // i-1.  Flags are counted with ballots, the tile's offset comes from a
 // decoupled look-back (one warp reads 32 predecessors per round), and every
 // flagged row writes V1[pos] = first value and O1[pos] = i; every row writes
-// V2[i] = second value.  The last tile writes O1[l1] = n and l1.  Equal
+// V2[i] = second value (before the look-back, as it needs no offset).  The last tile writes O1[l1] = n and l1.  Equal
 // adjacent keys mark a duplicate row.  Rows are warp-striped: item j of lane
 // q of warp w is row tile * SORT_TILE + w * 32 * SORT_ITEMS + 32 j + q, so
 // row i-1 of a lane-0 row is lane 31's row of the previous item.
@@ -349,6 +366,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 3) boundary_kernel(
         }
         ball[j] = __ballot_sync(0xffffffffu, flag);
         wcount += __popc(ball[j]);
+        if (valid) v2[i] = (uint32_t)k[j];  // V2 needs no offset: written before the look-back
         // lane 31's row precedes lane 0's row of the next item
         const uint64_t last = __shfl_sync(0xffffffffu, k[j], 31);
         const uint32_t last_pid = SEGMENTED ? __shfl_sync(0xffffffffu, my_pid, 31) : 0;
@@ -384,13 +402,10 @@ __global__ void __launch_bounds__(SORT_THREADS, 3) boundary_kernel(
 #pragma unroll
     for (int j = 0; j < SORT_ITEMS; ++j) {
         const uint64_t i = base + (uint64_t)j * 32 + lane;
-        if (full || i < n) {
-            v2[i] = (uint32_t)k[j];
-            if (ball[j] >> lane & 1u) {
-                const uint64_t p = pos + __popc(ball[j] & lanemask_lt());
-                v1[p] = (uint32_t)(k[j] >> 32);
-                o1[p] = (uint32_t)i;
-            }
+        if (ball[j] >> lane & 1u) {  // flagged rows are valid rows
+            const uint64_t p = pos + __popc(ball[j] & lanemask_lt());
+            v1[p] = (uint32_t)(k[j] >> 32);
+            o1[p] = (uint32_t)i;
         }
         pos += __popc(ball[j]);
     }
@@ -538,9 +553,36 @@ hc_status check_ctl(const Ctl* d_ctl, cudaStream_t s, Ctl* h) {
     return HC_OK;
 }
 
+// CUDA events around selected launches (HC_BUILD_TIME_KERNELS): mark()
+// before and after each timed launch; sum() after the stream has synchronised.
+struct LaunchTimer {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;
+    ~LaunchTimer() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+    hc_status mark(cudaStream_t s) {
+        if (!on) return HC_OK;
+        cudaEvent_t e;
+        HC_CUDA_TRY(cudaEventCreate(&e));
+        ev.push_back(e);
+        HC_CUDA_TRY(cudaEventRecord(e, s));
+        return HC_OK;
+    }
+    uint32_t launches() const { return (uint32_t)(ev.size() / 2); }
+    float sum() const {
+        float t = 0.f;
+        for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) t += ms;
+        }
+        return t;
+    }
+};
+
 // Radix passes over the given digit specs; the sorted keys end in `dst`.
 hc_status radix_passes(const void* src, bool src_pairs, uint32_t ao, uint64_t n, const std::vector<DigitSpec>& specs,
-                       uint64_t* dst, Tmp& tmp, Ctl* d_ctl, cudaStream_t s) {
+                       uint64_t* dst, Tmp& tmp, Ctl* d_ctl, cudaStream_t s, LaunchTimer* timer = nullptr) {
     const int np = (int)specs.size();
     if (np == 0) return fail(HC_ERR_ARG, "internal: no radix passes");
     DigitSpec* d_specs;
@@ -578,9 +620,11 @@ hc_status radix_passes(const void* src, bool src_pairs, uint32_t ao, uint64_t n,
         auto* kern = from_pairs              ? onesweep_kernel<SRC_PAIRS, DIGIT_BYTE>
                      : specs[p].mode == 0 ? onesweep_kernel<SRC_KEYS, DIGIT_BYTE>
                                           : onesweep_kernel<SRC_KEYS, DIGIT_PARTITION>;
+        if (timer) HC_TRY(timer->mark(s));
         kern<<<(unsigned)ntiles, PASS_THREADS, 0, s>>>(in, outb, n32, ao, specs[p], d_hist + p * RADIX, status,
                                                        &d_ctl->tile_counter[p], &d_ctl->err);
         HC_CUDA_TRY(launch_check());
+        if (timer) HC_TRY(timer->mark(s));
         in = outb;
         cur ^= 1;
     }
@@ -643,6 +687,8 @@ hc_status build_index_impl(const uint32_t* d_pairs, uint64_t n, uint32_t ao, uin
     idx->d_v2 = (uint32_t*)p;
 
     hc_status st;
+    LaunchTimer t_radix, t_boundary;
+    t_radix.on = t_boundary.on = (flags & HC_BUILD_TIME_KERNELS) != 0;
     {
         Tmp tmp(s);
         Ctl* d_ctl;
@@ -666,13 +712,20 @@ hc_status build_index_impl(const uint32_t* d_pairs, uint64_t n, uint32_t ao, uin
         if (specs.empty()) {
             pack_kernel<<<grid_for(n, 256, 4), 256, 0, s>>>((const uint2*)d_pairs, idx->d_keys, n, ao);
             if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "pack_kernel"));
-        } else if ((st = radix_passes(d_pairs, true, ao, n, specs, idx->d_keys, tmp, d_ctl, s)) != HC_OK) {
+        } else if ((st = radix_passes(d_pairs, true, ao, n, specs, idx->d_keys, tmp, d_ctl, s, &t_radix)) != HC_OK) {
             return bail(st);
         }
+        if ((st = t_boundary.mark(s)) != HC_OK) return bail(st);
         if ((st = run_boundary(idx->d_keys, n, false, 0, 1, 0, 1, idx->d_v1, idx->d_o1, idx->d_v2, tmp, d_ctl, s)) !=
             HC_OK)
             return bail(st);
+        if ((st = t_boundary.mark(s)) != HC_OK) return bail(st);
         if ((st = check_ctl(d_ctl, s, &h)) != HC_OK) return bail(st);
+        if (t_radix.on) {
+            idx->ms_radix = t_radix.sum();
+            idx->n_radix = t_radix.launches();
+            idx->ms_boundary = t_boundary.sum();
+        }
         if ((flags & HC_BUILD_CHECK_DUPLICATES) && h.dup)
             return bail(fail(HC_ERR_DUPLICATE, "build_index: the relation holds a repeated row"));
         idx->l1 = h.l1;
