@@ -61,6 +61,10 @@ struct hc_index {
     bool stats_only = false;     // sizes only (planning), no device arrays
     float ms_radix = 0.f, ms_boundary = 0.f;  // with HC_BUILD_TIME_KERNELS
     uint32_t n_radix = 0;
+    // V1 position map: v1pos[v] = position of v in V1, or V1POS_NONE; built
+    // when the first attribute's values are dense enough (v1pos_n = 0: none)
+    uint32_t* d_v1pos = nullptr;
+    uint32_t v1pos_n = 0;
 };
 
 struct hc_partitioned {
@@ -75,9 +79,24 @@ struct hc_partitioned {
     uint32_t* d_lvl1_start = nullptr;  // [np + 1]
     uint32_t* d_l1 = nullptr;          // [1] device copy of l1
     bool l1_known = false;
+    // V1 position map over the concatenated V1 (partitions on the first
+    // attribute only, so that each value sits in one partition)
+    uint32_t* d_v1pos = nullptr;
+    uint32_t v1pos_n = 0;
 };
 
 namespace hc {
+
+// V1 position maps (value -> position in V1, a dense direct-address table in
+// place of a binary search of V1).  Built only when the values span at most
+// V1POS_ROWS_FACTOR entries per row (plus a fixed allowance), so a map costs
+// at most about 4 * V1POS_ROWS_FACTOR bytes per row.
+constexpr uint32_t V1POS_NONE = 0xFFFFFFFFu;
+constexpr uint64_t V1POS_ROWS_FACTOR = 4;
+constexpr uint64_t V1POS_ALLOWANCE = 1ull << 20;
+inline bool v1pos_eligible(uint64_t rows, uint32_t max_value) {
+    return rows > 0 && (uint64_t)max_value + 1 <= V1POS_ROWS_FACTOR * rows + V1POS_ALLOWANCE;
+}
 
 // --------------------------------------------------------------- device code
 #if defined(__CUDACC__)

@@ -31,7 +31,9 @@ struct DAtom {
     const uint32_t* v1;
     const uint32_t* o1;
     const uint32_t* v2;
-    const uint32_t* l1s;  // level-1 start of each partition, [np + 1]; NULL when whole
+    const uint32_t* l1s;    // level-1 start of each partition, [np + 1]; NULL when whole
+    const uint32_t* v1pos;  // value -> position in v1 (V1POS_NONE if absent), or NULL
+    uint32_t v1pos_n;       // values covered by v1pos
     uint32_t l1_whole;
     uint32_t pb;                                     // shares of the second variable
     uint32_t stride_f, share_f, stride_s, share_s;  // cell -> partition identifiers
@@ -179,8 +181,16 @@ __global__ void l0_probe_kernel(const DPlan* __restrict__ gP, const uint64_t* __
             pos[q] = 0;
             if (q < n0) {
                 const DAtom& a = P.atom[P.src_atom[0][q]];
-                uint32_t p = (q == (int)best) ? rlo[q] + k : lower_bound_u32(a.v1, rlo[q], rhi[q], x);
-                ok = ok && p < rhi[q] && a.v1[p] == x;
+                uint32_t p;
+                if (q == (int)best) {
+                    p = rlo[q] + k;
+                } else if (a.v1pos != nullptr) {  // direct position of x in V1
+                    p = x < a.v1pos_n ? a.v1pos[x] : V1POS_NONE;
+                    ok = ok && p >= rlo[q] && p < rhi[q];
+                } else {
+                    p = lower_bound_u32(a.v1, rlo[q], rhi[q], x);
+                    ok = ok && p < rhi[q] && a.v1[p] == x;
+                }
                 pos[q] = p;
             }
         }
@@ -389,10 +399,16 @@ __device__ __forceinline__ bool probe(const DPlan& P, int best, const uint32_t (
     for (int q = 0; q < S; ++q) {
         if (q < P.nsrc[L]) {
             const uint32_t* list = src_list(P, L, q);
+            const DAtom& aq = P.atom[P.src_atom[L][q]];
             uint32_t p = kpos;
             if (q != best) {
-                p = ok ? lower_bound_u32(list, rlo[q], rhi[q], v) : rhi[q];
-                ok = ok && p < rhi[q] && list[p] == v;
+                if (P.src_top[L][q] && aq.v1pos != nullptr) {  // direct position of v in V1
+                    p = (ok && v < aq.v1pos_n) ? __ldg(aq.v1pos + v) : V1POS_NONE;
+                    ok = ok && p >= rlo[q] && p < rhi[q];
+                } else {
+                    p = ok ? lower_bound_u32(list, rlo[q], rhi[q], v) : rhi[q];
+                    ok = ok && p < rhi[q] && list[p] == v;
+                }
             }
             if (q < O && P.src_top[L][q] && ok) {  // top sources come first, slot == q
                 const DAtom& a = P.atom[P.src_atom[L][q]];
@@ -1199,11 +1215,14 @@ hc_status plan_query(const hc_query* q, const hc_index* const* idx, const hc_joi
             d.v2 = ix->d_v2;
             d.l1s = nullptr;
             d.l1_whole = (uint32_t)ix->l1;
+            d.v1pos = ix->d_v1pos;
+            d.v1pos_n = ix->v1pos_n;
         } else if (partition_bytes) {
             // estimate only: keys, levels and directory of the partitioned copy,
-            // plus the radix pass temporaries
+            // its V1 position map, plus the radix pass temporaries
             const uint64_t n = ix->n, np = (uint64_t)pa * pb;
             *partition_bytes += n * (8 + 8 + 4 + 4 + 4) + (np + 1) * 8 + ((n + 4095) / 4096) * 256 * 8 + 4096;
+            if (pb == 1 && v1pos_eligible(n, ix->max_first)) *partition_bytes += ((uint64_t)ix->max_first + 1) * 4;
             d.l1s = nullptr;
         } else {
             hc_partitioned* part = nullptr;
@@ -1215,6 +1234,8 @@ hc_status plan_query(const hc_query* q, const hc_index* const* idx, const hc_joi
             d.o1 = part->d_o1;
             d.v2 = part->d_v2;
             d.l1s = part->d_lvl1_start;
+            d.v1pos = part->d_v1pos;
+            d.v1pos_n = part->v1pos_n;
         }
     }
     for (int L = 0; L < nv; ++L) {

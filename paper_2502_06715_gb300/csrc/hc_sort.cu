@@ -433,6 +433,15 @@ __global__ void directory_kernel(const uint64_t* __restrict__ keys, uint64_t n, 
     }
 }
 
+// V1 position map: pos[V1[i]] = i for i < l1 (l1 from *d_l1 when given).
+// V1 values are distinct, so every entry is written at most once.
+__global__ void v1pos_kernel(const uint32_t* __restrict__ v1, uint64_t l1_max, const uint32_t* __restrict__ d_l1,
+                             uint32_t* __restrict__ pos) {
+    const uint64_t l1 = d_l1 ? min(l1_max, (uint64_t)*d_l1) : l1_max;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < l1; i += (uint64_t)gridDim.x * blockDim.x)
+        pos[v1[i]] = (uint32_t)i;
+}
+
 // ----------------------------------------------------------- device scan
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 8;
@@ -659,6 +668,7 @@ void index_release(hc_index* idx, cudaStream_t s) {
     dev_free(idx->d_v1, s);
     dev_free(idx->d_o1, s);
     dev_free(idx->d_v2, s);
+    dev_free(idx->d_v1pos, s);
     delete idx;
 }
 
@@ -729,6 +739,16 @@ hc_status build_index_impl(const uint32_t* d_pairs, uint64_t n, uint32_t ao, uin
         if ((flags & HC_BUILD_CHECK_DUPLICATES) && h.dup)
             return bail(fail(HC_ERR_DUPLICATE, "build_index: the relation holds a repeated row"));
         idx->l1 = h.l1;
+        if (v1pos_eligible(n, idx->max_first)) {
+            const uint64_t dn = (uint64_t)idx->max_first + 1;
+            if (dev_alloc(&p, dn * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+            idx->d_v1pos = (uint32_t*)p;
+            idx->v1pos_n = (uint32_t)dn;
+            if (cudaMemsetAsync(idx->d_v1pos, 0xFF, dn * 4, s) != cudaSuccess)
+                return bail(cuda_fail(cudaGetLastError(), "memset"));
+            v1pos_kernel<<<grid_for(idx->l1, 256, 8), 256, 0, s>>>(idx->d_v1, idx->l1, nullptr, idx->d_v1pos);
+            if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "v1pos_kernel"));
+        }
     }
     *out = idx;
     return HC_OK;
@@ -743,6 +763,7 @@ void partitioned_release(hc_partitioned* p, cudaStream_t s) {
     dev_free(p->d_v2, s);
     dev_free(p->d_lvl1_start, s);
     dev_free(p->d_l1, s);
+    dev_free(p->d_v1pos, s);
     delete p;
 }
 
@@ -813,6 +834,18 @@ hc_status partition_impl(const hc_index* idx, uint32_t seed_a, uint32_t pa, uint
         directory_kernel<<<grid_for(np + 1, 128, 2), 128, 0, s>>>(part->d_keys, n, seed_a, pa, seed_b, pb, part->d_o1,
                                                                   d_ctl, part->d_bpref, part->d_lvl1_start);
         if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "directory_kernel"));
+        // partitions on the first attribute alone hold each value once: one
+        // position map over the concatenated V1 serves every partition
+        if (pb == 1 && v1pos_eligible(n, idx->max_first)) {
+            const uint64_t dn = (uint64_t)idx->max_first + 1;
+            if (dev_alloc(&p, dn * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+            part->d_v1pos = (uint32_t*)p;
+            part->v1pos_n = (uint32_t)dn;
+            if (cudaMemsetAsync(part->d_v1pos, 0xFF, dn * 4, s) != cudaSuccess)
+                return bail(cuda_fail(cudaGetLastError(), "memset"));
+            v1pos_kernel<<<grid_for(n, 256, 8), 256, 0, s>>>(part->d_v1, n, &d_ctl->l1, part->d_v1pos);
+            if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "v1pos_kernel"));
+        }
     }
     *out = part;
     return HC_OK;
