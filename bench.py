@@ -267,7 +267,14 @@ def main():
     elif a.shares == "autotune":
         from paper_2502_06715_gb300.autotune import Tuner
 
-        tuned = Tuner().tune(q, [ix0] * 3, P_list=(64, 256, 1024), min_cells=a.min_cells)
+        # the output pool of a materializing run is sized from a count run
+        cap = 0
+        if a.mode == "materialize" and a.capacity == "plan":
+            cap = int(1.25 * hc.run_join(q, [ix0] * 3, shares=plan_shares).count) + 1
+        elif a.mode == "materialize":
+            cap = int(a.capacity)
+        tuned = Tuner().tune(q, [ix0] * 3, P_list=(64, 256, 1024), min_cells=a.min_cells, mode=a.mode,
+                             out_capacity=cap)
         shares = tuned.shares
         if not a.grain:
             a.grain = tuned.item_grain

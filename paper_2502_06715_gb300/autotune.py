@@ -13,8 +13,11 @@ hand and keeps the fastest configuration, searching one knob at a time
                 length ratio) or never;
   slice_grain   loop-3 candidates per slice of a hub (queries of 4+ loops).
 
-Results are cached per (query shape, log2 size bucket) in memory and, if a
-path is given, in a JSON file.  Tuning launches run in count mode.
+Results are cached per (query shape, log2 size bucket, mode) in memory and,
+if a path is given, in a JSON file.  Tuning launches run in count mode; for
+a materializing run the merge knobs are then re-chosen with materializing
+launches, since writing tuples from a merge walk costs more than counting
+them and moves the best threshold.
 """
 from __future__ import annotations
 
@@ -54,12 +57,12 @@ def shape_key(query: Query, indexes) -> str:
     return f"{query.n_vars}|{sorted(query.atoms, key=str)}|{query.loop_order()}|{bucket}"
 
 
-def _time(query, indexes, cfg: Config, reps: int, stream) -> float:
+def _time(query, indexes, cfg: Config, reps: int, stream, **extra) -> float:
     best = float("inf")
     for _ in range(reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        run_join(query, indexes, stream=stream, **cfg.options())
+        run_join(query, indexes, stream=stream, **cfg.options(), **extra)
         e1.record(stream)
         e1.synchronize()
         best = min(best, e0.elapsed_time(e1))
@@ -111,9 +114,12 @@ class Tuner:
                 json.dump(self.cache, f, indent=1)
 
     def tune(self, query: Query, indexes, P_list=(64, 256, 1024), min_cells: int = 1, stream=None,
-             log=None) -> Config:
-        """Fastest configuration for this query and data (count mode)."""
-        key = shape_key(query, indexes) + f"|P{tuple(P_list)}|min{min_cells}"
+             log=None, mode: str = "count", out_capacity: int = 0) -> Config:
+        """Fastest configuration for this query and data.  mode="materialize"
+        (with the output pool size out_capacity, 0 = two-pass) re-chooses the
+        merge knobs with materializing launches."""
+        key = shape_key(query, indexes) + f"|P{tuple(P_list)}|min{min_cells}" + (
+            "" if mode == "count" else f"|{mode}")
         if key in self.cache:
             c = self.cache[key]
             return Config(**c)
@@ -147,6 +153,17 @@ class Tuner:
                 else:
                     setattr(c, name, list(v) if name == "shares" else v)
                 c.ms = measure(c)
+                if c.ms < best.ms:
+                    best = c
+        if mode == "materialize":
+            extra = {"mode": "materialize", "out_capacity": out_capacity}
+            best.ms = _time(query, indexes, best, self.reps, stream, **extra)
+            for mm, mr in [(32, 2), (32, 4), (32, 8), (64, 4), (MERGE_OFF, 1)]:
+                c = Config(shares=list(best.shares), item_grain=best.item_grain, merge_min=mm, merge_ratio=mr,
+                           slice_grain=best.slice_grain)
+                if c.key() == best.key():
+                    continue
+                c.ms = _time(query, indexes, c, self.reps, stream, **extra)
                 if c.ms < best.ms:
                     best = c
         if log:
