@@ -793,7 +793,7 @@ __device__ __forceinline__ uint64_t search_item(const DPlan& P, Frame<NL, O>& F,
 // count; materialize writes into pool chunks); pass 1 writes tuples at
 // item_base[item].
 template <int NL, int S, int O, bool MAT>
-__global__ void __launch_bounds__(128, (NL <= 3 ? 8 : 6)) gj_kernel(const DPlan* __restrict__ gP, const uint32_t* __restrict__ e_cell,
+__global__ void __launch_bounds__(128, (NL <= 3 ? 16 : 12)) gj_kernel(const DPlan* __restrict__ gP, const uint32_t* __restrict__ e_cell,
                                                     const uint32_t* __restrict__ e_x,
                                                     const uint32_t* __restrict__ e_rng,
                                                     const uint32_t* __restrict__ e_split,
@@ -867,7 +867,7 @@ __global__ void batch_items_kernel(const BQuery* __restrict__ qs, uint32_t n, ui
 }
 
 template <int NLA, int SA, int OA, int NLB, int SB, int OB>
-__global__ void __launch_bounds__(128, ((NLA <= 3 && NLB <= 3) ? 8 : 6))
+__global__ void __launch_bounds__(128, ((NLA <= 3 && NLB <= 3) ? 16 : 12))
     gj_batch_kernel(const BQuery* __restrict__ qs, uint32_t n, const uint64_t* __restrict__ item_off,
                     uint32_t* __restrict__ ctr) {
     constexpr int NLM = NLA > NLB ? NLA : NLB;
