@@ -51,11 +51,12 @@ def parse_args():
     ap.add_argument("--edge-factor", type=int, default=16)
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--mode", choices=["materialize", "count"], default="materialize")
-    ap.add_argument("--workload", choices=["triangle", "clique4", "cycle4", "batched", "serve", "build"],
+    ap.add_argument("--workload", choices=["triangle", "clique4", "cycle4", "batched", "serve", "build", "order"],
                     default="triangle",
                     help="triangle: R-MAT triangle (default line); clique4 / cycle4: R-MAT 4-clique / 4-cycle "
                          "counts; batched: 512 triangle/4-clique queries on induced subgraphs in one launch; "
-                         "serve: continuous-batching server; build: CoCo index build of R-MAT E+")
+                         "serve: continuous-batching server; build: CoCo index build of R-MAT E+; "
+                         "order: 4-clique under every loop order beside the cost model's choice")
     ap.add_argument("--shares", default="autotune",
                     help="'autotune' (timed search from the paper's plan over HyperCube share vectors of "
                          ">= --min-cells cells and kernel schedules), 'plan' (Sec. 5.3 decision at --P cells), "
@@ -224,13 +225,16 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if a.scale is None:
-        a.scale = {"triangle": 22, "clique4": 20, "cycle4": 20, "batched": 21, "serve": 23, "build": 22}[a.workload]
+        a.scale = {"triangle": 22, "clique4": 20, "cycle4": 20, "batched": 21, "serve": 23, "build": 22,
+                   "order": 18}[a.workload]
     if a.impl == "reference":
         return reference_arm(a, world, rank)
     if a.workload == "serve":
         return serve_workload(a, world, rank, local)
     if a.workload == "build":
         return build_workload(a, world, rank, local)
+    if a.workload == "order":
+        return order_workload(a, world, rank, local)
     if a.workload != "triangle":
         return other_workload(a, world, rank, local)
 
@@ -563,6 +567,71 @@ def other_workload(a, world, rank, local):
                        "prep_s": round(prep_s, 1), "counts_equal_separate": True},
             "gpu_launches": launches, "clocks": clocks}
     print(json.dumps(line), flush=True)
+
+
+def order_workload(a, world, rank, local):
+    """Loop-order sweep (Sec. 5.3, the paper's order study): the 4-clique on
+    R-MAT E+ counted under every loop order (shares 1, each order's indexes in
+    the attribute orders it needs), beside the order hc_choose_plan picks from
+    the cost model.  The metric is the chosen plan's throughput."""
+    import itertools
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import datagen
+
+    __graft_entry__.build()
+    import paper_2502_06715_gb300 as hc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t = time.perf_counter()
+    sym = datagen.rmat_graph(a.scale, a.edge_factor, a.seed + rank, device=f"cuda:{local}")
+    ep = datagen.scatter_order(datagen.orient_lt(sym), a.seed)
+    gen_s = time.perf_counter() - t
+    d = torch.from_numpy(ep.view(np.int32)).to(dev)
+    q = hc.FOUR_CLIQUE
+    ix = {ao: hc.build_index(d, ao) for ao in (0, 1)}
+    chosen, chosen_shares = hc.choose_plan(q, [ix[0]] * len(q.atoms), 1)
+
+    def timed(order, steps):
+        qo = q.with_order(order)
+        idx = [ix[qo.attr_order(j)] for j in range(len(q.atoms))]
+        best, cnt = float("inf"), 0
+        for _ in range(steps):
+            r = hc.run_join(qo, idx, time_kernels=True)
+            best, cnt = min(best, r.ms_join_kernel), r.count
+        return best, cnt
+
+    for _ in range(a.warmup):
+        timed(chosen, 1)
+    sampler = ClockSampler(local)
+    times, counts = {}, set()
+    for order in itertools.permutations(range(q.n_vars)):
+        ms, cnt = timed(order, a.steps)
+        times["".join("XYZU"[v] for v in order)] = round(ms, 2)
+        counts.add(cnt)
+    clocks = sampler.stop()
+    if len(counts) != 1:
+        raise SystemExit(f"orders disagree on the count: {sorted(counts)}")
+    cnt = counts.pop()
+    key = "".join("XYZU"[v] for v in chosen)
+    ranked = sorted(times, key=times.get)
+    if rank == 0:
+        line = {"metric": "join output tuples/s (R-MAT 4-clique, order chosen by the cost model)",
+                "value": cnt / (times[key] / 1e3), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": times[key], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded R-MAT)",
+                "config": {"workload": f"4-clique on E+ of R-MAT scale {a.scale} ef {a.edge_factor}, count, shares 1, "
+                                       f"every loop order (search kernel time, best of {a.steps})",
+                           "tuples": cnt, "chosen_order": key, "chosen_rank": ranked.index(key) + 1,
+                           "orders": len(times), "best_order": ranked[0], "best_ms": times[ranked[0]],
+                           "worst_order": ranked[-1], "worst_ms": times[ranked[-1]], "ms_by_order": times,
+                           "generate_s": round(gen_s, 1)},
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
 
 
 def build_workload(a, world, rank, local):

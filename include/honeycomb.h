@@ -197,6 +197,21 @@ hc_status hc_partitioned_free(hc_partitioned* p);
 hc_status hc_choose_shares(const hc_query* q, const hc_index* const* idx, uint32_t P,
                            uint32_t shares_out[HC_MAX_VARS]);
 
+/* Variable order and shares together (Sec. 5.3, "Plan Decision"): for every
+ * order sigma of the query's variables (n_vars! of them; q->order is ignored)
+ * the shares are chosen as by hc_choose_shares under that order, and the
+ * order kept is the one whose replicated cost (Eq. "total:cost") at those
+ * shares is least; ties go to the smaller unpartitioned cost, then to the
+ * lexicographically smallest order.  Statistics are read from the indexes as
+ * by hc_choose_shares and do not depend on their attribute order (a
+ * statistics-only index serves).  order_out[0..n_vars) receives the loop
+ * order (variable ids); a run with it needs, for atom j, an index whose
+ * attr_order puts the atom's variables in that order.  shares_out as in
+ * hc_choose_shares.  Host only; HC_ERR_ARG as hc_choose_shares, and for
+ * n_vars > 8. */
+hc_status hc_choose_plan(const hc_query* q, const hc_index* const* idx, uint32_t P, uint8_t order_out[HC_MAX_VARS],
+                         uint32_t shares_out[HC_MAX_VARS]);
+
 /* Estimated cost of a plan (Sec. 5.2): level_cost[i] is the bound of Lemma
  * "cost-ub" for loop i with all shares 1, and *replicated_cost is Eq.
  * "total:cost" for the given shares (per variable id).  dom_out[v] is the

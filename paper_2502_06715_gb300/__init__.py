@@ -246,6 +246,18 @@ def choose_shares(query: Query, indexes: Sequence[Index], P: int = 1024) -> list
     return [int(out[v]) for v in range(query.n_vars)]
 
 
+def choose_plan(query: Query, indexes: Sequence[Index], P: int = 1024) -> tuple:
+    """Loop order and shares together (Sec. 5.3): (order, shares).  Run with
+    ``query.with_order(order)`` and, for atom j, an index of attr_order
+    ``query.with_order(order).attr_order(j)``."""
+    q = query._c()
+    ptr, keep = _index_array(indexes)
+    order = (ctypes.c_uint8 * _lib.HC_MAX_VARS)()
+    shares = (ctypes.c_uint32 * _lib.HC_MAX_VARS)()
+    _lib.check(_lib.load().hc_choose_plan(ctypes.byref(q), ptr, P, order, shares), "hc_choose_plan")
+    return tuple(int(order[i]) for i in range(query.n_vars)), [int(shares[v]) for v in range(query.n_vars)]
+
+
 def plan_cost(query: Query, indexes: Sequence[Index], shares: Sequence[int]) -> dict:
     """Estimated per-loop costs, domain sizes and replicated cost (Sec. 5.2)."""
     q = query._c()

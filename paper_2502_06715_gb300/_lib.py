@@ -79,6 +79,8 @@ SIGNATURES = {
     "hc_partitioned_free": (ctypes.c_int, [ctypes.c_void_p]),
     "hc_choose_shares": (ctypes.c_int, [ctypes.POINTER(hc_query), ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
+    "hc_choose_plan": (ctypes.c_int, [ctypes.POINTER(hc_query), ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint32,
+                                      ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ctypes.c_uint32)]),
     "hc_plan_cost": (ctypes.c_int, [ctypes.POINTER(hc_query), ctypes.POINTER(ctypes.c_void_p),
                                     ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),

@@ -245,6 +245,43 @@ hc_status choose_shares_impl(const hc_query* q, const hc_index* const* idx, uint
     return HC_OK;
 }
 
+// Sec. 5.3 plan decision over all loop orders: the shares of each order as
+// chosen above, the order of least replicated cost at its shares.
+hc_status choose_plan_impl(const hc_query* q, const hc_index* const* idx, uint32_t P, uint8_t* order_out,
+                           uint32_t* shares_out) {
+    if (!q || !idx || !order_out || !shares_out) return fail(HC_ERR_ARG, "choose_plan: NULL argument");
+    const int nv = (int)q->n_vars;
+    if (nv < 1 || nv > HC_MAX_VARS) return fail(HC_ERR_ARG, "choose_plan: need 1..8 variables");
+    hc_query w = *q;
+    std::vector<uint8_t> perm(nv), best_perm;
+    for (int i = 0; i < nv; ++i) perm[i] = (uint8_t)i;
+    uint32_t best_sh[HC_MAX_VARS];
+    double best_rep = 0.0, best_base = 0.0;
+    auto less = [](double a, double b) { return a < b - 1e-9 * std::max(1.0, std::fabs(b)); };
+    do {  // lexicographic order, so the first of equal plans is kept
+        for (int i = 0; i < nv; ++i) w.order[i] = perm[i];
+        uint32_t sh[HC_MAX_VARS];
+        HC_TRY(choose_shares_impl(&w, idx, P, sh));
+        int rank[HC_MAX_VARS];
+        double dom[HC_MAX_VARS], cost[HC_MAX_VARS];
+        HC_TRY(plan_inputs(&w, idx, rank, dom, cost));
+        double base = 0.0;
+        for (int i = 0; i < nv; ++i) base += cost[i];
+        const double rep = replicated(&w, cost, sh);
+        const bool better = best_perm.empty() || less(rep, best_rep) ||
+                            (!less(best_rep, rep) && less(base, best_base));
+        if (better) {
+            best_perm = perm;
+            best_rep = rep;
+            best_base = base;
+            std::copy(sh, sh + HC_MAX_VARS, best_sh);
+        }
+    } while (std::next_permutation(perm.begin(), perm.end()));
+    for (int i = 0; i < HC_MAX_VARS; ++i) order_out[i] = i < nv ? best_perm[i] : (uint8_t)0xFF;
+    std::copy(best_sh, best_sh + HC_MAX_VARS, shares_out);
+    return HC_OK;
+}
+
 }  // namespace hc
 
 // ------------------------------------------------------------------- C ABI
@@ -326,6 +363,11 @@ hc_status hc_partitioned_free(hc_partitioned* p) {
 
 hc_status hc_choose_shares(const hc_query* q, const hc_index* const* idx, uint32_t P, uint32_t shares_out[HC_MAX_VARS]) {
     return hc::choose_shares_impl(q, idx, P, shares_out);
+}
+
+hc_status hc_choose_plan(const hc_query* q, const hc_index* const* idx, uint32_t P, uint8_t order_out[HC_MAX_VARS],
+                         uint32_t shares_out[HC_MAX_VARS]) {
+    return hc::choose_plan_impl(q, idx, P, order_out, shares_out);
 }
 
 hc_status hc_plan_cost(const hc_query* q, const hc_index* const* idx, const uint32_t shares[HC_MAX_VARS],
