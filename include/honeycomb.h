@@ -227,6 +227,14 @@ hc_status hc_plan_cost(const hc_query* q, const hc_index* const* idx, const uint
 #define HC_FLAG_CELL_COUNTS 1u /* also return the count of each HyperCube cell        */
 #define HC_FLAG_STATS 2u       /* also return the intersection work counter           */
 #define HC_FLAG_TIME_KERNELS 4u /* time the search kernel launches with device events  */
+/* Query rewriting (Sec. 5.1) is on by default for queries of 4+ variables
+ * whose last loop has two or more lists fixed before the loop above it (the
+ * 4-clique's R3[y] and R6[x] under order X,Y,Z,U): their intersection is
+ * computed once per binding of loop n-3 (e.g. per y) and the last loop
+ * intersects it with the remaining lists.  It needs lift_arena words of
+ * device scratch per resident warp, and is off with HC_FLAG_STATS (the work
+ * counter measures the unrewritten loops) or with: */
+#define HC_FLAG_NO_LIFT 8u
 
 typedef struct {
     uint32_t shares[HC_MAX_VARS]; /* P_v per variable id (>= 1); their product = cells  */
@@ -242,7 +250,8 @@ typedef struct {
                                   /* (0: defaults 32 and 4; 0xFFFFFFFF: never merge)     */
     uint32_t slice_grain;         /* 4+ loops: loop-3 candidates per work slice of a     */
                                   /* loop-2 binding (0: default 256; 0xFFFFFFFF: none)   */
-    uint32_t reserved0;           /* must be 0                                           */
+    uint32_t lift_arena;          /* query rewriting: words of device scratch per warp   */
+                                  /* for lifted intersections (0: default 16384)          */
     uint64_t out_capacity;        /* materialize: 0 runs a counting pass, then an        */
                                   /* emitting pass (tuples cell-major, in a fixed order); */
                                   /* > 0 runs one pass writing into an output pool of    */

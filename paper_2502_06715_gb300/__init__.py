@@ -291,10 +291,13 @@ def run_join(query: Query, indexes: Sequence[Index], shares: Sequence[int] | Non
              seeds: Sequence[int] | None = None, mode: str = "count", cell_counts: bool = False,
              stats: bool = False, item_grain: int = 0, block_threads: int = 0, stream=None,
              keep_device: bool = False, time_kernels: bool = False, merge_min: int = 0,
-             merge_ratio: int = 0, out_capacity: int = 0, slice_grain: int = 0) -> Result:
+             merge_ratio: int = 0, out_capacity: int = 0, slice_grain: int = 0, lift: bool = True,
+             lift_arena: int = 0) -> Result:
     """Evaluate the query.  Tuples (materialize) come back as an
     (count, n_vars) int32 CUDA tensor in variable-id order (a copy, unless
-    ``keep_device`` keeps an alias of library memory tied to the result)."""
+    ``keep_device`` keeps an alias of library memory tied to the result).
+    ``lift`` allows the query rewriting of Sec. 5.1 (off with ``stats``);
+    ``lift_arena`` sets its device scratch, in words per warp (0: default)."""
     if len(indexes) != len(query.atoms):
         raise ValueError("one index per atom")
     q = query._c()
@@ -309,7 +312,8 @@ def run_join(query: Query, indexes: Sequence[Index], shares: Sequence[int] | Non
         raise ValueError("mode is 'count' or 'materialize'")
     prm.mode = _lib.HC_MODE_COUNT if mode == "count" else _lib.HC_MODE_MATERIALIZE
     prm.flags = ((_lib.HC_FLAG_CELL_COUNTS if cell_counts else 0) | (_lib.HC_FLAG_STATS if stats else 0)
-                 | (_lib.HC_FLAG_TIME_KERNELS if time_kernels else 0))
+                 | (_lib.HC_FLAG_TIME_KERNELS if time_kernels else 0) | (0 if lift else _lib.HC_FLAG_NO_LIFT))
+    prm.lift_arena = int(lift_arena)
     prm.item_grain = item_grain
     prm.block_threads = block_threads
     prm.merge_min = merge_min & 0xFFFFFFFF
@@ -345,7 +349,7 @@ def run_join(query: Query, indexes: Sequence[Index], shares: Sequence[int] | Non
 
 
 def _params(query: Query, shares=None, seeds=None, item_grain=0, block_threads=0, merge_min=0, merge_ratio=0,
-            slice_grain=0, mode="count", flags=0, out_capacity=0) -> _lib.hc_join_params:
+            slice_grain=0, mode="count", flags=0, out_capacity=0, lift=True, lift_arena=0) -> _lib.hc_join_params:
     prm = _lib.hc_join_params()
     sh = list(shares) if shares is not None else [1] * query.n_vars
     sd = list(seeds) if seeds is not None else list(DEFAULT_SEEDS)
@@ -353,7 +357,8 @@ def _params(query: Query, shares=None, seeds=None, item_grain=0, block_threads=0
         prm.shares[v] = sh[v] if v < len(sh) else 1
         prm.seeds[v] = (sd[v] if v < len(sd) else DEFAULT_SEEDS[v]) & 0xFFFFFFFF
     prm.mode = _lib.HC_MODE_COUNT if mode == "count" else _lib.HC_MODE_MATERIALIZE
-    prm.flags = flags
+    prm.flags = flags | (0 if lift else _lib.HC_FLAG_NO_LIFT)
+    prm.lift_arena = int(lift_arena)
     prm.item_grain = item_grain
     prm.block_threads = block_threads
     prm.merge_min = merge_min & 0xFFFFFFFF

@@ -18,6 +18,7 @@ HC_MODE_MATERIALIZE = 1
 HC_FLAG_CELL_COUNTS = 1
 HC_FLAG_STATS = 2
 HC_FLAG_TIME_KERNELS = 4
+HC_FLAG_NO_LIFT = 8
 HC_BUILD_CHECK_DUPLICATES = 1
 HC_BUILD_TIME_KERNELS = 2
 
@@ -53,7 +54,7 @@ class hc_join_params(ctypes.Structure):
     _fields_ = [("shares", ctypes.c_uint32 * HC_MAX_VARS), ("seeds", ctypes.c_uint32 * HC_MAX_VARS),
                 ("mode", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("item_grain", ctypes.c_uint32),
                 ("block_threads", ctypes.c_uint32), ("merge_min", ctypes.c_uint32), ("merge_ratio", ctypes.c_uint32),
-                ("slice_grain", ctypes.c_uint32), ("reserved0", ctypes.c_uint32), ("out_capacity", ctypes.c_uint64)]
+                ("slice_grain", ctypes.c_uint32), ("lift_arena", ctypes.c_uint32), ("out_capacity", ctypes.c_uint64)]
 
 
 class hc_result_view(ctypes.Structure):

@@ -65,7 +65,16 @@ struct DPlan {
     // entry) exceed slice_grain is cut into slices of about that many loop-3
     // candidates per loop-2 candidate (0: no slicing)
     uint32_t slice_grain;
+    // query rewriting (Sec. 5.1): the sources of the last loop that do not
+    // depend on the binding of the loop before it (bit q of far_mask) are
+    // intersected once per binding of loop nlev-3, into the warp's arena of
+    // arena_words words; the last loop reads that list in place of source
+    // far0 and skips the other far sources.  lift = 0: off.
+    int lift, far0;
+    uint32_t far_mask, arena_words;
 };
+
+constexpr uint32_t LIFT_ARENA_WORDS = 16384;  // per warp, by default
 
 struct JoinCtl {
     uint32_t err;
@@ -289,6 +298,9 @@ struct Frame {
     uint32_t par[NL];
     uint32_t olo[NL][O];
     uint32_t ohi[NL][O];
+    // lifted list of the loop nlev-3 binding held by this lane: arena[tlo, thi)
+    uint32_t tlo, thi;
+    bool lifted;  // the current batch's lifted lists fit the arena (lane-uniform)
 };
 
 struct Acc {
@@ -302,6 +314,7 @@ struct Acc {
     uint32_t chunk, fill, n_chunks;
     uint32_t* chunk_fill;
     JoinCtl* ctl;
+    uint32_t* arena;  // the warp's arena for lifted lists (query rewriting), or NULL
 };
 
 // Output slot of the lane holding rank r among the k = popc(ball) matches
@@ -386,6 +399,11 @@ __device__ __forceinline__ const uint32_t* src_list(const DPlan& P, int L, int q
     return P.src_top[L][q] ? a.v1 : a.v2;
 }
 
+// The list of source q of loop L, where source lift_q reads the arena.
+__device__ __forceinline__ const uint32_t* src_list_l(const DPlan& P, const Acc& A, int L, int q, int lift_q) {
+    return q == lift_q ? A.arena : src_list(P, L, q);
+}
+
 // Search candidate v (element kpos of source `best`) in the other lists of
 // loop L ("search(V, x)", Sec. 5: first position >= x, by binary search).  A
 // top-level list holding v opens its atom: the o1 range at v's position is
@@ -393,24 +411,29 @@ __device__ __forceinline__ const uint32_t* src_list(const DPlan& P, int L, int q
 template <int L, int S, int O>
 __device__ __forceinline__ bool probe(const DPlan& P, int best, const uint32_t (&rlo)[S], const uint32_t (&rhi)[S],
                                       uint32_t kpos, uint32_t v, bool active, uint32_t (&nlo)[O],
-                                      uint32_t (&nhi)[O]) {
+                                      uint32_t (&nhi)[O], uint32_t use = 0xFFFFFFFFu,
+                                      const uint32_t* lift_list = nullptr, int lift_q = -1) {
     bool ok = active;
 #pragma unroll
     for (int q = 0; q < S; ++q) {
-        if (q < P.nsrc[L]) {
-            const uint32_t* list = src_list(P, L, q);
+        if (q < P.nsrc[L] && ((use >> q) & 1u)) {
+            const uint32_t* list = q == lift_q ? lift_list : src_list(P, L, q);
             const DAtom& aq = P.atom[P.src_atom[L][q]];
             uint32_t p = kpos;
             if (q != best) {
-                if (P.src_top[L][q] && aq.v1pos != nullptr) {  // direct position of v in V1
+                if (q != lift_q && P.src_top[L][q] && aq.v1pos != nullptr) {  // direct position of v in V1
                     p = (ok && v < aq.v1pos_n) ? __ldg(aq.v1pos + v) : V1POS_NONE;
                     ok = ok && p >= rlo[q] && p < rhi[q];
+                } else if (q == lift_q) {  // the arena, written by this kernel: coherent loads
+                    uint32_t* al = const_cast<uint32_t*>(list);
+                    p = ok ? lower_bound_u32(al, rlo[q], rhi[q], v) : rhi[q];
+                    ok = ok && p < rhi[q] && al[p] == v;
                 } else {
                     p = ok ? lower_bound_u32(list, rlo[q], rhi[q], v) : rhi[q];
                     ok = ok && p < rhi[q] && list[p] == v;
                 }
             }
-            if (q < O && P.src_top[L][q] && ok) {  // top sources come first, slot == q
+            if (q < O && q != lift_q && P.src_top[L][q] && ok) {  // top sources come first, slot == q
                 const DAtom& a = P.atom[P.src_atom[L][q]];
                 nlo[q] = a.o1[p];
                 nhi[q] = a.o1[p + 1];
@@ -418,6 +441,123 @@ __device__ __forceinline__ bool probe(const DPlan& P, int best, const uint32_t (
         }
     }
     return ok;
+}
+
+// Range of source q of loop L for the loop L-2 binding held by lane
+// `lane_of` (all lanes call together): the source is fixed by the entry or
+// opened by loop L-2 or an earlier loop.
+template <int L, int NL, int S, int O>
+__device__ __forceinline__ void far_range(const DPlan& P, const Frame<NL, O>& F, const Entry<NL, S>& E, int q,
+                                          uint32_t lane_of, uint32_t& lo, uint32_t& hi) {
+    if (P.src_ec[L][q]) {
+        lo = E.lo[L][q];
+        hi = E.hi[L][q];
+        return;
+    }
+    const int f = P.src_f[L][q], s = P.src_slot[L][q];
+    uint32_t anc = lane_of;  // ancestor at loop f of the loop L-2 binding
+#pragma unroll
+    for (int g = L - 2; g >= 1; --g)
+        if (g > f) anc = __shfl_sync(0xffffffffu, F.par[g], anc);
+    uint32_t mylo = 0, myhi = 0;
+#pragma unroll
+    for (int g = 1; g <= L - 2; ++g)
+#pragma unroll
+        for (int ss = 0; ss < O; ++ss)
+            if (g == f && ss == s) {
+                mylo = F.olo[g][ss];
+                myhi = F.ohi[g][ss];
+            }
+    lo = __shfl_sync(0xffffffffu, mylo, anc);
+    hi = __shfl_sync(0xffffffffu, myhi, anc);
+}
+
+// Query rewriting (Sec. 5.1), at the start of loop NL-2: for each parent (a
+// loop NL-3 binding, lanes < nb) intersect the last loop's far sources once
+// and store the result, sorted, in the warp's arena at [F.tlo, F.thi) of the
+// parent's lane.  The parents' candidates are flattened over the lanes as in
+// run_level; a round's matches of one parent occupy consecutive lanes and are
+// written in lane order after those of earlier rounds.  Returns false (and
+// writes nothing) when the parents' lists could exceed the arena.
+template <int NL, int S, int O>
+__device__ __forceinline__ bool lift_compute(const DPlan& P, Frame<NL, O>& F, const Entry<NL, S>& E, const Acc& A,
+                                             uint32_t nb) {
+    constexpr int L = NL - 1;
+    const uint32_t lane = lane_id();
+    const int ns = P.nsrc[L];
+    uint32_t flo[S], fhi[S];
+    uint32_t best = 0, bestlen = 0xFFFFFFFFu;
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        flo[q] = fhi[q] = 0;
+        if (q < ns && ((P.far_mask >> q) & 1u)) {
+            far_range<L, NL, S, O>(P, F, E, q, lane < nb ? lane : 0, flo[q], fhi[q]);
+            const uint32_t len = fhi[q] - flo[q];
+            if (len < bestlen) {
+                bestlen = len;
+                best = q;
+            }
+        }
+    }
+    const uint32_t cnt = lane < nb ? bestlen : 0;  // candidates, and a bound on the parent's list
+    const uint32_t incl = warp_incl_scan(cnt);
+    const uint32_t excl = incl - cnt;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total > P.arena_words) return false;
+    uint32_t filled = 0;  // entries written for this lane's parent
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+        const uint32_t t = t0 + lane;
+        const bool active = t < total;
+        uint32_t p = 0;  // parent of candidate t: the last lane p < nb with excl_p <= t
+        if (nb > 1) {
+#pragma unroll
+            for (uint32_t step = 16; step >= 1; step >>= 1) {
+                const uint32_t c = p + step;
+                const uint32_t ex = __shfl_sync(0xffffffffu, excl, c & 31u);
+                if (c < nb && ex <= t) p = c;
+            }
+        }
+        const uint32_t pex = __shfl_sync(0xffffffffu, excl, p);
+        const uint32_t pbest = __shfl_sync(0xffffffffu, best, p);
+        const uint32_t pfill = __shfl_sync(0xffffffffu, filled, p);
+        uint32_t rlo[S], rhi[S];
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+            rlo[q] = __shfl_sync(0xffffffffu, flo[q], p);
+            rhi[q] = __shfl_sync(0xffffffffu, fhi[q], p);
+        }
+        uint32_t v = 0;
+#pragma unroll
+        for (int q = 0; q < S; ++q)
+            if (q == (int)pbest && active) v = src_list(P, L, q)[rlo[q] + (t - pex)];
+        bool ok = active;
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+            if (q < ns && ((P.far_mask >> q) & 1u) && q != (int)pbest) {
+                const uint32_t* list = src_list(P, L, q);
+                const uint32_t pos = ok ? lower_bound_u32(list, rlo[q], rhi[q], v) : rhi[q];
+                ok = ok && pos < rhi[q] && list[pos] == v;
+            }
+        }
+        const uint32_t ball = __ballot_sync(0xffffffffu, ok);
+        const uint32_t seg = pex > t0 ? pex - t0 : 0u;  // first lane of this round holding the parent
+        const uint32_t rank = __popc(ball & lanemask_lt() & ~((1u << seg) - 1u));
+        if (ok) A.arena[pex + pfill + rank] = v;
+        // a parent's matches in this round: rank + ok of its last lane here
+        const uint32_t mine = rank + (ok ? 1u : 0u);
+        uint32_t src = lane;
+        bool here = false;
+        if (lane < nb && cnt > 0 && excl < t0 + 32 && excl + cnt > t0) {
+            here = true;
+            src = min(excl + cnt, t0 + 32) - 1 - t0;
+        }
+        const uint32_t got = __shfl_sync(0xffffffffu, mine, src);
+        if (here) filled += got;
+    }
+    __syncwarp();
+    F.tlo = excl;
+    F.thi = excl + filled;
+    return true;
 }
 
 // Values bound by loops 1..L-1 for the binding of loop L-1 held by lane
@@ -466,13 +606,15 @@ __device__ __forceinline__ void finish_round(const DPlan& P, const Frame<NL, O>&
 // a sequential merge, so an equal pair is met by exactly one lane (the lane
 // owning its B position).  Count mode walks lanes independently; materialize
 // mode steps the lanes together and writes each step's matches in lane order.
-template <int L, int NL, int S, int O, bool MAT>
-__device__ __forceinline__ void merge_pair(const DPlan& P, const Entry<NL, S>& E, Acc& A, const uint32_t* la,
-                                           uint32_t a0, uint32_t a1, const uint32_t* lb, uint32_t b0, uint32_t b1,
+// LP is const uint32_t* for index lists (read through the read-only path)
+// and uint32_t* when a list is in the arena this kernel writes.
+template <int L, int NL, int S, int O, bool MAT, typename LP>
+__device__ __forceinline__ void merge_pair(const DPlan& P, const Entry<NL, S>& E, Acc& A, LP la, uint32_t a0,
+                                           uint32_t a1, LP lb, uint32_t b0, uint32_t b1,
                                            const uint32_t (&vals)[NL]) {
     const uint32_t lane = lane_id();
     if (a1 - a0 > b1 - b0) {  // B is the longer list
-        const uint32_t* t = la;
+        LP t = la;
         la = lb;
         lb = t;
         uint32_t u = a0;
@@ -499,16 +641,16 @@ __device__ __forceinline__ void merge_pair(const DPlan& P, const Entry<NL, S>& E
         // a step waits on no load issued in the same step
         uint32_t cnt = 0;
         if (i < i1 && j < j1) {
-            uint32_t x = __ldg(la + i), y = __ldg(lb + j);
-            uint32_t xn = __ldg(la + min(i + 1, i1 - 1)), yn = __ldg(lb + min(j + 1, j1 - 1));
+            uint32_t x = load_ro(la + i), y = load_ro(lb + j);
+            uint32_t xn = load_ro(la + min(i + 1, i1 - 1)), yn = load_ro(lb + min(j + 1, j1 - 1));
             for (;;) {
                 cnt += x == y ? 1u : 0u;
                 const bool ax = x <= y, ay = y <= x;
                 i += ax ? 1u : 0u;
                 j += ay ? 1u : 0u;
                 if (i >= i1 || j >= j1) break;
-                const uint32_t xnn = __ldg(la + min(i + 1, i1 - 1));
-                const uint32_t ynn = __ldg(lb + min(j + 1, j1 - 1));
+                const uint32_t xnn = load_ro(la + min(i + 1, i1 - 1));
+                const uint32_t ynn = load_ro(lb + min(j + 1, j1 - 1));
                 x = ax ? xn : x;
                 xn = ax ? xnn : xn;
                 y = ay ? yn : y;
@@ -566,13 +708,27 @@ __device__ __forceinline__ void run_level(const DPlan& P, Frame<NL, O>& F, const
     if constexpr (L < NL) {
         const uint32_t lane = lane_id();
         const int ns = P.nsrc[L];
+        // query rewriting: the last loop's far sources, once per parent of this loop
+        if constexpr (L == NL - 2 && NL >= 4) {
+            if (P.lift) F.lifted = lift_compute<NL, S, O>(P, F, E, A, nb);
+        }
+        bool lifted = false;
+        if constexpr (L == NL - 1 && NL >= 4) lifted = P.lift && F.lifted;
+        const uint32_t use = lifted ? ~(P.far_mask & ~(1u << P.far0)) : 0xFFFFFFFFu;  // sources read
+        const int lift_q = lifted ? P.far0 : -1;                                     // reads the arena
         uint32_t mlo[S], mhi[S];
         uint32_t best = 0, bestlen = 0xFFFFFFFFu;
 #pragma unroll
         for (int q = 0; q < S; ++q) {
             mlo[q] = mhi[q] = 0;
-            if (q < ns) {
-                src_range<L, NL, S, O>(P, F, E, q, lane < nb ? lane : 0, mlo[q], mhi[q]);
+            if (q < ns && ((use >> q) & 1u)) {
+                if (q == lift_q) {  // the lifted list of the parent's loop NL-3 ancestor
+                    const uint32_t anc = __shfl_sync(0xffffffffu, F.par[L - 1], lane < nb ? lane : 0);
+                    mlo[q] = __shfl_sync(0xffffffffu, F.tlo, anc);
+                    mhi[q] = __shfl_sync(0xffffffffu, F.thi, anc);
+                } else {
+                    src_range<L, NL, S, O>(P, F, E, q, lane < nb ? lane : 0, mlo[q], mhi[q]);
+                }
                 const uint32_t len = mhi[q] - mlo[q];
                 if (len < bestlen) {
                     bestlen = len;
@@ -605,11 +761,22 @@ __device__ __forceinline__ void run_level(const DPlan& P, Frame<NL, O>& F, const
             }
         }
         bool merge_class = false;
+        int qa = 0, qb = 1;  // the two lists of a merge pair
         if constexpr (L == NL - 1 && S >= 2) {
-            if (ns == 2 && lane < nb) {
-                const uint32_t l0 = mhi[0] - mlo[0], l1 = mhi[1] - mlo[1];
-                const uint32_t mn = min(l0, l1), mx = max(l0, l1);
-                merge_class = mn >= P.merge_min && (uint64_t)mx <= (uint64_t)P.merge_ratio * mn;
+            const uint32_t um = use & ((1u << ns) - 1u);
+            if (__popc(um) == 2) {
+                qa = __ffs(um) - 1;
+                qb = __ffs(um & (um - 1u)) - 1;
+                if (lane < nb) {
+                    uint32_t l0 = 0, l1 = 0;
+#pragma unroll
+                    for (int q = 0; q < S; ++q) {
+                        if (q == qa) l0 = mhi[q] - mlo[q];
+                        if (q == qb) l1 = mhi[q] - mlo[q];
+                    }
+                    const uint32_t mn = min(l0, l1), mx = max(l0, l1);
+                    merge_class = mn >= P.merge_min && (uint64_t)mx <= (uint64_t)P.merge_ratio * mn;
+                }
             }
         }
         if (A.stats && lane < nb) {
@@ -654,12 +821,12 @@ __device__ __forceinline__ void run_level(const DPlan& P, Frame<NL, O>& F, const
             for (int q = 0; q < S; ++q)
                 if (q == (int)pbest && active) {
                     kpos = rlo[q] + k;
-                    v = src_list(P, L, q)[kpos];
+                    v = src_list_l(P, A, L, q, lift_q)[kpos];
                 }
             uint32_t nlo[O], nhi[O];
 #pragma unroll
             for (int s = 0; s < O; ++s) nlo[s] = nhi[s] = 0;
-            const bool ok = probe<L, S, O>(P, (int)pbest, rlo, rhi, kpos, v, active, nlo, nhi);
+            const bool ok = probe<L, S, O>(P, (int)pbest, rlo, rhi, kpos, v, active, nlo, nhi, use, A.arena, lift_q);
             if constexpr (L == NL - 1)
                 finish_round<L, NL, S, O, MAT>(P, F, E, A, ok, v, p);
             else
@@ -667,14 +834,32 @@ __device__ __forceinline__ void run_level(const DPlan& P, Frame<NL, O>& F, const
         }
         if constexpr (L == NL - 1 && S >= 2) {
             uint32_t mball = __ballot_sync(0xffffffffu, merge_class);
+            uint32_t xa0 = 0, xa1 = 0, xb0 = 0, xb1 = 0;
+#pragma unroll
+            for (int q = 0; q < S; ++q) {
+                if (q == qa) {
+                    xa0 = mlo[q];
+                    xa1 = mhi[q];
+                }
+                if (q == qb) {
+                    xb0 = mlo[q];
+                    xb1 = mhi[q];
+                }
+            }
             while (mball) {
                 const uint32_t p = __ffs(mball) - 1;
                 mball &= mball - 1;
-                const uint32_t a0 = __shfl_sync(0xffffffffu, mlo[0], p), a1 = __shfl_sync(0xffffffffu, mhi[0], p);
-                const uint32_t b0 = __shfl_sync(0xffffffffu, mlo[1], p), b1 = __shfl_sync(0xffffffffu, mhi[1], p);
+                const uint32_t a0 = __shfl_sync(0xffffffffu, xa0, p), a1 = __shfl_sync(0xffffffffu, xa1, p);
+                const uint32_t b0 = __shfl_sync(0xffffffffu, xb0, p), b1 = __shfl_sync(0xffffffffu, xb1, p);
                 uint32_t vals[NL];
                 if constexpr (MAT) prefix_values<L, NL, O>(F, p, vals);
-                merge_pair<L, NL, S, O, MAT>(P, E, A, src_list(P, L, 0), a0, a1, src_list(P, L, 1), b0, b1, vals);
+                if (qa == lift_q || qb == lift_q)  // a list in the arena: coherent loads
+                    merge_pair<L, NL, S, O, MAT>(P, E, A, const_cast<uint32_t*>(src_list_l(P, A, L, qa, lift_q)), a0,
+                                                 a1, const_cast<uint32_t*>(src_list_l(P, A, L, qb, lift_q)), b0, b1,
+                                                 vals);
+                else
+                    merge_pair<L, NL, S, O, MAT>(P, E, A, src_list(P, L, qa), a0, a1, src_list(P, L, qb), b0, b1,
+                                                 vals);
             }
         }
     }
@@ -801,7 +986,8 @@ __global__ void __launch_bounds__(128, (NL <= 3 ? 16 : 12)) gj_kernel(const DPla
                                                     int pass, uint64_t* __restrict__ cell_counts,
                                                     uint64_t* __restrict__ item_counts,
                                                     const uint64_t* __restrict__ item_base, uint32_t* __restrict__ out,
-                                                    int stats, uint32_t* __restrict__ chunk_fill, uint32_t n_chunks) {
+                                                    int stats, uint32_t* __restrict__ chunk_fill, uint32_t n_chunks,
+                                                    uint32_t* __restrict__ arena) {
     __shared__ DPlan P;
     __shared__ uint32_t s_elo[4][NL][S], s_ehi[4][NL][S];  // per warp (blocks of <= 128 threads)
     load_plan(P, gP);
@@ -810,6 +996,7 @@ __global__ void __launch_bounds__(128, (NL <= 3 ? 16 : 12)) gj_kernel(const DPla
     const uint64_t U = uoff[E_n];
     const uint64_t nitems = (U + grain - 1) / grain;
     Frame<NL, O> F;
+    F.lifted = false;
     Acc A;
     A.count = 0;
     A.work = 0;
@@ -822,6 +1009,8 @@ __global__ void __launch_bounds__(128, (NL <= 3 ? 16 : 12)) gj_kernel(const DPla
     A.n_chunks = n_chunks;
     A.chunk_fill = chunk_fill;
     A.ctl = ctl;
+    A.arena = arena ? arena + (uint64_t)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * P.arena_words
+                    : nullptr;
     uint64_t total = 0;
     for (;;) {
         uint32_t item = 0;
@@ -889,6 +1078,7 @@ __global__ void __launch_bounds__(128, ((NLA <= 3 && NLB <= 3) ? 16 : 12))
     A.n_chunks = 0;
     A.chunk_fill = nullptr;
     A.ctl = nullptr;
+    A.arena = nullptr;  // batched plans do not lift
     for (;;) {
         uint32_t it = 0;
         if (lane == 0) it = atomicAdd(ctr, 1u);
@@ -919,11 +1109,13 @@ __global__ void __launch_bounds__(128, ((NLA <= 3 && NLB <= 3) ? 16 : 12))
         uint64_t c;
         if (b.shape == 0) {
             Frame<NLA, OA> F;
+            F.lifted = false;
             c = search_item<NLA, SA, OA, false>(P, F, A, (uint32_t(*)[SA])s_e[w], (uint32_t(*)[SA])(s_e[w] + NLA * SA),
                                                 local, b.grain, E_n, U, b.e_cell, b.e_x, b.e_rng, b.e_split, b.uoff,
                                                 nullptr, 0);
         } else {
             Frame<NLB, OB> F;
+            F.lifted = false;
             c = search_item<NLB, SB, OB, false>(P, F, A, (uint32_t(*)[SB])s_e[w], (uint32_t(*)[SB])(s_e[w] + NLB * SB),
                                                 local, b.grain, E_n, U, b.e_cell, b.e_x, b.e_rng, b.e_split, b.uoff,
                                                 nullptr, 0);
@@ -971,6 +1163,7 @@ struct GjArgs {
     int threads;
     uint32_t* chunk_fill;
     uint32_t n_chunks;
+    uint32_t* arena;  // lifted lists, P.arena_words per warp of the launch
 };
 
 template <int NL, int S, int O>
@@ -980,12 +1173,12 @@ hc_status launch_gj(bool mat, const GjArgs& g, cudaStream_t s) {
         gj_kernel<NL, S, O, true><<<grid, g.threads, 0, s>>>(g.plan, g.e_cell, g.e_x, g.e_rng, g.e_split, g.uoff,
                                                              g.grain, g.ctl,
                                                              g.pass, g.cell_counts, g.item_counts, g.item_base, g.out,
-                                                             g.stats, g.chunk_fill, g.n_chunks);
+                                                             g.stats, g.chunk_fill, g.n_chunks, g.arena);
     else
         gj_kernel<NL, S, O, false><<<grid, g.threads, 0, s>>>(g.plan, g.e_cell, g.e_x, g.e_rng, g.e_split, g.uoff,
                                                               g.grain,
                                                               g.ctl, g.pass, g.cell_counts, g.item_counts, g.item_base,
-                                                              g.out, g.stats, g.chunk_fill, g.n_chunks);
+                                                              g.out, g.stats, g.chunk_fill, g.n_chunks, g.arena);
     HC_CUDA_TRY(launch_check());
     return HC_OK;
 }
@@ -1272,6 +1465,31 @@ hc_status plan_query(const hc_query* q, const hc_index* const* idx, const hc_joi
     P.merge_min = prm->merge_min ? prm->merge_min : 32;
     P.merge_ratio = prm->merge_ratio ? prm->merge_ratio : 4;
     P.slice_grain = prm->slice_grain == 0xFFFFFFFFu ? 0 : (prm->slice_grain ? prm->slice_grain : 256);
+    // query rewriting (Sec. 5.1): the last loop's lists fixed before the loop
+    // above it ("far": top lists, lists of atoms opened by loop 1 or at least
+    // two loops up) are intersected once per binding of loop nv-3
+    P.lift = 0;
+    P.far0 = -1;
+    P.far_mask = 0;
+    P.arena_words = 0;
+    if (nv >= 4 && !out->stats && !(prm->flags & HC_FLAG_NO_LIFT)) {
+        const int Ls = nv - 1;
+        int nfar = 0;
+        for (int qq = 0; qq < P.nsrc[Ls]; ++qq) {
+            if (P.src_ec[Ls][qq] || P.src_f[Ls][qq] <= Ls - 2) {
+                P.far_mask |= 1u << qq;
+                if (P.far0 < 0) P.far0 = qq;
+                ++nfar;
+            }
+        }
+        if (nfar >= 2) {
+            P.lift = 1;
+            P.arena_words = prm->lift_arena ? prm->lift_arena : LIFT_ARENA_WORDS;
+        } else {
+            P.far0 = -1;
+            P.far_mask = 0;
+        }
+    }
     // loop-1 candidates are bounded by any loop-1 atom's rows times the
     // number of cells that read each of its partitions
     uint64_t cand_bound = UINT64_MAX;
@@ -1345,6 +1563,15 @@ hc_status enqueue_level1(const QueryPlan& qp, const Level1& L, JoinCtl* ctl, cud
     return HC_OK;
 }
 
+// Words of the lifted-list arena of a search launch: arena_words for every
+// warp either kind of search kernel (count or write) keeps resident.
+static uint64_t lift_arena_words(const QueryPlan& qp) {
+    if (!qp.P.lift) return 0;
+    const uint64_t blocks = (uint64_t)std::max(gj_grid_any(qp.nv, qp.shape_s, qp.shape_o, false, qp.threads),
+                                               gj_grid_any(qp.nv, qp.shape_s, qp.shape_o, true, qp.threads));
+    return blocks * (uint64_t)(qp.threads / 32) * qp.P.arena_words;
+}
+
 hc_status join_footprint_impl(const hc_query* q, const hc_index* const* idx, const hc_join_params* prm,
                               uint64_t* bytes) {
     if (!bytes) return fail(HC_ERR_ARG, "join_footprint: NULL argument");
@@ -1367,7 +1594,8 @@ hc_status join_footprint_impl(const hc_query* q, const hc_index* const* idx, con
     // loop-1 buffers (kept and temporary), per-cell arrays, scan look-back
     // words and the control block
     const uint64_t per_cand = 4 + 4 + 4 * 2 * MAXOPEN + 4 + 8 + 4 + 8 + 8;
-    *bytes = part_bytes + cb * per_cand + qp.ncells * (4 + 8 + 8) + ((cb + 2047) / 2048) * 8 * 3 + 65536;
+    *bytes = part_bytes + cb * per_cand + qp.ncells * (4 + 8 + 8) + ((cb + 2047) / 2048) * 8 * 3 + 65536 +
+             4 * lift_arena_words(qp);
     return HC_OK;
 }
 
@@ -1417,6 +1645,9 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
 
     GjArgs g{L.d_plan, L.e_cell, L.e_x,   L.e_rng, L.e_split, uoff,    grain,   ctl, 0, R->d_cell_counts,
              nullptr,  nullptr,  nullptr, stats,   threads,   nullptr, 0};
+    if (const uint64_t aw = lift_arena_words(qp)) {
+        if ((st = tmp.get(&g.arena, aw)) != HC_OK) return bail(st);
+    }
     const bool timed = (prm->flags & HC_FLAG_TIME_KERNELS) != 0;
     if (timed)
         for (auto& e : R->ev)
@@ -1628,6 +1859,7 @@ hc_status batch_create(const hc_query* qs, const hc_index* const* idx_flat, cons
         if (prm[i].mode != HC_MODE_COUNT) return bail(fail(HC_ERR_ARG, "batch: queries run in count mode"));
         hc_status st = plan_query(&qs[i], idx_flat + off, &prm[i], s, &B->plans[i]);
         if (st != HC_OK) return bail(st);
+        B->plans[i].P.lift = 0;  // the batched kernel's warps have no lifted-list arena
         off += qs[i].n_atoms;
         const int c = shape_class(B->plans[i]);
         if (c == SC_NONE) return bail(fail(HC_ERR_CAPACITY, "batch: queries of 3 or 4 variables are built in"));

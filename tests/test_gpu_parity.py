@@ -279,3 +279,53 @@ def test_wrong_attr_order_rejected(hc):
     with pytest.raises(hc.HoneycombError) as e:
         hc.run_join(hc.TRIANGLE, [ix1, ix1, ix1])
     assert e.value.status == 1
+
+
+# ------------------------------------------------------------ query rewriting
+
+@pytest.mark.parametrize("lift_arena", [0, 48, 1])
+def test_query_rewriting_four_clique(hc, lift_arena):
+    """Sec. 5.1: the last loop of the 4-clique (lists R3[y], R4[z], R6[x]) reads
+    R3[y] n R6[x], computed once per y.  Same result as without rewriting, for
+    the default arena, one that fits only some batches' lists and one that
+    fits none (every batch falls back to the unrewritten loop)."""
+    q = hc.FOUR_CLIQUE
+    for seed in range(3):
+        sym = datagen.random_graph(44 + 8 * seed, 0.32, 70 + seed)
+        for rel in (sym, datagen.orient_lt(sym)):
+            rels = [rel] * len(q.atoms)
+            ref = oracle.gj_enumerate(q.n_vars, list(q.atoms), rels)
+            for mmin, mratio in ((0, 0), (1, 1 << 30), (0xFFFFFFFF, 1)):
+                r = _run(hc, q, rels, lift_arena=lift_arena, merge_min=mmin, merge_ratio=mratio)
+                assert r.count == ref.shape[0], (seed, mmin)
+                r = _run(hc, q, rels, mode="materialize", lift_arena=lift_arena, merge_min=mmin, merge_ratio=mratio)
+                assert np.array_equal(sorted_rows(u32(r.tuples)), sorted_rows(ref)), (seed, mmin)
+                r = _run(hc, q, rels, mode="materialize", out_capacity=ref.shape[0] + 10, lift_arena=lift_arena,
+                         merge_min=mmin, merge_ratio=mratio)
+                assert np.array_equal(sorted_rows(u32(r.tuples)), sorted_rows(ref)), (seed, mmin)
+
+
+@pytest.mark.parametrize("order", [(0, 1, 2, 3), (1, 0, 2, 3), (2, 3, 0, 1), (3, 1, 0, 2)])
+def test_query_rewriting_orders_shares_and_relations(hc, order):
+    """Different relations per atom (the lifted lists differ from the loop's
+    own lists), loop orders and HyperCube shares."""
+    q = hc.FOUR_CLIQUE.with_order(order)
+    rng = np.random.default_rng(sum(order) + 5)
+    rels = [datagen.directed_set(rng.integers(0, 40, size=(500, 2)).astype(np.uint32)) for _ in q.atoms]
+    cnt, _, _ = oracle.gj_count(q.n_vars, list(q.atoms), rels, order=order)
+    for sh in ([1, 1, 1, 1], [2, 2, 1, 1], [1, 2, 2, 2]):
+        assert _run(hc, q, rels, shares=sh).count == cnt, sh
+        assert _run(hc, q, rels, shares=sh, lift=False).count == cnt, sh
+        assert _run(hc, q, rels, shares=sh, lift_arena=24).count == cnt, sh
+
+
+def test_query_rewriting_rmat_skew(hc):
+    """Skewed R-MAT degrees (hub lists larger than the arena in some batches)."""
+    q = hc.FOUR_CLIQUE
+    ep = datagen.orient_lt(datagen.rmat_graph(11, 16, 12))
+    rels = [ep] * len(q.atoms)
+    cnt, work, _ = oracle.gj_count(q.n_vars, list(q.atoms), rels)
+    for arena in (0, 256):
+        assert _run(hc, q, rels, lift_arena=arena).count == cnt
+    r = _run(hc, q, rels, stats=True)  # the work counter measures the unrewritten loops
+    assert r.count == cnt and r.work == work
