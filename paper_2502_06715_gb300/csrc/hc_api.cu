@@ -81,7 +81,8 @@ hc_status result_get(hc_result* r, hc_result_view* v);
 // intersection of lists of average lengths s_1..s_k over a domain of D values
 // keeps about s_1 * ... * s_k / D^(k-1) values (independence), at most
 // min s_q.  The per-binding averages give sum min N and sum max N (the
-// paper's own ratio estimate, the example after Lemma "cost-ub").
+// paper's own ratio estimate, the example after Lemma "cost-ub").  The
+// query rewriting run_join applies by default is part of the estimate.
 struct AtomStat {
     double rows, col0_distinct, col1_distinct;
 };
@@ -89,10 +90,19 @@ struct AtomStat {
 static void level_costs(const hc_query* q, const int* rank, const AtomStat* st, const double* dom, double* cost) {
     const int nv = (int)q->n_vars, na = (int)q->n_atoms;
     double bindings = 1.0;
+    double before[HC_MAX_VARS];  // bindings of the prefix query ahead of loop i
     for (int i = 0; i < nv; ++i) {
+        before[i] = bindings;
         int v = q->order[i];
+        // query rewriting (Sec. 5.1), as run_join applies it: at the last loop
+        // of a query of 4+ variables, two or more lists fixed before loop i-1
+        // ("far") are intersected once per binding of loop i-2; the result
+        // joins the last loop's lists, and its cost is charged to loop i-1
+        // (Sec. 5.2: the lifted relations count at the earlier loop)
+        const bool may_lift = i == nv - 1 && nv >= 4;
         double smin = INFINITY, smax = 0.0, prod = 1.0;
-        int k = 0;
+        double fmin = INFINITY, fmax = 0.0, fprod = 1.0;
+        int k = 0, kf = 0;
         for (int j = 0; j < na; ++j) {
             int a = q->atoms[j].var0, b = q->atoms[j].var1;
             if (a != v && b != v) continue;
@@ -102,9 +112,29 @@ static void level_costs(const hc_query* q, const int* rank, const AtomStat* st, 
             const int first = (unary || rank[a] < rank[b]) ? a : b;
             const double fd = first == a ? st[j].col0_distinct : st[j].col1_distinct;
             const double len = top ? fd : st[j].rows / std::max(1.0, fd);
+            if (may_lift && (top || rank[other] <= i - 2)) {
+                fmin = std::min(fmin, len);
+                fmax = std::max(fmax, len);
+                fprod *= len;
+                ++kf;
+                continue;
+            }
             smin = std::min(smin, len);
             smax = std::max(smax, len);
             prod *= len;
+            ++k;
+        }
+        if (kf == 1) {  // a single far list is not rewritten
+            smin = std::min(smin, fmin);
+            smax = std::max(smax, fmax);
+            prod *= fprod;
+            ++k;
+        } else if (kf >= 2) {
+            if (fmin > 0) cost[i - 1] += (double)kf * before[i - 1] * fmin * log2(1.0 + fmax / fmin);
+            const double lifted = std::min(fprod / pow(std::max(1.0, dom[v]), (double)(kf - 1)), fmin);
+            smin = std::min(smin, lifted);
+            smax = std::max(smax, lifted);
+            prod *= lifted;
             ++k;
         }
         if (k == 0 || !(smin > 0)) {
