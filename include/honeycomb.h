@@ -99,6 +99,18 @@ hc_status hc_build_index(const uint32_t* d_pairs, uint64_t n, uint32_t attr_orde
                          void* stream, hc_index** out);
 hc_status hc_index_free(hc_index* index);
 
+/* Index of a unary relation given as its values, strictly ascending, on the
+ * device (d_values[n], caller-owned, read only): the index of the pairs
+ * (value, 0) in attribute order 0 that hc_build_index would build, made
+ * without sorting and without waiting for the GPU.  V1 = the values, O1[i]
+ * = i (O1[n] = n), V2 = 0.  max_value must equal the largest value
+ * (d_values[n-1]); it sizes the V1 position map and the optimizer's domain
+ * estimate.  The order is not checked: unsorted or repeated values give
+ * wrong join results.  Used for the selections a serving request pushes into
+ * its query as unary atoms (Sec. 2).  0 <= n < 2^32 - 1. */
+hc_status hc_build_unary_index(const uint32_t* d_values, uint64_t n, uint32_t max_value, void* stream,
+                               hc_index** out);
+
 /* Read-only view of an index's device arrays (valid until hc_index_free). */
 typedef struct {
     uint64_t n;             /* rows                                            */

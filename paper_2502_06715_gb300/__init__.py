@@ -186,6 +186,25 @@ def build_index(pairs: torch.Tensor, attr_order: int = 0, check_duplicates: bool
     return Index(out.value)
 
 
+def build_unary_index(values: torch.Tensor, max_value: int | None = None, stream=None) -> Index:
+    """Index of a unary relation from its values, strictly ascending, as a 1-D
+    uint32 CUDA tensor (int32 storage), without sorting or waiting for the GPU
+    (pass ``max_value``, the last value, to avoid reading it back)."""
+    if values.dim() != 1 or values.element_size() != 4 or not values.is_cuda:
+        raise ValueError("values: a 1-D 32-bit CUDA tensor")
+    v = values.contiguous()
+    n = v.shape[0]
+    if max_value is None:
+        max_value = int(v[-1].item()) & 0xFFFFFFFF if n else 0
+    out = ctypes.c_void_p()
+    st = _lib.load().hc_build_unary_index(ctypes.c_void_p(v.data_ptr() if n else 0), n, int(max_value) & 0xFFFFFFFF,
+                                          ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(out))
+    _lib.check(st, "hc_build_unary_index")
+    ix = Index(out.value)
+    ix._values = v  # the build reads it on `stream`; kept until the index goes
+    return ix
+
+
 class Partitioned:
     def __init__(self, handle: int):
         self._h = ctypes.c_void_p(handle)

@@ -70,6 +70,8 @@ SIGNATURES = {
                                       ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "hc_index_from_stats": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                            ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)]),
+    "hc_build_unary_index": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_void_p)]),
     "hc_index_free": (ctypes.c_int, [ctypes.c_void_p]),
     "hc_coco_levels_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),

@@ -322,6 +322,11 @@ hc_status hc_build_index(const uint32_t* d_pairs, uint64_t n, uint32_t attr_orde
     return hc::build_index_impl(d_pairs, n, attr_order, flags, (cudaStream_t)stream, out);
 }
 
+hc_status hc_build_unary_index(const uint32_t* d_values, uint64_t n, uint32_t max_value, void* stream,
+                               hc_index** out) {
+    return hc::build_unary_impl(d_values, n, max_value, (cudaStream_t)stream, out);
+}
+
 hc_status hc_index_from_stats(uint64_t n, uint64_t l1, uint32_t attr_order, uint32_t max_first, uint32_t max_second,
                               hc_index** out) {
     if (!out) return hc::fail(HC_ERR_ARG, "index_from_stats: out is NULL");

@@ -235,6 +235,8 @@ hc_status partition_impl(const hc_index* idx, uint32_t seed_a, uint32_t pa, uint
                          uint32_t pb, cudaStream_t s, hc_partitioned** out);
 void partitioned_release(hc_partitioned* p, cudaStream_t s);
 void index_release(hc_index* idx, cudaStream_t s);
+hc_status build_unary_impl(const uint32_t* d_values, uint64_t n, uint32_t max_value, cudaStream_t s,
+                           hc_index** out);
 
 // Device-wide exclusive scan of counts into uint64 offsets; out[n] receives
 // the total.  n = min(n_max, *d_n) when d_n is given (a device-side count),

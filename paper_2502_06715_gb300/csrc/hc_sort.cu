@@ -754,6 +754,62 @@ hc_status build_index_impl(const uint32_t* d_pairs, uint64_t n, uint32_t ao, uin
     return HC_OK;
 }
 
+// Levels of a unary relation whose values are already sorted and distinct:
+// keys = value << 32, O1[i] = i (O1[n] = n), V2 = 0.
+__global__ void unary_levels_kernel(const uint32_t* __restrict__ values, uint64_t n, uint64_t* __restrict__ keys,
+                                    uint32_t* __restrict__ o1, uint32_t* __restrict__ v2) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i <= n; i += (uint64_t)gridDim.x * blockDim.x) {
+        o1[i] = (uint32_t)i;
+        if (i < n) {
+            keys[i] = (uint64_t)values[i] << 32;
+            v2[i] = 0;
+        }
+    }
+}
+
+hc_status build_unary_impl(const uint32_t* d_values, uint64_t n, uint32_t max_value, cudaStream_t s,
+                           hc_index** out) {
+    if (!out) return fail(HC_ERR_ARG, "build_unary_index: out is NULL");
+    *out = nullptr;
+    if (n > 0 && !d_values) return fail(HC_ERR_ARG, "build_unary_index: d_values is NULL");
+    if (n >= 0xFFFFFFFFull) return fail(HC_ERR_CAPACITY, "build_unary_index: n must be below 2^32 - 1");
+    hc_index* idx = new hc_index();
+    idx->n = n;
+    idx->l1 = n;  // distinct values: one run per row
+    idx->attr_order = 0;
+    idx->max_first = n ? max_value : 0;
+    idx->max_second = 0;
+    auto bail = [&](hc_status st) {
+        index_release(idx, s);
+        return st;
+    };
+    void* p;
+    if (dev_alloc(&p, std::max<uint64_t>(n, 1) * 8, s) != HC_OK) return bail(HC_ERR_OOM);
+    idx->d_keys = (uint64_t*)p;
+    if (dev_alloc(&p, std::max<uint64_t>(n, 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+    idx->d_v1 = (uint32_t*)p;
+    if (dev_alloc(&p, (n + 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+    idx->d_o1 = (uint32_t*)p;
+    if (dev_alloc(&p, std::max<uint64_t>(n, 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+    idx->d_v2 = (uint32_t*)p;
+    if (n > 0 && cudaMemcpyAsync(idx->d_v1, d_values, n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "copy"));
+    unary_levels_kernel<<<grid_for(n + 1, 256, 8), 256, 0, s>>>(d_values, n, idx->d_keys, idx->d_o1, idx->d_v2);
+    if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "unary_levels_kernel"));
+    if (v1pos_eligible(n, idx->max_first)) {
+        const uint64_t dn = (uint64_t)idx->max_first + 1;
+        if (dev_alloc(&p, dn * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+        idx->d_v1pos = (uint32_t*)p;
+        idx->v1pos_n = (uint32_t)dn;
+        if (cudaMemsetAsync(idx->d_v1pos, 0xFF, dn * 4, s) != cudaSuccess)
+            return bail(cuda_fail(cudaGetLastError(), "memset"));
+        v1pos_kernel<<<grid_for(n, 256, 8), 256, 0, s>>>(d_values, n, nullptr, idx->d_v1pos);
+        if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "v1pos_kernel"));
+    }
+    *out = idx;
+    return HC_OK;
+}
+
 void partitioned_release(hc_partitioned* p, cudaStream_t s) {
     if (!p) return;
     dev_free(p->d_keys, s);

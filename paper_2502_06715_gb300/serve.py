@@ -22,7 +22,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import Index, Query, build_index, join_footprint, run_join, run_join_async
+from . import Index, Query, build_unary_index, join_footprint, run_join, run_join_async
 
 
 @dataclass
@@ -47,10 +47,12 @@ class Outcome:
         return self.done - self.arrival
 
 
-def _unary_pairs(values: np.ndarray, device) -> torch.Tensor:
+def _unary_index(values: np.ndarray, device, stream) -> Index:
+    """The request's selection as a unary index (values sorted and distinct),
+    built on `stream` without waiting for the GPU."""
     v = np.ascontiguousarray(values, dtype=np.uint32)
-    pairs = np.stack([v, np.zeros_like(v)], axis=1)
-    return torch.from_numpy(pairs.view(np.int32)).to(device, non_blocking=False)
+    d = torch.from_numpy(v.view(np.int32)).to(device)
+    return build_unary_index(d, int(v[-1]) if v.shape[0] else 0, stream=stream)
 
 
 @dataclass
@@ -96,7 +98,7 @@ class Server:
                 queue.popleft()
                 s = streams.popleft()
                 with torch.cuda.stream(s):
-                    unary = build_index(_unary_pairs(req.restrict, self.device), 0, stream=s)
+                    unary = _unary_index(req.restrict, self.device, s)
                     pend = run_join_async(req.query, self._indexes(req, unary), stream=s, **self.options)
                     ev = torch.cuda.Event()
                     ev.record(s)
@@ -128,7 +130,7 @@ def serve_serial(server: Server, requests: list) -> list:
     for req in sorted(requests, key=lambda r: r.rid):
         t = time.perf_counter()
         with torch.cuda.stream(s):
-            unary = build_index(_unary_pairs(req.restrict, server.device), 0, stream=s)
+            unary = _unary_index(req.restrict, server.device, s)
             c = run_join(req.query, server._indexes(req, unary), stream=s, **server.options).count
             unary.free()
         s.synchronize()

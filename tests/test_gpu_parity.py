@@ -329,3 +329,31 @@ def test_query_rewriting_rmat_skew(hc):
         assert _run(hc, q, rels, lift_arena=arena).count == cnt
     r = _run(hc, q, rels, stats=True)  # the work counter measures the unrewritten loops
     assert r.count == cnt and r.work == work
+
+
+@pytest.mark.parametrize("n", [0, 1, 5, 4097, 100_000])
+def test_build_unary_index_matches_build_index(hc, n):
+    """The wait-free unary builder gives the index build_index makes of the
+    pairs (value, 0)."""
+    rng = np.random.default_rng(n + 3)
+    vals = np.unique(rng.integers(0, 1 << 22, size=2 * n + 1).astype(np.uint32))[:n]
+    import torch
+
+    d = torch.from_numpy(vals.view(np.int32)).cuda()
+    u = hc.build_unary_index(d, int(vals[-1]) if n else 0)
+    pairs = np.stack([vals, np.zeros_like(vals)], axis=1)
+    ref = hc.build_index(dev(pairs), 0)
+    assert (u.n, u.l1, u.max_first, u.max_second) == (ref.n, ref.l1, ref.max_first, ref.max_second)
+    if n:
+        assert np.array_equal(u32(u.v1()), u32(ref.v1()))
+        assert np.array_equal(u32(u.v2()), u32(ref.v2()))
+        assert np.array_equal(u.keys().cpu().numpy(), ref.keys().cpu().numpy())
+    assert np.array_equal(u32(u.o1()), u32(ref.o1()))
+    # as a selection in a join
+    sym = datagen.random_graph(60, 0.25, n % 7)
+    sel = np.unique(rng.integers(0, 60, size=25).astype(np.uint32))
+    q = hc.TRIANGLE.with_atoms([(0, -1)])
+    cnt, _, _ = oracle.gj_count(3, list(q.atoms), [sym] * 3 + [np.stack([sel, np.zeros_like(sel)], 1)])
+    us = hc.build_unary_index(torch.from_numpy(sel.view(np.int32)).cuda(), int(sel[-1]))
+    ix = hc.build_index(dev(sym), 0)
+    assert hc.run_join(q, [ix, ix, ix, us]).count == cnt
