@@ -62,6 +62,7 @@ class Server:
     max_inflight: int = 8
     device: str = "cuda"
     options: dict = field(default_factory=dict)
+    _fp: dict = field(default_factory=dict, repr=False)  # footprint cache
 
     def _indexes(self, req: Request, unary: Index) -> list:
         # every atom after the binary ones is a unary atom over the request's values
@@ -69,10 +70,20 @@ class Server:
         return [self.indexes[n] for n in req.relations] + [unary] * extra
 
     def footprint(self, req: Request) -> int:
-        # a statistics-only stand-in for the request's unary index
+        """Device bytes the request may take.  Cached per (query, relations,
+        size class of the selection): the class's largest selection (the next
+        power of two, values up to the next power of two) stands in for the
+        request's own, so the cached figure bounds every request of the class."""
         n = max(1, int(req.restrict.shape[0]))
-        stand_in = Index.from_stats(n, n, 0, int(req.restrict.max()) if req.restrict.shape[0] else 0, 0)
-        return join_footprint(req.query, self._indexes(req, stand_in), **self.options)
+        top = int(req.restrict.max()) if req.restrict.shape[0] else 0
+        cn, cv = 1 << (n - 1).bit_length(), (1 << max(1, top.bit_length())) - 1
+        key = (req.query.n_vars, tuple(req.query.atoms), req.query.order, tuple(req.relations), cn, cv)
+        fp = self._fp.get(key)
+        if fp is None:
+            stand_in = Index.from_stats(cn, cn, 0, cv, 0)
+            fp = join_footprint(req.query, self._indexes(req, stand_in), **self.options)
+            self._fp[key] = fp
+        return fp
 
     def run(self, requests: list, realtime: bool = True) -> list:
         """Serve requests arriving at req.arrival (seconds from now)."""
