@@ -1058,7 +1058,7 @@ __global__ void batch_items_kernel(const BQuery* __restrict__ qs, uint32_t n, ui
 template <int NLA, int SA, int OA, int NLB, int SB, int OB>
 __global__ void __launch_bounds__(128, ((NLA <= 3 && NLB <= 3) ? 16 : 12))
     gj_batch_kernel(const BQuery* __restrict__ qs, uint32_t n, const uint64_t* __restrict__ item_off,
-                    uint32_t* __restrict__ ctr) {
+                    uint32_t* __restrict__ ctr, uint32_t* __restrict__ arena, uint32_t arena_stride) {
     constexpr int NLM = NLA > NLB ? NLA : NLB;
     constexpr int SM = SA > SB ? SA : SB;
     __shared__ DPlan wplan[4];
@@ -1078,7 +1078,7 @@ __global__ void __launch_bounds__(128, ((NLA <= 3 && NLB <= 3) ? 16 : 12))
     A.n_chunks = 0;
     A.chunk_fill = nullptr;
     A.ctl = nullptr;
-    A.arena = nullptr;  // batched plans do not lift
+    A.arena = arena ? arena + (uint64_t)(blockIdx.x * 4 + w) * arena_stride : nullptr;
     for (;;) {
         uint32_t it = 0;
         if (lane == 0) it = atomicAdd(ctr, 1u);
@@ -1761,29 +1761,30 @@ static int shape_class(const QueryPlan& qp) {
 }
 
 template <int NLA, int SA, int OA, int NLB, int SB, int OB>
-hc_status launch_batch_kernel(const BQuery* q, uint32_t n, const uint64_t* item_off, uint32_t* ctr, cudaStream_t s) {
+hc_status launch_batch_kernel(const BQuery* q, uint32_t n, const uint64_t* item_off, uint32_t* ctr, uint32_t* arena,
+                              uint32_t stride, cudaStream_t s) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_batch_kernel<NLA, SA, OA, NLB, SB, OB>, 128, 0) !=
             cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
-    gj_batch_kernel<NLA, SA, OA, NLB, SB, OB><<<per_sm * num_sms(), 128, 0, s>>>(q, n, item_off, ctr);
+    gj_batch_kernel<NLA, SA, OA, NLB, SB, OB><<<per_sm * num_sms(), 128, 0, s>>>(q, n, item_off, ctr, arena, stride);
     HC_CUDA_TRY(launch_check());
     return HC_OK;
 }
 
 // (a, b) with a <= b; the kernel's shape 0 is class a, shape 1 class b.
 static hc_status launch_batch_pair(int a, int b, const BQuery* q, uint32_t n, const uint64_t* item_off, uint32_t* ctr,
-                                   cudaStream_t s) {
+                                   uint32_t* arena, uint32_t stride, cudaStream_t s) {
     switch (a * 8 + b) {
-        case SC_T * 8 + SC_T: return launch_batch_kernel<3, 2, 2, 3, 2, 2>(q, n, item_off, ctr, s);
-        case SC_T4 * 8 + SC_T4: return launch_batch_kernel<3, 4, 4, 3, 4, 4>(q, n, item_off, ctr, s);
-        case SC_C * 8 + SC_C: return launch_batch_kernel<4, 2, 2, 4, 2, 2>(q, n, item_off, ctr, s);
-        case SC_K * 8 + SC_K: return launch_batch_kernel<4, 4, 4, 4, 4, 4>(q, n, item_off, ctr, s);
-        case SC_T * 8 + SC_K: return launch_batch_kernel<3, 2, 2, 4, 4, 4>(q, n, item_off, ctr, s);
-        case SC_T * 8 + SC_C: return launch_batch_kernel<3, 2, 2, 4, 2, 2>(q, n, item_off, ctr, s);
-        case SC_C * 8 + SC_K: return launch_batch_kernel<4, 2, 2, 4, 4, 4>(q, n, item_off, ctr, s);
-        case SC_T4 * 8 + SC_K: return launch_batch_kernel<3, 4, 4, 4, 4, 4>(q, n, item_off, ctr, s);
+        case SC_T * 8 + SC_T: return launch_batch_kernel<3, 2, 2, 3, 2, 2>(q, n, item_off, ctr, arena, stride, s);
+        case SC_T4 * 8 + SC_T4: return launch_batch_kernel<3, 4, 4, 3, 4, 4>(q, n, item_off, ctr, arena, stride, s);
+        case SC_C * 8 + SC_C: return launch_batch_kernel<4, 2, 2, 4, 2, 2>(q, n, item_off, ctr, arena, stride, s);
+        case SC_K * 8 + SC_K: return launch_batch_kernel<4, 4, 4, 4, 4, 4>(q, n, item_off, ctr, arena, stride, s);
+        case SC_T * 8 + SC_K: return launch_batch_kernel<3, 2, 2, 4, 4, 4>(q, n, item_off, ctr, arena, stride, s);
+        case SC_T * 8 + SC_C: return launch_batch_kernel<3, 2, 2, 4, 2, 2>(q, n, item_off, ctr, arena, stride, s);
+        case SC_C * 8 + SC_K: return launch_batch_kernel<4, 2, 2, 4, 4, 4>(q, n, item_off, ctr, arena, stride, s);
+        case SC_T4 * 8 + SC_K: return launch_batch_kernel<3, 4, 4, 4, 4, 4>(q, n, item_off, ctr, arena, stride, s);
         default: return fail(HC_ERR_CAPACITY, "batch: this pair of query shapes is not built in");
     }
 }
@@ -1820,6 +1821,8 @@ struct hc_batch {
     uint32_t* d_ctr = nullptr;
     hc::Level1 temp;  // loop-1 temporaries shared by the queries (sized by the largest)
     int class_a = 0, class_b = 0;
+    uint32_t* d_arena = nullptr;  // lifted lists (query rewriting), arena_stride words per warp
+    uint32_t arena_stride = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t last_stream = nullptr;
@@ -1859,7 +1862,7 @@ hc_status batch_create(const hc_query* qs, const hc_index* const* idx_flat, cons
         if (prm[i].mode != HC_MODE_COUNT) return bail(fail(HC_ERR_ARG, "batch: queries run in count mode"));
         hc_status st = plan_query(&qs[i], idx_flat + off, &prm[i], s, &B->plans[i]);
         if (st != HC_OK) return bail(st);
-        B->plans[i].P.lift = 0;  // the batched kernel's warps have no lifted-list arena
+        if (B->plans[i].P.lift) B->arena_stride = std::max(B->arena_stride, B->plans[i].P.arena_words);
         off += qs[i].n_atoms;
         const int c = shape_class(B->plans[i]);
         if (c == SC_NONE) return bail(fail(HC_ERR_CAPACITY, "batch: queries of 3 or 4 variables are built in"));
@@ -1886,6 +1889,9 @@ hc_status batch_create(const hc_query* qs, const hc_index* const* idx_flat, cons
         if (st != HC_OK) return bail(st);
     }
     hc_status st;
+    if (B->arena_stride) {  // one arena per warp of the largest batched grid (16 blocks of 4 warps per SM)
+        if ((st = A.get(&B->d_arena, (size_t)num_sms() * 16 * 4 * B->arena_stride)) != HC_OK) return bail(st);
+    }
     if ((st = A.get(&B->d_ctl, n)) != HC_OK || (st = A.get(&B->d_q, n)) != HC_OK ||
         (st = A.get(&B->d_items, n)) != HC_OK || (st = A.get(&B->d_item_off, (size_t)n + 1)) != HC_OK ||
         (st = A.get(&B->d_ctr, 1)) != HC_OK)
@@ -1917,7 +1923,8 @@ static hc_status batch_enqueue(hc_batch* B, cudaStream_t s) {
     batch_items_kernel<<<(B->n + 255) / 256, 256, 0, s>>>(B->d_q, B->n, B->d_items);
     HC_CUDA_TRY(launch_check());
     HC_TRY(exclusive_scan_u64(B->d_items, B->d_item_off, B->n, nullptr, &B->d_ctl[0].err, s));
-    return launch_batch_pair(B->class_a, B->class_b, B->d_q, B->n, B->d_item_off, B->d_ctr, s);
+    return launch_batch_pair(B->class_a, B->class_b, B->d_q, B->n, B->d_item_off, B->d_ctr, B->d_arena,
+                             B->arena_stride, s);
 }
 
 hc_status batch_launch(hc_batch* B, cudaStream_t s) {
