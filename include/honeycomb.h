@@ -263,7 +263,8 @@ typedef struct {
     uint32_t slice_grain;         /* 4+ loops: loop-3 candidates per work slice of a     */
                                   /* loop-2 binding (0: default 256; 0xFFFFFFFF: none)   */
     uint32_t lift_arena;          /* query rewriting: words of device scratch per warp   */
-                                  /* for lifted intersections (0: default 16384)          */
+                                  /* for lifted intersections (0: default 16384; at most  */
+                                  /* 2^26)                                                 */
     uint64_t out_capacity;        /* materialize: 0 runs a counting pass, then an        */
                                   /* emitting pass (tuples cell-major, in a fixed order); */
                                   /* > 0 runs one pass writing into an output pool of    */
@@ -272,7 +273,10 @@ typedef struct {
 } hc_join_params;
 
 /* Generic Join of q over the indexes, one logical worker per HyperCube cell
- * (Sec. 5, Listing C of Fig. "algo-comp").
+ * (Sec. 5, Listing C of Fig. "algo-comp").  Limit: the search counts a
+ * batch's candidates (up to 32 bindings' shortest lists) in 32 bits, so no
+ * key of a relation may have 2^27 or more rows (R-MAT 23, 258 M rows, has
+ * at most about 10^6 per key).
  *   idx[j]   index bound to atom j; its attr_order must sort the atom's
  *            variables in loop order (Sec. 4: T(Z,X) under order X,Y,Z is
  *            sorted by X first), else HC_ERR_ARG.

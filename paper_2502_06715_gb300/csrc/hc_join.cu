@@ -500,6 +500,8 @@ __device__ __forceinline__ bool lift_compute(const DPlan& P, Frame<NL, O>& F, co
         }
     }
     const uint32_t cnt = lane < nb ? bestlen : 0;  // candidates, and a bound on the parent's list
+    // each bound fits the arena (arena_words <= 2^26), so their sum cannot wrap
+    if (__any_sync(0xffffffffu, cnt > P.arena_words)) return false;
     const uint32_t incl = warp_incl_scan(cnt);
     const uint32_t excl = incl - cnt;
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
@@ -1484,7 +1486,7 @@ hc_status plan_query(const hc_query* q, const hc_index* const* idx, const hc_joi
         }
         if (nfar >= 2) {
             P.lift = 1;
-            P.arena_words = prm->lift_arena ? prm->lift_arena : LIFT_ARENA_WORDS;
+            P.arena_words = std::min<uint32_t>(prm->lift_arena ? prm->lift_arena : LIFT_ARENA_WORDS, 1u << 26);
         } else {
             P.far0 = -1;
             P.far_mask = 0;
