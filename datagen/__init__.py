@@ -338,3 +338,81 @@ def random_graph(n: int, p: float, seed: int) -> np.ndarray:
     e = np.stack([iu[keep], ju[keep]], axis=1).astype(np.uint32)
     out = np.concatenate([e, e[:, ::-1]])
     return out[np.lexsort((out[:, 1], out[:, 0]))] if out.shape[0] else out.reshape(0, 2)
+
+
+# --- ternary relations (the tensor workloads of Sec. 6: ST-Dense, ST-Sparse) ---
+# The paper writes [N] for the integers 1..N; they are stored here as 0..N-1.
+
+
+def full_cube(n: int) -> np.ndarray:
+    """[n]^3 as an (n^3, 3) uint32 array, lexicographically sorted."""
+    g = np.arange(n, dtype=np.uint32)
+    a, b, c = np.meshgrid(g, g, g, indexing="ij")
+    return np.stack([a.ravel(), b.ravel(), c.ravel()], axis=1)
+
+
+def prefixed_square(first: np.ndarray, m: int) -> np.ndarray:
+    """first x [m] x [m]: every value of ``first`` (distinct) with every pair of [m]^2."""
+    f = np.unique(np.asarray(first, dtype=np.uint32))
+    g = np.arange(m, dtype=np.uint32)
+    a, b, c = np.meshgrid(f, g, g, indexing="ij")
+    return np.stack([a.ravel(), b.ravel(), c.ravel()], axis=1)
+
+
+def _distinct_keys(space: int, n: int, rng: np.random.Generator) -> np.ndarray:
+    """Exactly ``n`` distinct keys drawn uniformly from [0, space): draws are
+    kept in order of first appearance until ``n`` are found; sorted output."""
+    if n > space:
+        raise ValueError("more distinct keys requested than the space holds")
+    found = np.empty(0, dtype=np.uint64)
+    first_pos = np.empty(0, dtype=np.int64)
+    drawn = 0
+    while found.shape[0] < n:
+        need = n - found.shape[0]
+        frac = min(0.999, (found.shape[0] + need) / space)
+        k = max(1024, int(need * (1.05 - math.log1p(-frac) * 1.1)))
+        parts = []
+        for s0 in range(0, k, _CHUNK):
+            parts.append(rng.integers(0, space, size=min(_CHUNK, k - s0), dtype=np.int64).astype(np.uint64))
+        keys = np.concatenate(parts)
+        allk = np.concatenate([found, keys])
+        allpos = np.concatenate([first_pos, drawn + np.arange(keys.shape[0], dtype=np.int64)])
+        drawn += keys.shape[0]
+        uk, ui = np.unique(allk, return_index=True)
+        order = np.argsort(allpos[ui], kind="stable")
+        found = uk[order]
+        first_pos = allpos[ui][order]
+    return np.sort(found[:n])
+
+
+def st_dense(n: int = 512, m: int = 4096):
+    """ST-Dense (Sec. 6): four relations [n]^3, then three relations
+    F x [m] x [m] with first-attribute sets F = {0,1}, {0,2}, {1,2}."""
+    cube = full_cube(n)
+    return [cube, cube.copy(), cube.copy(), cube.copy()] + \
+        [prefixed_square(np.array(f, dtype=np.uint32), m) for f in ((0, 1), (0, 2), (1, 2))]
+
+
+def st_sparse(n: int = 512, domain: int = 5120, m: int = 4096, m_domain: int = 40960, seed: int = 0):
+    """ST-Sparse (Sec. 6): four relations of n^3 distinct tuples drawn
+    uniformly from [domain]^3, then three relations that keep ST-Dense's
+    first-attribute sets {0,1}, {0,2}, {1,2} and hold, under each first
+    value, m^2 distinct pairs drawn uniformly from [m_domain]^2.  Each
+    relation is lexicographically sorted; relation j draws from seed + j."""
+    out = []
+    for j in range(4):
+        k = _distinct_keys(domain ** 3, n ** 3, _rng(seed + j))
+        a = (k // np.uint64(domain * domain)).astype(np.uint32)
+        b = ((k // np.uint64(domain)) % np.uint64(domain)).astype(np.uint32)
+        c = (k % np.uint64(domain)).astype(np.uint32)
+        out.append(np.stack([a, b, c], axis=1))
+    for j, fs in enumerate(((0, 1), (0, 2), (1, 2))):
+        rng = _rng(seed + 4 + j)
+        parts = []
+        for f in fs:
+            k = _distinct_keys(m_domain * m_domain, m * m, rng)
+            b = (k // np.uint64(m_domain)).astype(np.uint32)
+            c = (k % np.uint64(m_domain)).astype(np.uint32)
+            parts.append(np.stack([np.full(k.shape[0], f, dtype=np.uint32), b, c], axis=1))
+        out.append(np.concatenate(parts))
+    return out

@@ -47,14 +47,14 @@ class OracleError(RuntimeError):
 
 
 def build(force: bool = False) -> str:
-    """Compile ``oracle.c`` with gcc into ``oracle/_build/liboracle.so``."""
+    """Compile ``oracle.c`` and ``oracle_kary.c`` with gcc into ``oracle/_build/liboracle.so``."""
     out_dir = os.path.join(_HERE, "_build")
     so = os.path.join(out_dir, "liboracle.so")
-    src = os.path.join(_HERE, "oracle.c")
-    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+    srcs = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "oracle_kary.c")]
+    if force or not os.path.exists(so) or any(os.path.getmtime(so) < os.path.getmtime(s) for s in srcs):
         os.makedirs(out_dir, exist_ok=True)
         tmp = so + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", src, "-o", tmp])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", *srcs, "-o", tmp])
         os.replace(tmp, so)
     return so
 
@@ -85,6 +85,9 @@ def _lib():
     lib.oc_gj_enumerate.restype = ctypes.c_int
     lib.oc_gj_enumerate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp), _u64p, _i32p,
                                     _i32p, _i32p, vp, u64, vp, u64, ctypes.POINTER(u64)]
+    lib.oc_kgj.restype = ctypes.c_int
+    lib.oc_kgj.argtypes = [ctypes.c_int, ctypes.c_int, _i32p, _i32p, ctypes.POINTER(vp), _u64p, vp, vp, u64,
+                           ctypes.POINTER(u64)]
     lib.oc_tuple_cells.restype = ctypes.c_int
     lib.oc_tuple_cells.argtypes = [vp, u64, ctypes.c_int, _u32p, _u32p, _u32p]
     _LIB = lib
@@ -231,3 +234,39 @@ FOUR_CYCLE = (4, [(0, 1), (0, 2), (1, 3), (2, 3)])           # Q2: R1(X,Y) R2(X,
 FOUR_DIAMOND = (4, [(0, 1), (0, 2), (1, 3), (2, 3), (1, 2)])  # Q4
 FOUR_CLIQUE = (4, [(0, 1), (0, 2), (1, 3), (2, 3), (1, 2), (0, 3)])  # Q6
 TWO_TRIANGLE = (5, [(0, 1), (0, 2), (1, 2), (2, 3), (2, 4), (3, 4)])  # Q8
+
+
+def kgj(n_vars: int, atoms, rels, order=None, tuples: bool = False, cap: int = 1 << 22):
+    """Generic Join over atoms of arity 1 to 3 (``oracle_kary.c``): atoms[j]
+    is a tuple of variable ids, rels[j] an (n, len(atoms[j])) array (a set).
+    Returns the output count, or (count, tuples in variable-id order) with
+    ``tuples`` (at most ``cap`` of them)."""
+    na = len(atoms)
+    if na != len(rels):
+        raise ValueError("one relation per atom")
+    arity = np.array([len(a) for a in atoms], dtype=np.int32)
+    vars_ = np.zeros(3 * na, dtype=np.int32)
+    keep = []
+    ptrs = (ctypes.c_void_p * na)()
+    ns = np.zeros(na, dtype=np.uint64)
+    for j, (a, r) in enumerate(zip(atoms, rels)):
+        if not 1 <= len(a) <= 3:
+            raise ValueError("atoms of arity 1 to 3")
+        vars_[3 * j:3 * j + len(a)] = a
+        arr = np.ascontiguousarray(np.asarray(r, dtype=np.uint32).reshape(-1, len(a)))
+        keep.append(arr)
+        ptrs[j] = arr.ctypes.data if arr.size else None
+        ns[j] = arr.shape[0]
+    ordv = None
+    if order is not None:
+        ordv = np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+    out = np.zeros((cap if tuples else 0, n_vars), dtype=np.uint32)
+    cnt = ctypes.c_uint64(0)
+    _check(_lib().oc_kgj(n_vars, na, arity, vars_, ptrs, ns,
+                         ordv.ctypes.data if ordv is not None else None,
+                         out.ctypes.data if tuples else None, cap if tuples else 0, ctypes.byref(cnt)), "kgj")
+    if not tuples:
+        return cnt.value
+    if cnt.value > cap:
+        raise OracleError("kgj: more tuples than cap")
+    return cnt.value, out[:cnt.value].copy()

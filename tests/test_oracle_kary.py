@@ -1,0 +1,186 @@
+"""Pins of the k-ary CPU oracle (oracle_kary.c) to facts other than itself.
+
+The queries are the paper's hypergraph queries over ternary relations
+(Table "Queries": LW, Loomis-Whitney; CT, Clover-Triangle) plus mixed
+arities.  Checks: brute force over every tuple of a tiny domain, closed
+forms on full cubes and on relations with prescribed first-attribute sets
+(the shapes of Sec. 6's ST-Dense tensors), agreement with the separately
+written binary Generic Join oracle on graphs, and the paper's invariant that
+the loop order changes the work but not the result (Sec. 5).
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+# Q(X,Y,Z,U) := R1(X,Y,Z), R2(X,Y,U), R3(X,Z,U), R4(Y,Z,U)   with X=0 Y=1 Z=2 U=3
+LW = (4, [(0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)])
+# Q(U,X,Y,Z) := R5(U,X,Y), R6(U,X,Z), R7(U,Y,Z)              with U=0 X=1 Y=2 Z=3
+CT = (4, [(0, 1, 2), (0, 1, 3), (0, 2, 3)])
+
+
+def brute(n_vars, atoms, rels, dom):
+    """Every assignment of the variables over range(dom), kept when each
+    atom's projection is one of its relation's rows."""
+    sets = [set(map(tuple, np.asarray(r, dtype=np.int64).reshape(-1, len(a)).tolist())) for a, r in zip(atoms, rels)]
+    out = []
+    for t in itertools.product(range(dom), repeat=n_vars):
+        if all(tuple(t[v] for v in a) in s for a, s in zip(atoms, sets)):
+            out.append(t)
+    return np.array(out, dtype=np.uint32).reshape(-1, n_vars)
+
+
+def random_rel(rng, k, dom, density):
+    full = np.array(list(itertools.product(range(dom), repeat=k)), dtype=np.uint32).reshape(-1, k)
+    keep = rng.random(full.shape[0]) < density
+    return full[keep]
+
+
+def sorted_rows(a):
+    a = np.asarray(a)
+    return a if a.shape[0] == 0 else a[np.lexsort(a.T[::-1])]
+
+
+@pytest.mark.parametrize("name,query", [("LW", LW), ("CT", CT)])
+@pytest.mark.parametrize("seed", range(6))
+def test_brute_force_hypergraph(name, query, seed):
+    nv, atoms = query
+    rng = np.random.default_rng(seed)
+    dom = 5
+    rels = [random_rel(rng, 3, dom, rng.choice([0.3, 0.6, 0.9])) for _ in atoms]
+    want = brute(nv, atoms, rels, dom)
+    cnt, got = oracle.kgj(nv, atoms, rels, tuples=True)
+    assert cnt == want.shape[0]
+    assert np.array_equal(sorted_rows(got), sorted_rows(want))
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_brute_force_mixed_arity(seed):
+    """Atoms of arity 1, 2 and 3 together, columns listing variables out of
+    their id order (a transposed column mapping fails here)."""
+    rng = np.random.default_rng(100 + seed)
+    dom = 5
+    nv = 5
+    atoms = [(2, 0, 4), (3, 1), (4,), (1, 2, 0), (3, 4)]
+    rels = [random_rel(rng, len(a), dom, rng.choice([0.4, 0.7, 0.95])) for a in atoms]
+    want = brute(nv, atoms, rels, dom)
+    cnt, got = oracle.kgj(nv, atoms, rels, tuples=True)
+    assert cnt == want.shape[0]
+    assert np.array_equal(sorted_rows(got), sorted_rows(want))
+
+
+def test_asymmetric_columns_are_not_swapped():
+    """R(X,Y,Z) = {(0,1,2)} joined with unary atoms on each variable: exactly
+    one output, and it is (0,1,2) in variable-id order, not a permutation."""
+    atoms = [(0, 1, 2), (0,), (1,), (2,)]
+    rels = [np.array([[0, 1, 2]]), np.array([[0]]), np.array([[1]]), np.array([[2]])]
+    for order in itertools.permutations(range(3)):
+        cnt, got = oracle.kgj(3, atoms, rels, order=order, tuples=True)
+        assert cnt == 1 and got.tolist() == [[0, 1, 2]]
+    rels[1] = np.array([[1]])  # X must be 0 in R: no output
+    assert oracle.kgj(3, atoms, rels) == 0
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 9])
+def test_lw_on_full_cubes(n):
+    """Every relation [n]^3: every assignment of (X,Y,Z,U) survives, n^4."""
+    cube = datagen.full_cube(n)
+    assert cube.shape == (n ** 3, 3)
+    assert oracle.kgj(*LW, [cube] * 4) == n ** 4
+
+
+@pytest.mark.parametrize("s,m", [(1, 4), (2, 6), (3, 5)])
+def test_ct_common_first_attribute(s, m):
+    """R5, R6, R7 = S x [m] x [m] with the same S: U ranges over S and X, Y,
+    Z over [m] freely, |S| m^3."""
+    first = np.arange(10, 10 + s, dtype=np.uint32)
+    rels = [datagen.prefixed_square(first, m)] * 3
+    assert oracle.kgj(*CT, rels) == s * m ** 3
+
+
+def test_ct_on_st_dense_first_attribute_sets():
+    """Sec. 6's last three ST-Dense relations take their first attribute from
+    {0,1}, {0,2} and {1,2}.  CT joins all three on that attribute, and the
+    three sets have no common value, so the count is 0; widening the middle
+    set to {0,1,2} leaves U = 1 and m^3 results."""
+    m = 6
+    sets = [np.array([0, 1]), np.array([0, 2]), np.array([1, 2])]
+    rels = [datagen.prefixed_square(s.astype(np.uint32), m) for s in sets]
+    assert oracle.kgj(*CT, rels) == 0
+    rels[1] = datagen.prefixed_square(np.array([0, 1, 2], dtype=np.uint32), m)
+    assert oracle.kgj(*CT, rels) == m ** 3
+
+
+def test_st_dense_generator_shapes():
+    rels = datagen.st_dense(n=8, m=16)
+    assert len(rels) == 7
+    for r in rels[:4]:
+        assert r.shape == (8 ** 3, 3) and r.dtype == np.uint32
+    for r, s in zip(rels[4:], ({0, 1}, {0, 2}, {1, 2})):
+        assert r.shape == (2 * 16 * 16, 3)
+        assert set(np.unique(r[:, 0]).tolist()) == s
+    # [N] is the positive integers up to N, stored as 0 .. N-1
+    assert int(rels[0].max()) == 7 and int(rels[4][:, 1:].max()) == 15
+
+
+def test_st_sparse_generator():
+    rels = datagen.st_sparse(n=6, domain=60, m=8, m_domain=80, seed=3)
+    assert len(rels) == 7
+    for r in rels[:4]:
+        assert r.shape == (6 ** 3, 3)
+        assert np.unique(r, axis=0).shape[0] == r.shape[0]  # a set
+        assert int(r.max()) < 60
+    for r, s in zip(rels[4:], ({0, 1}, {0, 2}, {1, 2})):
+        assert r.shape == (2 * 8 * 8, 3)
+        assert np.unique(r, axis=0).shape[0] == r.shape[0]
+        assert set(np.unique(r[:, 0]).tolist()) == s
+        for f in s:  # m^2 pairs under each first value
+            assert int((r[:, 0] == f).sum()) == 8 * 8
+        assert int(r[:, 1:].max()) < 80
+    again = datagen.st_sparse(n=6, domain=60, m=8, m_domain=80, seed=3)
+    assert all(np.array_equal(a, b) for a, b in zip(rels, again))
+
+
+@pytest.mark.parametrize("q", ["TRIANGLE", "FOUR_CYCLE", "FOUR_CLIQUE", "TWO_TRIANGLE"])
+def test_binary_atoms_match_binary_oracle(q):
+    nv, atoms = getattr(oracle, q)
+    sym = datagen.random_graph(40, 0.25, 5)
+    ep = datagen.orient_lt(sym)
+    for rel in (sym, ep):
+        want, _, _ = oracle.gj_count(nv, atoms, [rel] * len(atoms))
+        assert oracle.kgj(nv, atoms, [rel] * len(atoms)) == want
+
+
+@pytest.mark.parametrize("name,query", [("LW", LW), ("CT", CT)])
+def test_order_invariance(name, query):
+    nv, atoms = query
+    rng = np.random.default_rng(77)
+    rels = [random_rel(rng, 3, 6, 0.5) for _ in atoms]
+    ref = None
+    for order in itertools.permutations(range(nv)):
+        cnt, got = oracle.kgj(nv, atoms, rels, order=order, tuples=True)
+        got = sorted_rows(got)
+        if ref is None:
+            ref = got
+        assert cnt == ref.shape[0] and np.array_equal(got, ref), order
+
+
+def test_empty_relation_and_cap():
+    nv, atoms = LW
+    cube = datagen.full_cube(3)
+    assert oracle.kgj(nv, atoms, [cube, cube, cube, cube[:0]]) == 0
+    with pytest.raises(oracle.OracleError):
+        oracle.kgj(nv, atoms, [cube] * 4, tuples=True, cap=10)  # 81 > cap
+
+
+def test_bad_arguments():
+    cube = datagen.full_cube(2)
+    with pytest.raises(oracle.OracleError):
+        oracle.kgj(3, [(0, 0, 1)], [cube])  # a variable twice in one atom
+    with pytest.raises(oracle.OracleError):
+        oracle.kgj(4, [(0, 1, 2)], [cube])  # U in no atom
+    with pytest.raises(oracle.OracleError):
+        oracle.kgj(3, [(0, 1, 2)], [cube], order=[0, 0, 1])
