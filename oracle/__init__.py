@@ -87,7 +87,7 @@ def _lib():
                                     _i32p, _i32p, vp, u64, vp, u64, ctypes.POINTER(u64)]
     lib.oc_kgj.restype = ctypes.c_int
     lib.oc_kgj.argtypes = [ctypes.c_int, ctypes.c_int, _i32p, _i32p, ctypes.POINTER(vp), _u64p, vp, vp, u64,
-                           ctypes.POINTER(u64)]
+                           ctypes.POINTER(u64), ctypes.POINTER(u64)]
     lib.oc_tuple_cells.restype = ctypes.c_int
     lib.oc_tuple_cells.argtypes = [vp, u64, ctypes.c_int, _u32p, _u32p, _u32p]
     _LIB = lib
@@ -203,6 +203,36 @@ def gj_count(n_vars: int, atoms, rels, order=None, filt=None, nthreads: int = 1,
     return cnt.value, work.value, None
 
 
+def kcoco(rows, level_cols=None) -> dict:
+    """k-level CoCo of a relation of arity k = 1..3 (Sec. 4): the rows
+    sorted lexicographically with column level_cols[0] first; for each level
+    d, V_d = the level-d value of each distinct prefix of length d+1 (in
+    sorted order) and, for d < k-1, O_d[e] = the position in level d+1 of
+    prefix e's first child, O_d[l_d] = l_{d+1}; the last level holds every
+    row.  Returns {"V": [V_0, ..], "O": [O_0, ..]} as uint32 arrays."""
+    r = np.asarray(rows, dtype=np.uint32)
+    k = r.shape[1]
+    cols = list(range(k)) if level_cols is None else list(level_cols)
+    r = r[:, cols]
+    if r.shape[0]:
+        r = r[np.lexsort(r.T[::-1])]  # a library sort, lexicographic by level 0, 1, ..
+    first = []  # per level: the sorted rows' index where each distinct prefix starts
+    for d in range(k):
+        if r.shape[0] == 0:
+            first.append(np.zeros(0, dtype=np.int64))
+            continue
+        pref = r[:, :d + 1]
+        new = np.ones(r.shape[0], dtype=bool)
+        new[1:] = np.any(pref[1:] != pref[:-1], axis=1)
+        first.append(np.flatnonzero(new))
+    V = [r[first[d], d].astype(np.uint32) for d in range(k)]
+    O = []
+    for d in range(k - 1):
+        o = np.searchsorted(first[d + 1], first[d]).astype(np.uint32)
+        O.append(np.append(o, np.uint32(first[d + 1].shape[0])))
+    return {"V": V, "O": O}
+
+
 def gj_enumerate(n_vars: int, atoms, rels, order=None, filt=None) -> np.ndarray:
     """All output tuples, (count, n_vars) uint32 in variable-id order."""
     rels, ptrs, ns, v0, v1, od = _query_args(n_vars, atoms, rels, order)
@@ -236,11 +266,13 @@ FOUR_CLIQUE = (4, [(0, 1), (0, 2), (1, 3), (2, 3), (1, 2), (0, 3)])  # Q6
 TWO_TRIANGLE = (5, [(0, 1), (0, 2), (1, 2), (2, 3), (2, 4), (3, 4)])  # Q8
 
 
-def kgj(n_vars: int, atoms, rels, order=None, tuples: bool = False, cap: int = 1 << 22):
+def kgj(n_vars: int, atoms, rels, order=None, tuples: bool = False, cap: int = 1 << 22, work: bool = False):
     """Generic Join over atoms of arity 1 to 3 (``oracle_kary.c``): atoms[j]
     is a tuple of variable ids, rels[j] an (n, len(atoms[j])) array (a set).
     Returns the output count, or (count, tuples in variable-id order) with
-    ``tuples`` (at most ``cap`` of them)."""
+    ``tuples`` (at most ``cap`` of them); with ``work``, (count, work) or
+    (count, tuples, work), work being the sum over loops and bindings of
+    (number of lists) * (shortest list length)."""
     na = len(atoms)
     if na != len(rels):
         raise ValueError("one relation per atom")
@@ -262,11 +294,14 @@ def kgj(n_vars: int, atoms, rels, order=None, tuples: bool = False, cap: int = 1
         ordv = np.ascontiguousarray(np.asarray(order, dtype=np.int32))
     out = np.zeros((cap if tuples else 0, n_vars), dtype=np.uint32)
     cnt = ctypes.c_uint64(0)
+    wk = ctypes.c_uint64(0)
     _check(_lib().oc_kgj(n_vars, na, arity, vars_, ptrs, ns,
                          ordv.ctypes.data if ordv is not None else None,
-                         out.ctypes.data if tuples else None, cap if tuples else 0, ctypes.byref(cnt)), "kgj")
+                         out.ctypes.data if tuples else None, cap if tuples else 0, ctypes.byref(cnt),
+                         ctypes.byref(wk) if work else None), "kgj")
+    extra = (wk.value,) if work else ()
     if not tuples:
-        return cnt.value
+        return (cnt.value, *extra) if work else cnt.value
     if cnt.value > cap:
         raise OracleError("kgj: more tuples than cap")
-    return cnt.value, out[:cnt.value].copy()
+    return (cnt.value, out[:cnt.value].copy(), *extra)

@@ -17,6 +17,12 @@
  *     range), narrows every such atom's range to the value's rows and goes to
  *     loop i+1.  Each complete binding is one output tuple of Eq. "full:cq".
  *
+ * With a work output, each loop also adds (number of lists) * (shortest list
+ * length) for every binding it runs under, a list's length being the number
+ * of distinct values of the variable's column in the atom's range: the work
+ * measure of the library's statistics (the per-binding cost of Sec. 5.2
+ * without its log factor).
+ *
  * Errors are returned as non-zero codes.
  */
 #include <stdint.h>
@@ -48,6 +54,8 @@ typedef struct {
     uint64_t lo[OK_MAXA], hi[OK_MAXA];
     uint32_t bind[OK_MAXV];
     uint64_t count;
+    uint64_t work;
+    int want_work;
     uint32_t *out;
     uint64_t cap;
 } kplan_t;
@@ -90,7 +98,24 @@ static void emit(kplan_t *p) {
     p->count++;
 }
 
+/* Distinct values of column d in rows [lo, hi) (sorted there). */
+static uint64_t distinct_in(const katom_t *a, uint64_t lo, uint64_t hi, int d) {
+    uint64_t c = 0;
+    for (uint64_t r = lo; r < hi; ++r)
+        if (r == lo || a->r[r].c[d] != a->r[r - 1].c[d]) c++;
+    return c;
+}
+
 static void loop_level(kplan_t *p, int i) {
+    if (p->want_work) {
+        uint64_t shortest = UINT64_MAX;
+        for (int q = 0; q < p->nat[i]; ++q) {
+            const int j = p->at[i][q];
+            const uint64_t len = distinct_in(&p->a[j], p->lo[j], p->hi[j], p->dep[i][q]);
+            if (len < shortest) shortest = len;
+        }
+        p->work += (uint64_t)p->nat[i] * shortest;
+    }
     /* the atom with the fewest rows in range supplies the candidates */
     int drv = -1;
     for (int q = 0; q < p->nat[i]; ++q) {
@@ -148,9 +173,10 @@ static void loop_level(kplan_t *p, int i) {
  *   rows[j]        n[j] rows of arity[j] values, row-major (relations are sets)
  *   order          loop order (variable ids), or NULL for 0, 1, ...
  *   out, cap       optional: up to cap tuples of nv values (variable-id order)
- *   count_out      number of output tuples */
+ *   count_out      number of output tuples
+ *   work_out       optional: the work measure described at the top */
 int oc_kgj(int nv, int na, const int *arity, const int *vars, const uint32_t *const *rows, const uint64_t *n,
-           const int *order, uint32_t *out, uint64_t cap, uint64_t *count_out) {
+           const int *order, uint32_t *out, uint64_t cap, uint64_t *count_out, uint64_t *work_out) {
     if (nv < 1 || nv > OK_MAXV || na < 1 || na > OK_MAXA || !arity || !vars || !rows || !n || !count_out)
         return OK_EARG;
     kplan_t *p = (kplan_t *)calloc(1, sizeof(kplan_t));
@@ -223,8 +249,10 @@ int oc_kgj(int nv, int na, const int *arity, const int *vars, const uint32_t *co
         }
     p->out = out;
     p->cap = out ? cap : 0;
+    p->want_work = work_out != NULL;
     loop_level(p, 0);
     *count_out = p->count;
+    if (work_out) *work_out = p->work;
 done:
     for (int j = 0; j < na; ++j) free(p->a[j].r);
     free(p);

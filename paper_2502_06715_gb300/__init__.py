@@ -492,3 +492,8 @@ class _ResultHandle:
             self.free()
         except Exception:
             pass
+
+
+from .kary import CT, LW, KIndex, KQuery, build_kindex, run_kjoin  # noqa: E402  (k-ary relations)
+
+__all__ += ["KQuery", "KIndex", "build_kindex", "run_kjoin", "LW", "CT"]

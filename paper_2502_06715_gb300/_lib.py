@@ -1,4 +1,5 @@
-"""ctypes declarations of the C ABI in include/honeycomb.h.
+"""ctypes declarations of the C ABI in include/honeycomb.h and
+include/honeycomb_kary.h.
 
 Loading fails loudly when the library has not been built: there is no
 fallback implementation.
@@ -12,6 +13,8 @@ from . import build as _build
 
 HC_MAX_VARS = 8
 HC_MAX_ATOMS = 12
+HC_KMAX_ARITY = 3
+HC_KMAX_VARS = 6
 
 HC_MODE_COUNT = 0
 HC_MODE_MATERIALIZE = 1
@@ -64,6 +67,27 @@ class hc_result_view(ctypes.Structure):
                 ("n_join_launches", ctypes.c_uint32)]
 
 
+class hc_kindex_view(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("arity", ctypes.c_uint32), ("level_cols", ctypes.c_uint8 * HC_KMAX_ARITY),
+                ("packed", ctypes.c_uint8), ("len", ctypes.c_uint64 * HC_KMAX_ARITY),
+                ("max_value", ctypes.c_uint32 * HC_KMAX_ARITY), ("d_v", ctypes.c_void_p * HC_KMAX_ARITY),
+                ("d_o", ctypes.c_void_p * HC_KMAX_ARITY), ("ms_sort", ctypes.c_float), ("ms_levels", ctypes.c_float)]
+
+
+class hc_katom(ctypes.Structure):
+    _fields_ = [("arity", ctypes.c_uint8), ("var", ctypes.c_uint8 * HC_KMAX_ARITY)]
+
+
+class hc_kquery(ctypes.Structure):
+    _fields_ = [("n_vars", ctypes.c_uint32), ("n_atoms", ctypes.c_uint32),
+                ("atoms", hc_katom * HC_MAX_ATOMS), ("order", ctypes.c_uint8 * HC_MAX_VARS)]
+
+
+class hc_kjoin_params(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("item_grain", ctypes.c_uint32),
+                ("block_threads", ctypes.c_uint32)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "hc_build_index": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
@@ -101,6 +125,14 @@ SIGNATURES = {
     "hc_batch_capture": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "hc_batch_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
     "hc_batch_free": (ctypes.c_int, [ctypes.c_void_p]),
+    "hc_build_kindex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                                       ctypes.POINTER(ctypes.c_uint8), ctypes.c_uint32, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "hc_kindex_free": (ctypes.c_int, [ctypes.c_void_p]),
+    "hc_kindex_get_view": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hc_kindex_view)]),
+    "hc_run_kjoin": (ctypes.c_int, [ctypes.POINTER(hc_kquery), ctypes.POINTER(ctypes.c_void_p),
+                                    ctypes.POINTER(hc_kjoin_params), ctypes.c_void_p,
+                                    ctypes.POINTER(ctypes.c_void_p)]),
     "hc_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "hc_last_error": (ctypes.c_char_p, []),
     "hc_version": (ctypes.c_uint32, []),

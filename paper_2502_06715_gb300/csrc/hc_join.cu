@@ -76,17 +76,6 @@ struct DPlan {
 
 constexpr uint32_t LIFT_ARENA_WORDS = 16384;  // per warp, by default
 
-struct JoinCtl {
-    uint32_t err;
-    uint32_t item_ctr[2];
-    uint32_t n_entries;  // loop-1 bindings, written by the loop-1 pass
-    uint64_t total;      // |Q|
-    uint64_t work;       // work counter (stats)
-    uint64_t n_items;
-    uint32_t chunk_ctr;  // output chunks handed out (single-pass materialize)
-    uint32_t overflow;   // 1 when the output pool ran out of chunks
-};
-
 // Single-pass materialize: each warp writes its tuples into chunks of
 // OUT_CHUNK tuples taken from an output pool with one atomic per chunk.
 constexpr uint32_t OUT_CHUNK = 2048;
@@ -1223,24 +1212,6 @@ hc_status launch_any(int nl, int S, int O, bool mat, const GjArgs& g, cudaStream
 }  // namespace hc
 
 // ------------------------------------------------------------------ host
-struct hc_result {
-    cudaStream_t stream = nullptr;
-    uint32_t n_vars = 0;
-    uint64_t n_cells = 0;
-    hc::JoinCtl* d_ctl = nullptr;
-    uint64_t* d_cell_counts = nullptr;
-    uint32_t* d_tuples = nullptr;
-    uint64_t n_tuples = 0;
-    uint64_t n_items = 0;
-    bool materialized = false;
-    bool done = false;
-    hc::JoinCtl h_ctl{};
-    std::vector<hc_partitioned*> parts;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    int n_timed = 0;   // search launches bracketed by ev[2i], ev[2i+1]
-    int n_search = 0;  // search launches of this join
-};
-
 namespace hc {
 
 namespace {

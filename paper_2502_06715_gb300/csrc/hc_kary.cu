@@ -1,0 +1,1181 @@
+// Relations of arity 1..3: the k-level CoCo index (Sec. 4, one level
+// (V_r, O_r) per attribute) and Generic Join over it (Sec. 5), for
+// hypergraph queries such as LW and CT (Table "Queries").
+//
+// Build.  The rows are sorted lexicographically in level order, then one
+// scan over the sorted rows writes every level: row i opens an entry of
+// level d when its prefix of length d+1 differs from row i-1's, so each
+// level's entries are counted with ballots and placed by a decoupled
+// look-back (one per level with offsets).  When the levels' value bits add
+// up to at most 64, a row is one packed 64-bit key and the sort is the
+// library's LSD radix sort of 64-bit keys (the binary index builder, with
+// the key's high and low words as first and second attribute).  Otherwise
+// the rows are sorted one level at a time, last level first: each pass
+// sorts (level value, position in the previous order) pairs, which orders
+// by the level value and keeps the previous order among equal values.
+//
+// Join.  Loop 0 intersects the top levels of the atoms holding its variable
+// in a flat pass, one thread per value of the shortest list; every match
+// ("entry") records the level-1 ranges of the atoms it opens and its number
+// of loop-1 candidates.  The later loops run in a persistent kernel: a warp
+// takes a work item (a range of loop-1 candidates, over consecutive
+// entries) from an atomic counter and walks the remaining loops depth
+// first.  At each loop it holds up to 32 parent bindings and flattens their
+// candidates over its lanes, 32 a round; a candidate is an element of its
+// parent's shortest list (Sec. 5.2: iterate the smallest set, search the
+// others) and is searched in the parent's other lists by binary search (or
+// a direct position map of a top level); matches are compacted into the
+// next loop's bindings.  A binding keeps, for each list it matched that
+// has a deeper level, the range of its children there (the level
+// restriction of Sec. 5), and the index of its parent, so that a later
+// loop finds the range an earlier loop opened by walking up the parents.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/honeycomb_kary.h"
+#include "hc_internal.cuh"
+
+struct hc_kindex {
+    uint64_t n = 0;
+    uint32_t arity = 0;
+    uint8_t level_cols[HC_KMAX_ARITY] = {0, 0, 0};
+    bool packed = false;
+    uint64_t len[HC_KMAX_ARITY] = {0, 0, 0};
+    uint32_t maxv[HC_KMAX_ARITY] = {0, 0, 0};  // largest value of each level
+    uint32_t* d_v[HC_KMAX_ARITY] = {nullptr, nullptr, nullptr};
+    uint32_t* d_o[HC_KMAX_ARITY] = {nullptr, nullptr, nullptr};
+    // level-0 position map: pos[v] = position of v in V_0, or V1POS_NONE
+    uint32_t* d_v0pos = nullptr;
+    uint32_t v0pos_n = 0;
+    float ms_sort = 0.f, ms_levels = 0.f;
+};
+
+namespace hc {
+
+namespace {
+
+constexpr uint32_t FULL = 0xffffffffu;
+
+// Device allocations released (stream-ordered) when the holder goes.
+struct KScratch {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit KScratch(cudaStream_t st) : s(st) {}
+    ~KScratch() {
+        for (void* p : ptrs) dev_free(p, s);
+    }
+    template <typename T>
+    hc_status get(T** p, size_t count) {
+        void* v = nullptr;
+        HC_TRY(dev_alloc(&v, std::max<size_t>(count, 1) * sizeof(T), s));
+        ptrs.push_back(v);
+        *p = (T*)v;
+        return HC_OK;
+    }
+};
+
+int grid_of(uint64_t n, int threads, int per_sm) {
+    const uint64_t want = (n + threads - 1) / threads;
+    const uint64_t cap = (uint64_t)num_sms() * per_sm;
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, cap));
+}
+
+uint32_t bit_width(uint32_t v) { return v == 0 ? 0 : 32 - __builtin_clz(v); }
+
+// ==================================================================== build
+
+struct KBuildCtl {
+    uint32_t err;
+    uint32_t dup;
+    uint32_t maxv[HC_KMAX_ARITY];  // per column of the rows
+    uint32_t tile_counter;
+    uint32_t len[HC_KMAX_ARITY - 1];  // l_d of the levels with offsets
+};
+
+// Where level d of a row comes from: column col[d] of the row, or bits
+// [shift[d], shift[d] + width) of a packed key (mask[d] = 2^width - 1).
+struct KLayout {
+    uint32_t k;
+    uint32_t col[HC_KMAX_ARITY];
+    uint32_t shift[HC_KMAX_ARITY];
+    uint64_t mask[HC_KMAX_ARITY];
+};
+
+__global__ void kcolmax_kernel(const uint32_t* __restrict__ rows, uint64_t n, uint32_t k, KBuildCtl* ctl) {
+    uint32_t m[HC_KMAX_ARITY] = {0, 0, 0};
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t* r = rows + i * k;
+#pragma unroll
+        for (int c = 0; c < HC_KMAX_ARITY; ++c)
+            if (c < (int)k) m[c] = max(m[c], r[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < HC_KMAX_ARITY; ++c) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) m[c] = max(m[c], __shfl_xor_sync(FULL, m[c], d));
+        if (lane_id() == 0 && c < (int)k) atomicMax(&ctl->maxv[c], m[c]);
+    }
+}
+
+// Rows -> packed keys, stored as (high word, low word) pairs.
+__global__ void kpack_kernel(const uint32_t* __restrict__ rows, uint64_t n, KLayout L, uint2* __restrict__ out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t* r = rows + i * L.k;
+        uint64_t key = 0;
+#pragma unroll
+        for (int d = 0; d < HC_KMAX_ARITY; ++d)
+            if (d < (int)L.k) key |= (uint64_t)r[L.col[d]] << L.shift[d];
+        out[i] = make_uint2((uint32_t)(key >> 32), (uint32_t)key);
+    }
+}
+
+// Pairs (value of column `col` of row perm[i], i) for one level pass of the
+// unpacked sort (perm NULL: the identity).
+__global__ void kperm_pairs_kernel(const uint32_t* __restrict__ rows, uint64_t n, uint32_t k, uint32_t col,
+                                   const uint32_t* __restrict__ perm, uint2* __restrict__ out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t r = perm ? perm[i] : i;
+        out[i] = make_uint2(rows[r * k + col], (uint32_t)i);
+    }
+}
+
+// After a pass sorted the pairs: the new order is the old order read at the
+// positions the sorted keys carry in their low words.
+__global__ void kperm_compose_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ perm_old,
+                                     uint32_t* __restrict__ perm_new, uint64_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = (uint32_t)keys[i];
+        perm_new[i] = perm_old ? perm_old[j] : j;
+    }
+}
+
+// The sorted rows: packed keys, or the rows read through the sorted order.
+struct KSorted {
+    const uint64_t* keys;
+    const uint32_t* rows;
+    const uint32_t* perm;
+    KLayout L;
+};
+
+template <int K, bool PACKED>
+__device__ __forceinline__ void load_levels(const KSorted& s, uint64_t i, uint32_t (&c)[K]) {
+    if (PACKED) {
+        const uint64_t key = s.keys[i];
+#pragma unroll
+        for (int d = 0; d < K; ++d) c[d] = (uint32_t)((key >> s.L.shift[d]) & s.L.mask[d]);
+    } else {
+        const uint64_t r = s.perm[i];
+#pragma unroll
+        for (int d = 0; d < K; ++d) c[d] = s.rows[r * K + s.L.col[d]];
+    }
+}
+
+// Level scan.  Rows are warp-striped as in the binary run-boundary scan:
+// item j of lane q of warp w is row tile * KL_TILE + w * 32 * KL_ITEMS +
+// 32 j + q, so the row before a lane-0 row is lane 31's row of the previous
+// item.  fd = the first level at which a row differs from the row before
+// (0 for row 0, K for an equal row: a repeat).  Row i opens an entry of
+// every level d >= fd; an opened entry of level d < K-1 points at the row's
+// entry of level d+1 (opened too), or at the row itself for d = K-2.
+// Level K-1 is the last column of every row.  Warp d of each tile runs the
+// look-back of level d; the tile holding the last row closes every level
+// with O_d[l_d] = l_{d+1}.
+constexpr int KL_THREADS = 256;
+constexpr int KL_WARPS = KL_THREADS / 32;
+constexpr int KL_ITEMS = 16;
+constexpr int KL_TILE = KL_THREADS * KL_ITEMS;
+
+template <int K, bool PACKED>
+__global__ void __launch_bounds__(KL_THREADS) klevels_kernel(KSorted src, uint64_t n, uint32_t* __restrict__ v0,
+                                                             uint32_t* __restrict__ v1, uint32_t* __restrict__ v2,
+                                                             uint32_t* __restrict__ o0, uint32_t* __restrict__ o1,
+                                                             uint64_t* __restrict__ status, uint64_t ntiles,
+                                                             KBuildCtl* __restrict__ ctl) {
+    constexpr int NL = K - 1;              // levels with offsets
+    constexpr int NLA = NL > 0 ? NL : 1;  // array extent
+    __shared__ uint32_t wsum[NLA][KL_WARPS];
+    __shared__ uint64_t s_excl[NLA];
+    __shared__ uint32_t s_tile;
+    uint32_t* const vv[3] = {v0, v1, v2};
+    uint32_t* const oo[2] = {o0, o1};
+    const uint32_t tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(&ctl->tile_counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t base = (uint64_t)tile * KL_TILE + (uint64_t)w * (KL_ITEMS * 32);
+    const bool full = base + KL_ITEMS * 32 <= n;
+
+    uint32_t c[KL_ITEMS][K];
+#pragma unroll
+    for (int j = 0; j < KL_ITEMS; ++j) {
+        const uint64_t i = base + (uint64_t)j * 32 + lane;
+        if (full || i < n) {
+            load_levels<K, PACKED>(src, i, c[j]);
+        } else {
+#pragma unroll
+            for (int d = 0; d < K; ++d) c[j][d] = 0;
+        }
+    }
+    uint32_t carry[K];
+#pragma unroll
+    for (int d = 0; d < K; ++d) carry[d] = 0;
+    if (lane == 0 && base > 0 && base < n) load_levels<K, PACKED>(src, base - 1, carry);
+
+    uint32_t ball[KL_ITEMS][NLA];
+    uint32_t cnt[NLA];
+#pragma unroll
+    for (int d = 0; d < NLA; ++d) cnt[d] = 0;
+    bool dup = false;
+#pragma unroll
+    for (int j = 0; j < KL_ITEMS; ++j) {
+        const uint64_t i = base + (uint64_t)j * 32 + lane;
+        const bool valid = full || i < n;
+        int fd = K;
+#pragma unroll
+        for (int d = K - 1; d >= 0; --d) {
+            uint32_t prev = __shfl_up_sync(FULL, c[j][d], 1);
+            if (lane == 0) prev = carry[d];
+            if (c[j][d] != prev) fd = d;
+        }
+        if (i == 0) fd = 0;
+        dup |= valid && fd == K;
+#pragma unroll
+        for (int d = 0; d < NL; ++d) {
+            ball[j][d] = __ballot_sync(FULL, valid && fd <= d);
+            cnt[d] += __popc(ball[j][d]);
+        }
+        if (valid) vv[K - 1][i] = c[j][K - 1];  // the last level needs no offset
+#pragma unroll
+        for (int d = 0; d < K; ++d) {
+            const uint32_t last = __shfl_sync(FULL, c[j][d], 31);
+            if (lane == 0) carry[d] = last;
+        }
+    }
+    if (__any_sync(FULL, dup) && lane == 0) atomicOr(&ctl->dup, 1u);
+    if (NL == 0) return;
+
+    if (lane == 0) {
+#pragma unroll
+        for (int d = 0; d < NL; ++d) wsum[d][w] = cnt[d];
+    }
+    __syncthreads();
+    if (w < (uint32_t)NL) {
+        const int d = (int)w;
+        const uint64_t tot = warp_sum64(lane < (uint32_t)KL_WARPS ? wsum[d][lane] : 0u);
+        uint64_t* st = status + (uint64_t)d * ntiles + tile;
+        if (lane == 0) st_relaxed(st, (tile == 0 ? LB_INC : LB_AGG) | tot);
+        uint64_t excl = 0;
+        if (tile != 0) {
+            excl = warp_lookback(status + (uint64_t)d * ntiles, tile, &ctl->err);
+            if (lane == 0) st_relaxed(st, LB_INC | (excl + tot));
+        }
+        if (lane == 0) s_excl[d] = excl;
+    }
+    __syncthreads();
+    uint64_t pos[NLA];
+#pragma unroll
+    for (int d = 0; d < NL; ++d) {
+        pos[d] = s_excl[d];
+        for (uint32_t q = 0; q < w; ++q) pos[d] += wsum[d][q];
+    }
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int j = 0; j < KL_ITEMS; ++j) {
+        const uint64_t i = base + (uint64_t)j * 32 + lane;
+#pragma unroll
+        for (int d = 0; d < NL; ++d) {
+            if (ball[j][d] >> lane & 1u) {  // flagged rows are valid rows
+                const uint64_t e = pos[d] + __popc(ball[j][d] & lt);
+                vv[d][e] = c[j][d];
+                const int d1 = d + 1 < NL ? d + 1 : d;
+                const uint64_t child = d + 1 < NL ? pos[d1] + __popc(ball[j][d1] & lt) : i;
+                oo[d][e] = (uint32_t)child;
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < NL; ++d) pos[d] += __popc(ball[j][d]);
+    }
+    if (tid == 0 && (uint64_t)(tile + 1) * KL_TILE >= n) {
+        uint64_t l[NLA + 1];
+#pragma unroll
+        for (int d = 0; d < NL; ++d) {
+            uint64_t t = s_excl[d];
+            for (int q = 0; q < KL_WARPS; ++q) t += wsum[d][q];
+            l[d] = t;
+        }
+        l[NL] = n;
+#pragma unroll
+        for (int d = 0; d < NL; ++d) {
+            oo[d][l[d]] = (uint32_t)l[d + 1];
+            ctl->len[d] = (uint32_t)l[d];
+        }
+    }
+}
+
+// Level-0 position map: pos[V_0[i]] = i (values distinct, so each entry is
+// written at most once).
+__global__ void kpos_kernel(const uint32_t* __restrict__ v0, uint64_t l0, uint32_t* __restrict__ pos) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < l0; i += (uint64_t)gridDim.x * blockDim.x)
+        pos[v0[i]] = (uint32_t)i;
+}
+
+hc_status launch_levels(int k, bool packed, const KSorted& src, uint64_t n, uint32_t* const* v, uint32_t* const* o,
+                        uint64_t* status, uint64_t ntiles, KBuildCtl* ctl, cudaStream_t s) {
+    const unsigned grid = (unsigned)ntiles;
+#define HC_KLEV(K, P) \
+    klevels_kernel<K, P><<<grid, KL_THREADS, 0, s>>>(src, n, v[0], v[1], v[2], o[0], o[1], status, ntiles, ctl)
+    if (k == 1) {
+        if (packed) HC_KLEV(1, true); else HC_KLEV(1, false);
+    } else if (k == 2) {
+        if (packed) HC_KLEV(2, true); else HC_KLEV(2, false);
+    } else {
+        if (packed) HC_KLEV(3, true); else HC_KLEV(3, false);
+    }
+#undef HC_KLEV
+    HC_CUDA_TRY(launch_check());
+    return HC_OK;
+}
+
+}  // namespace
+
+void kindex_release(hc_kindex* x, cudaStream_t s) {
+    if (!x) return;
+    for (int d = 0; d < HC_KMAX_ARITY; ++d) {
+        dev_free(x->d_v[d], s);
+        dev_free(x->d_o[d], s);
+    }
+    dev_free(x->d_v0pos, s);
+    delete x;
+}
+
+hc_status build_kindex_impl(const uint32_t* d_rows, uint64_t n, uint32_t k, const uint8_t* level_cols,
+                            uint32_t flags, cudaStream_t s, hc_kindex** out) {
+    if (!out) return fail(HC_ERR_ARG, "build_kindex: out is NULL");
+    *out = nullptr;
+    if (k < 1 || k > HC_KMAX_ARITY) return fail(HC_ERR_ARG, "build_kindex: arity must be 1, 2 or 3");
+    if (n > 0 && !d_rows) return fail(HC_ERR_ARG, "build_kindex: d_rows is NULL");
+    if (n >= 0xFFFFFFFFull) return fail(HC_ERR_CAPACITY, "build_kindex: n must be below 2^32 - 1");
+    uint8_t cols[HC_KMAX_ARITY] = {0, 1, 2};
+    if (level_cols) {
+        bool seen[HC_KMAX_ARITY] = {false, false, false};
+        for (uint32_t d = 0; d < k; ++d) {
+            if (level_cols[d] >= k || seen[level_cols[d]])
+                return fail(HC_ERR_ARG, "build_kindex: level_cols must be a permutation of the columns");
+            seen[level_cols[d]] = true;
+            cols[d] = level_cols[d];
+        }
+    }
+    hc_kindex* x = new hc_kindex();
+    x->n = n;
+    x->arity = k;
+    for (uint32_t d = 0; d < k; ++d) x->level_cols[d] = cols[d];
+    auto bail = [&](hc_status st) {
+        kindex_release(x, s);
+        return st;
+    };
+    void* p = nullptr;
+    if (n == 0) {
+        for (uint32_t d = 0; d < k; ++d) {
+            if (dev_alloc(&p, 4, s) != HC_OK) return bail(HC_ERR_OOM);
+            x->d_v[d] = (uint32_t*)p;
+            if (d + 1 < k) {
+                if (dev_alloc(&p, 4, s) != HC_OK) return bail(HC_ERR_OOM);
+                x->d_o[d] = (uint32_t*)p;
+                if (cudaMemsetAsync(p, 0, 4, s) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
+            }
+        }
+        *out = x;
+        return HC_OK;
+    }
+
+    hc_status st;
+    KScratch tmp(s);
+    KBuildCtl* ctl;
+    if ((st = tmp.get(&ctl, 1)) != HC_OK) return bail(st);
+    if (cudaMemsetAsync(ctl, 0, sizeof(KBuildCtl), s) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "memset"));
+    kcolmax_kernel<<<grid_of(n, 256, 4), 256, 0, s>>>(d_rows, n, k, ctl);
+    if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "kcolmax_kernel"));
+    KBuildCtl h;
+    if (cudaMemcpyAsync(&h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "build_kindex: column maxima"));
+
+    KLayout L{};
+    L.k = k;
+    uint32_t bits[HC_KMAX_ARITY] = {0, 0, 0}, total_bits = 0;
+    for (uint32_t d = 0; d < k; ++d) {
+        L.col[d] = cols[d];
+        x->maxv[d] = h.maxv[cols[d]];
+        bits[d] = bit_width(x->maxv[d]);
+        total_bits += bits[d];
+        L.mask[d] = bits[d] >= 32 ? 0xFFFFFFFFull : ((1ull << bits[d]) - 1);
+    }
+    for (int d = (int)k - 1, sh = 0; d >= 0; --d) {
+        L.shift[d] = bits[d] ? (uint32_t)sh : 0u;  // a level of zeros takes no bits (and no shift of 64)
+        sh += (int)bits[d];
+    }
+
+    const bool timed = (flags & HC_BUILD_TIME_KERNELS) != 0;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    auto destroy_events = [&]() {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    };
+    if (timed) {
+        for (auto& e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                destroy_events();
+                return bail(cuda_fail(cudaGetLastError(), "cudaEventCreate"));
+            }
+        cudaEventRecord(ev[0], s);
+    }
+
+    // ---- sort
+    KSorted src{};
+    src.L = L;
+    hc_index* sorted = nullptr;  // holds the packed keys, sorted
+    auto bail2 = [&](hc_status e) {
+        if (sorted) index_release(sorted, s);
+        destroy_events();
+        return bail(e);
+    };
+    if (total_bits <= 64) {
+        x->packed = true;
+        uint2* pk;
+        if ((st = tmp.get(&pk, n)) != HC_OK) return bail2(st);
+        kpack_kernel<<<grid_of(n, 256, 8), 256, 0, s>>>(d_rows, n, L, pk);
+        if (cudaError_t le = launch_check()) return bail2(cuda_fail(le, "kpack_kernel"));
+        if ((st = build_index_impl((const uint32_t*)pk, n, 0, 0, s, &sorted)) != HC_OK) return bail2(st);
+        src.keys = sorted->d_keys;
+    } else {
+        uint2* pairs;
+        uint32_t *pa, *pb;
+        if ((st = tmp.get(&pairs, n)) != HC_OK || (st = tmp.get(&pa, n)) != HC_OK || (st = tmp.get(&pb, n)) != HC_OK)
+            return bail2(st);
+        const uint32_t* cur = nullptr;
+        for (int d = (int)k - 1; d >= 0; --d) {
+            kperm_pairs_kernel<<<grid_of(n, 256, 8), 256, 0, s>>>(d_rows, n, k, cols[d], cur, pairs);
+            if (cudaError_t le = launch_check()) return bail2(cuda_fail(le, "kperm_pairs_kernel"));
+            hc_index* pass = nullptr;
+            if ((st = build_index_impl((const uint32_t*)pairs, n, 0, 0, s, &pass)) != HC_OK) return bail2(st);
+            uint32_t* nxt = cur == pa ? pb : pa;
+            kperm_compose_kernel<<<grid_of(n, 256, 8), 256, 0, s>>>(pass->d_keys, cur, nxt, n);
+            cudaError_t le = launch_check();
+            index_release(pass, s);
+            if (le) return bail2(cuda_fail(le, "kperm_compose_kernel"));
+            cur = nxt;
+        }
+        src.rows = d_rows;
+        src.perm = cur;
+    }
+    if (timed) cudaEventRecord(ev[1], s);
+
+    // ---- levels: upper-bound arrays for the levels with offsets, exact for the last
+    uint32_t* v[3] = {nullptr, nullptr, nullptr};
+    uint32_t* o[2] = {nullptr, nullptr};
+    for (uint32_t d = 0; d + 1 < k; ++d) {
+        if ((st = tmp.get(&v[d], n)) != HC_OK || (st = tmp.get(&o[d], n + 1)) != HC_OK) return bail2(st);
+    }
+    if (dev_alloc(&p, n * 4, s) != HC_OK) return bail2(HC_ERR_OOM);
+    x->d_v[k - 1] = (uint32_t*)p;
+    v[k - 1] = x->d_v[k - 1];
+    const uint64_t ntiles = (n + KL_TILE - 1) / KL_TILE;
+    uint64_t* status;
+    if ((st = tmp.get(&status, (k > 1 ? k - 1 : 1) * ntiles)) != HC_OK) return bail2(st);
+    if (cudaMemsetAsync(status, 0, (k > 1 ? k - 1 : 1) * ntiles * sizeof(uint64_t), s) != cudaSuccess)
+        return bail2(cuda_fail(cudaGetLastError(), "memset"));
+    if ((st = launch_levels((int)k, x->packed, src, n, v, o, status, ntiles, ctl, s)) != HC_OK) return bail2(st);
+    if (timed) cudaEventRecord(ev[2], s);
+    if (cudaMemcpyAsync(&h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return bail2(cuda_fail(cudaGetLastError(), "build_kindex: level scan"));
+    if (sorted) {
+        index_release(sorted, s);
+        sorted = nullptr;
+    }
+    if (h.err & DEV_ERR_TIMEOUT) return bail2(fail(HC_ERR_TIMEOUT, "build_kindex: a look-back wait gave up"));
+    if ((flags & HC_BUILD_CHECK_DUPLICATES) && h.dup)
+        return bail2(fail(HC_ERR_DUPLICATE, "build_kindex: the relation holds a repeated row"));
+    if (timed) {
+        cudaEventElapsedTime(&x->ms_sort, ev[0], ev[1]);
+        cudaEventElapsedTime(&x->ms_levels, ev[1], ev[2]);
+    }
+    destroy_events();
+
+    // exact-size copies of the levels with offsets
+    x->len[k - 1] = n;
+    for (uint32_t d = 0; d + 1 < k; ++d) {
+        const uint64_t l = h.len[d];
+        if (l == 0 || l > n) return bail(fail(HC_ERR_CUDA, "build_kindex: level scan gave an invalid level size"));
+        x->len[d] = l;
+        if (dev_alloc(&p, l * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+        x->d_v[d] = (uint32_t*)p;
+        if (dev_alloc(&p, (l + 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+        x->d_o[d] = (uint32_t*)p;
+        if (cudaMemcpyAsync(x->d_v[d], v[d], l * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(x->d_o[d], o[d], (l + 1) * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return bail(cuda_fail(cudaGetLastError(), "build_kindex: level copy"));
+    }
+    if (v1pos_eligible(n, x->maxv[0])) {
+        const uint64_t dn = (uint64_t)x->maxv[0] + 1;
+        if (dev_alloc(&p, dn * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+        x->d_v0pos = (uint32_t*)p;
+        x->v0pos_n = (uint32_t)dn;
+        if (cudaMemsetAsync(x->d_v0pos, 0xFF, dn * 4, s) != cudaSuccess)
+            return bail(cuda_fail(cudaGetLastError(), "memset"));
+        kpos_kernel<<<grid_of(x->len[0], 256, 8), 256, 0, s>>>(x->d_v[0], x->len[0], x->d_v0pos);
+        if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "kpos_kernel"));
+    }
+    *out = x;
+    return HC_OK;
+}
+
+// ===================================================================== join
+
+namespace {
+
+constexpr int KMAXS = 4;          // lists intersected by one loop
+constexpr int KJ_MAXT = 128;      // threads per block of the search kernel, at most
+constexpr int KJ_WARPS = KJ_MAXT / 32;
+
+// One list of one loop: level `depth` of an atom.  A top level (depth 0) is
+// the whole V_0; a deeper level is the range of V_depth that the atom's
+// previous level opened at loop from_loop (through the binding's list
+// from_src there).  A list with an offset array `o` opens the atom's next
+// level at its match.
+struct KSrc {
+    const uint32_t* v;
+    const uint32_t* o;
+    const uint32_t* pos;  // depth 0: value -> position in V_0 (V1POS_NONE if absent), or NULL
+    uint32_t pos_n;       // values covered by pos
+    uint32_t top_len;     // l_0 of the atom
+    int32_t depth;
+    int32_t from_loop, from_src;
+};
+
+struct KPlan {
+    int32_t nv, drv0, stats, pad;
+    int32_t nsrc[HC_KMAX_VARS];
+    int32_t var_of_loop[HC_KMAX_VARS];
+    KSrc src[HC_KMAX_VARS][KMAXS];
+};
+
+// A loop-0 binding: its value and, per loop-0 list that opens a level, the
+// range of its children there.
+struct KEntry {
+    uint32_t val;
+    uint32_t lo[KMAXS], hi[KMAXS];
+};
+
+__device__ __forceinline__ void load_kplan(KPlan& dst, const KPlan* __restrict__ src) {
+    const uint32_t* sp = (const uint32_t*)src;
+    uint32_t* dp = (uint32_t*)&dst;
+    for (uint32_t i = threadIdx.x; i < sizeof(KPlan) / 4; i += blockDim.x) dp[i] = sp[i];
+    __syncthreads();
+}
+
+// search(V, x) of Sec. 5 within [lo, hi): the position of v, found or not.
+__device__ __forceinline__ uint32_t ksearch(const KSrc& s, uint32_t lo, uint32_t hi, uint32_t v, bool& ok) {
+    if (s.depth == 0 && s.pos != nullptr) {
+        const uint32_t p = v < s.pos_n ? __ldg(s.pos + v) : V1POS_NONE;
+        ok = p != V1POS_NONE;
+        return p;
+    }
+    const uint32_t p = lower_bound_u32(s.v, lo, hi, v);
+    ok = p < hi && __ldg(s.v + p) == v;
+    return p;
+}
+
+// ----------------------------------------------------------------- loop 0
+// Thread t takes value t of the shortest loop-0 list and searches it in the
+// others.  n_vars == 1: matches are the result (counted, or written with
+// MAT).  Otherwise a match with loop-1 candidates becomes an entry.
+template <bool MAT>
+__global__ void __launch_bounds__(256) kloop0_kernel(const KPlan* __restrict__ gP, KEntry* __restrict__ entries,
+                                                     uint32_t* __restrict__ units, JoinCtl* ctl,
+                                                     uint32_t* __restrict__ out, uint64_t cap) {
+    __shared__ KPlan P;
+    load_kplan(P, gP);
+    const uint32_t lane = lane_id();
+    const KSrc& s0 = P.src[0][P.drv0];
+    const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const bool valid = t < s0.top_len;
+    uint32_t v = 0;
+    bool ok = valid;
+    uint32_t pq[KMAXS];
+    if (valid) v = __ldg(s0.v + t);
+#pragma unroll
+    for (int q = 0; q < KMAXS; ++q) {
+        pq[q] = 0;
+        if (q < P.nsrc[0]) {
+            if (q == P.drv0) {
+                pq[q] = (uint32_t)t;
+            } else if (ok) {
+                const KSrc& s = P.src[0][q];
+                pq[q] = ksearch(s, 0, s.top_len, v, ok);
+            }
+        }
+    }
+    if (!MAT && P.stats && t == 0) atomicAdd((unsigned long long*)&ctl->work, (unsigned long long)P.nsrc[0] * s0.top_len);
+    if (P.nv == 1) {
+        const uint32_t m = __ballot_sync(FULL, ok);
+        if (!MAT) {
+            if (lane == 0 && m) atomicAdd((unsigned long long*)&ctl->total, (unsigned long long)__popc(m));
+            return;
+        }
+        unsigned long long b = 0;
+        if (lane == 0 && m) b = atomicAdd((unsigned long long*)&ctl->written, (unsigned long long)__popc(m));
+        b = __shfl_sync(FULL, b, 0);
+        if (ok) {
+            const uint64_t idx = b + __popc(m & lanemask_lt());
+            if (idx < cap)
+                out[idx] = v;
+            else
+                atomicOr(&ctl->overflow, 1u);
+        }
+        return;
+    }
+    if (MAT) return;  // entries are made by the counting pass
+    uint32_t lo[KMAXS], hi[KMAXS];
+#pragma unroll
+    for (int q = 0; q < KMAXS; ++q) {
+        lo[q] = hi[q] = 0;
+        if (ok && q < P.nsrc[0] && P.src[0][q].o != nullptr) {
+            const uint32_t* o = P.src[0][q].o;
+            lo[q] = __ldg(o + pq[q]);
+            hi[q] = __ldg(o + pq[q] + 1);
+        }
+    }
+    uint32_t nu = 0;
+    if (ok) {
+        nu = 0xFFFFFFFFu;
+#pragma unroll
+        for (int q = 0; q < KMAXS; ++q) {
+            if (q < P.nsrc[1]) {
+                const KSrc& s = P.src[1][q];
+                uint32_t len = s.top_len;
+                if (s.depth > 0) {
+#pragma unroll
+                    for (int r = 0; r < KMAXS; ++r)
+                        if (r == s.from_src) len = hi[r] - lo[r];
+                }
+                nu = min(nu, len);
+            }
+        }
+        if (nu == 0) ok = false;
+    }
+    if (P.stats) {
+        const uint64_t wk = warp_sum64(ok ? (uint64_t)P.nsrc[1] * nu : 0);
+        if (lane == 0 && wk) atomicAdd((unsigned long long*)&ctl->work, (unsigned long long)wk);
+    }
+    const uint32_t m = __ballot_sync(FULL, ok);
+    uint32_t b = 0;
+    if (lane == 0 && m) b = atomicAdd(&ctl->n_entries, (uint32_t)__popc(m));
+    b = __shfl_sync(FULL, b, 0);
+    if (ok) {
+        const uint32_t slot = b + __popc(m & lanemask_lt());
+        KEntry e;
+        e.val = v;
+#pragma unroll
+        for (int q = 0; q < KMAXS; ++q) {
+            e.lo[q] = lo[q];
+            e.hi[q] = hi[q];
+        }
+        entries[slot] = e;
+        units[slot] = nu;
+    }
+}
+
+// ------------------------------------------------------------ search loops
+// Per-warp state in shared memory.  Bindings of loops 1..NV-2 (frame f =
+// loop - 1), one per lane slot: value, parent slot in the loop above, and
+// the children range of each of the loop's lists that opens a level.
+// Candidate rounds of loops 1..NV-1 (level li = loop - 1): per parent the
+// prefix of candidate counts, the shortest list and its start.
+template <int NV>
+struct KWarp {
+    static constexpr int NF = NV > 2 ? NV - 2 : 1;
+    uint64_t pref[NV - 1][33];
+    uint64_t round[NV - 1], total[NV - 1];
+    uint32_t val[NF][32];
+    uint32_t rlo[NF][KMAXS][32];
+    uint32_t rhi[NF][KMAXS][32];
+    uint32_t dlo[NV - 1][32];
+    uint32_t e_lo[KMAXS], e_hi[KMAXS];
+    uint32_t e_val;
+    uint8_t par[NF][32];
+    uint8_t drv[NV - 1][32];
+};
+
+// Range of list q of loop L for parent slot b (a binding of loop L-1; the
+// entry when L == 1).
+template <int NV>
+__device__ __forceinline__ void krange(const KPlan& P, const KWarp<NV>& S, int L, int q, uint32_t b, uint32_t& lo,
+                                       uint32_t& hi) {
+    const KSrc& s = P.src[L][q];
+    if (s.depth == 0) {
+        lo = 0;
+        hi = s.top_len;
+        return;
+    }
+    const int f = s.from_loop, r = s.from_src;
+    if (f == 0) {
+        lo = S.e_lo[r];
+        hi = S.e_hi[r];
+        return;
+    }
+    uint32_t a = b;
+    for (int l = L - 1; l > f; --l) a = S.par[l - 1][a];
+    lo = S.rlo[f - 1][r][a];
+    hi = S.rhi[f - 1][r][a];
+}
+
+// Start loop L with parents 0..nb-1: each parent's shortest list and the
+// prefix of their candidate counts.  Loop 1 has the entry as its only
+// parent and takes candidates [t0, t1) of its shortest list.
+template <int NV>
+__device__ __forceinline__ void kinit_level(const KPlan& P, KWarp<NV>& S, int L, uint32_t nb, uint32_t t0,
+                                            uint32_t t1, uint64_t& work) {
+    const uint32_t lane = lane_id();
+    const int li = L - 1;
+    uint64_t c = 0;
+    uint32_t dsel = 0, dlo = 0;
+    if (lane < nb) {
+        uint32_t best = 0xFFFFFFFFu;
+        for (int q = 0; q < P.nsrc[L]; ++q) {
+            uint32_t lo, hi;
+            krange<NV>(P, S, L, q, lane, lo, hi);
+            if (hi - lo < best) {
+                best = hi - lo;
+                dsel = (uint32_t)q;
+                dlo = lo;
+            }
+        }
+        if (L == 1) {
+            dlo += t0;
+            c = t1 - t0;
+        } else {
+            c = best;
+            if (P.stats) work += (uint64_t)P.nsrc[L] * best;
+        }
+    }
+    const uint64_t incl = warp_incl_scan64(c);
+    __syncwarp();
+    S.pref[li][lane + 1] = incl;
+    if (lane == 0) {
+        S.pref[li][0] = 0;
+        S.round[li] = 0;
+    }
+    if (lane < nb) {
+        S.drv[li][lane] = (uint8_t)dsel;
+        S.dlo[li][lane] = dlo;
+    }
+    if (lane == 31) S.total[li] = incl;
+    __syncwarp();
+}
+
+// Walk loops 1..NV-1 below the entry in S, loop 1 over candidates [t0, t1).
+template <int NV, bool MAT>
+__device__ void kwalk(const KPlan& P, KWarp<NV>& S, uint32_t t0, uint32_t t1, uint64_t& cnt, uint64_t& work,
+                      JoinCtl* ctl, uint32_t* __restrict__ out, uint64_t cap) {
+    const uint32_t lane = lane_id();
+    kinit_level<NV>(P, S, 1, 1, t0, t1, work);
+    int L = 1;
+    while (true) {
+        const int li = L - 1;
+        __syncwarp();
+        const uint64_t r = S.round[li], tot = S.total[li];
+        __syncwarp();
+        if (r * 32 >= tot) {
+            if (L == 1) break;
+            --L;
+            continue;
+        }
+        if (lane == 0) S.round[li] = r + 1;
+        const uint64_t g = r * 32 + lane;
+        const bool valid = g < tot;
+        // parent: the last slot b whose prefix is <= g
+        uint32_t b = 0;
+        if (L > 1 && valid) {
+            uint32_t lo = 0, hi = 32;  // pref[li][b] for b < 32; slots past the parents have prefix == tot > g
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (S.pref[li][mid] <= g)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            b = lo;
+        }
+        uint32_t v = 0;
+        bool ok = valid;
+        uint32_t pq[KMAXS];
+#pragma unroll
+        for (int q = 0; q < KMAXS; ++q) pq[q] = 0;
+        if (valid) {
+            const uint32_t d = S.drv[li][b];
+            const uint32_t pos = S.dlo[li][b] + (uint32_t)(g - S.pref[li][b]);
+            v = __ldg(P.src[L][d].v + pos);
+#pragma unroll
+            for (int q = 0; q < KMAXS; ++q) {
+                if (q < P.nsrc[L]) {
+                    if (q == (int)d) {
+                        pq[q] = pos;
+                    } else if (ok) {
+                        uint32_t lo, hi;
+                        krange<NV>(P, S, L, q, b, lo, hi);
+                        pq[q] = ksearch(P.src[L][q], lo, hi, v, ok);
+                    }
+                }
+            }
+        }
+        const uint32_t m = __ballot_sync(FULL, ok);
+        if (L == NV - 1) {
+            if (!MAT) {
+                cnt += ok ? 1u : 0u;
+                continue;
+            }
+            if (m == 0) continue;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd((unsigned long long*)&ctl->written, (unsigned long long)__popc(m));
+            base = __shfl_sync(FULL, base, 0);
+            if (ok) {
+                const uint64_t idx = base + __popc(m & lanemask_lt());
+                if (idx < cap) {
+                    uint32_t* t = out + idx * (uint64_t)P.nv;
+                    t[P.var_of_loop[NV - 1]] = v;
+                    uint32_t a = b;
+                    for (int l = NV - 2; l >= 1; --l) {
+                        t[P.var_of_loop[l]] = S.val[l - 1][a];
+                        a = S.par[l - 1][a];
+                    }
+                    t[P.var_of_loop[0]] = S.e_val;
+                } else {
+                    atomicOr(&ctl->overflow, 1u);
+                }
+            }
+            continue;
+        }
+        // compact the matches into the bindings of loop L and descend
+        if (ok) {
+            const int f = L - 1;
+            const uint32_t rk = __popc(m & lanemask_lt());
+            S.val[f][rk] = v;
+            S.par[f][rk] = (uint8_t)b;
+#pragma unroll
+            for (int q = 0; q < KMAXS; ++q) {
+                if (q < P.nsrc[L] && P.src[L][q].o != nullptr) {
+                    const uint32_t* o = P.src[L][q].o;
+                    S.rlo[f][q][rk] = __ldg(o + pq[q]);
+                    S.rhi[f][q][rk] = __ldg(o + pq[q] + 1);
+                }
+            }
+        }
+        __syncwarp();
+        if (m) {
+            ++L;
+            kinit_level<NV>(P, S, L, (uint32_t)__popc(m), 0, 0, work);
+        }
+    }
+}
+
+// Persistent search kernel: warps take work items of `grain` loop-1
+// candidates (0: sized so that each warp gets about 8 items) from an atomic
+// counter, over the concatenation of all entries' candidates.
+template <int NV, bool MAT>
+__global__ void __launch_bounds__(KJ_MAXT) kjoin_kernel(const KPlan* __restrict__ gP,
+                                                        const KEntry* __restrict__ entries,
+                                                        const uint64_t* __restrict__ unit_off, JoinCtl* ctl,
+                                                        uint32_t grain_in, uint32_t* __restrict__ out, uint64_t cap) {
+    __shared__ KPlan P;
+    __shared__ KWarp<NV> WS[KJ_WARPS];
+    load_kplan(P, gP);
+    const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
+    KWarp<NV>& S = WS[w];
+    const uint32_t ne = ctl->n_entries;
+    const uint64_t total_units = unit_off[ne];
+    uint64_t grain = grain_in;
+    if (grain == 0) {
+        const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+        grain = total_units / (warps * 8);
+        if (grain == 0) grain = 1;
+    }
+    uint64_t cnt = 0, work = 0;
+    while (true) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(&ctl->item_ctr[MAT ? 1 : 0], 1u);
+        item = __shfl_sync(FULL, item, 0);
+        uint64_t u0 = (uint64_t)item * grain;
+        if (u0 >= total_units) break;
+        const uint64_t u1 = u0 + grain < total_units ? u0 + grain : total_units;
+        // the entry holding unit u0: first j in [1, ne] with unit_off[j] > u0, minus one
+        uint32_t lo = 1, hi = ne;
+        while (lo < hi) {
+            const uint32_t mid = lo + ((hi - lo) >> 1);
+            if (unit_off[mid] > u0)
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        uint32_t e = lo - 1;
+        while (u0 < u1 && e < ne) {
+            const uint64_t eb = unit_off[e], ee = unit_off[e + 1];
+            if (ee > u0) {
+                __syncwarp();
+                if (lane == 0) {
+                    const KEntry en = entries[e];
+                    S.e_val = en.val;
+#pragma unroll
+                    for (int q = 0; q < KMAXS; ++q) {
+                        S.e_lo[q] = en.lo[q];
+                        S.e_hi[q] = en.hi[q];
+                    }
+                }
+                __syncwarp();
+                const uint64_t u_end = u1 < ee ? u1 : ee;
+                kwalk<NV, MAT>(P, S, (uint32_t)(u0 - eb), (uint32_t)(u_end - eb), cnt, work, ctl, out, cap);
+                u0 = u_end;
+            }
+            ++e;
+        }
+    }
+    if (!MAT) {
+        cnt = warp_sum64(cnt);
+        work = warp_sum64(work);
+        if (lane == 0) {
+            if (cnt) atomicAdd((unsigned long long*)&ctl->total, (unsigned long long)cnt);
+            if (work) atomicAdd((unsigned long long*)&ctl->work, (unsigned long long)work);
+        }
+    }
+}
+
+template <int NV, bool MAT>
+hc_status launch_kjoin_t(int threads, const KPlan* P, const KEntry* entries, const uint64_t* unit_off, JoinCtl* ctl,
+                         uint32_t grain, uint32_t* out, uint64_t cap, cudaStream_t s) {
+    int per_sm = 0;
+    HC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kjoin_kernel<NV, MAT>, threads, 0));
+    const int grid = num_sms() * std::max(1, per_sm);
+    kjoin_kernel<NV, MAT><<<grid, threads, 0, s>>>(P, entries, unit_off, ctl, grain, out, cap);
+    HC_CUDA_TRY(launch_check());
+    return HC_OK;
+}
+
+template <bool MAT>
+hc_status launch_kjoin(int nv, int threads, const KPlan* P, const KEntry* entries, const uint64_t* unit_off,
+                       JoinCtl* ctl, uint32_t grain, uint32_t* out, uint64_t cap, cudaStream_t s) {
+    switch (nv) {
+        case 2: return launch_kjoin_t<2, MAT>(threads, P, entries, unit_off, ctl, grain, out, cap, s);
+        case 3: return launch_kjoin_t<3, MAT>(threads, P, entries, unit_off, ctl, grain, out, cap, s);
+        case 4: return launch_kjoin_t<4, MAT>(threads, P, entries, unit_off, ctl, grain, out, cap, s);
+        case 5: return launch_kjoin_t<5, MAT>(threads, P, entries, unit_off, ctl, grain, out, cap, s);
+        case 6: return launch_kjoin_t<6, MAT>(threads, P, entries, unit_off, ctl, grain, out, cap, s);
+        default: return fail(HC_ERR_CAPACITY, "run_kjoin: unsupported number of variables");
+    }
+}
+
+hc_status read_kctl(hc_result* R) {
+    HC_CUDA_TRY(cudaMemcpyAsync(&R->h_ctl, R->d_ctl, sizeof(JoinCtl), cudaMemcpyDeviceToHost, R->stream));
+    HC_CUDA_TRY(cudaStreamSynchronize(R->stream));
+    if (R->h_ctl.err & DEV_ERR_TIMEOUT) return fail(HC_ERR_TIMEOUT, "run_kjoin: a bounded device wait gave up");
+    return HC_OK;
+}
+
+// Validation and the lists of every loop (host only).
+hc_status make_kplan(const hc_kquery* q, const hc_kindex* const* idx, KPlan& P) {
+    memset(&P, 0, sizeof(P));
+    const uint32_t nv = q->n_vars, na = q->n_atoms;
+    if (nv < 1) return fail(HC_ERR_ARG, "run_kjoin: n_vars must be at least 1");
+    if (nv > HC_KMAX_VARS) return fail(HC_ERR_CAPACITY, "run_kjoin: at most 6 variables");
+    if (na < 1 || na > HC_MAX_ATOMS) return fail(HC_ERR_ARG, "run_kjoin: n_atoms must be 1..12");
+    int rank[HC_MAX_VARS];
+    bool seen[HC_MAX_VARS] = {false};
+    for (uint32_t i = 0; i < nv; ++i) {
+        const uint32_t v = q->order[i];
+        if (v >= nv || seen[v]) return fail(HC_ERR_ARG, "run_kjoin: order must list every variable once");
+        seen[v] = true;
+        rank[v] = (int)i;
+        P.var_of_loop[i] = (int32_t)v;
+    }
+    P.nv = (int32_t)nv;
+    for (uint32_t j = 0; j < na; ++j) {
+        const hc_katom& a = q->atoms[j];
+        const uint32_t k = a.arity;
+        if (k < 1 || k > HC_KMAX_ARITY) return fail(HC_ERR_ARG, "run_kjoin: atom arity must be 1, 2 or 3");
+        for (uint32_t c = 0; c < k; ++c) {
+            if (a.var[c] >= nv) return fail(HC_ERR_ARG, "run_kjoin: atom variable out of range");
+            for (uint32_t c2 = 0; c2 < c; ++c2)
+                if (a.var[c2] == a.var[c]) return fail(HC_ERR_ARG, "run_kjoin: a variable twice in one atom");
+        }
+        const hc_kindex* x = idx[j];
+        if (!x) return fail(HC_ERR_ARG, "run_kjoin: index is NULL");
+        if (x->arity != k) return fail(HC_ERR_ARG, "run_kjoin: index arity differs from the atom's");
+        int prev_loop = -1, prev_src = -1;
+        for (uint32_t d = 0; d < k; ++d) {
+            const int L = rank[a.var[x->level_cols[d]]];
+            if (L <= prev_loop)
+                return fail(HC_ERR_ARG, "run_kjoin: the index levels must hold the atom's variables in loop order");
+            if (P.nsrc[L] >= KMAXS) return fail(HC_ERR_CAPACITY, "run_kjoin: a variable is in more than 4 atoms");
+            const int qn = P.nsrc[L]++;
+            KSrc& s = P.src[L][qn];
+            s.v = x->d_v[d];
+            s.o = d + 1 < k ? x->d_o[d] : nullptr;
+            s.pos = d == 0 ? x->d_v0pos : nullptr;
+            s.pos_n = d == 0 ? x->v0pos_n : 0;
+            s.top_len = (uint32_t)x->len[0];
+            s.depth = (int32_t)d;
+            s.from_loop = prev_loop;
+            s.from_src = prev_src;
+            prev_loop = L;
+            prev_src = qn;
+        }
+    }
+    for (uint32_t i = 0; i < nv; ++i)
+        if (P.nsrc[i] == 0) return fail(HC_ERR_ARG, "run_kjoin: every variable must occur in some atom");
+    P.drv0 = 0;
+    for (int qn = 1; qn < P.nsrc[0]; ++qn)
+        if (P.src[0][qn].top_len < P.src[0][P.drv0].top_len) P.drv0 = qn;
+    return HC_OK;
+}
+
+}  // namespace
+
+hc_status run_kjoin_impl(const hc_kquery* q, const hc_kindex* const* idx, const hc_kjoin_params* prm,
+                         cudaStream_t s, hc_result** out) {
+    if (!out) return fail(HC_ERR_ARG, "run_kjoin: out is NULL");
+    *out = nullptr;
+    if (!q || !idx) return fail(HC_ERR_ARG, "run_kjoin: NULL argument");
+    hc_kjoin_params dp{};
+    if (prm) dp = *prm;
+    if (dp.mode > HC_MODE_MATERIALIZE) return fail(HC_ERR_ARG, "run_kjoin: unknown mode");
+    const int threads = dp.block_threads ? (int)dp.block_threads : KJ_MAXT;
+    if (threads % 32 != 0 || threads < 32 || threads > KJ_MAXT)
+        return fail(HC_ERR_ARG, "run_kjoin: block_threads must be 32, 64, 96 or 128");
+    KPlan P;
+    HC_TRY(make_kplan(q, idx, P));
+    P.stats = (dp.flags & HC_FLAG_STATS) ? 1 : 0;
+    const uint32_t nv = q->n_vars;
+
+    hc_result* R = new hc_result();
+    R->stream = s;
+    R->n_vars = nv;
+    R->n_cells = 1;
+    auto bail = [&](hc_status st) {
+        result_release(R);
+        return st;
+    };
+    void* p = nullptr;
+    if (dev_alloc(&p, sizeof(JoinCtl), s) != HC_OK) return bail(HC_ERR_OOM);
+    R->d_ctl = (JoinCtl*)p;
+    JoinCtl* ctl = R->d_ctl;
+    if (cudaMemsetAsync(ctl, 0, sizeof(JoinCtl), s) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
+    const bool timed = (dp.flags & HC_FLAG_TIME_KERNELS) != 0;
+    if (timed) {
+        for (auto& e : R->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "cudaEventCreate"));
+    }
+
+    KScratch tmp(s);
+    hc_status st;
+    KPlan* dP;
+    if ((st = tmp.get(&dP, 1)) != HC_OK) return bail(st);
+    if (cudaMemcpyAsync(dP, &P, sizeof(KPlan), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "plan copy"));
+    const uint32_t len0 = P.src[0][P.drv0].top_len;
+    KEntry* entries = nullptr;
+    uint32_t* units = nullptr;
+    uint64_t* unit_off = nullptr;
+    const unsigned l0_grid = (unsigned)((len0 + 255) / 256);
+    auto search = [&](bool mat, uint32_t* tup, uint64_t cap) -> hc_status {
+        if (timed) cudaEventRecord(R->ev[2 * R->n_timed], s);
+        if (nv == 1) {
+            if (mat)
+                kloop0_kernel<true><<<l0_grid, 256, 0, s>>>(dP, nullptr, nullptr, ctl, tup, cap);
+            else
+                kloop0_kernel<false><<<l0_grid, 256, 0, s>>>(dP, nullptr, nullptr, ctl, nullptr, 0);
+            HC_CUDA_TRY(launch_check());
+        } else if (mat) {
+            HC_TRY(launch_kjoin<true>((int)nv, threads, dP, entries, unit_off, ctl, dp.item_grain, tup, cap, s));
+        } else {
+            HC_TRY(launch_kjoin<false>((int)nv, threads, dP, entries, unit_off, ctl, dp.item_grain, nullptr, 0, s));
+        }
+        if (timed) {
+            cudaEventRecord(R->ev[2 * R->n_timed + 1], s);
+            R->n_timed++;
+        }
+        R->n_search++;
+        return HC_OK;
+    };
+    if (len0 > 0) {
+        if (nv > 1) {
+            if ((st = tmp.get(&entries, len0)) != HC_OK || (st = tmp.get(&units, len0)) != HC_OK ||
+                (st = tmp.get(&unit_off, (size_t)len0 + 1)) != HC_OK)
+                return bail(st);
+            kloop0_kernel<false><<<l0_grid, 256, 0, s>>>(dP, entries, units, ctl, nullptr, 0);
+            if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "kloop0_kernel"));
+            if ((st = exclusive_scan_u32_to_u64(units, unit_off, len0, &ctl->n_entries, &ctl->err, s)) != HC_OK)
+                return bail(st);
+        }
+        if ((st = search(false, nullptr, 0)) != HC_OK) return bail(st);
+    }
+    if (dp.mode == HC_MODE_MATERIALIZE) {
+        if ((st = read_kctl(R)) != HC_OK) return bail(st);
+        const uint64_t total = R->h_ctl.total;
+        if (total > 0) {
+            if (total > (~0ull) / 4 / nv) return bail(fail(HC_ERR_CAPACITY, "run_kjoin: output too large"));
+            if (dev_alloc(&p, total * nv * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+            R->d_tuples = (uint32_t*)p;
+            if ((st = search(true, R->d_tuples, total)) != HC_OK) return bail(st);
+            if ((st = read_kctl(R)) != HC_OK) return bail(st);
+            if (R->h_ctl.written != total || R->h_ctl.overflow)
+                return bail(fail(HC_ERR_CUDA, "run_kjoin: the writing pass disagrees with the count"));
+        }
+        R->materialized = true;
+        R->n_tuples = total;
+        R->done = true;
+    }
+    *out = R;
+    return HC_OK;
+}
+
+}  // namespace hc
+
+// ------------------------------------------------------------------- C ABI
+extern "C" {
+
+hc_status hc_build_kindex(const uint32_t* d_rows, uint64_t n, uint32_t arity, const uint8_t* level_cols,
+                          uint32_t flags, void* stream, hc_kindex** out) {
+    return hc::build_kindex_impl(d_rows, n, arity, level_cols, flags, (cudaStream_t)stream, out);
+}
+
+hc_status hc_kindex_free(hc_kindex* index) {
+    hc::kindex_release(index, nullptr);
+    return HC_OK;
+}
+
+hc_status hc_kindex_get_view(const hc_kindex* x, hc_kindex_view* v) {
+    if (!x || !v) return hc::fail(HC_ERR_ARG, "kindex_get_view: NULL argument");
+    memset(v, 0, sizeof(*v));
+    v->n = x->n;
+    v->arity = x->arity;
+    v->packed = x->packed ? 1 : 0;
+    for (int d = 0; d < HC_KMAX_ARITY; ++d) {
+        v->level_cols[d] = (uint32_t)d < x->arity ? x->level_cols[d] : 0;
+        v->len[d] = x->len[d];
+        v->max_value[d] = x->maxv[d];
+        v->d_v[d] = x->d_v[d];
+        v->d_o[d] = x->d_o[d];
+    }
+    v->ms_sort = x->ms_sort;
+    v->ms_levels = x->ms_levels;
+    return HC_OK;
+}
+
+hc_status hc_run_kjoin(const hc_kquery* q, const hc_kindex* const* idx, const hc_kjoin_params* params, void* stream,
+                       hc_result** out) {
+    return hc::run_kjoin_impl(q, idx, params, (cudaStream_t)stream, out);
+}
+
+}  // extern "C"

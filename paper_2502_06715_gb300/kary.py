@@ -1,0 +1,156 @@
+"""Relations of arity 1 to 3 (include/honeycomb_kary.h): the k-level CoCo
+index of Sec. 4 and Generic Join over it (Sec. 5), for hypergraph queries
+such as the paper's Loomis-Whitney (LW) and Clover-Triangle (CT) queries
+(Table "Queries").  Argument marshalling only; the work runs in the
+library's CUDA kernels.
+
+    build_kindex(rows, level_cols)     sort + k-level CoCo
+    run_kjoin(query, indexes, mode)    Generic Join (one cell)
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Sequence
+
+import torch
+
+from . import Result, _ResultHandle, _alias, _lib, _stream_ptr
+
+
+@dataclass(frozen=True)
+class KQuery:
+    """Full conjunctive query over atoms of arity 1..3 (Eq. "full:cq").
+
+    ``atoms[j]`` is the tuple of variables of atom j: column c of its
+    relation holds variable atoms[j][c].  ``order`` is the loop order
+    (default 0, 1, ...)."""
+    n_vars: int
+    atoms: tuple
+    order: tuple | None = None
+
+    def loop_order(self) -> tuple:
+        return tuple(range(self.n_vars)) if self.order is None else tuple(self.order)
+
+    def with_order(self, order) -> "KQuery":
+        return KQuery(self.n_vars, self.atoms, tuple(order))
+
+    def level_cols(self, j: int) -> tuple:
+        """Columns of atom j in loop order of their variables: the level
+        order an index needs for atom j under this query's loop order."""
+        rank = {v: i for i, v in enumerate(self.loop_order())}
+        a = self.atoms[j]
+        return tuple(sorted(range(len(a)), key=lambda c: rank[a[c]]))
+
+    def _c(self) -> _lib.hc_kquery:
+        q = _lib.hc_kquery()
+        q.n_vars = self.n_vars
+        q.n_atoms = len(self.atoms)
+        for j, a in enumerate(self.atoms):
+            q.atoms[j].arity = len(a)
+            for c, v in enumerate(a):
+                q.atoms[j].var[c] = v
+        for i, v in enumerate(self.loop_order()):
+            q.order[i] = v
+        return q
+
+
+# Table "Queries": LW Q(X,Y,Z,U) with X=0, Y=1, Z=2, U=3; CT Q(U,X,Y,Z) with U=0, X=1, Y=2, Z=3.
+LW = KQuery(4, ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)))
+CT = KQuery(4, ((0, 1, 2), (0, 1, 3), (0, 2, 3)))
+
+
+class KIndex:
+    """A k-level CoCo index (library-owned device memory)."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+        v = _lib.hc_kindex_view()
+        _lib.check(_lib.load().hc_kindex_get_view(self._h, ctypes.byref(v)), "hc_kindex_get_view")
+        self.n, self.arity, self.packed = v.n, v.arity, bool(v.packed)
+        self.level_cols = tuple(v.level_cols[d] for d in range(v.arity))
+        self.len = tuple(int(v.len[d]) for d in range(v.arity))
+        self.max_value = tuple(int(v.max_value[d]) for d in range(v.arity))
+        self.ms_sort, self.ms_levels = v.ms_sort, v.ms_levels
+        self._view = v
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("index already freed")
+        return self._h
+
+    def v(self, d: int) -> torch.Tensor:
+        """V_d as an int32 CUDA tensor aliasing the index."""
+        return _alias(self._view.d_v[d], (self.len[d],), torch.int32, self)
+
+    def o(self, d: int) -> torch.Tensor:
+        """O_d (d < arity-1) as an int32 CUDA tensor aliasing the index."""
+        if d >= self.arity - 1:
+            raise IndexError("the last level has no offsets")
+        return _alias(self._view.d_o[d], (self.len[d] + 1,), torch.int32, self)
+
+    def free(self) -> None:
+        if self._h is not None:
+            _lib.load().hc_kindex_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_kindex(rows: torch.Tensor, level_cols: Sequence[int] | None = None, check_duplicates: bool = False,
+                 stream=None, time_kernels: bool = False) -> KIndex:
+    """k-level CoCo of a relation given as an (n, k) 32-bit CUDA tensor, k = 1..3,
+    with level d holding column level_cols[d] (default 0, 1, ..)."""
+    if not isinstance(rows, torch.Tensor) or not rows.is_cuda or rows.dim() != 2 or rows.element_size() != 4:
+        raise TypeError("rows must be an (n, k) 32-bit CUDA tensor")
+    r = rows.contiguous()
+    k = r.shape[1]
+    cols = None
+    if level_cols is not None:
+        cols = (ctypes.c_uint8 * _lib.HC_KMAX_ARITY)(*([int(c) for c in level_cols] + [0] * (3 - len(level_cols))))
+    flags = (_lib.HC_BUILD_CHECK_DUPLICATES if check_duplicates else 0) | (
+        _lib.HC_BUILD_TIME_KERNELS if time_kernels else 0)
+    out = ctypes.c_void_p()
+    st = _lib.load().hc_build_kindex(ctypes.c_void_p(r.data_ptr() if r.numel() else 0), r.shape[0], k, cols, flags,
+                                     ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(out))
+    _lib.check(st, "hc_build_kindex")
+    return KIndex(out.value)
+
+
+def run_kjoin(query: KQuery, indexes: Sequence[KIndex], mode: str = "count", stats: bool = False,
+              item_grain: int = 0, block_threads: int = 0, time_kernels: bool = False, stream=None) -> Result:
+    """Generic Join of a k-ary query; tuples (materialize) come back as a
+    (count, n_vars) int32 CUDA tensor in variable-id order, in no fixed order."""
+    if len(indexes) != len(query.atoms):
+        raise ValueError("one index per atom")
+    if mode not in ("count", "materialize"):
+        raise ValueError("mode is 'count' or 'materialize'")
+    q = query._c()
+    arr = (ctypes.c_void_p * len(indexes))(*[ix.handle.value for ix in indexes])
+    prm = _lib.hc_kjoin_params()
+    prm.mode = _lib.HC_MODE_COUNT if mode == "count" else _lib.HC_MODE_MATERIALIZE
+    prm.flags = (_lib.HC_FLAG_STATS if stats else 0) | (_lib.HC_FLAG_TIME_KERNELS if time_kernels else 0)
+    prm.item_grain = item_grain
+    prm.block_threads = block_threads
+    lib = _lib.load()
+    out = ctypes.c_void_p()
+    _lib.check(lib.hc_run_kjoin(ctypes.byref(q), ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)),
+                                ctypes.byref(prm), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(out)),
+               "hc_run_kjoin")
+    holder = _ResultHandle(out.value)
+    v = _lib.hc_result_view()
+    _lib.check(lib.hc_result_get(ctypes.c_void_p(holder.h), ctypes.byref(v)), "hc_result_get")
+    res = Result(count=v.count, n_cells=v.n_cells, work=v.work, n_items=v.n_items,
+                 ms_join_kernel=v.ms_join_kernel, n_join_launches=v.n_join_launches)
+    if v.d_tuples:
+        res.tuples = _alias(v.d_tuples, (v.n_tuples, query.n_vars), torch.int32, holder).clone()
+    elif mode == "materialize":
+        res.tuples = torch.empty((0, query.n_vars), dtype=torch.int32, device="cuda")
+    torch.cuda.current_stream().synchronize()
+    holder.free()
+    return res

@@ -184,3 +184,107 @@ def test_bad_arguments():
         oracle.kgj(4, [(0, 1, 2)], [cube])  # U in no atom
     with pytest.raises(oracle.OracleError):
         oracle.kgj(3, [(0, 1, 2)], [cube], order=[0, 0, 1])
+
+
+# ---------------------------------------------------------------- k-level CoCo
+
+def trie_levels(rows, cols):
+    """The k-level trie written out by hand: prefixes of each length as a
+    Python set, sorted; a prefix's first child is the first longer prefix
+    that extends it."""
+    t = sorted(set(tuple(int(r[c]) for c in cols) for r in np.asarray(rows).tolist()))
+    k = len(cols)
+    prefixes = [sorted(set(p[:d + 1] for p in t)) for d in range(k)]
+    V = [[p[d] for p in prefixes[d]] for d in range(k)]
+    O = []
+    for d in range(k - 1):
+        nxt = prefixes[d + 1]
+        o = [next(i for i, q in enumerate(nxt) if q[:d + 1] == p) for p in prefixes[d]]
+        O.append(o + [len(nxt)])
+    return V, O
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("seed", range(4))
+def test_kcoco_matches_hand_trie(k, seed):
+    rng = np.random.default_rng(300 + seed)
+    rel = random_rel(rng, k, 4 if k == 3 else 7, 0.5)
+    for cols in itertools.permutations(range(k)):
+        c = oracle.kcoco(rel, cols)
+        V, O = trie_levels(rel, cols)
+        assert [v.tolist() for v in c["V"]] == V
+        assert [o.tolist() for o in c["O"]] == O
+
+
+def test_kcoco_binary_matches_coco_build():
+    """Arity 2 is the binary CoCo of Sec. 4, built by the separately written
+    oracle.c; both attribute orders."""
+    rel = datagen.random_graph(60, 0.2, 11)
+    for ao in (0, 1):
+        v1, o1, v2 = oracle.coco_build(rel, ao)
+        c = oracle.kcoco(rel, (0, 1) if ao == 0 else (1, 0))
+        assert np.array_equal(c["V"][0], v1) and np.array_equal(c["V"][1], v2)
+        assert np.array_equal(c["O"][0].astype(np.uint64), o1)
+
+
+def test_kcoco_rebuilds_rows_and_empty():
+    rng = np.random.default_rng(5)
+    rel = random_rel(rng, 3, 6, 0.3)
+    c = oracle.kcoco(rel, (2, 0, 1))
+    V, O = c["V"], c["O"]
+    rows = []
+    for a in range(V[0].shape[0]):
+        for b in range(O[0][a], O[0][a + 1]):
+            for e in range(O[1][b], O[1][b + 1]):
+                rows.append((V[0][a], V[1][b], V[2][e]))
+    want = sorted(tuple(int(r[c]) for c in (2, 0, 1)) for r in rel.tolist())
+    assert [tuple(map(int, r)) for r in rows] == want
+    e = oracle.kcoco(np.zeros((0, 3), dtype=np.uint32))
+    assert [v.shape[0] for v in e["V"]] == [0, 0, 0] and [o.tolist() for o in e["O"]] == [[0], [0]]
+
+
+# ------------------------------------------------------------------ work measure
+
+def brute_work(n_vars, atoms, rels, order, dom):
+    """Sum over loops i and bindings t of loops 0..i-1 (tuples of the prefix
+    query: every atom's bound variables, a prefix of its loop-ordered
+    columns, project to some row) of (lists at loop i) * (shortest list),
+    a list being the set of values of X_order[i] in the atom's rows that
+    agree with t."""
+    rank = {v: i for i, v in enumerate(order)}
+    sets = [set(map(tuple, np.asarray(r, dtype=np.int64).reshape(-1, len(a)).tolist())) for a, r in zip(atoms, rels)]
+    total = 0
+    for i in range(n_vars):
+        bound = order[:i]
+        x = order[i]
+        for t in itertools.product(range(dom), repeat=i):
+            val = dict(zip(bound, t))
+            ok = True
+            for a, s in zip(atoms, sets):
+                idx = [c for c in range(len(a)) if rank[a[c]] < i]
+                if idx and not any(all(row[c] == val[a[c]] for c in idx) for row in s):
+                    ok = False
+                    break
+            if not ok:
+                continue
+            lens = []
+            for a, s in zip(atoms, sets):
+                if x not in a:
+                    continue
+                cx = a.index(x)
+                idx = [c for c in range(len(a)) if rank[a[c]] < i]
+                lens.append(len({row[cx] for row in s if all(row[c] == val[a[c]] for c in idx)}))
+            total += len(lens) * min(lens)
+    return total
+
+
+@pytest.mark.parametrize("name,query", [("LW", LW), ("CT", CT), ("mixed", (4, [(2, 0, 3), (1, 2), (3,), (1, 0)]))])
+@pytest.mark.parametrize("seed", range(3))
+def test_work_measure_brute_force(name, query, seed):
+    nv, atoms = query
+    rng = np.random.default_rng(900 + seed)
+    dom = 4
+    rels = [random_rel(rng, len(a), dom, rng.choice([0.4, 0.8])) for a in atoms]
+    for order in ((0, 1, 2, 3), (3, 1, 0, 2)):
+        cnt, work = oracle.kgj(nv, atoms, rels, order=order, work=True)
+        assert work == brute_work(nv, atoms, rels, order, dom), order
