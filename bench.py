@@ -51,12 +51,15 @@ def parse_args():
     ap.add_argument("--edge-factor", type=int, default=16)
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--mode", choices=["materialize", "count"], default="materialize")
-    ap.add_argument("--workload", choices=["triangle", "clique4", "cycle4", "batched", "serve", "build", "order"],
+    ap.add_argument("--workload", choices=["triangle", "clique4", "cycle4", "batched", "serve", "build", "order",
+                                           "lw"],
                     default="triangle",
                     help="triangle: R-MAT triangle (default line); clique4 / cycle4: R-MAT 4-clique / 4-cycle "
                          "counts; batched: 512 triangle/4-clique queries on induced subgraphs in one launch; "
                          "serve: continuous-batching server; build: CoCo index build of R-MAT E+; "
-                         "order: 4-clique under every loop order beside the cost model's choice")
+                         "order: 4-clique under every loop order beside the cost model's choice; "
+                         "lw: Loomis-Whitney count over the four [n]^3 cubes of ST-Dense (k-ary relations)")
+    ap.add_argument("--lw-n", type=int, default=512, help="lw: cube side n of ST-Dense's [n]^3 relations")
     ap.add_argument("--shares", default="autotune",
                     help="'autotune' (timed search from the paper's plan over HyperCube share vectors of "
                          ">= --min-cells cells and kernel schedules), 'plan' (Sec. 5.3 decision at --P cells), "
@@ -226,13 +229,15 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if a.scale is None:
         a.scale = {"triangle": 22, "clique4": 20, "cycle4": 20, "batched": 21, "serve": 23, "build": 22,
-                   "order": 18}[a.workload]
+                   "order": 18, "lw": 0}[a.workload]
     if a.impl == "reference":
         return reference_arm(a, world, rank)
     if a.workload == "serve":
         return serve_workload(a, world, rank, local)
     if a.workload == "build":
         return build_workload(a, world, rank, local)
+    if a.workload == "lw":
+        return kary_workload(a, world, rank, local)
     if a.workload == "order":
         return order_workload(a, world, rank, local)
     if a.workload != "triangle":
@@ -737,6 +742,126 @@ def build_workload(a, world, rank, local):
                                        f"scrambled, symmetrised, deduplicated, rows in random order",
                            "rows": n, "l1": int(l1), "alg_bytes_per_step": b_build,
                            "l2": "inputs larger than L2 (%.0f MB of pairs)" % (8 * n / 1e6),
+                           "generate_s": round(gen_s, 1)},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+
+
+def kary_workload(a, world, rank, local):
+    """LW (Table "Queries") over ST-Dense's four [n]^3 relations (Sec. 6),
+    count mode; the step is one k-ary join over resident 3-level CoCo
+    indexes (built once, timed separately).  Metric: LW results per second.
+    Roofline of the search kernel: 4 bytes per unit of the work measure
+    (sum over loops and bindings of lists x shortest list) per launch."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import datagen
+    import paper_2502_06715_gb300 as hc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    n = a.lw_n
+    t0 = time.perf_counter()
+    cube = datagen.full_cube(n)
+    gen_s = time.perf_counter() - t0
+    rows = [torch.from_numpy(cube.view(np.int32)).to(dev) for _ in range(4)]
+    q = hc.LW
+    ixs = [hc.build_kindex(rows[j], q.level_cols(j), stream=stream, time_kernels=True) for j in range(4)]
+    build_ms = [ix.ms_sort + ix.ms_levels for ix in ixs]
+    expect = n ** 4
+    stats = hc.run_kjoin(q, ixs, stats=True, stream=stream)
+    if stats.count != expect:
+        raise RuntimeError(f"LW count {stats.count} != n^4 = {expect}")
+    work = stats.work
+
+    def step():
+        return hc.run_kjoin(q, ixs, stream=stream, time_kernels=True, item_grain=a.grain,
+                            block_threads=a.threads)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    launches0 = hc.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kern_ms = 0.0
+    e0.record(stream)
+    for _ in range(a.steps):
+        r = step()
+        if r.count != expect:
+            raise RuntimeError("LW count changed between steps")
+        kern_ms += r.ms_join_kernel
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = hc.kernel_launches() - launches0
+    ms = e0.elapsed_time(e1) / a.steps
+    value = expect / (ms / 1e3)
+    peak, peak_kind = measured_hbm_peak()
+    kms = kern_ms / a.steps
+    achieved = 4.0 * work / (kms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "kjoin_kernel<4> (k-ary search)", "achieved": round(achieved, 1),
+                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "alg_bytes_per_launch": 4 * work, "avg_launch_ms": round(kms, 3),
+                "note": "work measure x 4 B; the lists of a dense cube are short and L1/L2-resident, so this "
+                        "figure exceeds what DRAM moves"}
+
+    e2e = None
+    if not a.no_e2e:
+        host = torch.from_numpy(cube.view(np.int32)).pin_memory()
+        bufs = [torch.empty_like(rows[0]) for _ in range(4)]
+
+        def e2e_step():
+            for b in bufs:
+                b.copy_(host, non_blocking=True)
+            xs = [hc.build_kindex(bufs[j], q.level_cols(j), stream=stream) for j in range(4)]
+            c = hc.run_kjoin(q, xs, stream=stream).count
+            for x in xs:
+                x.free()
+            return c
+
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / a.steps
+        e2e = {"value": expect / (e2e_ms / 1e3), "unit": "tuples/s", "h2d_bytes_per_step": 4 * 12 * n ** 3,
+               "d2h_bytes_per_step": 8, "ms_per_step": e2e_ms, "includes": "H2D of the four relations, "
+               "four 3-level CoCo builds, the join, the count read back"}
+
+    cpu = None
+    if not a.no_cpu_baseline and rank == 0 and world == 1:
+        import oracle
+
+        # bounded sample: x in the first fx values and y in the first fy values of [n]
+        fx, fy = min(n, 8), min(n, 64)
+        r1 = cube[(cube[:, 0] < fx) & (cube[:, 1] < fy)]
+        r3 = cube[cube[:, 0] < fx]
+        r4 = cube[cube[:, 0] < fy]
+        t0 = time.perf_counter()
+        c = oracle.kgj(4, [tuple(x) for x in q.atoms], [r1, r1, r3, r4])
+        dt = time.perf_counter() - t0
+        if c != fx * fy * n * n:
+            raise RuntimeError("oracle sample count")
+        cpu = {"value": c / dt, "unit": "tuples/s", "cores": 1, "kind": "oracle",
+               "sample": f"LW with x < {fx} and y < {fy} ({c} results, {dt:.1f} s, tries built inside, one thread)"}
+
+    if rank == 0:
+        line = {"metric": "LW results/s (count)", "value": value, "unit": "tuples/s", "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (ST-Dense cubes)",
+                "config": {"workload": f"Loomis-Whitney over four [{n}]^3 relations (ST-Dense, Sec. 6), count",
+                           "rows_per_relation": n ** 3, "count": expect, "work": work,
+                           "index_build_ms": [round(b, 3) for b in build_ms],
+                           "l2": ("inputs larger than L2: %.0f MB of V_2 over the four indexes" if 16 * n ** 3 > 129e6
+                                  else "inputs within L2: %.0f MB of V_2 over the four indexes") % (16 * n ** 3 / 1e6),
                            "generate_s": round(gen_s, 1)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
