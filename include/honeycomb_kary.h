@@ -62,6 +62,14 @@ typedef struct {
 } hc_kindex_view;
 hc_status hc_kindex_get_view(const hc_kindex* index, hc_kindex_view* out);
 
+/* A statistics-only k-level index for planning: no device arrays, only the
+ * sizes the optimizer reads (n rows, l_d per level with l_{k-1} = n, the
+ * largest value of each level, the level order).  Host only, needs no GPU;
+ * hc_run_kjoin rejects it with HC_ERR_ARG.  Requires 1 <= l_0 <= .. <= n
+ * when n >= 1.  Free with hc_kindex_free. */
+hc_status hc_kindex_from_stats(uint64_t n, uint32_t arity, const uint8_t* level_cols, const uint64_t* len,
+                               const uint32_t* max_value, hc_kindex** out);
+
 /* ---------------------------------------------------------------- run_kjoin
  * One atom R_j(X_var[0], .., X_var[arity-1]): column c of its relation
  * holds the values of variable var[c]; the variables of an atom are
@@ -106,6 +114,27 @@ typedef struct {
  * (number of lists) * (shortest list length).  n_cells is 1 and n_items 0. */
 hc_status hc_run_kjoin(const hc_kquery* q, const hc_kindex* const* idx, const hc_kjoin_params* params,
                        void* stream, hc_result** out);
+
+/* --------------------------------------------------------------- planning
+ * Estimated cost of a k-ary query's loop order (Sec. 5.2, Lemma "cost-ub",
+ * one cell): level_cost[i] for loop i of q->order, with a binding's list in
+ * an atom estimated as D(bound columns + the loop's column) / D(bound
+ * columns), D the number of distinct combinations of a column set (exact for
+ * the prefixes of the index's level order and for all columns, else the
+ * product of single-column counts bounded by the rows), and a k-way
+ * intersection over a domain of dom values keeping prod(lengths) /
+ * dom^(k-1), at most the shortest.  dom_out[v]: the domain estimate of
+ * variable v (the least single-column count among its atoms).  For binary
+ * atoms these are hc_plan_cost's level costs without query rewriting.  Host
+ * only; statistics-only indexes serve; the indexes' level orders need not
+ * match q->order. */
+hc_status hc_kplan_cost(const hc_kquery* q, const hc_kindex* const* idx, double level_cost[HC_MAX_VARS],
+                        double dom_out[HC_MAX_VARS]);
+/* Loop order of least estimated cost (the sum of hc_kplan_cost's level
+ * costs) over all n_vars! orders; ties go to the lexicographically smallest
+ * order (q->order is ignored).  order_out[0..n_vars) receives it (0xFF
+ * after).  Host only. */
+hc_status hc_choose_korder(const hc_kquery* q, const hc_kindex* const* idx, uint8_t order_out[HC_MAX_VARS]);
 
 #ifdef __cplusplus
 }

@@ -494,6 +494,6 @@ class _ResultHandle:
             pass
 
 
-from .kary import CT, LW, KIndex, KQuery, build_kindex, run_kjoin  # noqa: E402  (k-ary relations)
+from .kary import CT, LW, KIndex, KQuery, build_kindex, choose_korder, kplan_cost, run_kjoin  # noqa: E402
 
-__all__ += ["KQuery", "KIndex", "build_kindex", "run_kjoin", "LW", "CT"]
+__all__ += ["KQuery", "KIndex", "build_kindex", "run_kjoin", "choose_korder", "kplan_cost", "LW", "CT"]

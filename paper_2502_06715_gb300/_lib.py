@@ -133,6 +133,13 @@ SIGNATURES = {
     "hc_run_kjoin": (ctypes.c_int, [ctypes.POINTER(hc_kquery), ctypes.POINTER(ctypes.c_void_p),
                                     ctypes.POINTER(hc_kjoin_params), ctypes.c_void_p,
                                     ctypes.POINTER(ctypes.c_void_p)]),
+    "hc_kindex_from_stats": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint8),
+                                            ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32),
+                                            ctypes.POINTER(ctypes.c_void_p)]),
+    "hc_kplan_cost": (ctypes.c_int, [ctypes.POINTER(hc_kquery), ctypes.POINTER(ctypes.c_void_p),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "hc_choose_korder": (ctypes.c_int, [ctypes.POINTER(hc_kquery), ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(ctypes.c_uint8)]),
     "hc_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "hc_last_error": (ctypes.c_char_p, []),
     "hc_version": (ctypes.c_uint32, []),

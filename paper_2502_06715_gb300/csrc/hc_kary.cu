@@ -29,6 +29,7 @@
 // has a deeper level, the range of its children there (the level
 // restriction of Sec. 5), and the index of its parent, so that a later
 // loop finds the range an earlier loop opened by walking up the parents.
+#include <math.h>
 #include <string.h>
 
 #include <algorithm>
@@ -50,6 +51,7 @@ struct hc_kindex {
     uint32_t* d_v0pos = nullptr;
     uint32_t v0pos_n = 0;
     float ms_sort = 0.f, ms_levels = 0.f;
+    bool stats_only = false;  // sizes only (planning), no device arrays
 };
 
 namespace hc {
@@ -1034,6 +1036,8 @@ hc_status make_kplan(const hc_kquery* q, const hc_kindex* const* idx, KPlan& P) 
     }
     for (uint32_t i = 0; i < nv; ++i)
         if (P.nsrc[i] == 0) return fail(HC_ERR_ARG, "run_kjoin: every variable must occur in some atom");
+    for (uint32_t j = 0; j < na; ++j)
+        if (idx[j]->stats_only) return fail(HC_ERR_ARG, "run_kjoin: a statistics-only index has no data");
     P.drv0 = 0;
     for (int qn = 1; qn < P.nsrc[0]; ++qn)
         if (P.src[0][qn].top_len < P.src[0][P.drv0].top_len) P.drv0 = qn;
@@ -1140,6 +1144,102 @@ hc_status run_kjoin_impl(const hc_kquery* q, const hc_kindex* const* idx, const 
     return HC_OK;
 }
 
+// ------------------------------------------------------------------ planning
+// Cost of one loop order (Sec. 5.2, Lemma "cost-ub", one cell): loop i costs
+//   C_i = |S(X_i)| * (sum min N) * log2(1 + sum max N / sum min N)
+// over the bindings of the prefix query, estimated as for binary atoms: a
+// binding's list in atom j at loop i has average length
+//   D(bound columns + X_i's column) / D(bound columns)
+// where D(C) is the number of distinct value combinations of the column set
+// C in the relation (a top level: D of one column), and a k-way intersection
+// over a domain of size dom keeps prod(s) / dom^(k-1) values, at most min s.
+// D is exact for the prefixes of the index's own level order (l_d) and for
+// all columns (n); other sets take the product of single-column counts (the
+// first level's l_0, else the value range) bounded by n.
+namespace {
+
+double kdistinct(const hc_kindex* x, uint32_t colmask) {
+    if (colmask == 0) return 1.0;
+    const double n = (double)x->n;
+    uint32_t pm = 0;
+    for (uint32_t d = 0; d < x->arity; ++d) {
+        pm |= 1u << x->level_cols[d];
+        if (pm == colmask) return (double)x->len[d];
+    }
+    double est = 1.0;
+    for (uint32_t d = 0; d < x->arity; ++d) {
+        if (!(colmask >> x->level_cols[d] & 1u)) continue;
+        est *= d == 0 ? (double)x->len[0] : std::min(n, (double)x->maxv[d] + 1.0);
+    }
+    return std::min(est, n);
+}
+
+hc_status kplan_check(const hc_kquery* q, const hc_kindex* const* idx) {
+    if (!q || !idx) return fail(HC_ERR_ARG, "kplan: NULL argument");
+    const uint32_t nv = q->n_vars, na = q->n_atoms;
+    if (nv < 1 || nv > HC_KMAX_VARS || na < 1 || na > HC_MAX_ATOMS)
+        return fail(HC_ERR_ARG, "kplan: need 1..6 variables and 1..12 atoms");
+    bool cover[HC_MAX_VARS] = {false};
+    for (uint32_t j = 0; j < na; ++j) {
+        const hc_katom& a = q->atoms[j];
+        if (a.arity < 1 || a.arity > HC_KMAX_ARITY) return fail(HC_ERR_ARG, "kplan: atom arity must be 1, 2 or 3");
+        if (!idx[j] || idx[j]->arity != a.arity) return fail(HC_ERR_ARG, "kplan: missing index or arity mismatch");
+        for (uint32_t c = 0; c < a.arity; ++c) {
+            if (a.var[c] >= nv) return fail(HC_ERR_ARG, "kplan: atom variable out of range");
+            for (uint32_t c2 = 0; c2 < c; ++c2)
+                if (a.var[c2] == a.var[c]) return fail(HC_ERR_ARG, "kplan: a variable twice in one atom");
+            cover[a.var[c]] = true;
+        }
+    }
+    for (uint32_t v = 0; v < nv; ++v)
+        if (!cover[v]) return fail(HC_ERR_ARG, "kplan: a variable occurs in no atom");
+    return HC_OK;
+}
+
+// Per-loop costs under `order` (variable ids) and the domain estimates.
+void kplan_costs(const hc_kquery* q, const hc_kindex* const* idx, const uint8_t* order, double* cost, double* dom) {
+    const int nv = (int)q->n_vars, na = (int)q->n_atoms;
+    int rank[HC_MAX_VARS];
+    for (int i = 0; i < nv; ++i) rank[order[i]] = i;
+    for (int v = 0; v < nv; ++v) dom[v] = INFINITY;
+    for (int j = 0; j < na; ++j)
+        for (int c = 0; c < q->atoms[j].arity; ++c)
+            dom[q->atoms[j].var[c]] = std::min(dom[q->atoms[j].var[c]], kdistinct(idx[j], 1u << c));
+    double bindings = 1.0;
+    for (int i = 0; i < nv; ++i) {
+        const int v = order[i];
+        double smin = INFINITY, smax = 0.0, prod = 1.0;
+        int k = 0;
+        for (int j = 0; j < na; ++j) {
+            const hc_katom& a = q->atoms[j];
+            int cv = -1;
+            uint32_t bound = 0;
+            for (int c = 0; c < a.arity; ++c) {
+                if (a.var[c] == v) cv = c;
+                else if (rank[a.var[c]] < i) bound |= 1u << c;
+            }
+            if (cv < 0) continue;
+            const double below = kdistinct(idx[j], bound);
+            const double len = below > 0 ? kdistinct(idx[j], bound | (1u << cv)) / below : 0.0;
+            smin = std::min(smin, len);
+            smax = std::max(smax, len);
+            prod *= len;
+            ++k;
+        }
+        if (k == 0 || !(smin > 0)) {
+            cost[i] = 0.0;
+            bindings = 0.0;
+            continue;
+        }
+        const double sum_min = bindings * smin, sum_max = bindings * smax;
+        cost[i] = (double)k * sum_min * log2(1.0 + sum_max / sum_min);
+        const double keep = prod / pow(std::max(1.0, dom[v]), (double)(k - 1));
+        bindings *= std::min(keep, smin);
+    }
+}
+
+}  // namespace
+
 }  // namespace hc
 
 // ------------------------------------------------------------------- C ABI
@@ -1151,7 +1251,7 @@ hc_status hc_build_kindex(const uint32_t* d_rows, uint64_t n, uint32_t arity, co
 }
 
 hc_status hc_kindex_free(hc_kindex* index) {
-    hc::kindex_release(index, nullptr);
+    hc::kindex_release(index, nullptr);  // a statistics-only index holds no device arrays
     return HC_OK;
 }
 
@@ -1176,6 +1276,77 @@ hc_status hc_kindex_get_view(const hc_kindex* x, hc_kindex_view* v) {
 hc_status hc_run_kjoin(const hc_kquery* q, const hc_kindex* const* idx, const hc_kjoin_params* params, void* stream,
                        hc_result** out) {
     return hc::run_kjoin_impl(q, idx, params, (cudaStream_t)stream, out);
+}
+
+hc_status hc_kindex_from_stats(uint64_t n, uint32_t arity, const uint8_t* level_cols, const uint64_t* len,
+                               const uint32_t* max_value, hc_kindex** out) {
+    if (!out) return hc::fail(HC_ERR_ARG, "kindex_from_stats: out is NULL");
+    *out = nullptr;
+    if (arity < 1 || arity > HC_KMAX_ARITY || !len || !max_value)
+        return hc::fail(HC_ERR_ARG, "kindex_from_stats: arity 1..3 with len and max_value");
+    uint8_t cols[HC_KMAX_ARITY] = {0, 1, 2};
+    bool seen[HC_KMAX_ARITY] = {false, false, false};
+    for (uint32_t d = 0; d < arity; ++d) {
+        if (level_cols) cols[d] = level_cols[d];
+        if (cols[d] >= arity || seen[cols[d]])
+            return hc::fail(HC_ERR_ARG, "kindex_from_stats: level_cols must be a permutation of the columns");
+        seen[cols[d]] = true;
+    }
+    if (len[arity - 1] != n) return hc::fail(HC_ERR_ARG, "kindex_from_stats: the last level holds every row");
+    for (uint32_t d = 0; d < arity; ++d) {
+        if ((n > 0 && len[d] == 0) || (d > 0 && len[d] < len[d - 1]) || len[d] > n)
+            return hc::fail(HC_ERR_ARG, "kindex_from_stats: need 1 <= l_0 <= l_1 <= .. <= n");
+    }
+    hc_kindex* x = new hc_kindex();
+    x->n = n;
+    x->arity = arity;
+    x->stats_only = true;
+    for (uint32_t d = 0; d < arity; ++d) {
+        x->level_cols[d] = cols[d];
+        x->len[d] = len[d];
+        x->maxv[d] = max_value[d];
+    }
+    *out = x;
+    return HC_OK;
+}
+
+hc_status hc_kplan_cost(const hc_kquery* q, const hc_kindex* const* idx, double level_cost[HC_MAX_VARS],
+                        double dom_out[HC_MAX_VARS]) {
+    HC_TRY(hc::kplan_check(q, idx));
+    bool seen[HC_MAX_VARS] = {false};
+    for (uint32_t i = 0; i < q->n_vars; ++i) {
+        if (q->order[i] >= q->n_vars || seen[q->order[i]])
+            return hc::fail(HC_ERR_ARG, "kplan_cost: order must list every variable once");
+        seen[q->order[i]] = true;
+    }
+    double cost[HC_MAX_VARS] = {0}, dom[HC_MAX_VARS] = {0};
+    hc::kplan_costs(q, idx, q->order, cost, dom);
+    for (int v = 0; v < HC_MAX_VARS; ++v) {
+        if (level_cost) level_cost[v] = v < (int)q->n_vars ? cost[v] : 0.0;
+        if (dom_out) dom_out[v] = v < (int)q->n_vars ? dom[v] : 0.0;
+    }
+    return HC_OK;
+}
+
+hc_status hc_choose_korder(const hc_kquery* q, const hc_kindex* const* idx, uint8_t order_out[HC_MAX_VARS]) {
+    HC_TRY(hc::kplan_check(q, idx));
+    if (!order_out) return hc::fail(HC_ERR_ARG, "choose_korder: NULL order_out");
+    const int nv = (int)q->n_vars;
+    uint8_t perm[HC_MAX_VARS], best[HC_MAX_VARS];
+    for (int i = 0; i < nv; ++i) perm[i] = best[i] = (uint8_t)i;
+    double best_cost = INFINITY;
+    do {  // lexicographic order, so a tie keeps the smaller order
+        double cost[HC_MAX_VARS], dom[HC_MAX_VARS];
+        hc::kplan_costs(q, idx, perm, cost, dom);
+        double total = 0.0;
+        for (int i = 0; i < nv; ++i) total += cost[i];
+        if (total < best_cost - 1e-9 * std::max(1.0, fabs(best_cost)) || best_cost == INFINITY) {
+            best_cost = total;
+            std::copy(perm, perm + nv, best);
+        }
+    } while (std::next_permutation(perm, perm + nv));
+    for (int i = 0; i < HC_MAX_VARS; ++i) order_out[i] = i < nv ? best[i] : (uint8_t)0xFF;
+    return HC_OK;
 }
 
 }  // extern "C"

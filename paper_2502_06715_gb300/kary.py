@@ -5,6 +5,7 @@ such as the paper's Loomis-Whitney (LW) and Clover-Triangle (CT) queries
 library's CUDA kernels.
 
     build_kindex(rows, level_cols)     sort + k-level CoCo
+    choose_korder(query, indexes)      Sec. 5.2-5.3: loop order of least estimated cost
     run_kjoin(query, indexes, mode)    Generic Join (one cell)
 """
 from __future__ import annotations
@@ -74,6 +75,19 @@ class KIndex:
         self.ms_sort, self.ms_levels = v.ms_sort, v.ms_levels
         self._view = v
 
+    @classmethod
+    def from_stats(cls, n: int, lengths: Sequence[int], max_value: Sequence[int],
+                   level_cols: Sequence[int] | None = None) -> "KIndex":
+        """Statistics-only index for planning (no GPU, no data): l_d per
+        level (the last is n) and the largest value of each level."""
+        k = len(lengths)
+        cols = None if level_cols is None else (ctypes.c_uint8 * 3)(*(list(level_cols) + [0] * (3 - k)))
+        ls = (ctypes.c_uint64 * 3)(*(list(lengths) + [0] * (3 - k)))
+        mv = (ctypes.c_uint32 * 3)(*(list(max_value) + [0] * (3 - k)))
+        out = ctypes.c_void_p()
+        _lib.check(_lib.load().hc_kindex_from_stats(n, k, cols, ls, mv, ctypes.byref(out)), "hc_kindex_from_stats")
+        return cls(out.value)
+
     @property
     def handle(self) -> ctypes.c_void_p:
         if self._h is None:
@@ -120,6 +134,30 @@ def build_kindex(rows: torch.Tensor, level_cols: Sequence[int] | None = None, ch
                                      ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(out))
     _lib.check(st, "hc_build_kindex")
     return KIndex(out.value)
+
+
+def _kindex_array(indexes):
+    arr = (ctypes.c_void_p * len(indexes))(*[ix.handle.value for ix in indexes])
+    return ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), arr
+
+
+def kplan_cost(query: KQuery, indexes: Sequence[KIndex]) -> dict:
+    """Estimated cost per loop of the query's order, and domain estimates (host only)."""
+    q = query._c()
+    ptr, keep = _kindex_array(indexes)
+    lc = (ctypes.c_double * _lib.HC_MAX_VARS)()
+    dm = (ctypes.c_double * _lib.HC_MAX_VARS)()
+    _lib.check(_lib.load().hc_kplan_cost(ctypes.byref(q), ptr, lc, dm), "hc_kplan_cost")
+    return {"level_cost": list(lc)[:query.n_vars], "dom": list(dm)[:query.n_vars]}
+
+
+def choose_korder(query: KQuery, indexes: Sequence[KIndex]) -> tuple:
+    """Loop order of least estimated cost (host only)."""
+    q = query._c()
+    ptr, keep = _kindex_array(indexes)
+    out = (ctypes.c_uint8 * _lib.HC_MAX_VARS)()
+    _lib.check(_lib.load().hc_choose_korder(ctypes.byref(q), ptr, out), "hc_choose_korder")
+    return tuple(out[i] for i in range(query.n_vars))
 
 
 def run_kjoin(query: KQuery, indexes: Sequence[KIndex], mode: str = "count", stats: bool = False,

@@ -254,3 +254,16 @@ def test_bad_arguments(hc):
     with pytest.raises(hc.HoneycombError) as ei:
         hc.run_kjoin(q7, [good[0], good[0], hc.build_kindex(dev(r3[:, :1].copy()))])
     assert ei.value.status == 5
+
+
+def test_chosen_order_matches_oracle(hc):
+    """The order hc_choose_korder picks from the built indexes' statistics
+    changes only the work: the result equals the oracle's."""
+    rng = np.random.default_rng(77)
+    atoms = [(2, 0, 3), (1, 2), (3,), (1, 0)]
+    rels = [distinct_rows(rng, n, len(a), 12) for a, n in zip(atoms, (900, 60, 8, 100))]
+    q = hc.KQuery(4, tuple(atoms))
+    stats = [hc.build_kindex(dev(r)) for r in rels]
+    order = hc.choose_korder(q, stats)
+    assert sorted(order) == [0, 1, 2, 3]
+    run_both(hc, 4, atoms, rels, order)
