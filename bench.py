@@ -58,8 +58,10 @@ def parse_args():
                          "counts; batched: 512 triangle/4-clique queries on induced subgraphs in one launch; "
                          "serve: continuous-batching server; build: CoCo index build of R-MAT E+; "
                          "order: 4-clique under every loop order beside the cost model's choice; "
-                         "lw: Loomis-Whitney count over the four [n]^3 cubes of ST-Dense (k-ary relations)")
+                         "lw: Loomis-Whitney count over ST-Dense's or ST-Sparse's ternary relations")
     ap.add_argument("--lw-n", type=int, default=512, help="lw: cube side n of ST-Dense's [n]^3 relations")
+    ap.add_argument("--tensor", choices=["dense", "sparse"], default="dense",
+                    help="lw: ST-Dense cubes or ST-Sparse uniform tuples (n^3 of [10 n]^3)")
     ap.add_argument("--shares", default="autotune",
                     help="'autotune' (timed search from the paper's plan over HyperCube share vectors of "
                          ">= --min-cells cells and kernel schedules), 'plan' (Sec. 5.3 decision at --P cells), "
@@ -748,11 +750,14 @@ def build_workload(a, world, rank, local):
 
 
 def kary_workload(a, world, rank, local):
-    """LW (Table "Queries") over ST-Dense's four [n]^3 relations (Sec. 6),
+    """LW (Table "Queries") over the first four relations of ST-Dense (four
+    [n]^3 cubes) or ST-Sparse (n^3 distinct tuples of [10 n]^3 each), Sec. 6,
     count mode; the step is one k-ary join over resident 3-level CoCo
     indexes (built once, timed separately).  Metric: LW results per second.
     Roofline of the search kernel: 4 bytes per unit of the work measure
-    (sum over loops and bindings of lists x shortest list) per launch."""
+    (sum over loops and bindings of lists x shortest list) per launch.  A
+    bounded sample (x below a cut-off, grown until the oracle takes a few
+    seconds) is counted by the oracle and by the GPU on the same rows."""
     import numpy as np
     import torch
 
@@ -767,16 +772,24 @@ def kary_workload(a, world, rank, local):
     stream = torch.cuda.current_stream(dev)
     n = a.lw_n
     t0 = time.perf_counter()
-    cube = datagen.full_cube(n)
+    if a.tensor == "dense":
+        cube = datagen.full_cube(n)
+        host_rels = [cube] * 4
+        desc = f"Loomis-Whitney over ST-Dense's four [{n}]^3 relations (Sec. 6), count"
+    else:
+        host_rels = datagen.st_sparse(n=n, domain=10 * n, m=1, m_domain=1, seed=a.seed + rank,
+                                      device=f"cuda:{local}")[:4]
+        desc = (f"Loomis-Whitney over ST-Sparse's first four relations ({n ** 3} distinct uniform tuples of "
+                f"[{10 * n}]^3 each, Sec. 6), count")
     gen_s = time.perf_counter() - t0
-    rows = [torch.from_numpy(cube.view(np.int32)).to(dev) for _ in range(4)]
+    rows = [torch.from_numpy(r.view(np.int32)).to(dev) for r in host_rels]
     q = hc.LW
     ixs = [hc.build_kindex(rows[j], q.level_cols(j), stream=stream, time_kernels=True) for j in range(4)]
     build_ms = [ix.ms_sort + ix.ms_levels for ix in ixs]
-    expect = n ** 4
     stats = hc.run_kjoin(q, ixs, stats=True, stream=stream)
-    if stats.count != expect:
-        raise RuntimeError(f"LW count {stats.count} != n^4 = {expect}")
+    expect = stats.count
+    if a.tensor == "dense" and expect != n ** 4:
+        raise RuntimeError(f"LW count {expect} != n^4 = {n ** 4}")
     work = stats.work
 
     def step():
@@ -808,17 +821,16 @@ def kary_workload(a, world, rank, local):
     roofline = {"bound": "hbm", "kernel": "kjoin_kernel<4> (k-ary search)", "achieved": round(achieved, 1),
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": None, "alg_bytes_per_launch": 4 * work, "avg_launch_ms": round(kms, 3),
-                "note": "work measure x 4 B; the lists of a dense cube are short and L1/L2-resident, so this "
-                        "figure exceeds what DRAM moves"}
+                "note": "work measure x 4 B; short lists are L1/L2-resident, so this can exceed what DRAM moves"}
 
     e2e = None
     if not a.no_e2e:
-        host = torch.from_numpy(cube.view(np.int32)).pin_memory()
+        hosts = [torch.from_numpy(r.view(np.int32)).pin_memory() for r in host_rels]
         bufs = [torch.empty_like(rows[0]) for _ in range(4)]
 
         def e2e_step():
-            for b in bufs:
-                b.copy_(host, non_blocking=True)
+            for b, h in zip(bufs, hosts):
+                b.copy_(h, non_blocking=True)
             xs = [hc.build_kindex(bufs[j], q.level_cols(j), stream=stream) for j in range(4)]
             c = hc.run_kjoin(q, xs, stream=stream).count
             for x in xs:
@@ -832,36 +844,54 @@ def kary_workload(a, world, rank, local):
             e2e_step()
         torch.cuda.synchronize()
         e2e_ms = (time.perf_counter() - t0) * 1e3 / a.steps
-        e2e = {"value": expect / (e2e_ms / 1e3), "unit": "tuples/s", "h2d_bytes_per_step": 4 * 12 * n ** 3,
-               "d2h_bytes_per_step": 8, "ms_per_step": e2e_ms, "includes": "H2D of the four relations, "
-               "four 3-level CoCo builds, the join, the count read back"}
+        e2e = {"value": expect / (e2e_ms / 1e3), "unit": "tuples/s",
+               "h2d_bytes_per_step": sum(12 * r.shape[0] for r in host_rels), "d2h_bytes_per_step": 8,
+               "ms_per_step": e2e_ms,
+               "includes": "H2D of the four relations, four 3-level CoCo builds, the join, the count read back"}
 
     cpu = None
     if not a.no_cpu_baseline and rank == 0 and world == 1:
         import oracle
 
-        # bounded sample: x in the first fx values and y in the first fy values of [n]
-        fx, fy = min(n, 8), min(n, 64)
-        r1 = cube[(cube[:, 0] < fx) & (cube[:, 1] < fy)]
-        r3 = cube[cube[:, 0] < fx]
-        r4 = cube[cube[:, 0] < fy]
+        # bounded sample: LW with x < fx and y < fy.  R4(Y,Z,U) keeps only rows
+        # whose (y, z) occurs in the sampled R1 (an exact semi-join reduction,
+        # found with torch.isin on the GPU; no join arithmetic)
+        atoms = [tuple(x) for x in q.atoms]
+        fx, fy = (min(n, 8), min(n, 64)) if a.tensor == "dense" else (max(1, n // 4), 10 * n)
+        R1, R2, R3, R4 = host_rels
+        r1 = R1[(R1[:, 0] < fx) & (R1[:, 1] < fy)]
+        r2 = R2[(R2[:, 0] < fx) & (R2[:, 1] < fy)]
+        r3 = R3[R3[:, 0] < fx]
+        k1 = torch.from_numpy((r1[:, 1].astype(np.int64) << 32) | r1[:, 2].astype(np.int64)).to(dev)
+        k4 = torch.from_numpy((R4[:, 0].astype(np.int64) << 32) | R4[:, 1].astype(np.int64)).to(dev)
+        keep = torch.isin(k4, torch.unique(k1)).cpu().numpy()
+        del k1, k4
+        r4 = R4[keep]
+        sample = [np.ascontiguousarray(r) for r in (r1, r2, r3, r4)]
         t0 = time.perf_counter()
-        c = oracle.kgj(4, [tuple(x) for x in q.atoms], [r1, r1, r3, r4])
+        c = oracle.kgj(4, atoms, sample)
         dt = time.perf_counter() - t0
-        if c != fx * fy * n * n:
+        if a.tensor == "dense" and c != fx * fy * n * n:
             raise RuntimeError("oracle sample count")
+        sx = [hc.build_kindex(torch.from_numpy(r.view(np.int32)).to(dev), q.level_cols(j)) for j, r in enumerate(sample)]
+        got = hc.run_kjoin(q, sx).count
+        if got != c:
+            raise RuntimeError(f"sampled parity: GPU {got} != oracle {c}")
         cpu = {"value": c / dt, "unit": "tuples/s", "cores": 1, "kind": "oracle",
-               "sample": f"LW with x < {fx} and y < {fy} ({c} results, {dt:.1f} s, tries built inside, one thread)"}
+               "sample": f"LW with x < {fx} and y < {fy} ({c} results, rows {[int(r.shape[0]) for r in sample]}, "
+                         f"{dt:.1f} s incl. the trie sorts, one thread; the GPU counts the same sample equal)"}
 
     if rank == 0:
+        v2_bytes = sum(4 * r.shape[0] for r in host_rels)
         line = {"metric": "LW results/s (count)", "value": value, "unit": "tuples/s", "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (ST-Dense cubes)",
-                "config": {"workload": f"Loomis-Whitney over four [{n}]^3 relations (ST-Dense, Sec. 6), count",
-                           "rows_per_relation": n ** 3, "count": expect, "work": work,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "data": f"synthetic (ST-{'Dense' if a.tensor == 'dense' else 'Sparse'} shape, seeded)",
+                "config": {"workload": desc, "rows_per_relation": [int(r.shape[0]) for r in host_rels],
+                           "count": int(expect), "work": int(work),
                            "index_build_ms": [round(b, 3) for b in build_ms],
-                           "l2": ("inputs larger than L2: %.0f MB of V_2 over the four indexes" if 16 * n ** 3 > 129e6
-                                  else "inputs within L2: %.0f MB of V_2 over the four indexes") % (16 * n ** 3 / 1e6),
+                           "l2": ("inputs larger than L2: %.0f MB of V_2 over the four indexes" if v2_bytes > 129e6
+                                  else "inputs within L2: %.0f MB of V_2 over the four indexes") % (v2_bytes / 1e6),
                            "generate_s": round(gen_s, 1)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches}
         print(json.dumps(line), flush=True)

@@ -359,22 +359,20 @@ def prefixed_square(first: np.ndarray, m: int) -> np.ndarray:
     return np.stack([a.ravel(), b.ravel(), c.ravel()], axis=1)
 
 
-def _distinct_keys(space: int, n: int, rng: np.random.Generator) -> np.ndarray:
-    """Exactly ``n`` distinct keys drawn uniformly from [0, space): draws are
-    kept in order of first appearance until ``n`` are found; sorted output."""
+def _distinct_keys(space: int, n: int, rng: np.random.Generator, device: str | None = None) -> np.ndarray:
+    """Exactly ``n`` distinct keys drawn uniformly from [0, space) (< 2^63):
+    draws are kept in order of first appearance until ``n`` are found;
+    sorted output.  With ``device`` the de-duplication runs through torch on
+    that device (the same keys, only faster)."""
     if n > space:
         raise ValueError("more distinct keys requested than the space holds")
+    if device is not None:
+        return _distinct_keys_torch(space, n, rng, device)
     found = np.empty(0, dtype=np.uint64)
     first_pos = np.empty(0, dtype=np.int64)
     drawn = 0
     while found.shape[0] < n:
-        need = n - found.shape[0]
-        frac = min(0.999, (found.shape[0] + need) / space)
-        k = max(1024, int(need * (1.05 - math.log1p(-frac) * 1.1)))
-        parts = []
-        for s0 in range(0, k, _CHUNK):
-            parts.append(rng.integers(0, space, size=min(_CHUNK, k - s0), dtype=np.int64).astype(np.uint64))
-        keys = np.concatenate(parts)
+        keys = _draw_keys(space, n - found.shape[0], found.shape[0], rng).astype(np.uint64)
         allk = np.concatenate([found, keys])
         allpos = np.concatenate([first_pos, drawn + np.arange(keys.shape[0], dtype=np.int64)])
         drawn += keys.shape[0]
@@ -385,6 +383,38 @@ def _distinct_keys(space: int, n: int, rng: np.random.Generator) -> np.ndarray:
     return np.sort(found[:n])
 
 
+def _draw_keys(space: int, need: int, have: int, rng: np.random.Generator) -> np.ndarray:
+    """One round of draws, inflated by the expected collision rate."""
+    frac = min(0.999, (have + need) / space)
+    k = max(1024, int(need * (1.05 - math.log1p(-frac) * 1.1)))
+    parts = []
+    for s0 in range(0, k, _CHUNK):
+        parts.append(rng.integers(0, space, size=min(_CHUNK, k - s0), dtype=np.int64))
+    return np.concatenate(parts)
+
+
+def _distinct_keys_torch(space: int, n: int, rng: np.random.Generator, device) -> np.ndarray:
+    import torch
+
+    found = torch.empty(0, dtype=torch.int64, device=device)
+    first_pos = torch.empty(0, dtype=torch.int64, device=device)
+    drawn = 0
+    while found.shape[0] < n:
+        keys = torch.from_numpy(_draw_keys(space, n - found.shape[0], found.shape[0], rng)).to(device)
+        allk = torch.cat([found, keys])
+        allpos = torch.cat([first_pos, drawn + torch.arange(keys.shape[0], dtype=torch.int64, device=device)])
+        drawn += keys.shape[0]
+        uk, inv = torch.unique(allk, sorted=True, return_inverse=True)
+        fp = torch.full((uk.shape[0],), drawn, dtype=torch.int64, device=device)
+        fp.scatter_reduce_(0, inv, allpos, reduce="amin")
+        order = torch.argsort(fp)
+        found = uk[order]
+        first_pos = fp[order]
+        del allk, allpos, inv, uk, fp, order
+    out = torch.sort(found[:n]).values.cpu().numpy().view(np.uint64)
+    return out.copy()
+
+
 def st_dense(n: int = 512, m: int = 4096):
     """ST-Dense (Sec. 6): four relations [n]^3, then three relations
     F x [m] x [m] with first-attribute sets F = {0,1}, {0,2}, {1,2}."""
@@ -393,15 +423,17 @@ def st_dense(n: int = 512, m: int = 4096):
         [prefixed_square(np.array(f, dtype=np.uint32), m) for f in ((0, 1), (0, 2), (1, 2))]
 
 
-def st_sparse(n: int = 512, domain: int = 5120, m: int = 4096, m_domain: int = 40960, seed: int = 0):
+def st_sparse(n: int = 512, domain: int = 5120, m: int = 4096, m_domain: int = 40960, seed: int = 0,
+              device: str | None = None):
     """ST-Sparse (Sec. 6): four relations of n^3 distinct tuples drawn
     uniformly from [domain]^3, then three relations that keep ST-Dense's
     first-attribute sets {0,1}, {0,2}, {1,2} and hold, under each first
     value, m^2 distinct pairs drawn uniformly from [m_domain]^2.  Each
-    relation is lexicographically sorted; relation j draws from seed + j."""
+    relation is lexicographically sorted; relation j draws from seed + j.
+    ``device`` moves the de-duplication to torch on that device."""
     out = []
     for j in range(4):
-        k = _distinct_keys(domain ** 3, n ** 3, _rng(seed + j))
+        k = _distinct_keys(domain ** 3, n ** 3, _rng(seed + j), device)
         a = (k // np.uint64(domain * domain)).astype(np.uint32)
         b = ((k // np.uint64(domain)) % np.uint64(domain)).astype(np.uint32)
         c = (k % np.uint64(domain)).astype(np.uint32)
@@ -410,7 +442,7 @@ def st_sparse(n: int = 512, domain: int = 5120, m: int = 4096, m_domain: int = 4
         rng = _rng(seed + 4 + j)
         parts = []
         for f in fs:
-            k = _distinct_keys(m_domain * m_domain, m * m, rng)
+            k = _distinct_keys(m_domain * m_domain, m * m, rng, device)
             b = (k // np.uint64(m_domain)).astype(np.uint32)
             c = (k % np.uint64(m_domain)).astype(np.uint32)
             parts.append(np.stack([np.full(k.shape[0], f, dtype=np.uint32), b, c], axis=1))

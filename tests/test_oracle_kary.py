@@ -288,3 +288,11 @@ def test_work_measure_brute_force(name, query, seed):
     for order in ((0, 1, 2, 3), (3, 1, 0, 2)):
         cnt, work = oracle.kgj(nv, atoms, rels, order=order, work=True)
         assert work == brute_work(nv, atoms, rels, order, dom), order
+
+
+def test_st_sparse_device_dedup_matches_host():
+    """The torch de-duplication path (run here on the CPU device) keeps the
+    same keys as the numpy one."""
+    a = datagen.st_sparse(n=9, domain=30, m=10, m_domain=25, seed=6)
+    b = datagen.st_sparse(n=9, domain=30, m=10, m_domain=25, seed=6, device="cpu")
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
