@@ -749,6 +749,39 @@ def build_workload(a, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def lw_relations(a, rank: int, device):
+    """The four relations of the LW workload (host arrays) and its description."""
+    import datagen
+
+    n = a.lw_n
+    if a.tensor == "dense":
+        cube = datagen.full_cube(n)
+        return [cube] * 4, f"Loomis-Whitney over ST-Dense's four [{n}]^3 relations (Sec. 6), count"
+    rels = datagen.st_sparse(n=n, domain=10 * n, m=1, m_domain=1, seed=a.seed + rank, device=device)[:4]
+    return rels, (f"Loomis-Whitney over ST-Sparse's first four relations ({n ** 3} distinct uniform tuples of "
+                  f"[{10 * n}]^3 each, Sec. 6), count")
+
+
+def lw_sample(a, host_rels, device):
+    """Bounded sample of LW: x < fx and y < fy.  R4(Y,Z,U) keeps only rows
+    whose (y, z) occurs in the sampled R1 (an exact semi-join reduction, found
+    with torch.isin; no join arithmetic)."""
+    import numpy as np
+    import torch
+
+    n = a.lw_n
+    fx, fy = (min(n, 8), min(n, 64)) if a.tensor == "dense" else (max(1, n // 4), 10 * n)
+    R1, R2, R3, R4 = host_rels
+    r1 = R1[(R1[:, 0] < fx) & (R1[:, 1] < fy)]
+    r2 = R2[(R2[:, 0] < fx) & (R2[:, 1] < fy)]
+    r3 = R3[R3[:, 0] < fx]
+    k1 = torch.from_numpy((r1[:, 1].astype(np.int64) << 32) | r1[:, 2].astype(np.int64)).to(device)
+    k4 = torch.from_numpy((R4[:, 0].astype(np.int64) << 32) | R4[:, 1].astype(np.int64)).to(device)
+    keep = torch.isin(k4, torch.unique(k1)).cpu().numpy()
+    del k1, k4
+    return [np.ascontiguousarray(r) for r in (r1, r2, r3, R4[keep])], fx, fy
+
+
 def kary_workload(a, world, rank, local):
     """LW (Table "Queries") over the first four relations of ST-Dense (four
     [n]^3 cubes) or ST-Sparse (n^3 distinct tuples of [10 n]^3 each), Sec. 6,
@@ -756,15 +789,14 @@ def kary_workload(a, world, rank, local):
     indexes (built once, timed separately).  Metric: LW results per second.
     Roofline of the search kernel: 4 bytes per unit of the work measure
     (sum over loops and bindings of lists x shortest list) per launch.  A
-    bounded sample (x below a cut-off, grown until the oracle takes a few
-    seconds) is counted by the oracle and by the GPU on the same rows."""
+    bounded sample (lw_sample) is counted by the oracle and by the GPU on the
+    same rows."""
     import numpy as np
     import torch
 
     import __graft_entry__
 
     __graft_entry__.build()
-    import datagen
     import paper_2502_06715_gb300 as hc
 
     torch.cuda.set_device(local)
@@ -772,15 +804,7 @@ def kary_workload(a, world, rank, local):
     stream = torch.cuda.current_stream(dev)
     n = a.lw_n
     t0 = time.perf_counter()
-    if a.tensor == "dense":
-        cube = datagen.full_cube(n)
-        host_rels = [cube] * 4
-        desc = f"Loomis-Whitney over ST-Dense's four [{n}]^3 relations (Sec. 6), count"
-    else:
-        host_rels = datagen.st_sparse(n=n, domain=10 * n, m=1, m_domain=1, seed=a.seed + rank,
-                                      device=f"cuda:{local}")[:4]
-        desc = (f"Loomis-Whitney over ST-Sparse's first four relations ({n ** 3} distinct uniform tuples of "
-                f"[{10 * n}]^3 each, Sec. 6), count")
+    host_rels, desc = lw_relations(a, rank, f"cuda:{local}")
     gen_s = time.perf_counter() - t0
     rows = [torch.from_numpy(r.view(np.int32)).to(dev) for r in host_rels]
     q = hc.LW
@@ -853,21 +877,8 @@ def kary_workload(a, world, rank, local):
     if not a.no_cpu_baseline and rank == 0 and world == 1:
         import oracle
 
-        # bounded sample: LW with x < fx and y < fy.  R4(Y,Z,U) keeps only rows
-        # whose (y, z) occurs in the sampled R1 (an exact semi-join reduction,
-        # found with torch.isin on the GPU; no join arithmetic)
         atoms = [tuple(x) for x in q.atoms]
-        fx, fy = (min(n, 8), min(n, 64)) if a.tensor == "dense" else (max(1, n // 4), 10 * n)
-        R1, R2, R3, R4 = host_rels
-        r1 = R1[(R1[:, 0] < fx) & (R1[:, 1] < fy)]
-        r2 = R2[(R2[:, 0] < fx) & (R2[:, 1] < fy)]
-        r3 = R3[R3[:, 0] < fx]
-        k1 = torch.from_numpy((r1[:, 1].astype(np.int64) << 32) | r1[:, 2].astype(np.int64)).to(dev)
-        k4 = torch.from_numpy((R4[:, 0].astype(np.int64) << 32) | R4[:, 1].astype(np.int64)).to(dev)
-        keep = torch.isin(k4, torch.unique(k1)).cpu().numpy()
-        del k1, k4
-        r4 = R4[keep]
-        sample = [np.ascontiguousarray(r) for r in (r1, r2, r3, r4)]
+        sample, fx, fy = lw_sample(a, host_rels, dev)
         t0 = time.perf_counter()
         c = oracle.kgj(4, atoms, sample)
         dt = time.perf_counter() - t0
@@ -982,6 +993,12 @@ def reference_arm(a, world, rank):
     the same workload each step."""
     if rank != 0:
         return
+    if a.workload == "lw":
+        return reference_lw(a, world)
+    if a.workload != "triangle":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm covers the triangle (default) and lw "
+                                                              "workloads"}), flush=True)
+        return
     ep, gen_s = make_graph(a, 0, device=None if os.environ.get("HC_GEN_CPU") else _maybe_cuda())
     times, counts = [], []
     desc, cores = "", 1
@@ -999,6 +1016,35 @@ def reference_arm(a, world, rank):
                        "sample_frac": a.cpu_frac},
             "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": desc, "value": total, "unit": UNIT},
             "e2e": {"value": total, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def reference_lw(a, world):
+    """The k-ary oracle on the LW workload's bounded sample, each step."""
+    import oracle
+
+    dev = _maybe_cuda() or "cpu"
+    host_rels, desc = lw_relations(a, 0, None if dev == "cpu" else dev)
+    sample, fx, fy = lw_sample(a, host_rels, dev)
+    atoms = [(0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)]
+    times, counts = [], []
+    for i in range(a.warmup + a.steps):
+        t0 = time.perf_counter()
+        c = oracle.kgj(4, atoms, sample)
+        dt = time.perf_counter() - t0
+        if i >= a.warmup:
+            times.append(dt)
+            counts.append(c)
+    total = sum(counts) / sum(times)
+    sdesc = (f"LW with x < {fx} and y < {fy} ({counts[0]} results, rows {[int(r.shape[0]) for r in sample]}, "
+             f"trie sorts included, one thread)")
+    line = {"impl": "reference", "metric": "LW results/s (count)", "value": total, "unit": "tuples/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": f"synthetic (ST-{'Dense' if a.tensor == 'dense' else 'Sparse'} shape, seeded)",
+            "config": {"workload": desc},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sdesc, "value": total, "unit": "tuples/s"},
+            "e2e": {"value": total, "unit": "tuples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
