@@ -52,16 +52,20 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--mode", choices=["materialize", "count"], default="materialize")
     ap.add_argument("--workload", choices=["triangle", "clique4", "cycle4", "batched", "serve", "build", "order",
-                                           "lw"],
+                                           "lw", "ct"],
                     default="triangle",
                     help="triangle: R-MAT triangle (default line); clique4 / cycle4: R-MAT 4-clique / 4-cycle "
                          "counts; batched: 512 triangle/4-clique queries on induced subgraphs in one launch; "
                          "serve: continuous-batching server; build: CoCo index build of R-MAT E+; "
                          "order: 4-clique under every loop order beside the cost model's choice; "
-                         "lw: Loomis-Whitney count over ST-Dense's or ST-Sparse's ternary relations")
+                         "lw / ct: Loomis-Whitney / Clover-Triangle counts over ST-Dense's or ST-Sparse's "
+                         "ternary relations")
     ap.add_argument("--lw-n", type=int, default=512, help="lw: cube side n of ST-Dense's [n]^3 relations")
     ap.add_argument("--tensor", choices=["dense", "sparse"], default="dense",
-                    help="lw: ST-Dense cubes or ST-Sparse uniform tuples (n^3 of [10 n]^3)")
+                    help="lw / ct: ST-Dense or ST-Sparse relations")
+    ap.add_argument("--ct-m", type=int, default=4096, help="ct: m of the F x [m] x [m] relations")
+    ap.add_argument("--ct-first", choices=["paper", "common"], default="paper",
+                    help="ct: first-attribute sets {0,1},{0,2},{1,2} as written (empty result) or {0,1} in all three")
     ap.add_argument("--shares", default="autotune",
                     help="'autotune' (timed search from the paper's plan over HyperCube share vectors of "
                          ">= --min-cells cells and kernel schedules), 'plan' (Sec. 5.3 decision at --P cells), "
@@ -231,14 +235,14 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if a.scale is None:
         a.scale = {"triangle": 22, "clique4": 20, "cycle4": 20, "batched": 21, "serve": 23, "build": 22,
-                   "order": 18, "lw": 0}[a.workload]
+                   "order": 18, "lw": 0, "ct": 0}[a.workload]
     if a.impl == "reference":
         return reference_arm(a, world, rank)
     if a.workload == "serve":
         return serve_workload(a, world, rank, local)
     if a.workload == "build":
         return build_workload(a, world, rank, local)
-    if a.workload == "lw":
+    if a.workload in ("lw", "ct"):
         return kary_workload(a, world, rank, local)
     if a.workload == "order":
         return order_workload(a, world, rank, local)
@@ -749,48 +753,93 @@ def build_workload(a, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
-def lw_relations(a, rank: int, device):
-    """The four relations of the LW workload (host arrays) and its description."""
+def tensor_relations(a, rank: int, device):
+    """Host relations of the k-ary workloads (Sec. 6 tensor data), the query's
+    atoms, a description and the closed-form count (or None).  lw: the first
+    four relations of ST-Dense ([n]^3 cubes, n^4 results) or ST-Sparse (n^3
+    distinct uniform tuples of [10 n]^3).  ct: the last three, F x [m] x [m];
+    with --ct-first paper the first-attribute sets are ST-Dense's {0,1},
+    {0,2}, {1,2} (no common value: 0 results, C22), with common all three
+    take {0,1} (2 m^3 results on ST-Dense)."""
+    import numpy as np
+
     import datagen
 
-    n = a.lw_n
+    if a.workload == "lw":
+        n = a.lw_n
+        atoms = [(0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)]
+        if a.tensor == "dense":
+            cube = datagen.full_cube(n)
+            return atoms, [cube] * 4, f"Loomis-Whitney over ST-Dense's four [{n}]^3 relations (Sec. 6), count", n ** 4
+        rels = datagen.st_sparse(n=n, domain=10 * n, m=1, m_domain=1, seed=a.seed + rank, device=device)[:4]
+        return atoms, rels, (f"Loomis-Whitney over ST-Sparse's first four relations ({n ** 3} distinct uniform "
+                             f"tuples of [{10 * n}]^3 each, Sec. 6), count"), None
+    m = a.ct_m
+    atoms = [(0, 1, 2), (0, 1, 3), (0, 2, 3)]
+    sets = [(0, 1), (0, 2), (1, 2)] if a.ct_first == "paper" else [(0, 1)] * 3
     if a.tensor == "dense":
-        cube = datagen.full_cube(n)
-        return [cube] * 4, f"Loomis-Whitney over ST-Dense's four [{n}]^3 relations (Sec. 6), count"
-    rels = datagen.st_sparse(n=n, domain=10 * n, m=1, m_domain=1, seed=a.seed + rank, device=device)[:4]
-    return rels, (f"Loomis-Whitney over ST-Sparse's first four relations ({n ** 3} distinct uniform tuples of "
-                  f"[{10 * n}]^3 each, Sec. 6), count")
+        rels = [datagen.prefixed_square(np.array(f, dtype=np.uint32), m) for f in sets]
+        expect = 0 if a.ct_first == "paper" else 2 * m ** 3
+        return atoms, rels, (f"Clover-Triangle over ST-Dense's F x [{m}] x [{m}] relations, F = {sets} "
+                             f"(Sec. 6), count"), expect
+    rels = datagen.st_sparse(n=1, domain=1, m=m, m_domain=10 * m, seed=a.seed + rank, device=device)[4:]
+    if a.ct_first != "paper":  # the same first values {0, 1} in all three
+        rels = [_common_first(r) for r in rels]
+    return atoms, rels, (f"Clover-Triangle over ST-Sparse's last three relations ({m}^2 distinct uniform pairs of "
+                         f"[{10 * m}]^2 per first value, first values {sets}, Sec. 6), count"), None
 
 
-def lw_sample(a, host_rels, device):
-    """Bounded sample of LW: x < fx and y < fy.  R4(Y,Z,U) keeps only rows
-    whose (y, z) occurs in the sampled R1 (an exact semi-join reduction, found
-    with torch.isin; no join arithmetic)."""
+def _common_first(r):
+    """Relabel a relation's two first-attribute values to 0 and 1 (rows stay distinct)."""
+    import numpy as np
+
+    lo = r[:, 0].min()
+    out = r.copy()
+    out[:, 0] = (r[:, 0] != lo).astype(np.uint32)
+    return out[np.lexsort(out.T[::-1])]
+
+
+def tensor_sample(a, atoms, host_rels, device):
+    """Bounded sample of the k-ary workload: the query restricted to
+    X < fx and Y < fy (X = variable 0 of LW, variable 1 of CT; Y the next).
+    For LW, R4(Y,Z,U) keeps only rows whose (y, z) occurs in the sampled R1
+    (an exact semi-join reduction, found with torch.isin; no join
+    arithmetic).  Returns the sampled relations and a description."""
     import numpy as np
     import torch
 
-    n = a.lw_n
-    fx, fy = (min(n, 8), min(n, 64)) if a.tensor == "dense" else (max(1, n // 4), 10 * n)
-    R1, R2, R3, R4 = host_rels
-    r1 = R1[(R1[:, 0] < fx) & (R1[:, 1] < fy)]
-    r2 = R2[(R2[:, 0] < fx) & (R2[:, 1] < fy)]
-    r3 = R3[R3[:, 0] < fx]
-    k1 = torch.from_numpy((r1[:, 1].astype(np.int64) << 32) | r1[:, 2].astype(np.int64)).to(device)
-    k4 = torch.from_numpy((R4[:, 0].astype(np.int64) << 32) | R4[:, 1].astype(np.int64)).to(device)
-    keep = torch.isin(k4, torch.unique(k1)).cpu().numpy()
-    del k1, k4
-    return [np.ascontiguousarray(r) for r in (r1, r2, r3, R4[keep])], fx, fy
+    if a.workload == "lw":
+        n = a.lw_n
+        fx, fy = (min(n, 8), min(n, 64)) if a.tensor == "dense" else (max(1, n // 4), 10 * n)
+        R1, R2, R3, R4 = host_rels
+        r1 = R1[(R1[:, 0] < fx) & (R1[:, 1] < fy)]
+        r2 = R2[(R2[:, 0] < fx) & (R2[:, 1] < fy)]
+        r3 = R3[R3[:, 0] < fx]
+        k1 = torch.from_numpy((r1[:, 1].astype(np.int64) << 32) | r1[:, 2].astype(np.int64)).to(device)
+        k4 = torch.from_numpy((R4[:, 0].astype(np.int64) << 32) | R4[:, 1].astype(np.int64)).to(device)
+        keep = torch.isin(k4, torch.unique(k1)).cpu().numpy()
+        del k1, k4
+        sample = [r1, r2, r3, R4[keep]]
+        desc = f"LW with x < {fx} and y < {fy}"
+    else:
+        m = a.ct_m
+        fx, fy = min(m, 16), min(m, 256)
+        R5, R6, R7 = host_rels  # R5(U,X,Y), R6(U,X,Z), R7(U,Y,Z)
+        sample = [R5[(R5[:, 1] < fx) & (R5[:, 2] < fy)], R6[R6[:, 1] < fx], R7[R7[:, 1] < fy]]
+        desc = f"CT with x < {fx} and y < {fy}"
+    sample = [np.ascontiguousarray(r) for r in sample]
+    return sample, f"{desc}, rows {[int(r.shape[0]) for r in sample]}"
 
 
 def kary_workload(a, world, rank, local):
-    """LW (Table "Queries") over the first four relations of ST-Dense (four
-    [n]^3 cubes) or ST-Sparse (n^3 distinct tuples of [10 n]^3 each), Sec. 6,
-    count mode; the step is one k-ary join over resident 3-level CoCo
-    indexes (built once, timed separately).  Metric: LW results per second.
-    Roofline of the search kernel: 4 bytes per unit of the work measure
-    (sum over loops and bindings of lists x shortest list) per launch.  A
-    bounded sample (lw_sample) is counted by the oracle and by the GPU on the
-    same rows."""
+    """LW or CT (Table "Queries") over Sec. 6's tensor relations
+    (tensor_relations), count mode, in the loop order hc_choose_korder picks;
+    the step is one k-ary join over resident 3-level CoCo indexes (built
+    once, timed separately).  Metric: results per second.  Roofline of the
+    search kernel: 4 bytes per unit of the work measure (sum over loops and
+    bindings of lists x shortest list) per launch.  A bounded sample
+    (tensor_sample) is counted by the oracle and by the GPU on the same
+    rows."""
     import numpy as np
     import torch
 
@@ -802,18 +851,23 @@ def kary_workload(a, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    n = a.lw_n
     t0 = time.perf_counter()
-    host_rels, desc = lw_relations(a, rank, f"cuda:{local}")
+    atoms, host_rels, desc, closed = tensor_relations(a, rank, f"cuda:{local}")
     gen_s = time.perf_counter() - t0
+    na = len(atoms)
     rows = [torch.from_numpy(r.view(np.int32)).to(dev) for r in host_rels]
-    q = hc.LW
-    ixs = [hc.build_kindex(rows[j], q.level_cols(j), stream=stream, time_kernels=True) for j in range(4)]
-    build_ms = [ix.ms_sort + ix.ms_levels for ix in ixs]
+    q = hc.KQuery(4, tuple(atoms))
+    ixs = [hc.build_kindex(rows[j], None, stream=stream) for j in range(na)]
+    q = q.with_order(hc.choose_korder(q, ixs))  # Sec. 5.2-5.3 from the built indexes' statistics
+    ixs = [ix if ix.level_cols == q.level_cols(j) else hc.build_kindex(rows[j], q.level_cols(j), stream=stream)
+           for j, ix in enumerate(ixs)]
+    tb = [hc.build_kindex(rows[j], q.level_cols(j), stream=stream, time_kernels=True) for j in range(na)]
+    build_ms = [ix.ms_sort + ix.ms_levels for ix in tb]
+    del tb
     stats = hc.run_kjoin(q, ixs, stats=True, stream=stream)
     expect = stats.count
-    if a.tensor == "dense" and expect != n ** 4:
-        raise RuntimeError(f"LW count {expect} != n^4 = {n ** 4}")
+    if closed is not None and expect != closed:
+        raise RuntimeError(f"count {expect} != closed form {closed}")
     work = stats.work
 
     def step():
@@ -831,7 +885,7 @@ def kary_workload(a, world, rank, local):
     for _ in range(a.steps):
         r = step()
         if r.count != expect:
-            raise RuntimeError("LW count changed between steps")
+            raise RuntimeError("the count changed between steps")
         kern_ms += r.ms_join_kernel
     e1.record(stream)
     torch.cuda.synchronize()
@@ -841,8 +895,10 @@ def kary_workload(a, world, rank, local):
     value = expect / (ms / 1e3)
     peak, peak_kind = measured_hbm_peak()
     kms = kern_ms / a.steps
+    metric = "LW results/s (count)" if a.workload == "lw" else "CT results/s (count)"
     achieved = 4.0 * work / (kms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": "kjoin_kernel<4> (k-ary search)", "achieved": round(achieved, 1),
+                "launches_per_step": 1,
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": None, "alg_bytes_per_launch": 4 * work, "avg_launch_ms": round(kms, 3),
                 "note": "work measure x 4 B; short lists are L1/L2-resident, so this can exceed what DRAM moves"}
@@ -850,12 +906,12 @@ def kary_workload(a, world, rank, local):
     e2e = None
     if not a.no_e2e:
         hosts = [torch.from_numpy(r.view(np.int32)).pin_memory() for r in host_rels]
-        bufs = [torch.empty_like(rows[0]) for _ in range(4)]
+        bufs = [torch.empty_like(r) for r in rows]
 
         def e2e_step():
             for b, h in zip(bufs, hosts):
                 b.copy_(h, non_blocking=True)
-            xs = [hc.build_kindex(bufs[j], q.level_cols(j), stream=stream) for j in range(4)]
+            xs = [hc.build_kindex(bufs[j], q.level_cols(j), stream=stream) for j in range(na)]
             c = hc.run_kjoin(q, xs, stream=stream).count
             for x in xs:
                 x.free()
@@ -871,38 +927,36 @@ def kary_workload(a, world, rank, local):
         e2e = {"value": expect / (e2e_ms / 1e3), "unit": "tuples/s",
                "h2d_bytes_per_step": sum(12 * r.shape[0] for r in host_rels), "d2h_bytes_per_step": 8,
                "ms_per_step": e2e_ms,
-               "includes": "H2D of the four relations, four 3-level CoCo builds, the join, the count read back"}
+               "includes": "H2D of the relations, their 3-level CoCo builds, the join, the count read back"}
 
     cpu = None
     if not a.no_cpu_baseline and rank == 0 and world == 1:
         import oracle
 
-        atoms = [tuple(x) for x in q.atoms]
-        sample, fx, fy = lw_sample(a, host_rels, dev)
+        sample, sdesc = tensor_sample(a, atoms, host_rels, dev)
         t0 = time.perf_counter()
-        c = oracle.kgj(4, atoms, sample)
+        c = oracle.kgj(4, atoms, sample, order=list(q.loop_order()))
         dt = time.perf_counter() - t0
-        if a.tensor == "dense" and c != fx * fy * n * n:
-            raise RuntimeError("oracle sample count")
         sx = [hc.build_kindex(torch.from_numpy(r.view(np.int32)).to(dev), q.level_cols(j)) for j, r in enumerate(sample)]
         got = hc.run_kjoin(q, sx).count
         if got != c:
             raise RuntimeError(f"sampled parity: GPU {got} != oracle {c}")
         cpu = {"value": c / dt, "unit": "tuples/s", "cores": 1, "kind": "oracle",
-               "sample": f"LW with x < {fx} and y < {fy} ({c} results, rows {[int(r.shape[0]) for r in sample]}, "
-                         f"{dt:.1f} s incl. the trie sorts, one thread; the GPU counts the same sample equal)"}
+               "sample": f"{sdesc} ({c} results, {dt:.1f} s incl. the trie sorts, one thread; the GPU counts "
+                         f"the same sample equal)"}
 
     if rank == 0:
         v2_bytes = sum(4 * r.shape[0] for r in host_rels)
-        line = {"metric": "LW results/s (count)", "value": value, "unit": "tuples/s", "n_gpus": world,
+        tname = "Dense" if a.tensor == "dense" else "Sparse"
+        line = {"metric": metric, "value": value, "unit": "tuples/s", "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-                "data": f"synthetic (ST-{'Dense' if a.tensor == 'dense' else 'Sparse'} shape, seeded)",
+                "data": f"synthetic (ST-{tname} shape, seeded)",
                 "config": {"workload": desc, "rows_per_relation": [int(r.shape[0]) for r in host_rels],
-                           "count": int(expect), "work": int(work),
+                           "order": list(q.loop_order()), "count": int(expect), "work": int(work),
                            "index_build_ms": [round(b, 3) for b in build_ms],
-                           "l2": ("inputs larger than L2: %.0f MB of V_2 over the four indexes" if v2_bytes > 129e6
-                                  else "inputs within L2: %.0f MB of V_2 over the four indexes") % (v2_bytes / 1e6),
+                           "l2": ("inputs larger than L2: %.0f MB of V_2 over the indexes" if v2_bytes > 129e6
+                                  else "inputs within L2: %.0f MB of V_2 over the indexes") % (v2_bytes / 1e6),
                            "generate_s": round(gen_s, 1)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
@@ -993,11 +1047,11 @@ def reference_arm(a, world, rank):
     the same workload each step."""
     if rank != 0:
         return
-    if a.workload == "lw":
-        return reference_lw(a, world)
+    if a.workload in ("lw", "ct"):
+        return reference_tensor(a, world)
     if a.workload != "triangle":
-        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm covers the triangle (default) and lw "
-                                                              "workloads"}), flush=True)
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm covers the triangle (default), lw "
+                                                              "and ct workloads"}), flush=True)
         return
     ep, gen_s = make_graph(a, 0, device=None if os.environ.get("HC_GEN_CPU") else _maybe_cuda())
     times, counts = [], []
@@ -1019,14 +1073,13 @@ def reference_arm(a, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def reference_lw(a, world):
-    """The k-ary oracle on the LW workload's bounded sample, each step."""
+def reference_tensor(a, world):
+    """The k-ary oracle on the k-ary workload's bounded sample, each step."""
     import oracle
 
     dev = _maybe_cuda() or "cpu"
-    host_rels, desc = lw_relations(a, 0, None if dev == "cpu" else dev)
-    sample, fx, fy = lw_sample(a, host_rels, dev)
-    atoms = [(0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)]
+    atoms, host_rels, desc, _ = tensor_relations(a, 0, None if dev == "cpu" else dev)
+    sample, sdesc = tensor_sample(a, atoms, host_rels, dev)
     times, counts = [], []
     for i in range(a.warmup + a.steps):
         t0 = time.perf_counter()
@@ -1036,15 +1089,16 @@ def reference_lw(a, world):
             times.append(dt)
             counts.append(c)
     total = sum(counts) / sum(times)
-    sdesc = (f"LW with x < {fx} and y < {fy} ({counts[0]} results, rows {[int(r.shape[0]) for r in sample]}, "
-             f"trie sorts included, one thread)")
-    line = {"impl": "reference", "metric": "LW results/s (count)", "value": total, "unit": "tuples/s",
+    unit = "tuples/s"
+    metric = "LW results/s (count)" if a.workload == "lw" else "CT results/s (count)"
+    line = {"impl": "reference", "metric": metric, "value": total, "unit": unit,
             "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": f"synthetic (ST-{'Dense' if a.tensor == 'dense' else 'Sparse'} shape, seeded)",
             "config": {"workload": desc},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sdesc, "value": total, "unit": "tuples/s"},
-            "e2e": {"value": total, "unit": "tuples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": total, "unit": unit,
+                             "sample": f"{sdesc} ({counts[0]} results, trie sorts included, one thread)"},
+            "e2e": {"value": total, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
