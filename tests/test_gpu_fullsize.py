@@ -141,3 +141,66 @@ def test_four_cycle_rmat20_sample(hc, rmat20):
     ixr = hc.build_index(dev(rx), 0)
     for sh in ([1, 1, 1, 1], [4, 2, 2, 1]):
         assert hc.run_join(q, [ixr, ixr, ix, ix], shares=sh).count == want
+
+
+# ---------------------------------------------------------- k-ary relations
+
+LW_ATOMS = [(0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)]
+
+
+def lw_sample(rels, fx, fy):
+    """LW restricted to x < fx and y < fy (selections pushed into the atoms
+    holding x and y); R4(Y,Z,U) keeps the rows whose (y, z) occurs in the
+    restricted R1 (an exact semi-join reduction)."""
+    r1, r2, r3, r4 = rels
+    s1 = r1[(r1[:, 0] < fx) & (r1[:, 1] < fy)]
+    s2 = r2[(r2[:, 0] < fx) & (r2[:, 1] < fy)]
+    s3 = r3[r3[:, 0] < fx]
+    import torch
+
+    k1 = torch.from_numpy((s1[:, 1].astype(np.int64) << 32) | s1[:, 2].astype(np.int64)).cuda()
+    k4 = torch.from_numpy((r4[:, 0].astype(np.int64) << 32) | r4[:, 1].astype(np.int64)).cuda()
+    s4 = r4[torch.isin(k4, torch.unique(k1)).cpu().numpy()]
+    return [np.ascontiguousarray(s) for s in (s1, s2, s3, s4)]
+
+
+def test_lw_st_dense_512(hc):
+    """LW over ST-Dense's four [512]^3 cubes (134 M rows each): 512^4
+    results; a sample (x < 2, y < 32) equal to the oracle's."""
+    n = 512
+    cube = datagen.full_cube(n)
+    q = hc.LW
+    ixs = [hc.build_kindex(dev(cube), q.level_cols(j)) for j in range(4)]
+    assert hc.run_kjoin(q, ixs).count == n ** 4
+    del ixs
+    sample = lw_sample([cube] * 4, 2, 32)
+    want = oracle.kgj(4, LW_ATOMS, sample)
+    assert want == 2 * 32 * n * n
+    sx = [hc.build_kindex(dev(r), q.level_cols(j)) for j, r in enumerate(sample)]
+    assert hc.run_kjoin(q, sx).count == want
+
+
+def test_lw_st_sparse_512(hc):
+    """LW over ST-Sparse's four relations (134 M distinct uniform tuples of
+    [5120]^3 each): every output tuple satisfies every atom, and a sample
+    (x < 128) equals the oracle's count."""
+    rels = datagen.st_sparse(n=512, domain=5120, m=1, m_domain=1, seed=3, device="cuda")[:4]
+    q = hc.LW
+    ixs = [hc.build_kindex(dev(r), q.level_cols(j)) for j, r in enumerate(rels)]
+    r = hc.run_kjoin(q, ixs, mode="materialize")
+    t = u32(r.tuples)
+    assert t.shape == (r.count, 4)
+    assert np.unique(t, axis=0).shape[0] == t.shape[0]
+    for (a, rel) in zip(LW_ATOMS, rels):  # rows are sorted, so packed keys (13 bits a value) are too
+        keys = (rel[:, 0].astype(np.uint64) << np.uint64(26)) | (rel[:, 1].astype(np.uint64) << np.uint64(13)) | rel[:, 2]
+        probe = ((t[:, a[0]].astype(np.uint64) << np.uint64(26)) | (t[:, a[1]].astype(np.uint64) << np.uint64(13))
+                 | t[:, a[2]])
+        pos = np.minimum(np.searchsorted(keys, probe), keys.shape[0] - 1)
+        assert (keys[pos] == probe).all()
+    del ixs
+    sample = lw_sample(rels, 128, 5120)
+    want = oracle.kgj(4, LW_ATOMS, sample)
+    sx = [hc.build_kindex(dev(s), q.level_cols(j)) for j, s in enumerate(sample)]
+    assert hc.run_kjoin(q, sx).count == want
+    # the sample's results are exactly the full result's tuples with x < 128
+    assert int((t[:, 0] < 128).sum()) == want
