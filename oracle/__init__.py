@@ -87,7 +87,7 @@ def _lib():
                                     _i32p, _i32p, vp, u64, vp, u64, ctypes.POINTER(u64)]
     lib.oc_kgj.restype = ctypes.c_int
     lib.oc_kgj.argtypes = [ctypes.c_int, ctypes.c_int, _i32p, _i32p, ctypes.POINTER(vp), _u64p, vp, vp, u64,
-                           ctypes.POINTER(u64), ctypes.POINTER(u64)]
+                           ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.c_int]
     lib.oc_tuple_cells.restype = ctypes.c_int
     lib.oc_tuple_cells.argtypes = [vp, u64, ctypes.c_int, _u32p, _u32p, _u32p]
     _LIB = lib
@@ -266,13 +266,15 @@ FOUR_CLIQUE = (4, [(0, 1), (0, 2), (1, 3), (2, 3), (1, 2), (0, 3)])  # Q6
 TWO_TRIANGLE = (5, [(0, 1), (0, 2), (1, 2), (2, 3), (2, 4), (3, 4)])  # Q8
 
 
-def kgj(n_vars: int, atoms, rels, order=None, tuples: bool = False, cap: int = 1 << 22, work: bool = False):
+def kgj(n_vars: int, atoms, rels, order=None, tuples: bool = False, cap: int = 1 << 22, work: bool = False,
+        nthreads: int = 1):
     """Generic Join over atoms of arity 1 to 3 (``oracle_kary.c``): atoms[j]
     is a tuple of variable ids, rels[j] an (n, len(atoms[j])) array (a set).
     Returns the output count, or (count, tuples in variable-id order) with
     ``tuples`` (at most ``cap`` of them); with ``work``, (count, work) or
     (count, tuples, work), work being the sum over loops and bindings of
-    (number of lists) * (shortest list length)."""
+    (number of lists) * (shortest list length).  ``nthreads`` > 1 counts on
+    that many threads (ignored with ``tuples``)."""
     na = len(atoms)
     if na != len(rels):
         raise ValueError("one relation per atom")
@@ -298,7 +300,7 @@ def kgj(n_vars: int, atoms, rels, order=None, tuples: bool = False, cap: int = 1
     _check(_lib().oc_kgj(n_vars, na, arity, vars_, ptrs, ns,
                          ordv.ctypes.data if ordv is not None else None,
                          out.ctypes.data if tuples else None, cap if tuples else 0, ctypes.byref(cnt),
-                         ctypes.byref(wk) if work else None), "kgj")
+                         ctypes.byref(wk) if work else None, int(nthreads)), "kgj")
     extra = (wk.value,) if work else ()
     if not tuples:
         return (cnt.value, *extra) if work else cnt.value

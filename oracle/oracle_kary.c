@@ -23,8 +23,15 @@
  * measure of the library's statistics (the per-binding cost of Sec. 5.2
  * without its log factor).
  *
+ * Counting can run on several threads: the rows of the first loop's
+ * shortest list are cut into pieces at value boundaries, each thread runs
+ * the loops over its piece (a value is searched in the other lists only
+ * within its own piece's range of that list, so every binding of the first
+ * loop belongs to exactly one thread), and the counts and work are summed.
+ *
  * Errors are returned as non-zero codes.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -56,6 +63,7 @@ typedef struct {
     uint64_t count;
     uint64_t work;
     int want_work;
+    int skip_work0; /* the first loop's work is added once, outside the threads */
     uint32_t *out;
     uint64_t cap;
 } kplan_t;
@@ -107,7 +115,7 @@ static uint64_t distinct_in(const katom_t *a, uint64_t lo, uint64_t hi, int d) {
 }
 
 static void loop_level(kplan_t *p, int i) {
-    if (p->want_work) {
+    if (p->want_work && !(i == 0 && p->skip_work0)) {
         uint64_t shortest = UINT64_MAX;
         for (int q = 0; q < p->nat[i]; ++q) {
             const int j = p->at[i][q];
@@ -166,6 +174,62 @@ static void loop_level(kplan_t *p, int i) {
     }
 }
 
+static void *count_worker(void *arg) {
+    loop_level((kplan_t *)arg, 0);
+    return NULL;
+}
+
+/* Count with up to nthreads threads (see the top of the file). */
+static int count_threaded(kplan_t *p, int nthreads) {
+    if (nthreads > 64) nthreads = 64;
+    /* the first loop's list with the fewest rows, and its column there */
+    int q0 = 0;
+    for (int q = 1; q < p->nat[0]; ++q)
+        if (p->a[p->at[0][q]].n < p->a[p->at[0][q0]].n) q0 = q;
+    const int j0 = p->at[0][q0], d0 = p->dep[0][q0];
+    const katom_t *a0 = &p->a[j0];
+    if (p->want_work) { /* the first loop's work, once, over the full lists */
+        uint64_t shortest = UINT64_MAX;
+        for (int q = 0; q < p->nat[0]; ++q) {
+            const int j = p->at[0][q];
+            const uint64_t len = distinct_in(&p->a[j], 0, p->a[j].n, p->dep[0][q]);
+            if (len < shortest) shortest = len;
+        }
+        p->work += (uint64_t)p->nat[0] * shortest;
+    }
+    /* piece t: rows [cut[t], cut[t+1]) of atom j0, cut at value boundaries */
+    uint64_t cut[65];
+    cut[0] = 0;
+    for (int t = 1; t < nthreads; ++t) {
+        uint64_t r = a0->n * (uint64_t)t / (uint64_t)nthreads;
+        if (r < cut[t - 1]) r = cut[t - 1];
+        while (r > 0 && r < a0->n && a0->r[r].c[d0] == a0->r[r - 1].c[d0]) ++r;
+        cut[t] = r;
+    }
+    cut[nthreads] = a0->n;
+    kplan_t *w = (kplan_t *)calloc((size_t)nthreads, sizeof(kplan_t));
+    pthread_t th[64];
+    int live[64];
+    if (!w) return OK_ENOMEM;
+    for (int t = 0; t < nthreads; ++t) {
+        w[t] = *p;
+        w[t].count = 0;
+        w[t].work = 0;
+        w[t].skip_work0 = 1;
+        w[t].lo[j0] = cut[t];
+        w[t].hi[j0] = cut[t + 1];
+        live[t] = pthread_create(&th[t], NULL, count_worker, &w[t]) == 0;
+        if (!live[t]) count_worker(&w[t]);
+    }
+    for (int t = 0; t < nthreads; ++t) {
+        if (live[t]) pthread_join(th[t], NULL);
+        p->count += w[t].count;
+        p->work += w[t].work;
+    }
+    free(w);
+    return OK_OK;
+}
+
 /* Generic Join of a full conjunctive query over atoms of arity 1..3.
  *   nv, na         variables (<= 8) and atoms (<= 16)
  *   arity[j]       1, 2 or 3
@@ -174,9 +238,10 @@ static void loop_level(kplan_t *p, int i) {
  *   order          loop order (variable ids), or NULL for 0, 1, ...
  *   out, cap       optional: up to cap tuples of nv values (variable-id order)
  *   count_out      number of output tuples
- *   work_out       optional: the work measure described at the top */
+ *   work_out       optional: the work measure described at the top
+ *   nthreads       threads for counting (ignored when tuples are written) */
 int oc_kgj(int nv, int na, const int *arity, const int *vars, const uint32_t *const *rows, const uint64_t *n,
-           const int *order, uint32_t *out, uint64_t cap, uint64_t *count_out, uint64_t *work_out) {
+           const int *order, uint32_t *out, uint64_t cap, uint64_t *count_out, uint64_t *work_out, int nthreads) {
     if (nv < 1 || nv > OK_MAXV || na < 1 || na > OK_MAXA || !arity || !vars || !rows || !n || !count_out)
         return OK_EARG;
     kplan_t *p = (kplan_t *)calloc(1, sizeof(kplan_t));
@@ -250,7 +315,12 @@ int oc_kgj(int nv, int na, const int *arity, const int *vars, const uint32_t *co
     p->out = out;
     p->cap = out ? cap : 0;
     p->want_work = work_out != NULL;
-    loop_level(p, 0);
+    if (nthreads > 1 && !out) {
+        rc = count_threaded(p, nthreads);
+        if (rc != OK_OK) goto done;
+    } else {
+        loop_level(p, 0);
+    }
     *count_out = p->count;
     if (work_out) *work_out = p->work;
 done:

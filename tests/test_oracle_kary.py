@@ -296,3 +296,14 @@ def test_st_sparse_device_dedup_matches_host():
     a = datagen.st_sparse(n=9, domain=30, m=10, m_domain=25, seed=6)
     b = datagen.st_sparse(n=9, domain=30, m=10, m_domain=25, seed=6, device="cpu")
     assert all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+@pytest.mark.parametrize("name,query", [("LW", LW), ("CT", CT), ("mixed", (5, [(2, 0, 4), (3, 1), (4,), (1, 2, 0), (3, 4)]))])
+def test_threaded_count_equals_sequential(name, query):
+    nv, atoms = query
+    rng = np.random.default_rng(31)
+    rels = [random_rel(rng, len(a), 7, 0.5) for a in atoms]
+    for order in (None, tuple(reversed(range(nv)))):
+        want = oracle.kgj(nv, atoms, rels, order=order, work=True)
+        for t in (2, 3, 8, 64, 100):
+            assert oracle.kgj(nv, atoms, rels, order=order, work=True, nthreads=t) == want, (order, t)
