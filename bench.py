@@ -851,6 +851,11 @@ def kary_workload(a, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    dist = None
+    if world > 1:  # independent replicas (seed + rank), no data-path collective
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
     t0 = time.perf_counter()
     atoms, host_rels, desc, closed = tensor_relations(a, rank, f"cuda:{local}")
     gen_s = time.perf_counter() - t0
@@ -877,6 +882,9 @@ def kary_workload(a, world, rank, local):
     for _ in range(a.warmup):
         step()
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+        torch.cuda.synchronize()
     sampler = ClockSampler(local)
     launches0 = hc.kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -889,10 +897,15 @@ def kary_workload(a, world, rank, local):
         kern_ms += r.ms_join_kernel
     e1.record(stream)
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     clocks = sampler.stop()
     launches = hc.kernel_launches() - launches0
-    ms = e0.elapsed_time(e1) / a.steps
-    value = expect / (ms / 1e3)
+    ms_total, results = e0.elapsed_time(e1), float(expect) * a.steps
+    if dist:  # the slowest rank's time, the results of all ranks
+        ms_total, results = combine_ranks(ms_total, results, dist, dev)
+    ms = ms_total / a.steps
+    value = results / (ms_total / 1e3)
     peak, peak_kind = measured_hbm_peak()
     kms = kern_ms / a.steps
     metric = "LW results/s (count)" if a.workload == "lw" else "CT results/s (count)"
@@ -919,12 +932,17 @@ def kary_workload(a, world, rank, local):
 
         e2e_step()
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
         for _ in range(a.steps):
             e2e_step()
         torch.cuda.synchronize()
-        e2e_ms = (time.perf_counter() - t0) * 1e3 / a.steps
-        e2e = {"value": expect / (e2e_ms / 1e3), "unit": "tuples/s",
+        e2e_total, e2e_results = (time.perf_counter() - t0) * 1e3, float(expect) * a.steps
+        if dist:
+            e2e_total, e2e_results = combine_ranks(e2e_total, e2e_results, dist, dev)
+        e2e_ms = e2e_total / a.steps
+        e2e = {"value": e2e_results / (e2e_total / 1e3), "unit": "tuples/s",
                "h2d_bytes_per_step": sum(12 * r.shape[0] for r in host_rels), "d2h_bytes_per_step": 8,
                "ms_per_step": e2e_ms,
                "includes": "H2D of the relations, their 3-level CoCo builds, the join, the count read back"}
@@ -961,6 +979,9 @@ def kary_workload(a, world, rank, local):
                            "generate_s": round(gen_s, 1)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 def serve_workload(a, world, rank, local):
