@@ -7,7 +7,9 @@
  * split into HyperCube shares.  Three calls follow the paper's architecture
  * (Sec. 3): hc_build_index (Preprocessor: sort + CoCo, Sec. 4),
  * hc_choose_shares (Optimizer: cost model and plan decision, Sec. 5.2-5.3),
- * hc_run_join (Preprocessor partitioning + Executor, Sec. 4-5).
+ * hc_run_join (Preprocessor partitioning + Executor, Sec. 4-5).  Relations of
+ * arity up to 3 (k-level CoCo, k-ary Generic Join, loop-order choice) are
+ * declared in honeycomb_kary.h.
  *
  * Conventions for every entry point:
  *  - Device pointers ("d_" prefix) are CUDA device memory of the current
