@@ -267,3 +267,15 @@ def test_chosen_order_matches_oracle(hc):
     order = hc.choose_korder(q, stats)
     assert sorted(order) == [0, 1, 2, 3]
     run_both(hc, 4, atoms, rels, order)
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_six_variables(hc, seed):
+    """The largest k-ary query (HC_KMAX_VARS = 6 loops): two ternary atoms,
+    binary and unary ones, against the oracle under two orders."""
+    rng = np.random.default_rng(90 + seed)
+    atoms = [(0, 1, 2), (2, 3, 4), (4, 5), (5, 0), (1, 3), (3,)]
+    dom = 7
+    rels = [distinct_rows(rng, {1: 5, 2: 30, 3: 200}[len(a)], len(a), dom) for a in atoms]
+    for order in ((0, 1, 2, 3, 4, 5), (5, 3, 1, 4, 0, 2)):
+        run_both(hc, 6, atoms, rels, order)
