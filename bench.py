@@ -804,7 +804,8 @@ def tensor_sample(a, atoms, host_rels, device):
     X < fx and Y < fy (X = variable 0 of LW, variable 1 of CT; Y the next).
     For LW, R4(Y,Z,U) keeps only rows whose (y, z) occurs in the sampled R1
     (an exact semi-join reduction, found with torch.isin; no join
-    arithmetic).  Returns the sampled relations and a description."""
+    arithmetic).  Returns the sampled relations, a description and the
+    restriction ((variable, bound), (variable, bound))."""
     import numpy as np
     import torch
 
@@ -821,14 +822,16 @@ def tensor_sample(a, atoms, host_rels, device):
         del k1, k4
         sample = [r1, r2, r3, R4[keep]]
         desc = f"LW with x < {fx} and y < {fy}"
+        restriction = ((0, fx), (1, fy))
     else:
         m = a.ct_m
         fx, fy = min(m, 16), min(m, 256)
         R5, R6, R7 = host_rels  # R5(U,X,Y), R6(U,X,Z), R7(U,Y,Z)
         sample = [R5[(R5[:, 1] < fx) & (R5[:, 2] < fy)], R6[R6[:, 1] < fx], R7[R7[:, 1] < fy]]
         desc = f"CT with x < {fx} and y < {fy}"
+        restriction = ((1, fx), (2, fy))
     sample = [np.ascontiguousarray(r) for r in sample]
-    return sample, f"{desc}, rows {[int(r.shape[0]) for r in sample]}"
+    return sample, f"{desc}, rows {[int(r.shape[0]) for r in sample]}", restriction
 
 
 def kary_workload(a, world, rank, local):
@@ -951,7 +954,7 @@ def kary_workload(a, world, rank, local):
     if not a.no_cpu_baseline and rank == 0 and world == 1:
         import oracle
 
-        sample, sdesc = tensor_sample(a, atoms, host_rels, dev)
+        sample, sdesc, _ = tensor_sample(a, atoms, host_rels, dev)
         threads = min(64, os.cpu_count() or 1)
         t0 = time.perf_counter()
         c = oracle.kgj(4, atoms, sample, order=list(q.loop_order()), nthreads=threads)
@@ -1101,7 +1104,7 @@ def reference_tensor(a, world):
 
     dev = _maybe_cuda() or "cpu"
     atoms, host_rels, desc, _ = tensor_relations(a, 0, None if dev == "cpu" else dev)
-    sample, sdesc = tensor_sample(a, atoms, host_rels, dev)
+    sample, sdesc, _ = tensor_sample(a, atoms, host_rels, dev)
     threads = min(64, os.cpu_count() or 1)
     times, counts = [], []
     for i in range(a.warmup + a.steps):
