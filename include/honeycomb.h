@@ -94,9 +94,22 @@ typedef struct hc_result hc_result;
  * The rows must be distinct; with HC_BUILD_CHECK_DUPLICATES in `flags` a
  * repeated row returns HC_ERR_DUPLICATE instead of an index.  With
  * HC_BUILD_TIME_KERNELS the radix passes and the run-boundary scan are timed
- * with CUDA events on `stream` (see hc_index_view). */
+ * with CUDA events on `stream` (see hc_index_view).
+ * A bounded device-side wait (a look-back of the sort or of the scan) that
+ * runs past hc_wait_limit_ns() returns HC_ERR_TIMEOUT and no index; the
+ * kernels after it do nothing, so no device memory outside the call's own
+ * buffers is touched and the context stays usable.  Two flags exist for
+ * testing that path only: with HC_BUILD_TEST_STALL_SORT the first tile of
+ * the first radix pass never publishes its look-back status (a relation
+ * whose values need no radix pass is not affected), with
+ * HC_BUILD_TEST_STALL_SCAN the first tile of the run-boundary scan never
+ * does; the tiles after it wait for it until the limit and the call returns
+ * HC_ERR_TIMEOUT (the relation must span more than one tile: 6,144 rows
+ * for the sort, 4,096 for the scan). */
 #define HC_BUILD_CHECK_DUPLICATES 1u
 #define HC_BUILD_TIME_KERNELS 2u
+#define HC_BUILD_TEST_STALL_SORT 0x100u
+#define HC_BUILD_TEST_STALL_SCAN 0x200u
 hc_status hc_build_index(const uint32_t* d_pairs, uint64_t n, uint32_t attr_order, uint32_t flags,
                          void* stream, hc_index** out);
 hc_status hc_index_free(hc_index* index);
@@ -128,17 +141,25 @@ typedef struct {
     float ms_radix_passes;    /* device time of the radix-pass launches, summed  */
     uint32_t n_radix_passes;  /* radix-pass launches                             */
     float ms_boundary;        /* device time of the run-boundary scan            */
+    uint64_t max_run;         /* rows of the most frequent first-attribute value */
+    uint32_t v1pos_n;         /* entries of the V1 position map (0: none; a map  */
+                              /* is built when the first attribute's values are  */
+                              /* dense: max_first + 1 <= 4 n + 2^20, max_first < */
+                              /* 0xFFFFFFFF), else V1 is searched                 */
 } hc_index_view;
 hc_status hc_index_get_view(const hc_index* index, hc_index_view* out);
 
 /* A statistics-only index: no device arrays, only the sizes the optimizer
  * reads (n rows, l1 distinct first-attribute values, attribute order and the
- * largest first / second values).  Host only, needs no GPU.  Accepted by
- * hc_choose_shares; hc_run_join and hc_partition_index reject it with
+ * largest first / second values) and, when known, max_run, the rows of the
+ * most frequent first-attribute value (0 = unknown; else 1 <= max_run <=
+ * n - l1 + 1).  Host only, needs no GPU.  Accepted by hc_choose_shares and
+ * hc_join_footprint (which applies hc_run_join's list-length limit when
+ * max_run is known); hc_run_join and hc_partition_index reject it with
  * HC_ERR_ARG.  Free with hc_index_free.  Requires l1 <= n and l1 >= 1 when
  * n >= 1. */
 hc_status hc_index_from_stats(uint64_t n, uint64_t l1, uint32_t attr_order, uint32_t max_first,
-                              uint32_t max_second, hc_index** out);
+                              uint32_t max_second, uint64_t max_run, hc_index** out);
 
 /* --------------------------------------------------- coco_levels_noalloc
  * The CoCo levels V1, O1, V2 (as hc_build_index writes them) of rows that
@@ -276,9 +297,12 @@ typedef struct {
 
 /* Generic Join of q over the indexes, one logical worker per HyperCube cell
  * (Sec. 5, Listing C of Fig. "algo-comp").  Limit: the search counts a
- * batch's candidates (up to 32 bindings' shortest lists) in 32 bits, so no
- * key of a relation may have 2^27 or more rows (R-MAT 23, 258 M rows, has
- * at most about 10^6 per key).
+ * batch's candidates (up to 32 bindings' shortest lists) in 32 bits, so at
+ * every loop after the first the shortest list must stay below 2^27 values;
+ * the call returns HC_ERR_CAPACITY before any device work when the indexes
+ * allow a longer one (a sub-list's bound is its index's max_run, a
+ * top-level list's its l1).  R-MAT 23, 258 M rows, has at most about 10^6
+ * rows per key.
  *   idx[j]   index bound to atom j; its attr_order must sort the atom's
  *            variables in loop order (Sec. 4: T(Z,X) under order X,Y,Z is
  *            sorted by X first), else HC_ERR_ARG.
@@ -345,6 +369,13 @@ hc_status hc_batch_free(hc_batch* b);
 /* -------------------------------------------------------------- utilities */
 const char* hc_status_str(hc_status s);
 const char* hc_last_error(void);
+/* Limit, in nanoseconds, of every bounded device-side wait (the decoupled
+ * look-backs of the sort, the scans and the level builds) in kernels
+ * launched after the call; process-wide, default 2,000,000,000 (2 s).  A wait
+ * that runs past it makes its call return HC_ERR_TIMEOUT.  0 gives up at the
+ * first status word that is not ready, which can fail a healthy build. */
+hc_status hc_set_wait_limit_ns(uint64_t ns);
+uint64_t hc_wait_limit_ns(void);
 /* Library version and the compute capability it was built for (e.g. 103). */
 uint32_t hc_version(void);
 /* Kernels this library has launched in this process so far (host counter). */

@@ -121,16 +121,20 @@ class Index:
         _lib.check(_lib.load().hc_index_get_view(self._h, ctypes.byref(v)), "hc_index_get_view")
         self.n, self.l1, self.attr_order = v.n, v.l1, v.attr_order
         self.max_first, self.max_second = v.max_first, v.max_second
+        self.max_run = v.max_run  # rows of the most frequent first-attribute value
+        self.v1pos_n = v.v1pos_n  # entries of the V1 position map (0: V1 is searched)
         # device times when built with time_kernels=True (else 0)
         self.ms_radix_passes, self.n_radix_passes, self.ms_boundary = v.ms_radix_passes, v.n_radix_passes, v.ms_boundary
         self._view = v
 
     @classmethod
-    def from_stats(cls, n: int, l1: int, attr_order: int = 0, max_first: int = 0, max_second: int = 0) -> "Index":
-        """Statistics-only index for planning (no GPU, no data)."""
+    def from_stats(cls, n: int, l1: int, attr_order: int = 0, max_first: int = 0, max_second: int = 0,
+                   max_run: int = 0) -> "Index":
+        """Statistics-only index for planning (no GPU, no data); ``max_run``,
+        the rows of the most frequent first value, is optional (0: unknown)."""
         out = ctypes.c_void_p()
-        _lib.check(_lib.load().hc_index_from_stats(n, l1, attr_order, max_first, max_second, ctypes.byref(out)),
-                   "hc_index_from_stats")
+        _lib.check(_lib.load().hc_index_from_stats(n, l1, attr_order, max_first, max_second, max_run,
+                                                   ctypes.byref(out)), "hc_index_from_stats")
         return cls(out.value)
 
     @property
@@ -172,18 +176,30 @@ def _check_pairs(pairs: torch.Tensor) -> torch.Tensor:
 
 
 def build_index(pairs: torch.Tensor, attr_order: int = 0, check_duplicates: bool = False, stream=None,
-                time_kernels: bool = False) -> Index:
+                time_kernels: bool = False, test_stall: str = "") -> Index:
     """CoCo index of a relation given as an (n, 2) uint32 CUDA tensor.  With
     time_kernels the radix passes and the run-boundary scan are timed with
-    CUDA events (Index.ms_radix_passes, n_radix_passes, ms_boundary)."""
+    CUDA events (Index.ms_radix_passes, n_radix_passes, ms_boundary).
+    ``test_stall`` ("sort" or "scan") is for testing the bounded-wait error
+    path only: the first tile of that step never publishes its status."""
     p = _check_pairs(pairs)
     out = ctypes.c_void_p()
+    stall = {"": 0, "sort": _lib.HC_BUILD_TEST_STALL_SORT, "scan": _lib.HC_BUILD_TEST_STALL_SCAN}[test_stall]
     flags = (_lib.HC_BUILD_CHECK_DUPLICATES if check_duplicates else 0) | (
-        _lib.HC_BUILD_TIME_KERNELS if time_kernels else 0)
+        _lib.HC_BUILD_TIME_KERNELS if time_kernels else 0) | stall
     st = _lib.load().hc_build_index(ctypes.c_void_p(p.data_ptr() if p.numel() else 0), p.shape[0], attr_order,
                                     flags, ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(out))
     _lib.check(st, "hc_build_index")
     return Index(out.value)
+
+
+def set_wait_limit_ns(ns: int) -> int:
+    """Set the limit of every bounded device-side wait of later launches
+    (process-wide); returns the previous limit."""
+    lib = _lib.load()
+    prev = int(lib.hc_wait_limit_ns())
+    _lib.check(lib.hc_set_wait_limit_ns(int(ns)), "hc_set_wait_limit_ns")
+    return prev
 
 
 def build_unary_index(values: torch.Tensor, max_value: int | None = None, stream=None) -> Index:

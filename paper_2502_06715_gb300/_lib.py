@@ -24,6 +24,8 @@ HC_FLAG_TIME_KERNELS = 4
 HC_FLAG_NO_LIFT = 8
 HC_BUILD_CHECK_DUPLICATES = 1
 HC_BUILD_TIME_KERNELS = 2
+HC_BUILD_TEST_STALL_SORT = 0x100
+HC_BUILD_TEST_STALL_SCAN = 0x200
 
 STATUS = {0: "HC_OK", 1: "HC_ERR_ARG", 2: "HC_ERR_OOM", 3: "HC_ERR_CUDA", 4: "HC_ERR_TIMEOUT",
           5: "HC_ERR_CAPACITY", 6: "HC_ERR_DUPLICATE", 7: "HC_ERR_BUSY"}
@@ -43,7 +45,8 @@ class hc_index_view(ctypes.Structure):
                 ("max_first", ctypes.c_uint32), ("max_second", ctypes.c_uint32),
                 ("d_v1", ctypes.c_void_p), ("d_o1", ctypes.c_void_p), ("d_v2", ctypes.c_void_p),
                 ("d_keys", ctypes.c_void_p), ("ms_radix_passes", ctypes.c_float),
-                ("n_radix_passes", ctypes.c_uint32), ("ms_boundary", ctypes.c_float)]
+                ("n_radix_passes", ctypes.c_uint32), ("ms_boundary", ctypes.c_float), ("max_run", ctypes.c_uint64),
+                ("v1pos_n", ctypes.c_uint32)]
 
 
 class hc_partitioned_view(ctypes.Structure):
@@ -93,7 +96,9 @@ SIGNATURES = {
     "hc_build_index": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                       ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "hc_index_from_stats": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
-                                           ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)]),
+                                           ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)]),
+    "hc_set_wait_limit_ns": (ctypes.c_int, [ctypes.c_uint64]),
+    "hc_wait_limit_ns": (ctypes.c_uint64, []),
     "hc_build_unary_index": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_void_p)]),
     "hc_index_free": (ctypes.c_int, [ctypes.c_void_p]),

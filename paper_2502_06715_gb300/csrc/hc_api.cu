@@ -14,8 +14,10 @@ namespace hc {
 
 static thread_local std::string g_last_error;
 static std::atomic<uint64_t> g_launches{0};
+static std::atomic<uint64_t> g_wait_ns{2000000000ull};  // bounded device waits: 2 s by default
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+uint64_t wait_limit_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -328,17 +330,20 @@ hc_status hc_build_unary_index(const uint32_t* d_values, uint64_t n, uint32_t ma
 }
 
 hc_status hc_index_from_stats(uint64_t n, uint64_t l1, uint32_t attr_order, uint32_t max_first, uint32_t max_second,
-                              hc_index** out) {
+                              uint64_t max_run, hc_index** out) {
     if (!out) return hc::fail(HC_ERR_ARG, "index_from_stats: out is NULL");
     *out = nullptr;
     if (attr_order > 1 || l1 > n || (n > 0 && l1 == 0))
         return hc::fail(HC_ERR_ARG, "index_from_stats: need attr_order 0/1 and 1 <= l1 <= n");
+    if (max_run > 0 && (n == 0 || max_run > n - l1 + 1))
+        return hc::fail(HC_ERR_ARG, "index_from_stats: max_run must be 0 (unknown) or in [1, n - l1 + 1]");
     hc_index* ix = new hc_index();
     ix->n = n;
     ix->l1 = l1;
     ix->attr_order = attr_order;
     ix->max_first = max_first;
     ix->max_second = max_second;
+    ix->max_run = max_run;  // 0: unknown (not checked against the search kernels' list limit)
     ix->stats_only = true;
     *out = ix;
     return HC_OK;
@@ -364,6 +369,8 @@ hc_status hc_index_get_view(const hc_index* ix, hc_index_view* out) {
     out->ms_radix_passes = ix->ms_radix;
     out->n_radix_passes = ix->n_radix;
     out->ms_boundary = ix->ms_boundary;
+    out->max_run = ix->max_run;
+    out->v1pos_n = ix->v1pos_n;
     return HC_OK;
 }
 
@@ -456,6 +463,12 @@ const char* hc_status_str(hc_status s) {
 const char* hc_last_error(void) { return hc::g_last_error.c_str(); }
 
 uint32_t hc_version(void) { return 100; }
+
+hc_status hc_set_wait_limit_ns(uint64_t ns) {
+    hc::g_wait_ns.store(ns, std::memory_order_relaxed);
+    return HC_OK;
+}
+uint64_t hc_wait_limit_ns(void) { return hc::g_wait_ns.load(std::memory_order_relaxed); }
 uint64_t hc_kernel_launches(void) { return hc::g_launches.load(std::memory_order_relaxed); }
 uint32_t hc_target_sm(void) { return 103; }
 

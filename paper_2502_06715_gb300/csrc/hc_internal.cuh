@@ -43,6 +43,15 @@ void dev_free(void* p, cudaStream_t s);
 // Device-side error word: bit 0 = a bounded wait gave up.
 enum : uint32_t { DEV_ERR_TIMEOUT = 1u };
 
+// Limit of each bounded device-side wait, in nanoseconds, for kernels
+// launched from now on (hc_set_wait_limit_ns; default 2 s).
+uint64_t wait_limit_ns();
+
+// Longest list the search kernels may iterate: they sum up to 32 bindings'
+// list lengths in 32 bits, so every list they iterate must be shorter than
+// 2^27 (checked by run_join against the indexes' longest runs).
+constexpr uint64_t MAX_LIST_LEN = 1ull << 27;
+
 // Library-wide per-device scratch holding the error word and work counters.
 struct DevScratch {
     uint32_t* err;  // [1]
@@ -66,6 +75,9 @@ struct hc_index {
     // when the first attribute's values are dense enough (v1pos_n = 0: none)
     uint32_t* d_v1pos = nullptr;
     uint32_t v1pos_n = 0;
+    // longest run of V2 (rows of one first-attribute value): exact for a
+    // built index, the caller's figure (0 = unknown) for a statistics-only one
+    uint64_t max_run = 0;
 };
 
 struct hc_partitioned {
@@ -126,12 +138,15 @@ namespace hc {
 // V1 position maps (value -> position in V1, a dense direct-address table in
 // place of a binary search of V1).  Built only when the values span at most
 // V1POS_ROWS_FACTOR entries per row (plus a fixed allowance), so a map costs
-// at most about 4 * V1POS_ROWS_FACTOR bytes per row.
+// at most about 4 * V1POS_ROWS_FACTOR bytes per row.  The map's length
+// (max_value + 1) is stored in 32 bits, so a relation holding the value
+// 0xFFFFFFFF never gets one (its length 2^32 would not fit).
 constexpr uint32_t V1POS_NONE = 0xFFFFFFFFu;
 constexpr uint64_t V1POS_ROWS_FACTOR = 4;
 constexpr uint64_t V1POS_ALLOWANCE = 1ull << 20;
 inline bool v1pos_eligible(uint64_t rows, uint32_t max_value) {
-    return rows > 0 && (uint64_t)max_value + 1 <= V1POS_ROWS_FACTOR * rows + V1POS_ALLOWANCE;
+    return rows > 0 && max_value < 0xFFFFFFFFu &&
+           (uint64_t)max_value + 1 <= V1POS_ROWS_FACTOR * rows + V1POS_ALLOWANCE;
 }
 
 // --------------------------------------------------------------- device code
@@ -180,7 +195,14 @@ __device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
 constexpr uint64_t LB_AGG = 1ull << 62;
 constexpr uint64_t LB_INC = 2ull << 62;
 constexpr uint64_t LB_VAL = (1ull << 62) - 1;
-constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // a single wait gives up after 2 s
+
+// The error word of a launch sequence, read past the caches: set by a wait
+// that gave up in this kernel or an earlier one on the same stream.  Kernels
+// that consume a look-back's output check it first and do nothing once it is
+// set, so offsets from an abandoned look-back are never used.
+__device__ __forceinline__ bool dev_err_set(const uint32_t* err) {
+    return *(const volatile uint32_t*)err != 0u;
+}
 
 __device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
 #pragma unroll
@@ -193,10 +215,11 @@ __device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
 // of tile top - q, so each round covers 32 predecessors; the round sums the
 // values up to the nearest inclusive word and stops there.  Tile ids are
 // taken in launch order, so every predecessor has started and each wait
-// ends unless the device stalls; a wait longer than WAIT_LIMIT_NS sets
-// DEV_ERR_TIMEOUT in *err and returns what it has.  All 32 lanes call it and
-// all get the result.
-__device__ __forceinline__ uint64_t warp_lookback(const uint64_t* status, uint32_t tile, uint32_t* err) {
+// ends unless the device stalls; a wait longer than wait_ns nanoseconds
+// sets DEV_ERR_TIMEOUT in *err and returns what it has (a prefix no larger
+// than the true one).  All 32 lanes call it and all get the result.
+__device__ __forceinline__ uint64_t warp_lookback(const uint64_t* status, uint32_t tile, uint32_t* err,
+                                                  uint64_t wait_ns) {
     const uint32_t lane = threadIdx.x & 31u;
     uint64_t excl = 0;
     int64_t top = (int64_t)tile - 1;
@@ -207,7 +230,7 @@ __device__ __forceinline__ uint64_t warp_lookback(const uint64_t* status, uint32
         for (uint32_t spins = 0;; ++spins) {
             const bool ready = (x & ~LB_VAL) != 0;
             if (__all_sync(0xffffffffu, ready)) break;
-            if (__any_sync(0xffffffffu, globaltimer_ns() - t0 > WAIT_LIMIT_NS)) {
+            if (__any_sync(0xffffffffu, globaltimer_ns() - t0 > wait_ns)) {
                 if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
                 return excl;
             }

@@ -128,14 +128,17 @@ __global__ void l0_count_kernel(const DPlan* __restrict__ gP, uint32_t* __restri
 // candidate); WRITE=true writes each matching candidate as an entry at its
 // compacted slot, with the ranges of the atoms it opens and its number of
 // loop-2 candidates.
+// Nothing runs once the join's error word is set (a scan before it gave up
+// a wait, so its offsets are not valid).
 template <bool WRITE>
 __global__ void l0_probe_kernel(const DPlan* __restrict__ gP, const uint64_t* __restrict__ candoff, uint64_t tmax,
                                 uint32_t* __restrict__ flags, const uint64_t* __restrict__ flagoff,
                                 uint32_t* __restrict__ e_cell, uint32_t* __restrict__ e_x,
                                 uint32_t* __restrict__ e_rng, uint64_t* __restrict__ e_units,
-                                uint32_t* __restrict__ e_split) {
+                                uint32_t* __restrict__ e_split, const JoinCtl* __restrict__ ctl) {
     __shared__ DPlan P;
     load_plan(P, gP);
+    if (dev_err_set(&ctl->err)) return;
     const uint64_t T = min(tmax, candoff[P.ncells]);
     const int n0 = P.nsrc[0];
     const uint64_t tend = WRITE ? T : tmax;
@@ -982,6 +985,7 @@ __global__ void __launch_bounds__(128, (NL <= 3 ? 16 : 12)) gj_kernel(const DPla
     __shared__ DPlan P;
     __shared__ uint32_t s_elo[4][NL][S], s_ehi[4][NL][S];  // per warp (blocks of <= 128 threads)
     load_plan(P, gP);
+    if (dev_err_set(&ctl->err)) return;  // a scan of the loop-1 pass gave up a wait
     const uint32_t lane = lane_id();
     const uint32_t E_n = ctl->n_entries;
     const uint64_t U = uoff[E_n];
@@ -1055,6 +1059,7 @@ __global__ void __launch_bounds__(128, ((NLA <= 3 && NLB <= 3) ? 16 : 12))
     __shared__ DPlan wplan[4];
     __shared__ uint32_t s_e[4][2 * NLM * SM];
     const uint32_t w = threadIdx.x >> 5, lane = lane_id();
+    if (dev_err_set(&qs[0].ctl->err)) return;  // the item-offset scan gave up a wait
     const uint64_t total_items = item_off[n];
     uint32_t cur = 0xFFFFFFFFu;
     Acc A;
@@ -1085,6 +1090,7 @@ __global__ void __launch_bounds__(128, ((NLA <= 3 && NLB <= 3) ? 16 : 12))
         }
         const uint32_t q = lo;
         const BQuery& b = qs[q];
+        if (dev_err_set(&b.ctl->err)) continue;  // a scan of this query's loop-1 pass gave up a wait
         if (q != cur) {
             __syncwarp();
             const uint32_t* src = (const uint32_t*)b.plan;
@@ -1435,6 +1441,21 @@ hc_status plan_query(const hc_query* q, const hc_index* const* idx, const hc_joi
             P.src_slot[L][qq] = a.slot;
         }
     }
+    // the search kernels sum up to 32 bindings' candidate counts in 32 bits:
+    // at every loop after the first, the shortest of its lists must stay
+    // below 2^27 (a top-level list is at most the relation's l1 long, a
+    // sub-list at most its longest run)
+    for (int L = 1; L < nv; ++L) {
+        uint64_t bound = UINT64_MAX;
+        for (int qq = 0; qq < P.nsrc[L]; ++qq) {
+            const hc_index* ix = idx[P.src_atom[L][qq]];
+            bound = std::min<uint64_t>(bound, P.src_top[L][qq] ? ix->l1 : ix->max_run);
+        }
+        if (P.nsrc[L] > 0 && bound >= MAX_LIST_LEN)
+            return bail(fail(HC_ERR_CAPACITY, "run_join: a loop's shortest list can reach 2^27 values (a key with "
+                                              "2^27 or more rows), beyond the search kernels' 32-bit candidate "
+                                              "counts"));
+    }
     P.merge_min = prm->merge_min ? prm->merge_min : 32;
     P.merge_ratio = prm->merge_ratio ? prm->merge_ratio : 4;
     P.slice_grain = prm->slice_grain == 0xFFFFFFFFu ? 0 : (prm->slice_grain ? prm->slice_grain : 256);
@@ -1524,11 +1545,11 @@ hc_status enqueue_level1(const QueryPlan& qp, const Level1& L, JoinCtl* ctl, cud
     HC_TRY(exclusive_scan_u32_to_u64(L.cand, L.candoff, ncells, nullptr, &ctl->err, s));
     const unsigned pgrid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((cb + tpb - 1) / tpb, (uint64_t)num_sms() * 16));
     l0_probe_kernel<false><<<pgrid, tpb, 0, s>>>(L.d_plan, L.candoff, cb, L.flags, nullptr, nullptr, nullptr, nullptr,
-                                                 nullptr, nullptr);
+                                                 nullptr, nullptr, ctl);
     if (cudaError_t le = launch_check()) return cuda_fail(le, "l0_probe_kernel");
     HC_TRY(exclusive_scan_u32_to_u64(L.flags, L.flagoff, cb, nullptr, &ctl->err, s));
     l0_probe_kernel<true><<<pgrid, tpb, 0, s>>>(L.d_plan, L.candoff, cb, L.flags, L.flagoff, L.e_cell, L.e_x, L.e_rng,
-                                                L.e_units, L.e_split);
+                                                L.e_units, L.e_split, ctl);
     if (cudaError_t le = launch_check()) return cuda_fail(le, "l0_probe_kernel");
     entries_total_kernel<<<1, 1, 0, s>>>(L.flagoff, L.candoff, (uint32_t)ncells, cb, ctl);
     if (cudaError_t le = launch_check()) return cuda_fail(le, "entries_total_kernel");

@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(KL_THREADS) klevels_kernel(KSorted src, uint64
                                                              uint32_t* __restrict__ v1, uint32_t* __restrict__ v2,
                                                              uint32_t* __restrict__ o0, uint32_t* __restrict__ o1,
                                                              uint64_t* __restrict__ status, uint64_t ntiles,
-                                                             KBuildCtl* __restrict__ ctl) {
+                                                             KBuildCtl* __restrict__ ctl, uint64_t wait_ns) {
     constexpr int NL = K - 1;              // levels with offsets
     constexpr int NLA = NL > 0 ? NL : 1;  // array extent
     __shared__ uint32_t wsum[NLA][KL_WARPS];
@@ -203,9 +203,11 @@ __global__ void __launch_bounds__(KL_THREADS) klevels_kernel(KSorted src, uint64
     uint32_t* const vv[3] = {v0, v1, v2};
     uint32_t* const oo[2] = {o0, o1};
     const uint32_t tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(&ctl->tile_counter, 1u);
+    // nothing once a sort pass before this scan gave up a wait
+    if (tid == 0) s_tile = dev_err_set(&ctl->err) ? 0xFFFFFFFFu : atomicAdd(&ctl->tile_counter, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
+    if (tile == 0xFFFFFFFFu) return;
     const uint64_t base = (uint64_t)tile * KL_TILE + (uint64_t)w * (KL_ITEMS * 32);
     const bool full = base + KL_ITEMS * 32 <= n;
 
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(KL_THREADS) klevels_kernel(KSorted src, uint64
         if (lane == 0) st_relaxed(st, (tile == 0 ? LB_INC : LB_AGG) | tot);
         uint64_t excl = 0;
         if (tile != 0) {
-            excl = warp_lookback(status + (uint64_t)d * ntiles, tile, &ctl->err);
+            excl = warp_lookback(status + (uint64_t)d * ntiles, tile, &ctl->err, wait_ns);
             if (lane == 0) st_relaxed(st, LB_INC | (excl + tot));
         }
         if (lane == 0) s_excl[d] = excl;
@@ -318,16 +320,19 @@ __global__ void __launch_bounds__(KL_THREADS) klevels_kernel(KSorted src, uint64
 
 // Level-0 position map: pos[V_0[i]] = i (values distinct, so each entry is
 // written at most once).
-__global__ void kpos_kernel(const uint32_t* __restrict__ v0, uint64_t l0, uint32_t* __restrict__ pos) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < l0; i += (uint64_t)gridDim.x * blockDim.x)
-        pos[v0[i]] = (uint32_t)i;
+__global__ void kpos_kernel(const uint32_t* __restrict__ v0, uint64_t l0, uint32_t* __restrict__ pos, uint32_t pos_n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < l0; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = v0[i];
+        if (v < pos_n) pos[v] = (uint32_t)i;
+    }
 }
 
 hc_status launch_levels(int k, bool packed, const KSorted& src, uint64_t n, uint32_t* const* v, uint32_t* const* o,
                         uint64_t* status, uint64_t ntiles, KBuildCtl* ctl, cudaStream_t s) {
     const unsigned grid = (unsigned)ntiles;
 #define HC_KLEV(K, P) \
-    klevels_kernel<K, P><<<grid, KL_THREADS, 0, s>>>(src, n, v[0], v[1], v[2], o[0], o[1], status, ntiles, ctl)
+    klevels_kernel<K, P><<<grid, KL_THREADS, 0, s>>>(src, n, v[0], v[1], v[2], o[0], o[1], status, ntiles, ctl, \
+                                                     wait_limit_ns())
     if (k == 1) {
         if (packed) HC_KLEV(1, true); else HC_KLEV(1, false);
     } else if (k == 2) {
@@ -528,7 +533,7 @@ hc_status build_kindex_impl(const uint32_t* d_rows, uint64_t n, uint32_t k, cons
         x->v0pos_n = (uint32_t)dn;
         if (cudaMemsetAsync(x->d_v0pos, 0xFF, dn * 4, s) != cudaSuccess)
             return bail(cuda_fail(cudaGetLastError(), "memset"));
-        kpos_kernel<<<grid_of(x->len[0], 256, 8), 256, 0, s>>>(x->d_v[0], x->len[0], x->d_v0pos);
+        kpos_kernel<<<grid_of(x->len[0], 256, 8), 256, 0, s>>>(x->d_v[0], x->len[0], x->d_v0pos, x->v0pos_n);
         if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "kpos_kernel"));
     }
     *out = x;
@@ -897,6 +902,7 @@ __global__ void __launch_bounds__(KJ_MAXT) kjoin_kernel(const KPlan* __restrict_
     load_kplan(P, gP);
     const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
     KWarp<NV>& S = WS[w];
+    if (dev_err_set(&ctl->err)) return;  // the unit-offset scan gave up a wait
     const uint32_t ne = ctl->n_entries;
     const uint64_t total_units = unit_off[ne];
     uint64_t grain = grain_in;

@@ -52,7 +52,7 @@ struct Ctl {
     uint32_t dup;
     uint32_t maxv[2];
     uint32_t l1;
-    uint32_t pad;
+    uint32_t maxrun;  // longest run of the level-1 entries (maxrun_kernel)
     uint32_t tile_counter[MAX_PASSES + 2];
 };
 
@@ -144,8 +144,11 @@ __device__ __forceinline__ uint32_t pass_digit(uint64_t key, const DigitSpec& d)
 
 // Exclusive prefix of one digit's count over the tiles before `tile`:
 // status[t * RADIX] holds tile t's word for this digit.  Each round reads
-// PASS_LOOKBACK words at once and stops at the nearest inclusive one.
-__device__ __forceinline__ uint64_t digit_lookback(const uint64_t* status, uint32_t tile, uint32_t* err) {
+// PASS_LOOKBACK words at once and stops at the nearest inclusive one.  A
+// wait longer than wait_ns sets DEV_ERR_TIMEOUT in *err and returns the
+// prefix summed so far (no larger than the true one).
+__device__ __forceinline__ uint64_t digit_lookback(const uint64_t* status, uint32_t tile, uint32_t* err,
+                                                   uint64_t wait_ns) {
     uint64_t excl = 0;
     int64_t t = (int64_t)tile - 1;
     while (t >= 0) {
@@ -165,7 +168,7 @@ __device__ __forceinline__ uint64_t digit_lookback(const uint64_t* status, uint3
                 do {
                     if (++spins > 16) __nanosleep(32);
                     x = ld_relaxed(p);
-                    if ((x & ~LB_VAL) == 0 && globaltimer_ns() - t0 > WAIT_LIMIT_NS) {
+                    if ((x & ~LB_VAL) == 0 && globaltimer_ns() - t0 > wait_ns) {
                         atomicOr(err, DEV_ERR_TIMEOUT);
                         return excl;
                     }
@@ -180,11 +183,15 @@ __device__ __forceinline__ uint64_t digit_lookback(const uint64_t* status, uint3
     return excl;
 }
 
+// A pass does nothing once *err is set (by an earlier pass that gave up a
+// wait): its input would not hold the rows its digit counts describe.  With
+// `withhold` (testing only) tile 0 never publishes its status words, so every
+// wait on them runs out.
 template <int SRC, int DIG>
 __global__ void __launch_bounds__(PASS_THREADS, 2) onesweep_kernel(
     const void* __restrict__ in, uint64_t* __restrict__ out, uint32_t n, uint32_t ao, DigitSpec ds,
     const uint32_t* __restrict__ gbase, uint64_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
-    uint32_t* __restrict__ err) {
+    uint32_t* __restrict__ err, uint64_t wait_ns, uint32_t withhold) {
     constexpr bool KEEP_DIGITS = DIG == DIGIT_PARTITION;  // hashing twice costs more than a byte of smem
     __shared__ uint64_t skeys[PASS_TILE];
     __shared__ uint8_t sdig[KEEP_DIGITS ? PASS_TILE : 1];
@@ -195,13 +202,14 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) onesweep_kernel(
     __shared__ uint32_t s_tile;
 
     const uint32_t tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+    if (tid == 0) s_tile = dev_err_set(err) ? 0xFFFFFFFFu : atomicAdd(tile_counter, 1u);
     for (int i = tid; i < PASS_WARPS * RADIX; i += PASS_THREADS) {
         (&whist[0][0])[i] = 0;
         (&peers_word[0][0])[i] = 0;
     }
     __syncthreads();
     const uint32_t tile = s_tile;
+    if (tile == 0xFFFFFFFFu) return;  // no tile id taken: no later tile waits on this block
     const uint32_t base = tile * (uint32_t)PASS_TILE;
     const uint32_t wb = base + w * (PASS_ITEMS * 32) + lane;  // row of item 0 of this lane
     const bool full = n - base >= (uint32_t)PASS_TILE;
@@ -254,7 +262,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) onesweep_kernel(
         run += c;
     }
     uint64_t* st = status + (uint64_t)tile * RADIX + d;
-    st_relaxed(st, (tile == 0 ? LB_INC : LB_AGG) | run);
+    if (!(withhold && tile == 0)) st_relaxed(st, (tile == 0 ? LB_INC : LB_AGG) | run);
     const uint32_t inc = warp_incl_scan(run);
     if (lane == 31) wsum[w] = inc;
     __syncthreads();
@@ -277,7 +285,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) onesweep_kernel(
     }
     uint64_t excl = 0;
     if (tile != 0) {
-        excl = digit_lookback(status + d, tile, err);
+        excl = digit_lookback(status + d, tile, err, wait_ns);
         st_relaxed(st, LB_INC | (excl + run));
     }
     goff[d] = gbase[d] + (uint32_t)excl - lstart;  // mod 2^32; goff + row is below n
@@ -319,18 +327,23 @@ __global__ void pack_kernel(const uint2* __restrict__ pairs, uint64_t* __restric
 // adjacent keys mark a duplicate row.  Rows are warp-striped: item j of lane
 // q of warp w is row tile * SORT_TILE + w * 32 * SORT_ITEMS + 32 j + q, so
 // row i-1 of a lane-0 row is lane 31's row of the previous item.
+// The scan does nothing once ctl->err is set (a radix pass gave up a wait,
+// so the keys are not sorted); `withhold` (testing only) keeps tile 0 from
+// publishing its status word, so every wait on it runs out.
 template <bool SEGMENTED>
 __global__ void __launch_bounds__(SORT_THREADS, 3) boundary_kernel(
     const uint64_t* __restrict__ keys, uint64_t n, uint32_t seed_a, uint32_t pa, uint32_t seed_b,
     uint32_t pb, uint32_t* __restrict__ v1, uint32_t* __restrict__ o1, uint32_t* __restrict__ v2,
-    uint64_t* __restrict__ status, uint32_t* __restrict__ tile_counter, Ctl* __restrict__ ctl) {
+    uint64_t* __restrict__ status, uint32_t* __restrict__ tile_counter, Ctl* __restrict__ ctl, uint64_t wait_ns,
+    uint32_t withhold) {
     __shared__ uint32_t wsum[SORT_WARPS];
     __shared__ uint64_t s_excl;
     __shared__ uint32_t s_tile;
     const uint32_t tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+    if (tid == 0) s_tile = dev_err_set(&ctl->err) ? 0xFFFFFFFFu : atomicAdd(tile_counter, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
+    if (tile == 0xFFFFFFFFu) return;
     const uint64_t base = (uint64_t)tile * SORT_TILE + (uint64_t)w * (SORT_ITEMS * 32);
     const bool full = base + SORT_ITEMS * 32 <= n;
 
@@ -381,10 +394,10 @@ __global__ void __launch_bounds__(SORT_THREADS, 3) boundary_kernel(
     if (w == 0) {
         const uint32_t tot = warp_sum64(lane < (uint32_t)SORT_WARPS ? wsum[lane] : 0u);
         uint64_t* st = status + tile;
-        if (lane == 0) st_relaxed(st, (tile == 0 ? LB_INC : LB_AGG) | tot);
+        if (lane == 0 && !(withhold && tile == 0)) st_relaxed(st, (tile == 0 ? LB_INC : LB_AGG) | tot);
         uint64_t excl = 0;
         if (tile != 0) {
-            excl = warp_lookback(status, tile, &ctl->err);
+            excl = warp_lookback(status, tile, &ctl->err, wait_ns);
             if (lane == 0) st_relaxed(st, LB_INC | (excl + tot));
         }
         if (lane == 0) {
@@ -434,12 +447,30 @@ __global__ void directory_kernel(const uint64_t* __restrict__ keys, uint64_t n, 
 }
 
 // V1 position map: pos[V1[i]] = i for i < l1 (l1 from *d_l1 when given).
-// V1 values are distinct, so every entry is written at most once.
+// V1 values are distinct, so every entry is written at most once.  A value
+// at or past the map's length pos_n (a caller's max_value below the data)
+// is not written; a lookup of it then misses, as the map's bound check in the
+// search tells it to.
 __global__ void v1pos_kernel(const uint32_t* __restrict__ v1, uint64_t l1_max, const uint32_t* __restrict__ d_l1,
-                             uint32_t* __restrict__ pos) {
+                             uint32_t* __restrict__ pos, uint32_t pos_n) {
     const uint64_t l1 = d_l1 ? min(l1_max, (uint64_t)*d_l1) : l1_max;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < l1; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = v1[i];
+        if (v < pos_n) pos[v] = (uint32_t)i;
+    }
+}
+
+// Longest run of a CoCo level: max over i < l1 of O1[i+1] - O1[i], with l1
+// read from ctl (a device-side count); nothing once ctl->err is set.
+__global__ void maxrun_kernel(const uint32_t* __restrict__ o1, uint64_t l1_max, Ctl* __restrict__ ctl) {
+    if (dev_err_set(&ctl->err)) return;
+    const uint64_t l1 = min(l1_max, (uint64_t)ctl->l1);
+    uint32_t m = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < l1; i += (uint64_t)gridDim.x * blockDim.x)
-        pos[v1[i]] = (uint32_t)i;
+        m = max(m, o1[i + 1] - o1[i]);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, d));
+    if (lane_id() == 0 && m) atomicMax(&ctl->maxrun, m);
 }
 
 // ----------------------------------------------------------- device scan
@@ -453,21 +484,24 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 // of a tile owns SCAN_ITEMS consecutive elements; with VEC (both arrays
 // 16-byte aligned) a full tile moves them as 16-byte vectors.  The tile
 // offset comes from a warp-wide decoupled look-back.
+// Does nothing once *err is set: its input then comes from a pass that gave
+// up a wait.
 template <typename T, bool VEC>
 __global__ void __launch_bounds__(SCAN_THREADS) scan_kernel(const T* __restrict__ in, uint64_t* __restrict__ out,
                                                             uint64_t n_max, const uint32_t* __restrict__ d_n,
                                                             uint64_t* __restrict__ status,
                                                             uint32_t* __restrict__ tile_counter,
-                                                            uint32_t* __restrict__ err) {
+                                                            uint32_t* __restrict__ err, uint64_t wait_ns) {
     __shared__ uint64_t wsum[SCAN_THREADS / 32];
     __shared__ uint64_t s_excl;
     __shared__ uint32_t s_tile;
     const uint32_t tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
     const uint64_t n = d_n ? (n_max < (uint64_t)*d_n ? n_max : (uint64_t)*d_n) : n_max;
     const uint64_t ntiles = (n_max + SCAN_TILE - 1) / SCAN_TILE;
-    if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+    if (tid == 0) s_tile = dev_err_set(err) ? 0xFFFFFFFFu : atomicAdd(tile_counter, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
+    if (tile == 0xFFFFFFFFu) return;
     const uint64_t base = (uint64_t)tile * SCAN_TILE + (uint64_t)tid * SCAN_ITEMS;
     const bool full = (uint64_t)(tile + 1) * SCAN_TILE <= n;
     uint64_t v[SCAN_ITEMS];
@@ -502,7 +536,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_kernel(const T* __restrict_
         if (lane == 0) st_relaxed(st, (tile == 0 ? LB_INC : LB_AGG) | tot);
         uint64_t excl = 0;
         if (tile != 0) {
-            excl = warp_lookback(status, tile, err);
+            excl = warp_lookback(status, tile, err, wait_ns);
             if (lane == 0) st_relaxed(st, LB_INC | (excl + tot));
         }
         if (lane == 0) {
@@ -591,7 +625,8 @@ struct LaunchTimer {
 
 // Radix passes over the given digit specs; the sorted keys end in `dst`.
 hc_status radix_passes(const void* src, bool src_pairs, uint32_t ao, uint64_t n, const std::vector<DigitSpec>& specs,
-                       uint64_t* dst, Tmp& tmp, Ctl* d_ctl, cudaStream_t s, LaunchTimer* timer = nullptr) {
+                       uint64_t* dst, Tmp& tmp, Ctl* d_ctl, cudaStream_t s, LaunchTimer* timer = nullptr,
+                       bool withhold_first = false) {
     const int np = (int)specs.size();
     if (np == 0) return fail(HC_ERR_ARG, "internal: no radix passes");
     DigitSpec* d_specs;
@@ -631,7 +666,8 @@ hc_status radix_passes(const void* src, bool src_pairs, uint32_t ao, uint64_t n,
                                           : onesweep_kernel<SRC_KEYS, DIGIT_PARTITION>;
         if (timer) HC_TRY(timer->mark(s));
         kern<<<(unsigned)ntiles, PASS_THREADS, 0, s>>>(in, outb, n32, ao, specs[p], d_hist + p * RADIX, status,
-                                                       &d_ctl->tile_counter[p], &d_ctl->err);
+                                                       &d_ctl->tile_counter[p], &d_ctl->err, wait_limit_ns(),
+                                                       (withhold_first && p == 0) ? 1u : 0u);
         HC_CUDA_TRY(launch_check());
         if (timer) HC_TRY(timer->mark(s));
         in = outb;
@@ -642,7 +678,7 @@ hc_status radix_passes(const void* src, bool src_pairs, uint32_t ao, uint64_t n,
 
 hc_status run_boundary(const uint64_t* keys, uint64_t n, bool segmented, uint32_t seed_a, uint32_t pa,
                        uint32_t seed_b, uint32_t pb, uint32_t* v1, uint32_t* o1, uint32_t* v2, Tmp& tmp,
-                       Ctl* d_ctl, cudaStream_t s) {
+                       Ctl* d_ctl, cudaStream_t s, bool withhold = false) {
     const uint64_t ntiles = std::max<uint64_t>(1, (n + SORT_TILE - 1) / SORT_TILE);
     uint64_t* status;
     HC_TRY(tmp.get(&status, ntiles));
@@ -650,10 +686,12 @@ hc_status run_boundary(const uint64_t* keys, uint64_t n, bool segmented, uint32_
     uint32_t* tc = &d_ctl->tile_counter[MAX_PASSES];
     if (segmented)
         boundary_kernel<true><<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(keys, n, seed_a, pa, seed_b, pb, v1, o1, v2,
-                                                                         status, tc, d_ctl);
+                                                                         status, tc, d_ctl, wait_limit_ns(),
+                                                                         withhold ? 1u : 0u);
     else
         boundary_kernel<false><<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(keys, n, 0, 1, 0, 1, v1, o1, v2, status,
-                                                                          tc, d_ctl);
+                                                                          tc, d_ctl, wait_limit_ns(),
+                                                                          withhold ? 1u : 0u);
     HC_CUDA_TRY(launch_check());
     return HC_OK;
 }
@@ -722,14 +760,17 @@ hc_status build_index_impl(const uint32_t* d_pairs, uint64_t n, uint32_t ao, uin
         if (specs.empty()) {
             pack_kernel<<<grid_for(n, 256, 4), 256, 0, s>>>((const uint2*)d_pairs, idx->d_keys, n, ao);
             if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "pack_kernel"));
-        } else if ((st = radix_passes(d_pairs, true, ao, n, specs, idx->d_keys, tmp, d_ctl, s, &t_radix)) != HC_OK) {
+        } else if ((st = radix_passes(d_pairs, true, ao, n, specs, idx->d_keys, tmp, d_ctl, s, &t_radix,
+                                      (flags & HC_BUILD_TEST_STALL_SORT) != 0)) != HC_OK) {
             return bail(st);
         }
         if ((st = t_boundary.mark(s)) != HC_OK) return bail(st);
-        if ((st = run_boundary(idx->d_keys, n, false, 0, 1, 0, 1, idx->d_v1, idx->d_o1, idx->d_v2, tmp, d_ctl, s)) !=
-            HC_OK)
+        if ((st = run_boundary(idx->d_keys, n, false, 0, 1, 0, 1, idx->d_v1, idx->d_o1, idx->d_v2, tmp, d_ctl, s,
+                               (flags & HC_BUILD_TEST_STALL_SCAN) != 0)) != HC_OK)
             return bail(st);
         if ((st = t_boundary.mark(s)) != HC_OK) return bail(st);
+        maxrun_kernel<<<grid_for(n, 256, 8), 256, 0, s>>>(idx->d_o1, n, d_ctl);
+        if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "maxrun_kernel"));
         if ((st = check_ctl(d_ctl, s, &h)) != HC_OK) return bail(st);
         if (t_radix.on) {
             idx->ms_radix = t_radix.sum();
@@ -739,6 +780,7 @@ hc_status build_index_impl(const uint32_t* d_pairs, uint64_t n, uint32_t ao, uin
         if ((flags & HC_BUILD_CHECK_DUPLICATES) && h.dup)
             return bail(fail(HC_ERR_DUPLICATE, "build_index: the relation holds a repeated row"));
         idx->l1 = h.l1;
+        idx->max_run = h.maxrun;
         if (v1pos_eligible(n, idx->max_first)) {
             const uint64_t dn = (uint64_t)idx->max_first + 1;
             if (dev_alloc(&p, dn * 4, s) != HC_OK) return bail(HC_ERR_OOM);
@@ -746,7 +788,8 @@ hc_status build_index_impl(const uint32_t* d_pairs, uint64_t n, uint32_t ao, uin
             idx->v1pos_n = (uint32_t)dn;
             if (cudaMemsetAsync(idx->d_v1pos, 0xFF, dn * 4, s) != cudaSuccess)
                 return bail(cuda_fail(cudaGetLastError(), "memset"));
-            v1pos_kernel<<<grid_for(idx->l1, 256, 8), 256, 0, s>>>(idx->d_v1, idx->l1, nullptr, idx->d_v1pos);
+            v1pos_kernel<<<grid_for(idx->l1, 256, 8), 256, 0, s>>>(idx->d_v1, idx->l1, nullptr, idx->d_v1pos,
+                                                                    idx->v1pos_n);
             if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "v1pos_kernel"));
         }
     }
@@ -776,6 +819,7 @@ hc_status build_unary_impl(const uint32_t* d_values, uint64_t n, uint32_t max_va
     hc_index* idx = new hc_index();
     idx->n = n;
     idx->l1 = n;  // distinct values: one run per row
+    idx->max_run = n ? 1 : 0;
     idx->attr_order = 0;
     idx->max_first = n ? max_value : 0;
     idx->max_second = 0;
@@ -803,7 +847,7 @@ hc_status build_unary_impl(const uint32_t* d_values, uint64_t n, uint32_t max_va
         idx->v1pos_n = (uint32_t)dn;
         if (cudaMemsetAsync(idx->d_v1pos, 0xFF, dn * 4, s) != cudaSuccess)
             return bail(cuda_fail(cudaGetLastError(), "memset"));
-        v1pos_kernel<<<grid_for(n, 256, 8), 256, 0, s>>>(d_values, n, nullptr, idx->d_v1pos);
+        v1pos_kernel<<<grid_for(n, 256, 8), 256, 0, s>>>(d_values, n, nullptr, idx->d_v1pos, idx->v1pos_n);
         if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "v1pos_kernel"));
     }
     *out = idx;
@@ -899,7 +943,8 @@ hc_status partition_impl(const hc_index* idx, uint32_t seed_a, uint32_t pa, uint
             part->v1pos_n = (uint32_t)dn;
             if (cudaMemsetAsync(part->d_v1pos, 0xFF, dn * 4, s) != cudaSuccess)
                 return bail(cuda_fail(cudaGetLastError(), "memset"));
-            v1pos_kernel<<<grid_for(n, 256, 8), 256, 0, s>>>(part->d_v1, n, &d_ctl->l1, part->d_v1pos);
+            v1pos_kernel<<<grid_for(n, 256, 8), 256, 0, s>>>(part->d_v1, n, &d_ctl->l1, part->d_v1pos,
+                                                              part->v1pos_n);
             if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "v1pos_kernel"));
         }
     }
@@ -934,9 +979,11 @@ hc_status exclusive_scan_impl(const T* d_in, uint64_t* d_out, uint64_t n_max, co
     HC_CUDA_TRY(cudaMemsetAsync(status, 0, ntiles * sizeof(uint64_t), s));
     HC_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t), s));
     if ((((uintptr_t)d_in | (uintptr_t)d_out) & 15u) == 0)
-        scan_kernel<T, true><<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(d_in, d_out, n_max, d_n, status, ctr, d_err);
+        scan_kernel<T, true><<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(d_in, d_out, n_max, d_n, status, ctr, d_err,
+                                                                        wait_limit_ns());
     else
-        scan_kernel<T, false><<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(d_in, d_out, n_max, d_n, status, ctr, d_err);
+        scan_kernel<T, false><<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(d_in, d_out, n_max, d_n, status, ctr, d_err,
+                                                                         wait_limit_ns());
     HC_CUDA_TRY(launch_check());
     return HC_OK;
 }
@@ -1032,7 +1079,7 @@ extern "C" hc_status hc_coco_levels_noalloc(const uint64_t* d_sorted_keys, uint6
     } else {
         boundary_kernel<false><<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(d_sorted_keys, n, 0, 1, 0, 1, d_v1, d_o1,
                                                                           d_v2, scratch, &ctl->tile_counter[MAX_PASSES],
-                                                                          ctl);
+                                                                          ctl, wait_limit_ns(), 0u);
         HC_CUDA_TRY(launch_check());
     }
     // d_info[0] = l1, d_info[1] = flags: bit 0 a look-back wait gave up,

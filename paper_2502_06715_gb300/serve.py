@@ -47,10 +47,17 @@ class Outcome:
         return self.done - self.arrival
 
 
+def _selection_values(values) -> np.ndarray:
+    """A request's selection as the unary builder needs it: uint32 values,
+    strictly ascending (sorted and de-duplicated on the host, because the
+    builder trusts its input order and takes the last value as the largest)."""
+    return np.unique(np.asarray(values, dtype=np.uint32))
+
+
 def _unary_index(values: np.ndarray, device, stream) -> Index:
-    """The request's selection as a unary index (values sorted and distinct),
-    built on `stream` without waiting for the GPU."""
-    v = np.ascontiguousarray(values, dtype=np.uint32)
+    """The request's selection as a unary index, built on `stream` without
+    waiting for the GPU."""
+    v = _selection_values(values)
     d = torch.from_numpy(v.view(np.int32)).to(device)
     return build_unary_index(d, int(v[-1]) if v.shape[0] else 0, stream=stream)
 

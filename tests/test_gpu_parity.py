@@ -54,6 +54,7 @@ def test_build_index_matches_oracle(hc, n, ao):
     ix = hc.build_index(dev(pairs), ao, check_duplicates=True)
     v1, o1, v2 = oracle.coco_build(pairs, ao)
     assert ix.n == pairs.shape[0] and ix.l1 == v1.shape[0]
+    assert ix.max_run == int(np.diff(o1).max())  # the longest run, for run_join's list limit
     assert np.array_equal(u32(ix.v1()), v1)
     assert np.array_equal(u32(ix.o1()).astype(np.uint64), o1)
     assert np.array_equal(u32(ix.v2()), v2)
@@ -357,3 +358,84 @@ def test_build_unary_index_matches_build_index(hc, n):
     us = hc.build_unary_index(torch.from_numpy(sel.view(np.int32)).cuda(), int(sel[-1]))
     ix = hc.build_index(dev(sym), 0)
     assert hc.run_join(q, [ix, ix, ix, us]).count == cnt
+
+
+# ------------------------------------------- sparse 32-bit ids: no position maps
+
+def _sparse_ids(n, seed):
+    """An injective map of n vertex ids onto values spread over all 32 bits,
+    holding 0, 0xFFFFFFFE and 0xFFFFFFFF, in a scrambled order."""
+    rng = np.random.default_rng(seed)
+    ids = np.unique(rng.integers(1, 0xFFFFFFFE, size=2 * n + 8, dtype=np.uint64).astype(np.uint32))
+    ids = ids[rng.permutation(ids.shape[0])][: n - 3]
+    ids = np.concatenate([ids, np.array([0, 0xFFFFFFFE, 0xFFFFFFFF], dtype=np.uint32)])
+    return ids[rng.permutation(n)]
+
+
+@pytest.mark.parametrize("qname", QUERIES)
+def test_sparse_ids_without_position_maps(hc, qname):
+    """Relations whose values spread over 32 bits (0 and 0xFFFFFFFF included)
+    get no V1 position map, so every top-level search is a binary search of
+    V1 (whole, or a partition's range).  Counts, work counters and sorted
+    tuples equal the oracle's on the same relations, at one share and mixed
+    shares, in both output modes."""
+    q = getattr(hc, qname)
+    sym0 = datagen.rmat_graph(9, 8, 41)
+    ids = _sparse_ids(int(sym0.max()) + 1, 5)
+    sym = sorted_rows(ids[sym0])
+    rel = sym if qname == "FOUR_CYCLE" else np.ascontiguousarray(sym[sym[:, 0] < sym[:, 1]])
+    rels = [rel] * len(q.atoms)
+    for ao in (0, 1):
+        assert hc.build_index(dev(rel), ao).v1pos_n == 0
+    cnt, work, _ = oracle.gj_count(q.n_vars, list(q.atoms), rels)
+    ref = oracle.gj_enumerate(q.n_vars, list(q.atoms), rels)
+    assert cnt > 0
+    r = _run(hc, q, rels, stats=True)
+    assert r.count == cnt and r.work == work
+    rng = np.random.default_rng(len(qname))
+    for sh in ([1] * q.n_vars, [2] * q.n_vars, [4] + [1] * (q.n_vars - 1),
+               [int(2 ** rng.integers(0, 3)) for _ in range(q.n_vars)]):
+        assert _run(hc, q, rels, shares=sh).count == cnt, sh
+        for cap in (0, cnt + 1):
+            r = _run(hc, q, rels, shares=sh, mode="materialize", out_capacity=cap)
+            assert np.array_equal(sorted_rows(u32(r.tuples)), sorted_rows(ref)), (sh, cap)
+
+
+def test_sparse_ids_top_level_searches(hc):
+    """Loops that search a whole top level: the 4-cycle's R1[x] n R3.V1 at
+    loop y over a relation of 20,000 sparse values (a multi-step binary search
+    of V1), against the oracle, with and without shares on y."""
+    rng = np.random.default_rng(8)
+    ids = _sparse_ids(20_000, 9)
+    rels = [datagen.directed_set(ids[rng.integers(0, 20_000, size=(60_000, 2))]) for _ in range(4)]
+    q = hc.FOUR_CYCLE
+    cnt, work, _ = oracle.gj_count(q.n_vars, list(q.atoms), rels)
+    r = _run(hc, q, rels, stats=True)
+    assert r.count == cnt and r.work == work
+    for sh in ([1, 4, 1, 1], [1, 2, 2, 1], [2, 1, 1, 4]):
+        assert _run(hc, q, rels, shares=sh).count == cnt, sh
+
+
+# ------------------------------------------------------- hub slicing sweep
+
+@pytest.mark.parametrize("qname", ["FOUR_CLIQUE", "FOUR_CYCLE"])
+def test_slice_grain_sweep_skewed(hc, qname):
+    """Deep queries cut the work of an entry whose loop-3 lists are long into
+    slices of about slice_grain candidates.  On a skewed R-MAT graph every
+    grain (1, 7, the default 256, and no slicing) gives the oracle's count and
+    work counter (one share) and its tuples; shares keep the count."""
+    q = getattr(hc, qname)
+    sym = datagen.rmat_graph(10, 16, 13)
+    rel = sym if qname == "FOUR_CYCLE" else datagen.orient_lt(sym)
+    rels = [rel] * len(q.atoms)
+    cnt, work, _ = oracle.gj_count(q.n_vars, list(q.atoms), rels)
+    ref = oracle.gj_enumerate(q.n_vars, list(q.atoms), rels) if cnt < 3_000_000 else None
+    for sg in (1, 7, 0, 0xFFFFFFFF):
+        r = _run(hc, q, rels, slice_grain=sg, stats=True)
+        assert r.count == cnt and r.work == work, sg
+        assert _run(hc, q, rels, slice_grain=sg).count == cnt, sg
+        for sh in ([4, 1, 1, 1], [2, 2, 1, 2]):
+            assert _run(hc, q, rels, slice_grain=sg, shares=sh).count == cnt, (sg, sh)
+        if ref is not None and sg in (1, 7):
+            r = _run(hc, q, rels, slice_grain=sg, mode="materialize", out_capacity=cnt + 1)
+            assert np.array_equal(sorted_rows(u32(r.tuples)), sorted_rows(ref)), sg

@@ -162,6 +162,31 @@ def test_brute_force_random_relations(name):
         assert np.array_equal(_sorted_rows(got), _sorted_rows(expect)), (name, case)
 
 
+SPARSE_IDS = np.array([0, 1, 0x7FFFFFFF, 0x80000000, 0xDEADBEEF, 0xFFFFFFFD, 0xFFFFFFFE, 0xFFFFFFFF],
+                      dtype=np.uint32)
+
+
+@pytest.mark.parametrize("name", list(QUERIES))
+def test_brute_force_sparse_32bit_ids(name):
+    """Values spread over all 32 bits, including 0, 0xFFFFFFFE and 0xFFFFFFFF:
+    relations over a small domain are relabelled by an injective map onto
+    such ids (monotone, and in a scrambled order); the oracle's result on the
+    relabelled relations is the brute-force result on the small domain,
+    relabelled the same way."""
+    n_vars, atoms = QUERIES[name]
+    rng = np.random.default_rng(31 + len(name))
+    dom = 6 if n_vars == 5 else 8
+    for case in range(12):
+        rels = [np.argwhere(rng.random((dom, dom)) < rng.uniform(0.2, 0.8)).astype(np.uint32) for _ in atoms]
+        expect = brute_force(n_vars, atoms, rels, dom)
+        ids = SPARSE_IDS[:dom] if case % 2 == 0 else rng.permutation(SPARSE_IDS)[:dom]
+        mapped = [ids[r] for r in rels]
+        cnt, _, _ = oracle.gj_count(n_vars, atoms, mapped)
+        assert cnt == expect.shape[0], (name, case)
+        got = oracle.gj_enumerate(n_vars, atoms, mapped)
+        assert np.array_equal(_sorted_rows(got), _sorted_rows(ids[expect])), (name, case)
+
+
 @pytest.mark.parametrize("name", ["triangle", "four_cycle", "four_clique"])
 def test_brute_force_with_unary_atoms(name):
     """Unary atoms F(X_v) restrict a variable to a set of values."""
