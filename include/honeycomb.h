@@ -293,6 +293,16 @@ typedef struct {
                                   /* > 0 runs one pass writing into an output pool of    */
                                   /* about this many tuples (order not fixed), and falls */
                                   /* back to the emitting pass if the pool overflows     */
+    uint32_t dir_min;             /* a list search in a sorted run of at least this     */
+                                  /* many values reads the run's bucket directory first */
+                                  /* (Sec. 5 search; built with every index for runs of */
+                                  /* 16 or more): 0 = 16; 0xFFFFFFFF = plain binary     */
+                                  /* search everywhere                                   */
+    uint32_t pair_min;            /* last loop of two lists, not merged: a binding whose */
+                                  /* shorter list has at least this many values is      */
+                                  /* searched by the whole warp, its values 32 at a time */
+                                  /* (0: default 32; 0xFFFFFFFF: never, all bindings'    */
+                                  /* values are spread over the lanes together)          */
 } hc_join_params;
 
 /* Generic Join of q over the indexes, one logical worker per HyperCube cell

@@ -327,12 +327,16 @@ def run_join(query: Query, indexes: Sequence[Index], shares: Sequence[int] | Non
              stats: bool = False, item_grain: int = 0, block_threads: int = 0, stream=None,
              keep_device: bool = False, time_kernels: bool = False, merge_min: int = 0,
              merge_ratio: int = 0, out_capacity: int = 0, slice_grain: int = 0, lift: bool = True,
-             lift_arena: int = 0) -> Result:
+             lift_arena: int = 0, dir_min: int = 0, pair_min: int = 0) -> Result:
     """Evaluate the query.  Tuples (materialize) come back as an
     (count, n_vars) int32 CUDA tensor in variable-id order (a copy, unless
     ``keep_device`` keeps an alias of library memory tied to the result).
     ``lift`` allows the query rewriting of Sec. 5.1 (off with ``stats``);
-    ``lift_arena`` sets its device scratch, in words per warp (0: default)."""
+    ``lift_arena`` sets its device scratch, in words per warp (0: default).
+    ``dir_min``: list searches in runs at least this long read the run's
+    bucket directory first (0: 16; 0xFFFFFFFF: plain binary search).
+    ``pair_min``: last-loop bindings whose shorter list has at least this many
+    values are searched by the whole warp (0: 32; 0xFFFFFFFF: never)."""
     if len(indexes) != len(query.atoms):
         raise ValueError("one index per atom")
     q = query._c()
@@ -355,6 +359,8 @@ def run_join(query: Query, indexes: Sequence[Index], shares: Sequence[int] | Non
     prm.merge_ratio = merge_ratio & 0xFFFFFFFF
     prm.out_capacity = int(out_capacity)
     prm.slice_grain = slice_grain & 0xFFFFFFFF
+    prm.dir_min = dir_min & 0xFFFFFFFF
+    prm.pair_min = pair_min & 0xFFFFFFFF
     lib = _lib.load()
     out = ctypes.c_void_p()
     _lib.check(lib.hc_run_join(ctypes.byref(q), ptr, ctypes.byref(prm), ctypes.c_void_p(_stream_ptr(stream)),
@@ -384,7 +390,8 @@ def run_join(query: Query, indexes: Sequence[Index], shares: Sequence[int] | Non
 
 
 def _params(query: Query, shares=None, seeds=None, item_grain=0, block_threads=0, merge_min=0, merge_ratio=0,
-            slice_grain=0, mode="count", flags=0, out_capacity=0, lift=True, lift_arena=0) -> _lib.hc_join_params:
+            slice_grain=0, mode="count", flags=0, out_capacity=0, lift=True, lift_arena=0,
+            dir_min=0, pair_min=0) -> _lib.hc_join_params:
     prm = _lib.hc_join_params()
     sh = list(shares) if shares is not None else [1] * query.n_vars
     sd = list(seeds) if seeds is not None else list(DEFAULT_SEEDS)
@@ -400,6 +407,8 @@ def _params(query: Query, shares=None, seeds=None, item_grain=0, block_threads=0
     prm.merge_ratio = merge_ratio & 0xFFFFFFFF
     prm.slice_grain = slice_grain & 0xFFFFFFFF
     prm.out_capacity = int(out_capacity)
+    prm.dir_min = dir_min & 0xFFFFFFFF
+    prm.pair_min = pair_min & 0xFFFFFFFF
     return prm
 
 

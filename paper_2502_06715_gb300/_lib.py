@@ -60,7 +60,8 @@ class hc_join_params(ctypes.Structure):
     _fields_ = [("shares", ctypes.c_uint32 * HC_MAX_VARS), ("seeds", ctypes.c_uint32 * HC_MAX_VARS),
                 ("mode", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("item_grain", ctypes.c_uint32),
                 ("block_threads", ctypes.c_uint32), ("merge_min", ctypes.c_uint32), ("merge_ratio", ctypes.c_uint32),
-                ("slice_grain", ctypes.c_uint32), ("lift_arena", ctypes.c_uint32), ("out_capacity", ctypes.c_uint64)]
+                ("slice_grain", ctypes.c_uint32), ("lift_arena", ctypes.c_uint32), ("out_capacity", ctypes.c_uint64),
+                ("dir_min", ctypes.c_uint32), ("pair_min", ctypes.c_uint32)]
 
 
 class hc_result_view(ctypes.Structure):

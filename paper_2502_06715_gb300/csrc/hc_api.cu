@@ -321,7 +321,7 @@ extern "C" {
 
 hc_status hc_build_index(const uint32_t* d_pairs, uint64_t n, uint32_t attr_order, uint32_t flags, void* stream,
                          hc_index** out) {
-    return hc::build_index_impl(d_pairs, n, attr_order, flags, (cudaStream_t)stream, out);
+    return hc::build_index_impl(d_pairs, n, attr_order, flags & ~hc::BUILD_NO_DIRECTORIES, (cudaStream_t)stream, out);
 }
 
 hc_status hc_build_unary_index(const uint32_t* d_values, uint64_t n, uint32_t max_value, void* stream,

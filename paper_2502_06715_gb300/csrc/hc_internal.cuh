@@ -78,6 +78,11 @@ struct hc_index {
     // longest run of V2 (rows of one first-attribute value): exact for a
     // built index, the caller's figure (0 = unknown) for a statistics-only one
     uint64_t max_run = 0;
+    // bucket directories (search acceleration, see dir_lower_bound): d_g2
+    // parallel to V2 for the runs of O1; d_g1 parallel to V1 for the single
+    // run [0, l1) when there is no position map
+    uint32_t* d_g2 = nullptr;
+    uint32_t* d_g1 = nullptr;
 };
 
 struct hc_partitioned {
@@ -96,6 +101,10 @@ struct hc_partitioned {
     // attribute only, so that each value sits in one partition)
     uint32_t* d_v1pos = nullptr;
     uint32_t v1pos_n = 0;
+    // bucket directories: d_g2 parallel to V2 (runs of O1), d_g1 parallel to
+    // V1 (one run per partition, lvl1_start) when there is no position map
+    uint32_t* d_g2 = nullptr;
+    uint32_t* d_g1 = nullptr;
 };
 
 namespace hc {
@@ -265,12 +274,12 @@ __device__ __forceinline__ uint64_t warp_incl_scan64(uint64_t v) {
     }
     return v;
 }
-// First index in [lo, hi) of sorted a[] whose value is >= x (hi if none).
-// Branch-free halving: each step keeps the upper half when its first
-// element is still below x.
 __device__ __forceinline__ uint32_t load_ro(const uint32_t* p) { return __ldg(p); }
 __device__ __forceinline__ uint32_t load_ro(uint32_t* p) { return *p; }
 
+// First index in [lo, hi) of sorted a[] whose value is >= x (hi if none).
+// Branch-free halving: each step keeps the upper half when its first
+// element is still below x.
 template <typename P>
 __device__ __forceinline__ uint32_t lower_bound_u32(P a, uint32_t lo, uint32_t hi, uint32_t x) {
     uint32_t len = hi - lo;
@@ -284,10 +293,58 @@ __device__ __forceinline__ uint32_t lower_bound_u32(P a, uint32_t lo, uint32_t h
     return base + (load_ro(a + base) < x ? 1u : 0u);
 }
 
+// ------------------------------------------------------- bucket directories
+// The search primitive of Sec. 5 ("search(V, x)": the first position of a
+// sorted list holding a value >= x) over a run a[lo, hi) of n >= DIR_MIN
+// distinct ascending values, narrowed by a directory stored in an array g
+// parallel to a.  With vmin = a[lo], vmax = a[hi-1] the run's values fall in
+// nb = ((vmax - vmin) >> s) + 1 buckets of width 2^s, where s = dir_shift(n,
+// vmax - vmin) makes nb at most n / 2^DIR_LOGB (so 2 to 8 values a bucket on
+// average); g[lo + k] is the first position in [lo, hi) whose value is in
+// bucket k or above, for k = 0..nb (g[lo + nb] = hi).  A search of x in
+// (vmin, vmax] reads g[lo + k] and g[lo + k + 1] for x's bucket k and
+// searches only between them: the values before that range are below
+// vmin + k 2^s <= x, those after it are at least vmin + (k + 1) 2^s > x.  The
+// answer is the one the plain binary search gives; the paper's fixed-stride
+// ("quadratic") search jumps by strides to reach the same range, here the
+// stride holding x is addressed directly.
+constexpr uint32_t DIR_MIN = 16;  // shorter runs have no directory
+constexpr uint32_t DIR_LOGB = 1;  // at most n / 2 buckets
+
+__device__ __forceinline__ uint32_t shr32(uint32_t x, uint32_t s) { return s >= 32u ? 0u : x >> s; }
+
+// Bucket width exponent for a run of n >= DIR_MIN values spanning `span`.
+__device__ __forceinline__ uint32_t dir_shift(uint32_t n, uint32_t span) {
+    const uint32_t lm = (31u - __clz(n)) - DIR_LOGB;  // 2^lm <= n / 2^DIR_LOGB
+    const uint32_t t = span >> lm;
+    return t ? 32u - __clz(t) : 0u;  // 2^s > t: span >> s < 2^lm
+}
+
+// lower_bound_u32 of x in the run a[lo, hi), through the run's directory when
+// g is given and the run has at least dmin (>= DIR_MIN) values.
+template <typename P>
+__device__ __forceinline__ uint32_t dir_lower_bound(P a, const uint32_t* __restrict__ g, uint32_t lo, uint32_t hi,
+                                                    uint32_t x, uint32_t dmin) {
+    const uint32_t n = hi - lo;
+    if (g == nullptr || n < dmin) return lower_bound_u32(a, lo, hi, x);
+    const uint32_t vmin = load_ro(a + lo), vmax = load_ro(a + hi - 1);
+    if (x <= vmin) return lo;
+    if (x > vmax) return hi;
+    const uint32_t k = shr32(x - vmin, dir_shift(n, vmax - vmin));
+    // the clamps keep a run built from unsorted input (a caller's broken
+    // promise) inside its own memory; for sorted runs they change nothing
+    const uint32_t b1 = min(__ldg(g + lo + k + 1), hi);
+    const uint32_t b0 = min(__ldg(g + lo + k), b1);
+    return lower_bound_u32(a, b0, b1, x);
+}
+
 #endif  // __CUDACC__
 
 // --------------------------------------------------------------- host entry
-// Sorting and CoCo construction (hc_sort.cu).
+// Sorting and CoCo construction (hc_sort.cu).  BUILD_NO_DIRECTORIES (a
+// flag of internal callers that only want the sorted keys) skips the
+// position map and the bucket directories.
+constexpr uint32_t BUILD_NO_DIRECTORIES = 0x80000000u;
 hc_status build_index_impl(const uint32_t* d_pairs, uint64_t n, uint32_t attr_order, uint32_t flags,
                            cudaStream_t s, hc_index** out);
 hc_status partition_impl(const hc_index* idx, uint32_t seed_a, uint32_t pa, uint32_t seed_b,
@@ -296,6 +353,12 @@ void partitioned_release(hc_partitioned* p, cudaStream_t s);
 void index_release(hc_index* idx, cudaStream_t s);
 hc_status build_unary_impl(const uint32_t* d_values, uint64_t n, uint32_t max_value, cudaStream_t s,
                            hc_index** out);
+// Bucket directory g (parallel to a, alen entries, allocated here) of the
+// runs [o[r], o[r+1]) of a, r < nruns (nruns = min(nruns_max, *d_nruns) when
+// d_nruns is given), or with o == NULL of the one run [0, nruns_max);
+// nothing is computed once *d_err is set.
+hc_status build_directory(const uint32_t* a, uint64_t alen, const uint32_t* o, uint64_t nruns_max,
+                          const uint32_t* d_nruns, const uint32_t* d_err, cudaStream_t s, uint32_t** out_g);
 
 // Device-wide exclusive scan of counts into uint64 offsets; out[n] receives
 // the total.  n = min(n_max, *d_n) when d_n is given (a device-side count),

@@ -34,6 +34,8 @@ struct DAtom {
     const uint32_t* l1s;    // level-1 start of each partition, [np + 1]; NULL when whole
     const uint32_t* v1pos;  // value -> position in v1 (V1POS_NONE if absent), or NULL
     uint32_t v1pos_n;       // values covered by v1pos
+    const uint32_t* g1;     // bucket directory of v1's top-level runs, or NULL
+    const uint32_t* g2;     // bucket directory of v2's runs, or NULL
     uint32_t l1_whole;
     uint32_t pb;                                     // shares of the second variable
     uint32_t stride_f, share_f, stride_s, share_s;  // cell -> partition identifiers
@@ -59,8 +61,13 @@ struct DPlan {
     int src_f[HC_MAX_VARS][MAXSRC];
     int src_slot[HC_MAX_VARS][MAXSRC];
     // last loop: a parent whose two lists are both >= merge_min long and
-    // within merge_ratio of each other takes the block-merge path
-    uint32_t merge_min, merge_ratio;
+    // within merge_ratio of each other takes the block-merge path; of the
+    // others, one whose shorter list has >= pair_min values is searched by
+    // the whole warp (probe_pair); the rest are flattened over the lanes
+    uint32_t merge_min, merge_ratio, pair_min;
+    // searches of runs at least dir_min long go through their bucket
+    // directory (0xFFFFFFFF: never)
+    uint32_t dir_min;
     // queries of 4+ loops: an entry whose loop-3 lists (those fixed by the
     // entry) exceed slice_grain is cut into slices of about that many loop-3
     // candidates per loop-2 candidate (0: no slicing)
@@ -189,7 +196,7 @@ __global__ void l0_probe_kernel(const DPlan* __restrict__ gP, const uint64_t* __
                     p = x < a.v1pos_n ? a.v1pos[x] : V1POS_NONE;
                     ok = ok && p >= rlo[q] && p < rhi[q];
                 } else {
-                    p = lower_bound_u32(a.v1, rlo[q], rhi[q], x);
+                    p = dir_lower_bound(a.v1, a.g1, rlo[q], rhi[q], x, P.dir_min);
                     ok = ok && p < rhi[q] && a.v1[p] == x;
                 }
                 pos[q] = p;
@@ -421,7 +428,8 @@ __device__ __forceinline__ bool probe(const DPlan& P, int best, const uint32_t (
                     p = ok ? lower_bound_u32(al, rlo[q], rhi[q], v) : rhi[q];
                     ok = ok && p < rhi[q] && al[p] == v;
                 } else {
-                    p = ok ? lower_bound_u32(list, rlo[q], rhi[q], v) : rhi[q];
+                    p = ok ? dir_lower_bound(list, P.src_top[L][q] ? aq.g1 : aq.g2, rlo[q], rhi[q], v, P.dir_min)
+                           : rhi[q];
                     ok = ok && p < rhi[q] && list[p] == v;
                 }
             }
@@ -529,7 +537,9 @@ __device__ __forceinline__ bool lift_compute(const DPlan& P, Frame<NL, O>& F, co
         for (int q = 0; q < S; ++q) {
             if (q < ns && ((P.far_mask >> q) & 1u) && q != (int)pbest) {
                 const uint32_t* list = src_list(P, L, q);
-                const uint32_t pos = ok ? lower_bound_u32(list, rlo[q], rhi[q], v) : rhi[q];
+                const DAtom& aq = P.atom[P.src_atom[L][q]];
+                const uint32_t pos =
+                    ok ? dir_lower_bound(list, P.src_top[L][q] ? aq.g1 : aq.g2, rlo[q], rhi[q], v, P.dir_min) : rhi[q];
                 ok = ok && pos < rhi[q] && list[pos] == v;
             }
         }
@@ -672,6 +682,64 @@ __device__ __forceinline__ void merge_pair(const DPlan& P, const Entry<NL, S>& E
     }
 }
 
+// Last loop, one parent whose shorter list A has many values: the warp takes
+// A's values 32 at a time (consecutive lanes, consecutive positions) and
+// each lane searches its value in the longer list B ("search(V, x)", Sec. 5)
+// through B's bucket directory.  B's range, bounds and bucket width are the
+// same for every value, so they are read once per parent.  Count mode counts
+// per lane; materialize mode writes each round's matches in lane order.
+template <int L, int NL, int S, int O, bool MAT, typename LP>
+__device__ __forceinline__ void probe_pair(const DPlan& P, const Entry<NL, S>& E, Acc& A, LP la,
+                                           const uint32_t* ga, uint32_t a0, uint32_t a1, LP lb,
+                                           const uint32_t* gb, uint32_t b0, uint32_t b1,
+                                           const uint32_t (&vals)[NL]) {
+    const uint32_t lane = lane_id();
+    if (a1 - a0 > b1 - b0) {  // A is the shorter list
+        LP t = la;
+        la = lb;
+        lb = t;
+        const uint32_t* tg = ga;
+        ga = gb;
+        gb = tg;
+        uint32_t u = a0;
+        a0 = b0;
+        b0 = u;
+        u = a1;
+        a1 = b1;
+        b1 = u;
+    }
+    const uint32_t nbv = b1 - b0;
+    if (nbv == 0) return;
+    const uint32_t vmin = load_ro(lb + b0), vmax = load_ro(lb + b1 - 1);
+    const bool dir = gb != nullptr && nbv >= P.dir_min;
+    const uint32_t sh = dir ? dir_shift(nbv, vmax - vmin) : 0u;
+    uint32_t cnt = 0;
+    for (uint32_t t0 = a0; t0 < a1; t0 += 32) {
+        const uint32_t t = t0 + lane;
+        const uint32_t v = t < a1 ? load_ro(la + t) : 0u;
+        bool ok = t < a1 && v >= vmin && v <= vmax;
+        if (ok) {
+            uint32_t lo = b0, hi = b1;
+            if (dir) {
+                const uint32_t k = shr32(v - vmin, sh);
+                hi = min(__ldg(gb + b0 + k + 1), b1);
+                lo = min(__ldg(gb + b0 + k), hi);
+            }
+            const uint32_t pos = lower_bound_u32(lb, lo, hi, v);
+            ok = pos < hi && load_ro(lb + pos) == v;
+        }
+        if constexpr (MAT) {
+            const uint32_t ball = __ballot_sync(0xffffffffu, ok);
+            const uint64_t slot = out_reserve(A, ball);
+            if (ok && slot != ~0ull) write_tuple<L, NL>(P, A.out + slot * (uint64_t)P.nv, E.x, vals, v);
+            A.count += __popc(ball);
+        } else {
+            cnt += ok ? 1u : 0u;
+        }
+    }
+    if constexpr (!MAT) A.count += __reduce_add_sync(0xffffffffu, cnt);
+}
+
 // Compact this round's matches into the batch of loop L and descend.
 template <int L, int NL, int S, int O, bool MAT>
 __device__ __forceinline__ void descend(const DPlan& P, Frame<NL, O>& F, const Entry<NL, S>& E, Acc& A, bool ok,
@@ -754,7 +822,7 @@ __device__ __forceinline__ void run_level(const DPlan& P, Frame<NL, O>& F, const
                     }
             }
         }
-        bool merge_class = false;
+        bool merge_class = false, pair_class = false;
         int qa = 0, qb = 1;  // the two lists of a merge pair
         if constexpr (L == NL - 1 && S >= 2) {
             const uint32_t um = use & ((1u << ns) - 1u);
@@ -770,6 +838,7 @@ __device__ __forceinline__ void run_level(const DPlan& P, Frame<NL, O>& F, const
                     }
                     const uint32_t mn = min(l0, l1), mx = max(l0, l1);
                     merge_class = mn >= P.merge_min && (uint64_t)mx <= (uint64_t)P.merge_ratio * mn;
+                    pair_class = !merge_class && mn >= P.pair_min;
                 }
             }
         }
@@ -786,7 +855,7 @@ __device__ __forceinline__ void run_level(const DPlan& P, Frame<NL, O>& F, const
                     if (q == (int)best) bestlen = mhi[q] - mlo[q];
             }
         }
-        const uint32_t cnt = (lane < nb && !merge_class) ? bestlen : 0;
+        const uint32_t cnt = (lane < nb && !merge_class && !pair_class) ? bestlen : 0;
         const uint32_t incl = warp_incl_scan(cnt);
         const uint32_t excl = incl - cnt;
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
@@ -854,6 +923,28 @@ __device__ __forceinline__ void run_level(const DPlan& P, Frame<NL, O>& F, const
                 else
                     merge_pair<L, NL, S, O, MAT>(P, E, A, src_list(P, L, qa), a0, a1, src_list(P, L, qb), b0, b1,
                                                  vals);
+            }
+            uint32_t pball = __ballot_sync(0xffffffffu, pair_class);
+            if (pball) {
+                const DAtom& da = P.atom[P.src_atom[L][qa]];
+                const DAtom& db = P.atom[P.src_atom[L][qb]];
+                const uint32_t* ga = qa == lift_q ? nullptr : (P.src_top[L][qa] ? da.g1 : da.g2);
+                const uint32_t* gb = qb == lift_q ? nullptr : (P.src_top[L][qb] ? db.g1 : db.g2);
+                while (pball) {
+                    const uint32_t p = __ffs(pball) - 1;
+                    pball &= pball - 1;
+                    const uint32_t a0 = __shfl_sync(0xffffffffu, xa0, p), a1 = __shfl_sync(0xffffffffu, xa1, p);
+                    const uint32_t b0 = __shfl_sync(0xffffffffu, xb0, p), b1 = __shfl_sync(0xffffffffu, xb1, p);
+                    uint32_t vals[NL];
+                    if constexpr (MAT) prefix_values<L, NL, O>(F, p, vals);
+                    if (qa == lift_q || qb == lift_q)  // a list in the arena: coherent loads
+                        probe_pair<L, NL, S, O, MAT>(P, E, A, const_cast<uint32_t*>(src_list_l(P, A, L, qa, lift_q)),
+                                                     ga, a0, a1, const_cast<uint32_t*>(src_list_l(P, A, L, qb, lift_q)),
+                                                     gb, b0, b1, vals);
+                    else
+                        probe_pair<L, NL, S, O, MAT>(P, E, A, src_list(P, L, qa), ga, a0, a1, src_list(P, L, qb), gb,
+                                                     b0, b1, vals);
+                }
             }
         }
     }
@@ -1389,12 +1480,16 @@ hc_status plan_query(const hc_query* q, const hc_index* const* idx, const hc_joi
             d.l1_whole = (uint32_t)ix->l1;
             d.v1pos = ix->d_v1pos;
             d.v1pos_n = ix->v1pos_n;
+            d.g1 = ix->d_g1;
+            d.g2 = ix->d_g2;
         } else if (partition_bytes) {
             // estimate only: keys, levels and directory of the partitioned copy,
             // its V1 position map, plus the radix pass temporaries
             const uint64_t n = ix->n, np = (uint64_t)pa * pb;
             *partition_bytes += n * (8 + 8 + 4 + 4 + 4) + (np + 1) * 8 + ((n + 4095) / 4096) * 256 * 8 + 4096;
-            if (pb == 1 && v1pos_eligible(n, ix->max_first)) *partition_bytes += ((uint64_t)ix->max_first + 1) * 4;
+            const bool map = pb == 1 && v1pos_eligible(n, ix->max_first);
+            if (map) *partition_bytes += ((uint64_t)ix->max_first + 1) * 4;
+            *partition_bytes += n * 4 * (map ? 1 : 2);  // bucket directories of V2 (and V1 without a map)
             d.l1s = nullptr;
         } else {
             hc_partitioned* part = nullptr;
@@ -1408,6 +1503,8 @@ hc_status plan_query(const hc_query* q, const hc_index* const* idx, const hc_joi
             d.l1s = part->d_lvl1_start;
             d.v1pos = part->d_v1pos;
             d.v1pos_n = part->v1pos_n;
+            d.g1 = part->d_g1;
+            d.g2 = part->d_g2;
         }
     }
     for (int L = 0; L < nv; ++L) {
@@ -1456,7 +1553,9 @@ hc_status plan_query(const hc_query* q, const hc_index* const* idx, const hc_joi
                                               "2^27 or more rows), beyond the search kernels' 32-bit candidate "
                                               "counts"));
     }
+    P.dir_min = prm->dir_min == 0 ? DIR_MIN : std::max(prm->dir_min, DIR_MIN);
     P.merge_min = prm->merge_min ? prm->merge_min : 32;
+    P.pair_min = prm->pair_min ? prm->pair_min : 32;
     P.merge_ratio = prm->merge_ratio ? prm->merge_ratio : 4;
     P.slice_grain = prm->slice_grain == 0xFFFFFFFFu ? 0 : (prm->slice_grain ? prm->slice_grain : 256);
     // query rewriting (Sec. 5.1): the last loop's lists fixed before the loop

@@ -455,7 +455,7 @@ hc_status build_kindex_impl(const uint32_t* d_rows, uint64_t n, uint32_t k, cons
         if ((st = tmp.get(&pk, n)) != HC_OK) return bail2(st);
         kpack_kernel<<<grid_of(n, 256, 8), 256, 0, s>>>(d_rows, n, L, pk);
         if (cudaError_t le = launch_check()) return bail2(cuda_fail(le, "kpack_kernel"));
-        if ((st = build_index_impl((const uint32_t*)pk, n, 0, 0, s, &sorted)) != HC_OK) return bail2(st);
+        if ((st = build_index_impl((const uint32_t*)pk, n, 0, BUILD_NO_DIRECTORIES, s, &sorted)) != HC_OK) return bail2(st);
         src.keys = sorted->d_keys;
     } else {
         uint2* pairs;
@@ -467,7 +467,7 @@ hc_status build_kindex_impl(const uint32_t* d_rows, uint64_t n, uint32_t k, cons
             kperm_pairs_kernel<<<grid_of(n, 256, 8), 256, 0, s>>>(d_rows, n, k, cols[d], cur, pairs);
             if (cudaError_t le = launch_check()) return bail2(cuda_fail(le, "kperm_pairs_kernel"));
             hc_index* pass = nullptr;
-            if ((st = build_index_impl((const uint32_t*)pairs, n, 0, 0, s, &pass)) != HC_OK) return bail2(st);
+            if ((st = build_index_impl((const uint32_t*)pairs, n, 0, BUILD_NO_DIRECTORIES, s, &pass)) != HC_OK) return bail2(st);
             uint32_t* nxt = cur == pa ? pb : pa;
             kperm_compose_kernel<<<grid_of(n, 256, 8), 256, 0, s>>>(pass->d_keys, cur, nxt, n);
             cudaError_t le = launch_check();

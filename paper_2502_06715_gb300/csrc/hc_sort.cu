@@ -473,6 +473,36 @@ __global__ void maxrun_kernel(const uint32_t* __restrict__ o1, uint64_t l1_max, 
     if (lane_id() == 0 && m) atomicMax(&ctl->maxrun, m);
 }
 
+// Bucket directory of the runs of a level (layout at dir_lower_bound): the
+// runs [o[r], o[r+1]) for r < nruns, or with o == NULL the one run
+// [0, nruns_max); one warp per run, its lanes striding over the run's values.  The value at
+// position j opens the buckets above its predecessor's bucket up to its own
+// and writes g[lo + k] = j for each; the run's last value also writes
+// g[lo + nb] = hi.  Buckets are clamped to [0, nb - 1], so unsorted input
+// (never produced by the builders here) cannot write outside the run.
+__global__ void dir_build_kernel(const uint32_t* __restrict__ a, const uint32_t* __restrict__ o, uint64_t nruns_max,
+                                 const uint32_t* __restrict__ d_nruns, uint32_t* __restrict__ g,
+                                 const uint32_t* __restrict__ err) {
+    if (err && dev_err_set(err)) return;
+    const uint64_t nruns = o == nullptr ? 1 : d_nruns ? min(nruns_max, (uint64_t)*d_nruns) : nruns_max;
+    const uint32_t lane = lane_id();
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t r = warp; r < nruns; r += nwarps) {
+        const uint32_t lo = o ? o[r] : 0u, hi = o ? o[r + 1] : (uint32_t)nruns_max;
+        if (hi < lo || hi - lo < DIR_MIN) continue;
+        const uint32_t vmin = a[lo], vmax = a[hi - 1];
+        const uint32_t sh = dir_shift(hi - lo, vmax - vmin);
+        const uint32_t kmax = shr32(vmax - vmin, sh);  // nb - 1
+        for (uint32_t j = lo + lane; j < hi; j += 32) {
+            const uint32_t k = min(shr32(a[j] - vmin, sh), kmax);
+            const uint32_t k0 = j == lo ? 0u : min(shr32(a[j - 1] - vmin, sh), kmax) + 1u;
+            for (uint32_t b = k0; b <= k; ++b) g[lo + b] = j;
+            if (j == hi - 1) g[lo + kmax + 1] = hi;
+        }
+    }
+}
+
 // ----------------------------------------------------------- device scan
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 8;
@@ -700,6 +730,26 @@ uint32_t bits_of(uint32_t v) { return v == 0 ? 0 : 32 - __builtin_clz(v); }
 
 }  // namespace
 
+hc_status build_directory(const uint32_t* a, uint64_t alen, const uint32_t* o, uint64_t nruns_max,
+                          const uint32_t* d_nruns, const uint32_t* d_err, cudaStream_t s, uint32_t** out_g) {
+    *out_g = nullptr;
+    if (alen < DIR_MIN || nruns_max == 0) return HC_OK;  // no run can have a directory
+    void* p = nullptr;
+    HC_TRY(dev_alloc(&p, alen * 4, s));
+    // warps over the runs, a few per SM resident
+    const uint64_t want = o == nullptr ? 1 : (nruns_max + 7) / 8;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)num_sms() * 16));
+    dir_build_kernel<<<grid, 256, 0, s>>>(a, o, nruns_max, d_nruns, (uint32_t*)p, d_err);
+    if (cudaError_t le = launch_check()) {
+        dev_free(p, s);
+        return cuda_fail(le, "dir_build_kernel");
+    }
+    *out_g = (uint32_t*)p;
+    return HC_OK;
+}
+
+hc_status build_level_directories(hc_index* idx, cudaStream_t s);
+
 void index_release(hc_index* idx, cudaStream_t s) {
     if (!idx) return;
     dev_free(idx->d_keys, s);
@@ -707,6 +757,8 @@ void index_release(hc_index* idx, cudaStream_t s) {
     dev_free(idx->d_o1, s);
     dev_free(idx->d_v2, s);
     dev_free(idx->d_v1pos, s);
+    dev_free(idx->d_g1, s);
+    dev_free(idx->d_g2, s);
     delete idx;
 }
 
@@ -781,6 +833,10 @@ hc_status build_index_impl(const uint32_t* d_pairs, uint64_t n, uint32_t ao, uin
             return bail(fail(HC_ERR_DUPLICATE, "build_index: the relation holds a repeated row"));
         idx->l1 = h.l1;
         idx->max_run = h.maxrun;
+        if (flags & BUILD_NO_DIRECTORIES) {
+            *out = idx;
+            return HC_OK;
+        }
         if (v1pos_eligible(n, idx->max_first)) {
             const uint64_t dn = (uint64_t)idx->max_first + 1;
             if (dev_alloc(&p, dn * 4, s) != HC_OK) return bail(HC_ERR_OOM);
@@ -792,8 +848,19 @@ hc_status build_index_impl(const uint32_t* d_pairs, uint64_t n, uint32_t ao, uin
                                                                     idx->v1pos_n);
             if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "v1pos_kernel"));
         }
+        if ((st = build_level_directories(idx, s)) != HC_OK) return bail(st);
     }
     *out = idx;
+    return HC_OK;
+}
+
+// Directories of a built index: V2 by the runs of O1, and V1 as one run
+// when it has no position map.
+hc_status build_level_directories(hc_index* idx, cudaStream_t s) {
+    if (idx->max_run >= DIR_MIN)
+        HC_TRY(build_directory(idx->d_v2, idx->n, idx->d_o1, idx->l1, nullptr, nullptr, s, &idx->d_g2));
+    if (idx->d_v1pos == nullptr && idx->l1 >= DIR_MIN)
+        HC_TRY(build_directory(idx->d_v1, idx->l1, nullptr, idx->l1, nullptr, nullptr, s, &idx->d_g1));
     return HC_OK;
 }
 
@@ -850,6 +917,8 @@ hc_status build_unary_impl(const uint32_t* d_values, uint64_t n, uint32_t max_va
         v1pos_kernel<<<grid_for(n, 256, 8), 256, 0, s>>>(d_values, n, nullptr, idx->d_v1pos, idx->v1pos_n);
         if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "v1pos_kernel"));
     }
+    hc_status st = build_level_directories(idx, s);
+    if (st != HC_OK) return bail(st);
     *out = idx;
     return HC_OK;
 }
@@ -864,6 +933,8 @@ void partitioned_release(hc_partitioned* p, cudaStream_t s) {
     dev_free(p->d_lvl1_start, s);
     dev_free(p->d_l1, s);
     dev_free(p->d_v1pos, s);
+    dev_free(p->d_g1, s);
+    dev_free(p->d_g2, s);
     delete p;
 }
 
@@ -947,6 +1018,14 @@ hc_status partition_impl(const hc_index* idx, uint32_t seed_a, uint32_t pa, uint
                                                               part->v1pos_n);
             if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "v1pos_kernel"));
         }
+        // bucket directories: V2 by the runs of O1 (l1 runs, a device-side
+        // count), V1 by partitions when it has no position map
+        if (idx->max_run >= DIR_MIN &&
+            (st = build_directory(part->d_v2, n, part->d_o1, n, &d_ctl->l1, &d_ctl->err, s, &part->d_g2)) != HC_OK)
+            return bail(st);
+        if (part->d_v1pos == nullptr &&
+            (st = build_directory(part->d_v1, n, part->d_lvl1_start, np, nullptr, &d_ctl->err, s, &part->d_g1)) != HC_OK)
+            return bail(st);
     }
     *out = part;
     return HC_OK;

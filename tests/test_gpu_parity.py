@@ -439,3 +439,38 @@ def test_slice_grain_sweep_skewed(hc, qname):
         if ref is not None and sg in (1, 7):
             r = _run(hc, q, rels, slice_grain=sg, mode="materialize", out_capacity=cnt + 1)
             assert np.array_equal(sorted_rows(u32(r.tuples)), sorted_rows(ref)), sg
+
+
+# ------------------------------------------------------- bucket directories
+
+@pytest.mark.parametrize("scramble", [True, False])
+@pytest.mark.parametrize("qname", ["TRIANGLE", "FOUR_CYCLE", "FOUR_CLIQUE", "TWO_TRIANGLE"])
+def test_directory_thresholds(hc, qname, scramble):
+    """List searches through the runs' bucket directories (runs of at least
+    dir_min values) give exactly the plain binary search's results: every
+    threshold, and none, on R-MAT graphs with scrambled ids (values spread
+    evenly over each run's range) and unscrambled ones (hubs on low ids,
+    values bunched), with and without shares and position maps."""
+    q = getattr(hc, qname)
+    sym = datagen.rmat_graph(11, 16, 23, scramble=scramble)
+    rel = sym if qname == "FOUR_CYCLE" else datagen.orient_lt(sym)
+    if qname == "FOUR_CYCLE":
+        rel = rel[: rel.shape[0] // 3]  # keep the oracle's closed walks few enough
+        rel = np.ascontiguousarray(rel)
+    rels = [rel] * len(q.atoms)
+    cnt, work, _ = oracle.gj_count(q.n_vars, list(q.atoms), rels)
+    # pair_min: last-loop bindings searched by the whole warp (1: all, the
+    # default 32, 0xFFFFFFFF: none, every binding's values flattened)
+    for dmin, pmin in ((0, 0), (17, 1), (100, 0xFFFFFFFF), (0xFFFFFFFF, 0), (0xFFFFFFFF, 0xFFFFFFFF)):
+        r = _run(hc, q, rels, dir_min=dmin, pair_min=pmin, stats=True)
+        assert r.count == cnt and r.work == work, (dmin, pmin)
+        assert _run(hc, q, rels, dir_min=dmin, pair_min=pmin).count == cnt, (dmin, pmin)
+        for sh in ([2] * q.n_vars, [1, 4] + [1] * (q.n_vars - 2)):
+            assert _run(hc, q, rels, dir_min=dmin, pair_min=pmin, shares=sh).count == cnt, (dmin, pmin, sh)
+    if cnt < 2_000_000:
+        ref = oracle.gj_enumerate(q.n_vars, list(q.atoms), rels)
+        for dmin, pmin in ((0, 0), (0, 1), (0xFFFFFFFF, 0xFFFFFFFF)):
+            for cap in (0, cnt + 1):
+                r = _run(hc, q, rels, dir_min=dmin, pair_min=pmin, mode="materialize", shares=[2] * q.n_vars,
+                         out_capacity=cap, merge_min=0xFFFFFFFF)
+                assert np.array_equal(sorted_rows(u32(r.tuples)), sorted_rows(ref)), (dmin, pmin, cap)
