@@ -47,6 +47,11 @@ enum : uint32_t { DEV_ERR_TIMEOUT = 1u };
 // launched from now on (hc_set_wait_limit_ns; default 2 s).
 uint64_t wait_limit_ns();
 
+// Level arrays V1 and V2 (of indexes and partitioned copies) are allocated
+// with LIST_PAD spare entries, so a 16-byte vector load that starts at a
+// multiple of 4 entries inside the array stays inside the allocation.
+constexpr uint64_t LIST_PAD = 4;
+
 // Longest list the search kernels may iterate: they sum up to 32 bindings'
 // list lengths in 32 bits, so every list they iterate must be shorter than
 // 2^27 (checked by run_join against the indexes' longest runs).
@@ -81,8 +86,8 @@ struct hc_index {
     // bucket directories (search acceleration, see dir_lower_bound): d_g2
     // parallel to V2 for the runs of O1; d_g1 parallel to V1 for the single
     // run [0, l1) when there is no position map
-    uint32_t* d_g2 = nullptr;
-    uint32_t* d_g1 = nullptr;
+    uint64_t* d_g2 = nullptr;
+    uint64_t* d_g1 = nullptr;
 };
 
 struct hc_partitioned {
@@ -103,8 +108,8 @@ struct hc_partitioned {
     uint32_t v1pos_n = 0;
     // bucket directories: d_g2 parallel to V2 (runs of O1), d_g1 parallel to
     // V1 (one run per partition, lvl1_start) when there is no position map
-    uint32_t* d_g2 = nullptr;
-    uint32_t* d_g1 = nullptr;
+    uint64_t* d_g2 = nullptr;
+    uint64_t* d_g1 = nullptr;
 };
 
 namespace hc {
@@ -293,49 +298,113 @@ __device__ __forceinline__ uint32_t lower_bound_u32(P a, uint32_t lo, uint32_t h
     return base + (load_ro(a + base) < x ? 1u : 0u);
 }
 
+// Membership form of the same search: the last position i in [lo, hi) with
+// a[i] <= x (lo if none), its value in w, true when w == x (then i is the
+// first position holding x, the lower bound).  The value at the answer comes
+// out of the search itself, so no second read is needed.  hi > lo.
+template <typename P>
+__device__ __forceinline__ bool find_u32(P a, uint32_t lo, uint32_t hi, uint32_t x, uint32_t& pos) {
+    uint32_t len = hi - lo, base = lo;
+    while (len > 1) {
+        const uint32_t half = len >> 1;
+        base = load_ro(a + base + half) <= x ? base + half : base;
+        len -= half;
+    }
+    pos = base;
+    return load_ro(a + base) == x;
+}
+
 // ------------------------------------------------------- bucket directories
 // The search primitive of Sec. 5 ("search(V, x)": the first position of a
 // sorted list holding a value >= x) over a run a[lo, hi) of n >= DIR_MIN
-// distinct ascending values, narrowed by a directory stored in an array g
-// parallel to a.  With vmin = a[lo], vmax = a[hi-1] the run's values fall in
-// nb = ((vmax - vmin) >> s) + 1 buckets of width 2^s, where s = dir_shift(n,
-// vmax - vmin) makes nb at most n / 2^DIR_LOGB (so 2 to 8 values a bucket on
-// average); g[lo + k] is the first position in [lo, hi) whose value is in
-// bucket k or above, for k = 0..nb (g[lo + nb] = hi).  A search of x in
-// (vmin, vmax] reads g[lo + k] and g[lo + k + 1] for x's bucket k and
-// searches only between them: the values before that range are below
-// vmin + k 2^s <= x, those after it are at least vmin + (k + 1) 2^s > x.  The
-// answer is the one the plain binary search gives; the paper's fixed-stride
-// ("quadratic") search jumps by strides to reach the same range, here the
-// stride holding x is addressed directly.
+// distinct ascending values, narrowed by a directory stored in an array g of
+// 64-bit entries parallel to a.  With vmin = a[lo], vmax = a[hi-1] the run's
+// values fall in nb = ((vmax - vmin) >> s) + 1 buckets of width 2^s, where
+// s = dir_shift(n, vmax - vmin) makes nb at most n (one to four values a
+// bucket on average).  Entry k of the run, g[lo + k] for k < nb, holds
+// p_k = the first position in [lo, hi) whose value is in bucket k or above
+// (low 32 bits) and a[p_k] (high 32 bits); every p_k exists, since vmax lies
+// in the last bucket.  A search of x in (vmin, vmax] reads the entry of x's
+// bucket k: every value before p_k is below vmin + k 2^s <= x, so the answer
+// is p_k when a[p_k] >= x, and otherwise lies a few positions further (a
+// forward walk that stops at the latest at hi - 1, because vmax >= x).  The
+// answer is the plain binary search's.  The paper's fixed-stride
+// ("quadratic") search jumps by strides to reach the stride holding x; here
+// that stride is addressed directly, and its first value comes with it, so
+// most searches of a value that is absent end after one 8-byte read.
 constexpr uint32_t DIR_MIN = 16;  // shorter runs have no directory
-constexpr uint32_t DIR_LOGB = 1;  // at most n / 2 buckets
 
-__device__ __forceinline__ uint32_t shr32(uint32_t x, uint32_t s) { return s >= 32u ? 0u : x >> s; }
-
-// Bucket width exponent for a run of n >= DIR_MIN values spanning `span`.
+// Bucket width exponent for a run of n >= DIR_MIN values spanning `span`:
+// with 2^lm <= n < 2^(lm+1) and s the bit length of span >> lm, 2^s > span
+// >> lm, so the last bucket index span >> s is below 2^lm <= n; s <= 29.
 __device__ __forceinline__ uint32_t dir_shift(uint32_t n, uint32_t span) {
-    const uint32_t lm = (31u - __clz(n)) - DIR_LOGB;  // 2^lm <= n / 2^DIR_LOGB
+    const uint32_t lm = 31u - __clz(n);
     const uint32_t t = span >> lm;
-    return t ? 32u - __clz(t) : 0u;  // 2^s > t: span >> s < 2^lm
+    return t ? 32u - __clz(t) : 0u;
+}
+
+__device__ __forceinline__ uint64_t dir_entry(uint32_t pos, uint32_t value) {
+    return ((uint64_t)value << 32) | pos;
+}
+
+// The answer from entry e = g[lo + k] for x in (vmin, vmax]: p_k if
+// a[p_k] >= x, else the first later position holding a value >= x.  A
+// position outside the run (a directory of unsorted input, a caller's broken
+// promise) is pulled back to hi - 1, where the walk ends.
+template <typename P>
+__device__ __forceinline__ uint32_t dir_walk(P a, uint64_t e, uint32_t hi, uint32_t x) {
+    uint32_t p = (uint32_t)e, w = (uint32_t)(e >> 32);
+    if (p >= hi) {
+        p = hi - 1;
+        w = load_ro(a + p);
+    }
+    while (w < x) w = load_ro(a + (++p));
+    return p;
+}
+
+// Membership of x in the run a[lo, hi) from the entry e of x's bucket, x in
+// (vmin, vmax]: the walk ends at the lower bound, whose value it holds.
+template <typename P>
+__device__ __forceinline__ bool dir_walk_find(P a, uint64_t e, uint32_t hi, uint32_t x, uint32_t& pos) {
+    uint32_t p = (uint32_t)e, w = (uint32_t)(e >> 32);
+    if (p >= hi) {
+        p = hi - 1;
+        w = load_ro(a + p);
+    }
+    while (w < x) w = load_ro(a + (++p));
+    pos = p;
+    return w == x;
+}
+
+// Membership of x in the run a[lo, hi) and, when present, its position:
+// through the run's directory when g is given and the run has at least dmin
+// (>= DIR_MIN) values, else by find_u32.
+template <typename P>
+__device__ __forceinline__ bool dir_find(P a, const uint64_t* __restrict__ g, uint32_t lo, uint32_t hi, uint32_t x,
+                                         uint32_t dmin, uint32_t& pos) {
+    const uint32_t n = hi - lo;
+    pos = lo;
+    if (n == 0) return false;
+    if (g == nullptr || n < dmin) return find_u32(a, lo, hi, x, pos);
+    const uint32_t vmin = load_ro(a + lo), vmax = load_ro(a + hi - 1);
+    if (x <= vmin) return x == vmin;
+    if (x > vmax) return false;
+    const uint32_t k = (x - vmin) >> dir_shift(n, vmax - vmin);
+    return dir_walk_find(a, __ldg((const unsigned long long*)g + lo + k), hi, x, pos);
 }
 
 // lower_bound_u32 of x in the run a[lo, hi), through the run's directory when
 // g is given and the run has at least dmin (>= DIR_MIN) values.
 template <typename P>
-__device__ __forceinline__ uint32_t dir_lower_bound(P a, const uint32_t* __restrict__ g, uint32_t lo, uint32_t hi,
+__device__ __forceinline__ uint32_t dir_lower_bound(P a, const uint64_t* __restrict__ g, uint32_t lo, uint32_t hi,
                                                     uint32_t x, uint32_t dmin) {
     const uint32_t n = hi - lo;
     if (g == nullptr || n < dmin) return lower_bound_u32(a, lo, hi, x);
     const uint32_t vmin = load_ro(a + lo), vmax = load_ro(a + hi - 1);
     if (x <= vmin) return lo;
     if (x > vmax) return hi;
-    const uint32_t k = shr32(x - vmin, dir_shift(n, vmax - vmin));
-    // the clamps keep a run built from unsorted input (a caller's broken
-    // promise) inside its own memory; for sorted runs they change nothing
-    const uint32_t b1 = min(__ldg(g + lo + k + 1), hi);
-    const uint32_t b0 = min(__ldg(g + lo + k), b1);
-    return lower_bound_u32(a, b0, b1, x);
+    const uint32_t k = (x - vmin) >> dir_shift(n, vmax - vmin);
+    return dir_walk(a, __ldg((const unsigned long long*)g + lo + k), hi, x);
 }
 
 #endif  // __CUDACC__
@@ -353,12 +422,12 @@ void partitioned_release(hc_partitioned* p, cudaStream_t s);
 void index_release(hc_index* idx, cudaStream_t s);
 hc_status build_unary_impl(const uint32_t* d_values, uint64_t n, uint32_t max_value, cudaStream_t s,
                            hc_index** out);
-// Bucket directory g (parallel to a, alen entries, allocated here) of the
+// Bucket directory g (parallel to a, alen 64-bit entries, allocated here) of the
 // runs [o[r], o[r+1]) of a, r < nruns (nruns = min(nruns_max, *d_nruns) when
 // d_nruns is given), or with o == NULL of the one run [0, nruns_max);
 // nothing is computed once *d_err is set.
 hc_status build_directory(const uint32_t* a, uint64_t alen, const uint32_t* o, uint64_t nruns_max,
-                          const uint32_t* d_nruns, const uint32_t* d_err, cudaStream_t s, uint32_t** out_g);
+                          const uint32_t* d_nruns, const uint32_t* d_err, cudaStream_t s, uint64_t** out_g);
 
 // Device-wide exclusive scan of counts into uint64 offsets; out[n] receives
 // the total.  n = min(n_max, *d_n) when d_n is given (a device-side count),

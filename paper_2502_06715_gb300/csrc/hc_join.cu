@@ -16,6 +16,7 @@
 // compacted with ballots into the next batch.  At the last loop a match is
 // counted (count mode) or written (materialize mode).
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "hc_internal.cuh"
@@ -34,8 +35,8 @@ struct DAtom {
     const uint32_t* l1s;    // level-1 start of each partition, [np + 1]; NULL when whole
     const uint32_t* v1pos;  // value -> position in v1 (V1POS_NONE if absent), or NULL
     uint32_t v1pos_n;       // values covered by v1pos
-    const uint32_t* g1;     // bucket directory of v1's top-level runs, or NULL
-    const uint32_t* g2;     // bucket directory of v2's runs, or NULL
+    const uint64_t* g1;     // bucket directory of v1's top-level runs, or NULL
+    const uint64_t* g2;     // bucket directory of v2's runs, or NULL
     uint32_t l1_whole;
     uint32_t pb;                                     // shares of the second variable
     uint32_t stride_f, share_f, stride_s, share_s;  // cell -> partition identifiers
@@ -196,8 +197,7 @@ __global__ void l0_probe_kernel(const DPlan* __restrict__ gP, const uint64_t* __
                     p = x < a.v1pos_n ? a.v1pos[x] : V1POS_NONE;
                     ok = ok && p >= rlo[q] && p < rhi[q];
                 } else {
-                    p = dir_lower_bound(a.v1, a.g1, rlo[q], rhi[q], x, P.dir_min);
-                    ok = ok && p < rhi[q] && a.v1[p] == x;
+                    ok = dir_find(a.v1, a.g1, rlo[q], rhi[q], x, P.dir_min, p) && ok;
                 }
                 pos[q] = p;
             }
@@ -425,12 +425,9 @@ __device__ __forceinline__ bool probe(const DPlan& P, int best, const uint32_t (
                     ok = ok && p >= rlo[q] && p < rhi[q];
                 } else if (q == lift_q) {  // the arena, written by this kernel: coherent loads
                     uint32_t* al = const_cast<uint32_t*>(list);
-                    p = ok ? lower_bound_u32(al, rlo[q], rhi[q], v) : rhi[q];
-                    ok = ok && p < rhi[q] && al[p] == v;
+                    ok = ok && rhi[q] > rlo[q] && find_u32(al, rlo[q], rhi[q], v, p);
                 } else {
-                    p = ok ? dir_lower_bound(list, P.src_top[L][q] ? aq.g1 : aq.g2, rlo[q], rhi[q], v, P.dir_min)
-                           : rhi[q];
-                    ok = ok && p < rhi[q] && list[p] == v;
+                    ok = ok && dir_find(list, P.src_top[L][q] ? aq.g1 : aq.g2, rlo[q], rhi[q], v, P.dir_min, p);
                 }
             }
             if (q < O && q != lift_q && P.src_top[L][q] && ok) {  // top sources come first, slot == q
@@ -538,9 +535,8 @@ __device__ __forceinline__ bool lift_compute(const DPlan& P, Frame<NL, O>& F, co
             if (q < ns && ((P.far_mask >> q) & 1u) && q != (int)pbest) {
                 const uint32_t* list = src_list(P, L, q);
                 const DAtom& aq = P.atom[P.src_atom[L][q]];
-                const uint32_t pos =
-                    ok ? dir_lower_bound(list, P.src_top[L][q] ? aq.g1 : aq.g2, rlo[q], rhi[q], v, P.dir_min) : rhi[q];
-                ok = ok && pos < rhi[q] && list[pos] == v;
+                uint32_t pos;
+                ok = ok && dir_find(list, P.src_top[L][q] ? aq.g1 : aq.g2, rlo[q], rhi[q], v, P.dir_min, pos);
             }
         }
         const uint32_t ball = __ballot_sync(0xffffffffu, ok);
@@ -683,22 +679,38 @@ __device__ __forceinline__ void merge_pair(const DPlan& P, const Entry<NL, S>& E
 }
 
 // Last loop, one parent whose shorter list A has many values: the warp takes
-// A's values 32 at a time (consecutive lanes, consecutive positions) and
-// each lane searches its value in the longer list B ("search(V, x)", Sec. 5)
-// through B's bucket directory.  B's range, bounds and bucket width are the
-// same for every value, so they are read once per parent.  Count mode counts
-// per lane; materialize mode writes each round's matches in lane order.
+// A's values 128 at a time, four consecutive ones per lane in one 16-byte
+// load (index lists; a list in the arena is read one value per lane), and
+// each lane searches its values in the longer list B ("search(V, x)",
+// Sec. 5) through B's bucket directory, the four directory reads issued
+// together.  B's range, bounds and bucket width are the same for every value,
+// so they are read once per parent.  Count mode counts per lane;
+// materialize mode writes each slot's matches in lane order.
+template <int L, int NL, int S, int O, bool MAT>
+__device__ __forceinline__ void pair_match(const DPlan& P, const Entry<NL, S>& E, Acc& A, bool ok, uint32_t v,
+                                           const uint32_t (&vals)[NL], uint32_t& cnt) {
+    if constexpr (MAT) {
+        const uint32_t ball = __ballot_sync(0xffffffffu, ok);
+        const uint64_t slot = out_reserve(A, ball);
+        if (ok && slot != ~0ull) write_tuple<L, NL>(P, A.out + slot * (uint64_t)P.nv, E.x, vals, v);
+        A.count += __popc(ball);
+    } else {
+        cnt += ok ? 1u : 0u;
+    }
+}
+
 template <int L, int NL, int S, int O, bool MAT, typename LP>
 __device__ __forceinline__ void probe_pair(const DPlan& P, const Entry<NL, S>& E, Acc& A, LP la,
-                                           const uint32_t* ga, uint32_t a0, uint32_t a1, LP lb,
-                                           const uint32_t* gb, uint32_t b0, uint32_t b1,
+                                           const uint64_t* ga, uint32_t a0, uint32_t a1, LP lb,
+                                           const uint64_t* gb, uint32_t b0, uint32_t b1,
                                            const uint32_t (&vals)[NL]) {
+    constexpr bool VEC = std::is_same<LP, const uint32_t*>::value;  // an index list: padded, 16-byte aligned base
     const uint32_t lane = lane_id();
     if (a1 - a0 > b1 - b0) {  // A is the shorter list
         LP t = la;
         la = lb;
         lb = t;
-        const uint32_t* tg = ga;
+        const uint64_t* tg = ga;
         ga = gb;
         gb = tg;
         uint32_t u = a0;
@@ -709,32 +721,42 @@ __device__ __forceinline__ void probe_pair(const DPlan& P, const Entry<NL, S>& E
         b1 = u;
     }
     const uint32_t nbv = b1 - b0;
-    if (nbv == 0) return;
+    if (nbv == 0 || a1 == a0) return;
     const uint32_t vmin = load_ro(lb + b0), vmax = load_ro(lb + b1 - 1);
     const bool dir = gb != nullptr && nbv >= P.dir_min;
     const uint32_t sh = dir ? dir_shift(nbv, vmax - vmin) : 0u;
+    const unsigned long long* gd = (const unsigned long long*)gb + b0;
     uint32_t cnt = 0;
-    for (uint32_t t0 = a0; t0 < a1; t0 += 32) {
-        const uint32_t t = t0 + lane;
-        const uint32_t v = t < a1 ? load_ro(la + t) : 0u;
-        bool ok = t < a1 && v >= vmin && v <= vmax;
-        if (ok) {
-            uint32_t lo = b0, hi = b1;
-            if (dir) {
-                const uint32_t k = shr32(v - vmin, sh);
-                hi = min(__ldg(gb + b0 + k + 1), b1);
-                lo = min(__ldg(gb + b0 + k), hi);
+    if constexpr (VEC) {
+        for (uint32_t t0 = a0 & ~3u; t0 < a1; t0 += 128) {
+            const uint32_t t = t0 + 4 * lane;
+            uint4 q4 = make_uint4(0u, 0u, 0u, 0u);
+            if (t < a1) q4 = __ldg(reinterpret_cast<const uint4*>(la + t));
+            const uint32_t vv[4] = {q4.x, q4.y, q4.z, q4.w};
+            bool okv[4];
+            uint64_t ev[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                okv[j] = t + j >= a0 && t + j < a1 && vv[j] >= vmin && vv[j] <= vmax;
+                ev[j] = (okv[j] && dir) ? __ldg(gd + ((vv[j] - vmin) >> sh)) : 0ull;
             }
-            const uint32_t pos = lower_bound_u32(lb, lo, hi, v);
-            ok = pos < hi && load_ro(lb + pos) == v;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                uint32_t pos;
+                if (okv[j]) okv[j] = dir ? dir_walk_find(lb, ev[j], b1, vv[j], pos) : find_u32(lb, b0, b1, vv[j], pos);
+                pair_match<L, NL, S, O, MAT>(P, E, A, okv[j], vv[j], vals, cnt);
+            }
         }
-        if constexpr (MAT) {
-            const uint32_t ball = __ballot_sync(0xffffffffu, ok);
-            const uint64_t slot = out_reserve(A, ball);
-            if (ok && slot != ~0ull) write_tuple<L, NL>(P, A.out + slot * (uint64_t)P.nv, E.x, vals, v);
-            A.count += __popc(ball);
-        } else {
-            cnt += ok ? 1u : 0u;
+    } else {
+        for (uint32_t t0 = a0; t0 < a1; t0 += 32) {
+            const uint32_t t = t0 + lane;
+            const uint32_t v = t < a1 ? load_ro(la + t) : 0u;
+            bool ok = t < a1 && v >= vmin && v <= vmax;
+            if (ok) {
+                uint32_t pos;
+                ok = dir ? dir_walk_find(lb, __ldg(gd + ((v - vmin) >> sh)), b1, v, pos) : find_u32(lb, b0, b1, v, pos);
+            }
+            pair_match<L, NL, S, O, MAT>(P, E, A, ok, v, vals, cnt);
         }
     }
     if constexpr (!MAT) A.count += __reduce_add_sync(0xffffffffu, cnt);
@@ -928,8 +950,8 @@ __device__ __forceinline__ void run_level(const DPlan& P, Frame<NL, O>& F, const
             if (pball) {
                 const DAtom& da = P.atom[P.src_atom[L][qa]];
                 const DAtom& db = P.atom[P.src_atom[L][qb]];
-                const uint32_t* ga = qa == lift_q ? nullptr : (P.src_top[L][qa] ? da.g1 : da.g2);
-                const uint32_t* gb = qb == lift_q ? nullptr : (P.src_top[L][qb] ? db.g1 : db.g2);
+                const uint64_t* ga = qa == lift_q ? nullptr : (P.src_top[L][qa] ? da.g1 : da.g2);
+                const uint64_t* gb = qb == lift_q ? nullptr : (P.src_top[L][qb] ? db.g1 : db.g2);
                 while (pball) {
                     const uint32_t p = __ffs(pball) - 1;
                     pball &= pball - 1;
@@ -1212,17 +1234,69 @@ __global__ void __launch_bounds__(128, ((NLA <= 3 && NLB <= 3) ? 16 : 12))
     }
 }
 
-// Single-pass materialize: concatenate the filled part of each used pool
-// chunk at its offset in the output.
-__global__ void gather_chunks_kernel(const uint32_t* __restrict__ pool, const uint32_t* __restrict__ chunk_fill,
-                                     const uint64_t* __restrict__ chunk_off, uint32_t n_used, uint32_t nv,
-                                     uint32_t* __restrict__ out) {
+// Single-pass materialize: the pool becomes the output in place.  Every
+// used chunk is full except each warp's last one, so the n_full full chunks
+// are arranged to fill chunk slots [0, n_full) and the partial chunks'
+// tuples follow them: a partial chunk below n_full (a hole) receives a full
+// chunk from slot n_full or above (a donor), k-th hole from k-th donor.
+// Only the partial chunks' tuples and the donors move (at most a chunk per
+// resident warp each), not the whole output.
+//   chunk_class_kernel   is_partial[c], fill of partial chunks (0 for full)
+//   (two exclusive scans: prank = partials before c, poff = their tuples)
+//   save_partials_kernel partial chunks' tuples -> tmp at poff; pslot[prank] = c
+//   move_donors_kernel   donor of rank r -> slot pslot[r]
+//   place_partials_kernel tmp -> output after the n_full full chunks
+__global__ void chunk_class_kernel(const uint32_t* __restrict__ chunk_fill, uint32_t n_used,
+                                   uint32_t* __restrict__ is_partial, uint32_t* __restrict__ pfill) {
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n_used; c += gridDim.x * blockDim.x) {
+        const uint32_t f = chunk_fill[c];
+        is_partial[c] = f < OUT_CHUNK ? 1u : 0u;
+        pfill[c] = f < OUT_CHUNK ? f : 0u;
+    }
+}
+
+__global__ void save_partials_kernel(const uint32_t* __restrict__ pool, const uint32_t* __restrict__ chunk_fill,
+                                     const uint64_t* __restrict__ prank, const uint64_t* __restrict__ poff,
+                                     uint32_t n_used, uint32_t nv, uint32_t* __restrict__ tmp,
+                                     uint32_t* __restrict__ pslot, const uint32_t* __restrict__ err) {
+    if (dev_err_set(err)) return;  // the scans gave up a wait: their offsets are not valid
     for (uint32_t c = blockIdx.x; c < n_used; c += gridDim.x) {
-        const uint64_t words = (uint64_t)chunk_fill[c] * nv;
+        const uint32_t f = chunk_fill[c];
+        if (f >= OUT_CHUNK) continue;
+        if (threadIdx.x == 0) pslot[prank[c]] = c;
+        const uint64_t words = (uint64_t)f * nv;
         const uint32_t* src = pool + (uint64_t)c * OUT_CHUNK * nv;
-        uint32_t* dst = out + chunk_off[c] * nv;
+        uint32_t* dst = tmp + poff[c] * nv;
         for (uint64_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
     }
+}
+
+__global__ void move_donors_kernel(uint32_t* __restrict__ pool, const uint32_t* __restrict__ chunk_fill,
+                                   const uint64_t* __restrict__ prank, const uint32_t* __restrict__ pslot,
+                                   uint32_t n_used, uint32_t nv, const uint32_t* __restrict__ err) {
+    if (dev_err_set(err)) return;
+    const uint32_t n_full = n_used - (uint32_t)prank[n_used];
+    for (uint32_t c = n_full + blockIdx.x; c < n_used; c += gridDim.x) {
+        if (chunk_fill[c] < OUT_CHUNK) continue;
+        // full chunks in [n_full, c), i.e. this donor's rank among donors
+        const uint64_t r = (uint64_t)(c - n_full) - (prank[c] - prank[n_full]);
+        const uint32_t dst_slot = pslot[r];  // the r-th partial chunk overall, a hole (below n_full)
+        const uint4* src = reinterpret_cast<const uint4*>(pool + (uint64_t)c * OUT_CHUNK * nv);
+        uint4* dst = reinterpret_cast<uint4*>(pool + (uint64_t)dst_slot * OUT_CHUNK * nv);
+        const uint32_t vecs = OUT_CHUNK * nv / 4;  // a chunk is a multiple of 16 bytes
+        for (uint32_t i = threadIdx.x; i < vecs; i += blockDim.x) dst[i] = src[i];
+    }
+}
+
+__global__ void place_partials_kernel(uint32_t* __restrict__ pool, const uint32_t* __restrict__ tmp,
+                                      const uint64_t* __restrict__ prank, const uint64_t* __restrict__ poff,
+                                      uint32_t n_used, uint32_t nv, const uint32_t* __restrict__ err) {
+    if (dev_err_set(err)) return;
+    const uint32_t n_full = n_used - (uint32_t)prank[n_used];
+    const uint64_t words = poff[n_used] * nv;
+    uint32_t* dst = pool + (uint64_t)n_full * OUT_CHUNK * nv;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < words; i += (uint64_t)gridDim.x * blockDim.x)
+        dst[i] = tmp[i];
 }
 
 // Search kernels are compiled for NL = 2..5 loops and for S (lists per
@@ -1489,7 +1563,7 @@ hc_status plan_query(const hc_query* q, const hc_index* const* idx, const hc_joi
             *partition_bytes += n * (8 + 8 + 4 + 4 + 4) + (np + 1) * 8 + ((n + 4095) / 4096) * 256 * 8 + 4096;
             const bool map = pb == 1 && v1pos_eligible(n, ix->max_first);
             if (map) *partition_bytes += ((uint64_t)ix->max_first + 1) * 4;
-            *partition_bytes += n * 4 * (map ? 1 : 2);  // bucket directories of V2 (and V1 without a map)
+            *partition_bytes += n * 8 * (map ? 1 : 2);  // bucket directories of V2 (and V1 without a map)
             d.l1s = nullptr;
         } else {
             hc_partitioned* part = nullptr;
@@ -1782,30 +1856,59 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
         const uint64_t n_chunks64 = (prm->out_capacity + OUT_CHUNK - 1) / OUT_CHUNK + warps;
         if (n_chunks64 >= 0xFFFFFFFFull) return bail(fail(HC_ERR_CAPACITY, "run_join: out_capacity too large"));
         const uint32_t n_chunks = (uint32_t)n_chunks64;
-        uint32_t *pool, *chunk_fill;
-        uint64_t* chunk_off;
-        if ((st = tmp.get(&pool, (size_t)n_chunks * OUT_CHUNK * nv)) != HC_OK) return bail(st);
-        if ((st = tmp.get(&chunk_fill, n_chunks)) != HC_OK) return bail(st);
-        if ((st = tmp.get(&chunk_off, (size_t)n_chunks + 1)) != HC_OK) return bail(st);
+        uint32_t *pool = nullptr, *chunk_fill;
+        {
+            void* pp;
+            if (dev_alloc(&pp, (size_t)n_chunks * OUT_CHUNK * nv * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+            pool = (uint32_t*)pp;
+        }
+        if ((st = tmp.get(&chunk_fill, n_chunks)) != HC_OK) {
+            dev_free(pool, s);
+            return bail(st);
+        }
         g.out = pool;
         g.chunk_fill = chunk_fill;
         g.n_chunks = n_chunks;
-        if ((st = search(true)) != HC_OK) return bail(st);
-        if ((st = read_ctl(R)) != HC_OK) return bail(st);
+        st = search(true);
+        if (st == HC_OK) st = read_ctl(R);
+        if (st != HC_OK) {
+            dev_free(pool, s);
+            return bail(st);
+        }
         total = R->h_ctl.total;
         if (!R->h_ctl.overflow) {
+            // the pool becomes the result; compact it in place (see chunk_class_kernel)
+            R->d_tuples = pool;
             const uint32_t n_used = std::min<uint32_t>(R->h_ctl.chunk_ctr, n_chunks);
-            if ((st = exclusive_scan_u32_to_u64(chunk_fill, chunk_off, n_used, nullptr, &ctl->err, s)) != HC_OK)
-                return bail(st);
-            void* p;
-            if (dev_alloc(&p, std::max<uint64_t>(total, 1) * nv * 4, s) != HC_OK) return bail(HC_ERR_OOM);
-            R->d_tuples = (uint32_t*)p;
             if (n_used > 0) {
-                gather_chunks_kernel<<<std::min<uint32_t>(n_used, (uint32_t)num_sms() * 16), 256, 0, s>>>(
-                    pool, chunk_fill, chunk_off, n_used, (uint32_t)nv, R->d_tuples);
-                if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "gather_chunks_kernel"));
+                uint32_t *is_partial, *pfill, *pslot, *ptmp;
+                uint64_t *prank, *poff;
+                if ((st = tmp.get(&is_partial, n_used)) != HC_OK || (st = tmp.get(&pfill, n_used)) != HC_OK ||
+                    (st = tmp.get(&prank, (size_t)n_used + 1)) != HC_OK ||
+                    (st = tmp.get(&poff, (size_t)n_used + 1)) != HC_OK ||
+                    (st = tmp.get(&pslot, std::min<uint64_t>(n_used, warps) + 1)) != HC_OK ||
+                    (st = tmp.get(&ptmp, (size_t)std::min<uint64_t>(n_used, warps) * OUT_CHUNK * nv)) != HC_OK)
+                    return bail(st);
+                const unsigned cgrid = std::min<uint32_t>((n_used + 255) / 256, (uint32_t)num_sms() * 8);
+                chunk_class_kernel<<<cgrid, 256, 0, s>>>(chunk_fill, n_used, is_partial, pfill);
+                if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "chunk_class_kernel"));
+                if ((st = exclusive_scan_u32_to_u64(is_partial, prank, n_used, nullptr, &ctl->err, s)) != HC_OK ||
+                    (st = exclusive_scan_u32_to_u64(pfill, poff, n_used, nullptr, &ctl->err, s)) != HC_OK)
+                    return bail(st);
+                const unsigned bgrid = std::min<uint32_t>(n_used, (uint32_t)num_sms() * 16);
+                save_partials_kernel<<<bgrid, 256, 0, s>>>(pool, chunk_fill, prank, poff, n_used, (uint32_t)nv,
+                                                           ptmp, pslot, &ctl->err);
+                if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "save_partials_kernel"));
+                move_donors_kernel<<<bgrid, 256, 0, s>>>(pool, chunk_fill, prank, pslot, n_used, (uint32_t)nv,
+                                                         &ctl->err);
+                if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "move_donors_kernel"));
+                place_partials_kernel<<<(unsigned)num_sms() * 4, 256, 0, s>>>(pool, ptmp, prank, poff, n_used,
+                                                                              (uint32_t)nv, &ctl->err);
+                if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "place_partials_kernel"));
             }
             written = true;
+        } else {
+            dev_free(pool, s);
         }
         // on overflow the item counts of the single pass place the tuples of a
         // second, deterministic emitting pass

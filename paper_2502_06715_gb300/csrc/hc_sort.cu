@@ -475,13 +475,13 @@ __global__ void maxrun_kernel(const uint32_t* __restrict__ o1, uint64_t l1_max, 
 
 // Bucket directory of the runs of a level (layout at dir_lower_bound): the
 // runs [o[r], o[r+1]) for r < nruns, or with o == NULL the one run
-// [0, nruns_max); one warp per run, its lanes striding over the run's values.  The value at
-// position j opens the buckets above its predecessor's bucket up to its own
-// and writes g[lo + k] = j for each; the run's last value also writes
-// g[lo + nb] = hi.  Buckets are clamped to [0, nb - 1], so unsorted input
-// (never produced by the builders here) cannot write outside the run.
+// [0, nruns_max); one warp per run, its lanes striding over the run's values.
+// The value at position j opens the buckets above its predecessor's bucket
+// up to its own and writes entry (j, a[j]) for each.  Buckets are clamped to
+// [0, nb - 1], so unsorted input (never produced by the builders here)
+// cannot write outside the run.
 __global__ void dir_build_kernel(const uint32_t* __restrict__ a, const uint32_t* __restrict__ o, uint64_t nruns_max,
-                                 const uint32_t* __restrict__ d_nruns, uint32_t* __restrict__ g,
+                                 const uint32_t* __restrict__ d_nruns, uint64_t* __restrict__ g,
                                  const uint32_t* __restrict__ err) {
     if (err && dev_err_set(err)) return;
     const uint64_t nruns = o == nullptr ? 1 : d_nruns ? min(nruns_max, (uint64_t)*d_nruns) : nruns_max;
@@ -493,12 +493,13 @@ __global__ void dir_build_kernel(const uint32_t* __restrict__ a, const uint32_t*
         if (hi < lo || hi - lo < DIR_MIN) continue;
         const uint32_t vmin = a[lo], vmax = a[hi - 1];
         const uint32_t sh = dir_shift(hi - lo, vmax - vmin);
-        const uint32_t kmax = shr32(vmax - vmin, sh);  // nb - 1
+        const uint32_t kmax = (vmax - vmin) >> sh;  // nb - 1 < hi - lo
         for (uint32_t j = lo + lane; j < hi; j += 32) {
-            const uint32_t k = min(shr32(a[j] - vmin, sh), kmax);
-            const uint32_t k0 = j == lo ? 0u : min(shr32(a[j - 1] - vmin, sh), kmax) + 1u;
-            for (uint32_t b = k0; b <= k; ++b) g[lo + b] = j;
-            if (j == hi - 1) g[lo + kmax + 1] = hi;
+            const uint32_t v = a[j];
+            const uint32_t k = min((v - vmin) >> sh, kmax);
+            const uint32_t k0 = j == lo ? 0u : min((a[j - 1] - vmin) >> sh, kmax) + 1u;
+            const uint64_t e = dir_entry(j, v);
+            for (uint32_t b = k0; b <= k; ++b) g[lo + b] = e;
         }
     }
 }
@@ -731,20 +732,20 @@ uint32_t bits_of(uint32_t v) { return v == 0 ? 0 : 32 - __builtin_clz(v); }
 }  // namespace
 
 hc_status build_directory(const uint32_t* a, uint64_t alen, const uint32_t* o, uint64_t nruns_max,
-                          const uint32_t* d_nruns, const uint32_t* d_err, cudaStream_t s, uint32_t** out_g) {
+                          const uint32_t* d_nruns, const uint32_t* d_err, cudaStream_t s, uint64_t** out_g) {
     *out_g = nullptr;
     if (alen < DIR_MIN || nruns_max == 0) return HC_OK;  // no run can have a directory
     void* p = nullptr;
-    HC_TRY(dev_alloc(&p, alen * 4, s));
+    HC_TRY(dev_alloc(&p, alen * 8, s));
     // warps over the runs, a few per SM resident
     const uint64_t want = o == nullptr ? 1 : (nruns_max + 7) / 8;
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)num_sms() * 16));
-    dir_build_kernel<<<grid, 256, 0, s>>>(a, o, nruns_max, d_nruns, (uint32_t*)p, d_err);
+    dir_build_kernel<<<grid, 256, 0, s>>>(a, o, nruns_max, d_nruns, (uint64_t*)p, d_err);
     if (cudaError_t le = launch_check()) {
         dev_free(p, s);
         return cuda_fail(le, "dir_build_kernel");
     }
-    *out_g = (uint32_t*)p;
+    *out_g = (uint64_t*)p;
     return HC_OK;
 }
 
@@ -779,11 +780,11 @@ hc_status build_index_impl(const uint32_t* d_pairs, uint64_t n, uint32_t ao, uin
     void* p;
     if (dev_alloc(&p, std::max<uint64_t>(n, 1) * 8, s) != HC_OK) return bail(HC_ERR_OOM);
     idx->d_keys = (uint64_t*)p;
-    if (dev_alloc(&p, std::max<uint64_t>(n, 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+    if (dev_alloc(&p, (n + LIST_PAD) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
     idx->d_v1 = (uint32_t*)p;
     if (dev_alloc(&p, (n + 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
     idx->d_o1 = (uint32_t*)p;
-    if (dev_alloc(&p, std::max<uint64_t>(n, 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+    if (dev_alloc(&p, (n + LIST_PAD) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
     idx->d_v2 = (uint32_t*)p;
 
     hc_status st;
@@ -897,11 +898,11 @@ hc_status build_unary_impl(const uint32_t* d_values, uint64_t n, uint32_t max_va
     void* p;
     if (dev_alloc(&p, std::max<uint64_t>(n, 1) * 8, s) != HC_OK) return bail(HC_ERR_OOM);
     idx->d_keys = (uint64_t*)p;
-    if (dev_alloc(&p, std::max<uint64_t>(n, 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+    if (dev_alloc(&p, (n + LIST_PAD) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
     idx->d_v1 = (uint32_t*)p;
     if (dev_alloc(&p, (n + 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
     idx->d_o1 = (uint32_t*)p;
-    if (dev_alloc(&p, std::max<uint64_t>(n, 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+    if (dev_alloc(&p, (n + LIST_PAD) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
     idx->d_v2 = (uint32_t*)p;
     if (n > 0 && cudaMemcpyAsync(idx->d_v1, d_values, n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return bail(cuda_fail(cudaGetLastError(), "copy"));
@@ -965,11 +966,11 @@ hc_status partition_impl(const hc_index* idx, uint32_t seed_a, uint32_t pa, uint
     part->d_keys = (uint64_t*)p;
     if (dev_alloc(&p, (uint64_t)(np + 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
     part->d_bpref = (uint32_t*)p;
-    if (dev_alloc(&p, std::max<uint64_t>(n, 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+    if (dev_alloc(&p, (n + LIST_PAD) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
     part->d_v1 = (uint32_t*)p;
     if (dev_alloc(&p, (n + 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
     part->d_o1 = (uint32_t*)p;
-    if (dev_alloc(&p, std::max<uint64_t>(n, 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+    if (dev_alloc(&p, (n + LIST_PAD) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
     part->d_v2 = (uint32_t*)p;
     if (dev_alloc(&p, (uint64_t)(np + 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
     part->d_lvl1_start = (uint32_t*)p;
