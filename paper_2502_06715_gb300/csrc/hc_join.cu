@@ -88,6 +88,10 @@ constexpr uint32_t LIFT_ARENA_WORDS = 16384;  // per warp, by default
 // OUT_CHUNK tuples taken from an output pool with one atomic per chunk.
 constexpr uint32_t OUT_CHUNK = 2048;
 constexpr uint32_t NO_CHUNK = 0xFFFFFFFFu;
+// Materializing search: the last loop's per-binding path stages its matches
+// (the last variable's values) in a per-warp shared-memory buffer of OBUF
+// values and writes them out 32 tuples at a time.
+constexpr uint32_t OBUF = 256;
 
 __device__ __forceinline__ void load_plan(DPlan& dst, const DPlan* __restrict__ src) {
     const uint32_t* s = (const uint32_t*)src;
@@ -314,6 +318,7 @@ struct Acc {
     uint32_t* chunk_fill;
     JoinCtl* ctl;
     uint32_t* arena;  // the warp's arena for lifted lists (query rewriting), or NULL
+    uint32_t* obuf;   // the warp's staging buffer of OBUF values (materialize), or NULL
 };
 
 // Output slot of the lane holding rank r among the k = popc(ball) matches
@@ -351,6 +356,38 @@ __device__ __forceinline__ uint64_t out_reserve(Acc& A, uint32_t ball) {
     A.chunk = nc;
     A.fill = k - room;
     return slot;
+}
+
+// Reserve n <= OUT_CHUNK consecutive output slots for the warp (all lanes
+// call, n lane-uniform).  Tuple t of the n goes to slot s0 + t when t < room,
+// else to s1 + (t - room); a base of ~0 means the pool is exhausted and those
+// tuples are not written (the overflow flag makes the join rerun them).
+__device__ __forceinline__ void out_reserve_n(Acc& A, uint32_t n, uint64_t& s0, uint32_t& room, uint64_t& s1) {
+    s1 = ~0ull;
+    if (!A.pool) {
+        s0 = A.out_pos;
+        room = n;
+        A.out_pos += n;
+        return;
+    }
+    room = OUT_CHUNK - A.fill;
+    s0 = A.chunk == NO_CHUNK ? ~0ull : (uint64_t)A.chunk * OUT_CHUNK + A.fill;
+    if (n <= room) {
+        room = n;
+        A.fill += n;
+        return;
+    }
+    uint32_t nc = 0;
+    if (lane_id() == 0) {
+        if (A.chunk != NO_CHUNK) A.chunk_fill[A.chunk] = OUT_CHUNK;
+        nc = atomicAdd(&A.ctl->chunk_ctr, 1u);
+        if (nc >= A.n_chunks) atomicOr(&A.ctl->overflow, 1u);
+    }
+    nc = __shfl_sync(0xffffffffu, nc, 0);
+    if (nc >= A.n_chunks) nc = NO_CHUNK;
+    s1 = nc == NO_CHUNK ? ~0ull : (uint64_t)nc * OUT_CHUNK;
+    A.chunk = nc;
+    A.fill = n - room;
 }
 
 // Position of the r-th (0-based) set bit of m (r < popc(m)).
@@ -699,6 +736,28 @@ __device__ __forceinline__ void pair_match(const DPlan& P, const Entry<NL, S>& E
     }
 }
 
+// Write the n staged values of the warp's buffer as tuples (E.x, the
+// parent's values, value) at freshly reserved slots; lane i writes tuples
+// i, i + 32, ... (all lanes call, n lane-uniform).
+template <int L, int NL, int S>
+__device__ __forceinline__ void flush_staged(const DPlan& P, const Entry<NL, S>& E, Acc& A, uint32_t n,
+                                             const uint32_t (&vals)[NL]) {
+    if (n == 0) return;
+    __syncwarp();
+    uint64_t s0, s1;
+    uint32_t room;
+    out_reserve_n(A, n, s0, room, s1);
+    for (uint32_t t = lane_id(); t < n; t += 32) {
+        const uint64_t base = t < room ? s0 : s1;
+        if (base != ~0ull) {
+            const uint64_t slot = base + (t < room ? t : t - room);
+            write_tuple<L, NL>(P, A.out + slot * (uint64_t)P.nv, E.x, vals, A.obuf[t]);
+        }
+    }
+    __syncwarp();
+    A.count += n;
+}
+
 template <int L, int NL, int S, int O, bool MAT, typename LP>
 __device__ __forceinline__ void probe_pair(const DPlan& P, const Entry<NL, S>& E, Acc& A, LP la,
                                            const uint64_t* ga, uint32_t a0, uint32_t a1, LP lb,
@@ -727,6 +786,7 @@ __device__ __forceinline__ void probe_pair(const DPlan& P, const Entry<NL, S>& E
     const uint32_t sh = dir ? dir_shift(nbv, vmax - vmin) : 0u;
     const unsigned long long* gd = (const unsigned long long*)gb + b0;
     uint32_t cnt = 0;
+    uint32_t staged = 0;  // values in the warp's buffer (materialize, VEC)
     if constexpr (VEC) {
         for (uint32_t t0 = a0 & ~3u; t0 < a1; t0 += 128) {
             const uint32_t t = t0 + 4 * lane;
@@ -740,13 +800,31 @@ __device__ __forceinline__ void probe_pair(const DPlan& P, const Entry<NL, S>& E
                 okv[j] = t + j >= a0 && t + j < a1 && vv[j] >= vmin && vv[j] <= vmax;
                 ev[j] = (okv[j] && dir) ? __ldg(gd + ((vv[j] - vmin) >> sh)) : 0ull;
             }
+            uint32_t mine = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 uint32_t pos;
                 if (okv[j]) okv[j] = dir ? dir_walk_find(lb, ev[j], b1, vv[j], pos) : find_u32(lb, b0, b1, vv[j], pos);
-                pair_match<L, NL, S, O, MAT>(P, E, A, okv[j], vv[j], vals, cnt);
+                mine += okv[j] ? 1u : 0u;
+            }
+            if constexpr (MAT) {
+                // stage this round's matches: lane l's go after those of lanes < l
+                const uint32_t incl = warp_incl_scan(mine);
+                const uint32_t k = __shfl_sync(0xffffffffu, incl, 31);
+                if (staged + k > OBUF) {
+                    flush_staged<L, NL, S>(P, E, A, staged, vals);
+                    staged = 0;
+                }
+                uint32_t at = staged + incl - mine;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (okv[j]) A.obuf[at++] = vv[j];
+                staged += k;
+            } else {
+                cnt += mine;
             }
         }
+        if constexpr (MAT) flush_staged<L, NL, S>(P, E, A, staged, vals);
     } else {
         for (uint32_t t0 = a0; t0 < a1; t0 += 32) {
             const uint32_t t = t0 + lane;
@@ -1097,6 +1175,7 @@ __global__ void __launch_bounds__(128, (NL <= 3 ? 16 : 12)) gj_kernel(const DPla
                                                     uint32_t* __restrict__ arena) {
     __shared__ DPlan P;
     __shared__ uint32_t s_elo[4][NL][S], s_ehi[4][NL][S];  // per warp (blocks of <= 128 threads)
+    __shared__ uint32_t s_obuf[MAT ? 4 : 1][MAT ? OBUF : 1];
     load_plan(P, gP);
     if (dev_err_set(&ctl->err)) return;  // a scan of the loop-1 pass gave up a wait
     const uint32_t lane = lane_id();
@@ -1119,6 +1198,7 @@ __global__ void __launch_bounds__(128, (NL <= 3 ? 16 : 12)) gj_kernel(const DPla
     A.ctl = ctl;
     A.arena = arena ? arena + (uint64_t)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * P.arena_words
                     : nullptr;
+    A.obuf = MAT ? s_obuf[MAT ? (threadIdx.x >> 5) : 0] : nullptr;
     uint64_t total = 0;
     for (;;) {
         uint32_t item = 0;
@@ -1188,6 +1268,7 @@ __global__ void __launch_bounds__(128, ((NLA <= 3 && NLB <= 3) ? 16 : 12))
     A.chunk_fill = nullptr;
     A.ctl = nullptr;
     A.arena = arena ? arena + (uint64_t)(blockIdx.x * 4 + w) * arena_stride : nullptr;
+    A.obuf = nullptr;
     for (;;) {
         uint32_t it = 0;
         if (lane == 0) it = atomicAdd(ctr, 1u);
