@@ -74,6 +74,15 @@ def parse_args():
                     help="autotune: smallest number of cells (so the routing steps always run)")
     ap.add_argument("--P", type=int, default=1024)
     ap.add_argument("--grain", type=int, default=0)
+    ap.add_argument("--merge", default="auto",
+                    help="last-loop merge path: 'auto' (the autotuner's choice, else the library default), "
+                         "'off', or MIN,RATIO")
+    ap.add_argument("--dir-min", type=int, default=0,
+                    help="searches of runs at least this long use the bucket directory (0: library default 16; "
+                         "-1: plain binary search)")
+    ap.add_argument("--pair-min", type=int, default=0,
+                    help="last-loop bindings with a shorter list this long are searched by the whole warp "
+                         "(0: library default 32; -1: never)")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--capacity", default="plan",
                     help="materialize output pool: 'plan' = 1.25 x the planning run's count (one pass), "
@@ -211,9 +220,17 @@ def measured_hbm_peak():
         return 6800.0, "fallback"
 
 
-def profiled_traffic(note: str = None, source: str = "hc_join.cu"):
+def source_hash(sources) -> str:
+    """sha256 over the concatenated bytes of the given csrc files."""
+    h = hashlib.sha256()
+    for name in sources:
+        h.update(open(os.path.join(ROOT, "paper_2502_06715_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
+def profiled_traffic(note: str = None, sources=("hc_join.cu", "hc_internal.cuh")):
     """Per-launch DRAM bytes of a kernel from a committed ncu summary, if it
-    was taken on the current source of the file that holds the kernel."""
+    was taken on the current source of the files that hold the kernel."""
     try:
         text = open(note or PROFILE_NOTE).read()
     except OSError:
@@ -222,8 +239,7 @@ def profiled_traffic(note: str = None, source: str = "hc_join.cu"):
     h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
     if not m or not h:
         return None
-    src = os.path.join(ROOT, "paper_2502_06715_gb300", "csrc", source)
-    if hashlib.sha256(open(src, "rb").read()).hexdigest() != h.group(1):
+    if source_hash(sources) != h.group(1):
         return None
     return int(m.group(1))
 
@@ -296,6 +312,13 @@ def main():
     else:
         shares = [int(x) for x in a.shares.split(",")]
     knobs = {"merge_min": tuned.merge_min, "merge_ratio": tuned.merge_ratio} if tuned else {}
+    if a.merge == "off":
+        knobs = {"merge_min": 0xFFFFFFFF, "merge_ratio": 1}
+    elif a.merge != "auto":
+        mm, mr = (int(x) for x in a.merge.split(","))
+        knobs = {"merge_min": mm, "merge_ratio": mr}
+    knobs["dir_min"] = a.dir_min & 0xFFFFFFFF
+    knobs["pair_min"] = a.pair_min & 0xFFFFFFFF
     stats = hc.run_join(q, [ix0] * 3, shares=shares, stats=True, item_grain=a.grain, block_threads=a.threads,
                         **knobs)
     work, expect = stats.work, stats.count
@@ -380,6 +403,7 @@ def main():
                         f"autotune (>= {a.min_cells} cells; candidates include choose_shares(P=64..1024))"),
                        "plan_shares_P1024": plan_shares, "item_grain": a.grain or 64,
                        "merge": [knobs.get("merge_min", 32), knobs.get("merge_ratio", 4)],
+                       "dir_min": knobs["dir_min"] or 16, "pair_min": knobs["pair_min"] or 32,
                        "out_capacity": capacity if a.mode == "materialize" else None,
                        "search_launches_per_step": n_launch_per_step,
                        "work_counter": work, "l2": "inputs larger than L2 (E+ is %.0f MB)" % (n * 8 / 1e6),
@@ -698,7 +722,7 @@ def build_workload(a, world, rank, local):
     bnd_alg = 8 * n + 4 * n + 8 * l1 + 4  # keys read; V2, V1, O1 written
     roofline = {"bound": "hbm", "kernel": "onesweep_kernel (radix pass)", "achieved": round(achieved, 1),
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": profiled_traffic(BUILD_PROFILE_NOTE, "hc_sort.cu"),
+                "traffic": profiled_traffic(BUILD_PROFILE_NOTE, ("hc_sort.cu", "hc_internal.cuh")),
                 "alg_bytes_per_launch": 16 * n, "avg_launch_ms": round(pass_ms, 4),
                 "passes_per_step": radix_n / a.steps,
                 "boundary_kernel": {"achieved": round(bnd_alg / (bnd_ms / a.steps / 1e3) / 1e9, 1),

@@ -475,26 +475,62 @@ __global__ void maxrun_kernel(const uint32_t* __restrict__ o1, uint64_t l1_max, 
 
 // Bucket directory of the runs of a level (layout at dir_lower_bound): the
 // runs [o[r], o[r+1]) for r < nruns, or with o == NULL the one run
-// [0, nruns_max); one warp per run, its lanes striding over the run's values.
-// The value at position j opens the buckets above its predecessor's bucket
-// up to its own and writes entry (j, a[j]) for each.  Buckets are clamped to
-// [0, nb - 1], so unsorted input (never produced by the builders here)
-// cannot write outside the run.
-__global__ void dir_build_kernel(const uint32_t* __restrict__ a, const uint32_t* __restrict__ o, uint64_t nruns_max,
-                                 const uint32_t* __restrict__ d_nruns, uint64_t* __restrict__ g,
-                                 const uint32_t* __restrict__ err) {
+// [0, nruns_max).  Element-parallel: a block takes tiles of DIRB_TILE
+// consecutive positions; thread 0 finds the runs that hold the tile's first
+// and last positions, and each thread finds the run of its position by a
+// binary search of the run starts between them.  The value at position j
+// opens the buckets above its predecessor's bucket up to its own and writes
+// entry (j, a[j]) for each.  Buckets are clamped to [0, nb - 1], so unsorted
+// input (never produced by the builders here) cannot write outside the run.
+constexpr uint32_t DIRB_TILE = 2048;
+
+__global__ void __launch_bounds__(256) dir_build_kernel(const uint32_t* __restrict__ a, const uint32_t* __restrict__ o,
+                                                        uint64_t nruns_max, const uint32_t* __restrict__ d_nruns,
+                                                        uint64_t* __restrict__ g, const uint32_t* __restrict__ err) {
+    __shared__ uint32_t s_r0, s_r1;
     if (err && dev_err_set(err)) return;
-    const uint64_t nruns = o == nullptr ? 1 : d_nruns ? min(nruns_max, (uint64_t)*d_nruns) : nruns_max;
-    const uint32_t lane = lane_id();
-    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t r = warp; r < nruns; r += nwarps) {
-        const uint32_t lo = o ? o[r] : 0u, hi = o ? o[r + 1] : (uint32_t)nruns_max;
-        if (hi < lo || hi - lo < DIR_MIN) continue;
-        const uint32_t vmin = a[lo], vmax = a[hi - 1];
-        const uint32_t sh = dir_shift(hi - lo, vmax - vmin);
-        const uint32_t kmax = (vmax - vmin) >> sh;  // nb - 1 < hi - lo
-        for (uint32_t j = lo + lane; j < hi; j += 32) {
+    const uint32_t nruns = o == nullptr ? 1u : (uint32_t)(d_nruns ? min(nruns_max, (uint64_t)*d_nruns) : nruns_max);
+    const uint32_t total = o == nullptr ? (uint32_t)nruns_max : o[nruns];
+    for (uint32_t base = blockIdx.x * DIRB_TILE; base < total; base += gridDim.x * DIRB_TILE) {
+        const uint32_t end = min(base + DIRB_TILE, total);
+        __syncthreads();  // the previous tile's run bounds are no longer read
+        if (threadIdx.x == 0) {
+            uint32_t r0 = 0, r1 = 0;
+            if (o != nullptr) {
+                // last r with o[r] <= base, and last r with o[r] <= end - 1
+                uint32_t lo = 0, hi = nruns;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (o[mid] <= base) lo = mid; else hi = mid;
+                }
+                r0 = lo;
+                hi = nruns;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (o[mid] <= end - 1) lo = mid; else hi = mid;
+                }
+                r1 = lo;
+            }
+            s_r0 = r0;
+            s_r1 = r1;
+        }
+        __syncthreads();
+        const uint32_t r0 = s_r0, r1 = s_r1;
+        for (uint32_t j = base + threadIdx.x; j < end; j += blockDim.x) {
+            uint32_t lo = 0, hi = total;
+            if (o != nullptr) {
+                uint32_t rl = r0, rh = r1 + 1;  // last r in [r0, r1] with o[r] <= j
+                while (rh - rl > 1) {
+                    const uint32_t mid = (rl + rh) >> 1;
+                    if (o[mid] <= j) rl = mid; else rh = mid;
+                }
+                lo = o[rl];
+                hi = o[rl + 1];
+            }
+            if (hi < lo || hi - lo < DIR_MIN) continue;
+            const uint32_t vmin = a[lo], vmax = a[hi - 1];
+            const uint32_t sh = dir_shift(hi - lo, vmax - vmin);
+            const uint32_t kmax = (vmax - vmin) >> sh;  // nb - 1 < hi - lo
             const uint32_t v = a[j];
             const uint32_t k = min((v - vmin) >> sh, kmax);
             const uint32_t k0 = j == lo ? 0u : min((a[j - 1] - vmin) >> sh, kmax) + 1u;
@@ -737,9 +773,9 @@ hc_status build_directory(const uint32_t* a, uint64_t alen, const uint32_t* o, u
     if (alen < DIR_MIN || nruns_max == 0) return HC_OK;  // no run can have a directory
     void* p = nullptr;
     HC_TRY(dev_alloc(&p, alen * 8, s));
-    // warps over the runs, a few per SM resident
-    const uint64_t want = o == nullptr ? 1 : (nruns_max + 7) / 8;
-    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)num_sms() * 16));
+    // tiles of the level's positions, a few blocks per SM resident
+    const uint64_t want = (alen + DIRB_TILE - 1) / DIRB_TILE;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)num_sms() * 8));
     dir_build_kernel<<<grid, 256, 0, s>>>(a, o, nruns_max, d_nruns, (uint64_t*)p, d_err);
     if (cudaError_t le = launch_check()) {
         dev_free(p, s);
