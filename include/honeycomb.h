@@ -329,6 +329,26 @@ typedef struct {
 hc_status hc_run_join(const hc_query* q, const hc_index* const* idx, const hc_join_params* params,
                       void* stream, hc_result** out);
 
+/* Generic Join as hc_run_join in materialize mode, with the tuples delivered
+ * to host memory (Sec. 6 measures a join end to end, from the relations to
+ * all output tuples).  The search runs as up to 16 launches over consecutive
+ * ranges of its work items; after each launch its part of the output pool is
+ * compacted on the device and copied to h_tuples on a second stream while
+ * the next launch runs, so the transfer overlaps the search.
+ *   h_tuples   host, [capacity][n_vars] uint32, caller-owned; receives the
+ *              tuples (variable-id order, order of rows not fixed).  Page-
+ *              locked memory (cudaHostAlloc / cudaHostRegister) lets the
+ *              copies overlap the search; pageable memory works, slower.
+ *   capacity   rows h_tuples holds.
+ *   count_out  receives |Q|.
+ * params->mode and params->out_capacity are ignored (the device pool is sized
+ * from capacity).  Waits for the stream before returning; h_tuples is
+ * complete then.  If |Q| > capacity the call returns HC_ERR_CAPACITY with
+ * *count_out = |Q| (the rows written are then incomplete): call again with a
+ * buffer that large.  Other errors as hc_run_join. */
+hc_status hc_run_join_to_host(const hc_query* q, const hc_index* const* idx, const hc_join_params* params,
+                              uint32_t* h_tuples, uint64_t capacity, uint64_t* count_out, void* stream);
+
 /* Device memory a count-mode hc_run_join with these arguments may allocate
  * at most (bytes), for admission control; host only, enqueues nothing.  The
  * arguments are checked as hc_run_join checks them. */

@@ -389,6 +389,29 @@ def run_join(query: Query, indexes: Sequence[Index], shares: Sequence[int] | Non
         raise
 
 
+def run_join_to_host(query: Query, indexes: Sequence[Index], out: torch.Tensor, stream=None, **options) -> int:
+    """Evaluate the query with its tuples delivered into ``out``, a host
+    (n, n_vars) int32 tensor (pinned memory lets the copies overlap the
+    search), as the C ABI's hc_run_join_to_host.  Returns |Q|; raises
+    HoneycombError with status HC_ERR_CAPACITY when |Q| exceeds out's rows.
+    ``options`` as for ``run_join`` (mode is materialize)."""
+    if len(indexes) != len(query.atoms):
+        raise ValueError("one index per atom")
+    if out.is_cuda or out.dtype not in (torch.int32, torch.uint32) or out.dim() != 2 or out.shape[1] != query.n_vars:
+        raise ValueError("out: a host (n, n_vars) int32 tensor")
+    if not out.is_contiguous():
+        raise ValueError("out must be contiguous")
+    q = query._c()
+    ptr, keep = _index_array(indexes)
+    prm = _params(query, mode="materialize", **options)
+    cnt = ctypes.c_uint64()
+    _lib.check(_lib.load().hc_run_join_to_host(ctypes.byref(q), ptr, ctypes.byref(prm),
+                                               ctypes.c_void_p(out.data_ptr() if out.numel() else 0), out.shape[0],
+                                               ctypes.byref(cnt), ctypes.c_void_p(_stream_ptr(stream))),
+               "hc_run_join_to_host")
+    return int(cnt.value)
+
+
 def _params(query: Query, shares=None, seeds=None, item_grain=0, block_threads=0, merge_min=0, merge_ratio=0,
             slice_grain=0, mode="count", flags=0, out_capacity=0, lift=True, lift_arena=0,
             dir_min=0, pair_min=0) -> _lib.hc_join_params:

@@ -99,6 +99,9 @@ SIGNATURES = {
     "hc_index_from_stats": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                            ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)]),
     "hc_set_wait_limit_ns": (ctypes.c_int, [ctypes.c_uint64]),
+    "hc_run_join_to_host": (ctypes.c_int, [ctypes.POINTER(hc_query), ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.POINTER(hc_join_params), ctypes.c_void_p, ctypes.c_uint64,
+                                           ctypes.POINTER(ctypes.c_uint64), ctypes.c_void_p]),
     "hc_wait_limit_ns": (ctypes.c_uint64, []),
     "hc_build_unary_index": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_void_p)]),

@@ -424,6 +424,11 @@ hc_status hc_run_join(const hc_query* q, const hc_index* const* idx, const hc_jo
 
 hc_status hc_result_get(hc_result* r, hc_result_view* out) { return hc::result_get(r, out); }
 
+hc_status hc_run_join_to_host(const hc_query* q, const hc_index* const* idx, const hc_join_params* params,
+                              uint32_t* h_tuples, uint64_t capacity, uint64_t* count_out, void* stream) {
+    return hc::run_join_to_host_impl(q, idx, params, h_tuples, capacity, count_out, (cudaStream_t)stream);
+}
+
 hc_status hc_join_footprint(const hc_query* q, const hc_index* const* idx, const hc_join_params* params,
                             uint64_t* bytes_out) {
     return hc::join_footprint_impl(q, idx, params, bytes_out);

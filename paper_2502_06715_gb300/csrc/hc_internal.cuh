@@ -142,7 +142,7 @@ struct hc_result {
     bool done = false;
     hc::JoinCtl h_ctl{};
     std::vector<hc_partitioned*> parts;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::vector<cudaEvent_t> ev;  // timed search launches: ev[2i] before, ev[2i+1] after launch i
     int n_timed = 0;   // search launches bracketed by ev[2i], ev[2i+1]
     int n_search = 0;  // search launches of this join
 };
@@ -439,8 +439,14 @@ hc_status exclusive_scan_u64(const uint64_t* d_in, uint64_t* d_out, uint64_t n_m
                              uint32_t* d_err, cudaStream_t s);
 hc_status partitioned_sync(hc_partitioned* p);
 void result_release(hc_result* r);
+// Record the event that opens (end = false) or closes timed search launch
+// R->n_timed on s, creating it first; closing advances n_timed.
+hc_status time_mark(hc_result* R, bool end, cudaStream_t s);
+struct HostOut;
 hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_join_params* prm, cudaStream_t s,
-                        hc_result** out);
+                        hc_result** out, const HostOut* host = nullptr);
+hc_status run_join_to_host_impl(const hc_query* q, const hc_index* const* idx, const hc_join_params* prm,
+                                uint32_t* h_tuples, uint64_t capacity, uint64_t* count_out, cudaStream_t s);
 hc_status join_footprint_impl(const hc_query* q, const hc_index* const* idx, const hc_join_params* prm,
                               uint64_t* bytes);
 hc_status batch_create(const hc_query* qs, const hc_index* const* idx_flat, const hc_join_params* prm, uint32_t n,

@@ -1172,7 +1172,8 @@ __global__ void __launch_bounds__(128, (NL <= 3 ? 16 : 12)) gj_kernel(const DPla
                                                     uint64_t* __restrict__ item_counts,
                                                     const uint64_t* __restrict__ item_base, uint32_t* __restrict__ out,
                                                     int stats, uint32_t* __restrict__ chunk_fill, uint32_t n_chunks,
-                                                    uint32_t* __restrict__ arena) {
+                                                    uint32_t* __restrict__ arena, uint32_t item_lo, uint32_t item_hi,
+                                                    uint32_t* __restrict__ item_ctr) {
     __shared__ DPlan P;
     __shared__ uint32_t s_elo[4][NL][S], s_ehi[4][NL][S];  // per warp (blocks of <= 128 threads)
     __shared__ uint32_t s_obuf[MAT ? 4 : 1][MAT ? OBUF : 1];
@@ -1202,9 +1203,9 @@ __global__ void __launch_bounds__(128, (NL <= 3 ? 16 : 12)) gj_kernel(const DPla
     uint64_t total = 0;
     for (;;) {
         uint32_t item = 0;
-        if (lane == 0) item = atomicAdd(&ctl->item_ctr[pass], 1u);
+        if (lane == 0) item = item_lo + atomicAdd(item_ctr, 1u);  // items [item_lo, item_hi) of this launch
         item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= nitems) break;
+        if (item >= item_hi || item >= nitems) break;
         A.out_pos = (MAT && !A.pool) ? item_base[item] : 0;
         const uint64_t item_count =
             search_item<NL, S, O, MAT>(P, F, A, s_elo[threadIdx.x >> 5], s_ehi[threadIdx.x >> 5], item, grain, E_n, U,
@@ -1315,69 +1316,92 @@ __global__ void __launch_bounds__(128, ((NLA <= 3 && NLB <= 3) ? 16 : 12))
     }
 }
 
-// Single-pass materialize: the pool becomes the output in place.  Every
-// used chunk is full except each warp's last one, so the n_full full chunks
-// are arranged to fill chunk slots [0, n_full) and the partial chunks'
-// tuples follow them: a partial chunk below n_full (a hole) receives a full
-// chunk from slot n_full or above (a donor), k-th hole from k-th donor.
+// Single-pass materialize: the pool becomes the output in place.  A search
+// launch (a segment of the work items) fills the chunk range [cb, ce) of the
+// pool; every chunk of it is full except each warp's last one, so the n_full
+// full chunks are arranged to fill slots [cb, cb + n_full) and the partial
+// chunks' tuples follow them: a partial chunk in that prefix (a hole)
+// receives a full chunk from above it (a donor), k-th hole from k-th donor.
 // Only the partial chunks' tuples and the donors move (at most a chunk per
-// resident warp each), not the whole output.
-//   chunk_class_kernel   is_partial[c], fill of partial chunks (0 for full)
-//   (two exclusive scans: prank = partials before c, poff = their tuples)
-//   save_partials_kernel partial chunks' tuples -> tmp at poff; pslot[prank] = c
-//   move_donors_kernel   donor of rank r -> slot pslot[r]
-//   place_partials_kernel tmp -> output after the n_full full chunks
-__global__ void chunk_class_kernel(const uint32_t* __restrict__ chunk_fill, uint32_t n_used,
+// resident warp each), not the whole output.  The range comes from the device
+// (seg_mark_kernel); local chunk index i stands for chunk cb + i.
+//   seg_mark_kernel       seg = {cb, ce, ce - cb}, cb = the previous segment's ce
+//   chunk_class_kernel    is_partial[i], fill of partial chunks (0 for full)
+//   (two exclusive scans: prank = partials before i, poff = their tuples)
+//   save_partials_kernel  partial chunks' tuples -> tmp at poff; pslot[prank] = i
+//   move_donors_kernel    donor of rank r -> local slot pslot[r]
+//   place_partials_kernel tmp -> after the n_full full chunks; seg.tuples
+struct Seg {
+    uint32_t cb, ce, n, pad;
+    uint64_t tuples;  // tuples of the segment, contiguous from chunk cb after compaction
+};
+
+__global__ void seg_mark_kernel(const JoinCtl* __restrict__ ctl, uint32_t n_chunks, const Seg* __restrict__ prev,
+                                Seg* __restrict__ seg) {
+    const uint32_t cb = prev ? prev->ce : 0u;
+    const uint32_t ce = max(cb, min(ctl->chunk_ctr, n_chunks));
+    seg->cb = cb;
+    seg->ce = ce;
+    seg->n = ce - cb;
+    seg->tuples = 0;
+}
+
+__global__ void chunk_class_kernel(const uint32_t* __restrict__ chunk_fill, const Seg* __restrict__ seg,
                                    uint32_t* __restrict__ is_partial, uint32_t* __restrict__ pfill) {
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n_used; c += gridDim.x * blockDim.x) {
-        const uint32_t f = chunk_fill[c];
-        is_partial[c] = f < OUT_CHUNK ? 1u : 0u;
-        pfill[c] = f < OUT_CHUNK ? f : 0u;
+    const uint32_t cb = seg->cb, n = seg->n;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t f = chunk_fill[cb + i];
+        is_partial[i] = f < OUT_CHUNK ? 1u : 0u;
+        pfill[i] = f < OUT_CHUNK ? f : 0u;
     }
 }
 
 __global__ void save_partials_kernel(const uint32_t* __restrict__ pool, const uint32_t* __restrict__ chunk_fill,
-                                     const uint64_t* __restrict__ prank, const uint64_t* __restrict__ poff,
-                                     uint32_t n_used, uint32_t nv, uint32_t* __restrict__ tmp,
+                                     const Seg* __restrict__ seg, const uint64_t* __restrict__ prank,
+                                     const uint64_t* __restrict__ poff, uint32_t nv, uint32_t* __restrict__ tmp,
                                      uint32_t* __restrict__ pslot, const uint32_t* __restrict__ err) {
     if (dev_err_set(err)) return;  // the scans gave up a wait: their offsets are not valid
-    for (uint32_t c = blockIdx.x; c < n_used; c += gridDim.x) {
-        const uint32_t f = chunk_fill[c];
+    const uint32_t cb = seg->cb, n = seg->n;
+    for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const uint32_t f = chunk_fill[cb + i];
         if (f >= OUT_CHUNK) continue;
-        if (threadIdx.x == 0) pslot[prank[c]] = c;
+        if (threadIdx.x == 0) pslot[prank[i]] = i;
         const uint64_t words = (uint64_t)f * nv;
-        const uint32_t* src = pool + (uint64_t)c * OUT_CHUNK * nv;
-        uint32_t* dst = tmp + poff[c] * nv;
-        for (uint64_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+        const uint32_t* src = pool + (uint64_t)(cb + i) * OUT_CHUNK * nv;
+        uint32_t* dst = tmp + poff[i] * nv;
+        for (uint64_t w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
     }
 }
 
 __global__ void move_donors_kernel(uint32_t* __restrict__ pool, const uint32_t* __restrict__ chunk_fill,
-                                   const uint64_t* __restrict__ prank, const uint32_t* __restrict__ pslot,
-                                   uint32_t n_used, uint32_t nv, const uint32_t* __restrict__ err) {
+                                   const Seg* __restrict__ seg, const uint64_t* __restrict__ prank,
+                                   const uint32_t* __restrict__ pslot, uint32_t nv, const uint32_t* __restrict__ err) {
     if (dev_err_set(err)) return;
-    const uint32_t n_full = n_used - (uint32_t)prank[n_used];
-    for (uint32_t c = n_full + blockIdx.x; c < n_used; c += gridDim.x) {
-        if (chunk_fill[c] < OUT_CHUNK) continue;
-        // full chunks in [n_full, c), i.e. this donor's rank among donors
-        const uint64_t r = (uint64_t)(c - n_full) - (prank[c] - prank[n_full]);
-        const uint32_t dst_slot = pslot[r];  // the r-th partial chunk overall, a hole (below n_full)
-        const uint4* src = reinterpret_cast<const uint4*>(pool + (uint64_t)c * OUT_CHUNK * nv);
+    const uint32_t cb = seg->cb, n = seg->n;
+    const uint32_t n_full = n - (uint32_t)prank[n];
+    for (uint32_t i = n_full + blockIdx.x; i < n; i += gridDim.x) {
+        if (chunk_fill[cb + i] < OUT_CHUNK) continue;
+        // full chunks in [n_full, i), i.e. this donor's rank among donors
+        const uint64_t r = (uint64_t)(i - n_full) - (prank[i] - prank[n_full]);
+        const uint32_t dst_slot = cb + pslot[r];  // the r-th partial chunk of the segment, a hole
+        const uint4* src = reinterpret_cast<const uint4*>(pool + (uint64_t)(cb + i) * OUT_CHUNK * nv);
         uint4* dst = reinterpret_cast<uint4*>(pool + (uint64_t)dst_slot * OUT_CHUNK * nv);
         const uint32_t vecs = OUT_CHUNK * nv / 4;  // a chunk is a multiple of 16 bytes
-        for (uint32_t i = threadIdx.x; i < vecs; i += blockDim.x) dst[i] = src[i];
+        for (uint32_t w = threadIdx.x; w < vecs; w += blockDim.x) dst[w] = src[w];
     }
 }
 
 __global__ void place_partials_kernel(uint32_t* __restrict__ pool, const uint32_t* __restrict__ tmp,
-                                      const uint64_t* __restrict__ prank, const uint64_t* __restrict__ poff,
-                                      uint32_t n_used, uint32_t nv, const uint32_t* __restrict__ err) {
+                                      Seg* __restrict__ seg, const uint64_t* __restrict__ prank,
+                                      const uint64_t* __restrict__ poff, uint32_t nv, const uint32_t* __restrict__ err) {
     if (dev_err_set(err)) return;
-    const uint32_t n_full = n_used - (uint32_t)prank[n_used];
-    const uint64_t words = poff[n_used] * nv;
-    uint32_t* dst = pool + (uint64_t)n_full * OUT_CHUNK * nv;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < words; i += (uint64_t)gridDim.x * blockDim.x)
-        dst[i] = tmp[i];
+    const uint32_t cb = seg->cb, n = seg->n;
+    const uint32_t n_full = n - (uint32_t)prank[n];
+    const uint64_t words = poff[n] * nv;
+    uint32_t* dst = pool + (uint64_t)(cb + n_full) * OUT_CHUNK * nv;
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < words; w += (uint64_t)gridDim.x * blockDim.x)
+        dst[w] = tmp[w];
+    if (blockIdx.x == 0 && threadIdx.x == 0) seg->tuples = (uint64_t)n_full * OUT_CHUNK + poff[n];
 }
 
 // Search kernels are compiled for NL = 2..5 loops and for S (lists per
@@ -1407,21 +1431,28 @@ struct GjArgs {
     uint32_t* chunk_fill;
     uint32_t n_chunks;
     uint32_t* arena;  // lifted lists, P.arena_words per warp of the launch
+    // work items [item_lo, item_hi) taken through item_ctr (NULL: the join's
+    // counter of the pass, all items)
+    uint32_t item_lo = 0, item_hi = 0xFFFFFFFFu;
+    uint32_t* item_ctr = nullptr;
 };
 
 template <int NL, int S, int O>
 hc_status launch_gj(bool mat, const GjArgs& g, cudaStream_t s) {
     const int grid = gj_grid<NL, S, O>(mat, g.threads);
+    uint32_t* ctr = g.item_ctr ? g.item_ctr : &g.ctl->item_ctr[g.pass];
     if (mat)
         gj_kernel<NL, S, O, true><<<grid, g.threads, 0, s>>>(g.plan, g.e_cell, g.e_x, g.e_rng, g.e_split, g.uoff,
                                                              g.grain, g.ctl,
                                                              g.pass, g.cell_counts, g.item_counts, g.item_base, g.out,
-                                                             g.stats, g.chunk_fill, g.n_chunks, g.arena);
+                                                             g.stats, g.chunk_fill, g.n_chunks, g.arena, g.item_lo,
+                                                             g.item_hi, ctr);
     else
         gj_kernel<NL, S, O, false><<<grid, g.threads, 0, s>>>(g.plan, g.e_cell, g.e_x, g.e_rng, g.e_split, g.uoff,
                                                               g.grain,
                                                               g.ctl, g.pass, g.cell_counts, g.item_counts, g.item_base,
-                                                              g.out, g.stats, g.chunk_fill, g.n_chunks, g.arena);
+                                                              g.out, g.stats, g.chunk_fill, g.n_chunks, g.arena,
+                                                              g.item_lo, g.item_hi, ctr);
     HC_CUDA_TRY(launch_check());
     return HC_OK;
 }
@@ -1504,6 +1535,15 @@ void result_release(hc_result* r) {
     for (auto& e : r->ev)
         if (e) cudaEventDestroy(e);
     delete r;
+}
+
+hc_status time_mark(hc_result* R, bool end, cudaStream_t s) {
+    const size_t i = 2 * (size_t)R->n_timed + (end ? 1 : 0);
+    if (R->ev.size() <= i) R->ev.resize(i + 1, nullptr);
+    if (!R->ev[i]) HC_CUDA_TRY(cudaEventCreate(&R->ev[i]));
+    HC_CUDA_TRY(cudaEventRecord(R->ev[i], s));
+    if (end) R->n_timed++;
+    return HC_OK;
 }
 
 hc_status result_get(hc_result* R, hc_result_view* v) {
@@ -1847,8 +1887,50 @@ hc_status join_footprint_impl(const hc_query* q, const hc_index* const* idx, con
     return HC_OK;
 }
 
+// Host delivery of a materialized result (hc_run_join_to_host).
+struct HostOut {
+    uint32_t* h_tuples;
+    uint64_t capacity;
+    uint64_t* count_out;
+};
+
+// Search launches of a host-delivered join (consecutive item ranges).
+constexpr uint64_t HOST_SEGMENTS = 16;
+
+// Per-call host side of the segments: a stream for the copies to the host,
+// one event per segment, and pinned host copies of the segments' ranges.
+struct HostSegs {
+    cudaStream_t copy = nullptr;
+    std::vector<cudaEvent_t> ev;
+    Seg* h = nullptr;
+    ~HostSegs() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (copy) cudaStreamDestroy(copy);
+        if (h) cudaFreeHost(h);
+    }
+    hc_status init(uint32_t n) {
+        HC_CUDA_TRY(cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking));
+        HC_CUDA_TRY(cudaMallocHost((void**)&h, n * sizeof(Seg)));
+        ev.assign(n, nullptr);
+        for (auto& e : ev) HC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        return HC_OK;
+    }
+    // after segment k's compaction on s: its range to the host, then the event
+    hc_status mark(uint32_t k, const Seg* d, cudaStream_t s) {
+        HC_CUDA_TRY(cudaMemcpyAsync(h + k, d, sizeof(Seg), cudaMemcpyDeviceToHost, s));
+        HC_CUDA_TRY(cudaEventRecord(ev[k], s));
+        return HC_OK;
+    }
+    hc_status wait(uint32_t k, Seg* out) {
+        HC_CUDA_TRY(cudaEventSynchronize(ev[k]));
+        *out = h[k];
+        return HC_OK;
+    }
+};
+
 hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_join_params* prm, cudaStream_t s,
-                        hc_result** out) {
+                        hc_result** out, const HostOut* host) {
     if (!out) return fail(HC_ERR_ARG, "run_join: out is NULL");
     *out = nullptr;
     QueryPlan qp;
@@ -1897,21 +1979,15 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
         if ((st = tmp.get(&g.arena, aw)) != HC_OK) return bail(st);
     }
     const bool timed = (prm->flags & HC_FLAG_TIME_KERNELS) != 0;
-    if (timed)
-        for (auto& e : R->ev)
-            if (cudaEventCreate(&e) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "cudaEventCreate"));
     // one search launch, bracketed by events when timed
     auto search = [&](bool mat) -> hc_status {
-        if (timed && cudaEventRecord(R->ev[2 * R->n_timed], s) != cudaSuccess) return cuda_fail(cudaGetLastError(), "event");
+        if (timed) HC_TRY(time_mark(R, false, s));
         HC_TRY(launch_any(nv, shape_s, shape_o, mat, g, s));
         R->n_search++;
-        if (timed) {
-            if (cudaEventRecord(R->ev[2 * R->n_timed + 1], s) != cudaSuccess) return cuda_fail(cudaGetLastError(), "event");
-            R->n_timed++;
-        }
+        if (timed) HC_TRY(time_mark(R, true, s));
         return HC_OK;
     };
-    if (prm->mode == HC_MODE_COUNT) {
+    if (prm->mode == HC_MODE_COUNT && !host) {
         if ((st = search(false)) != HC_OK) return bail(st);
         *out = R;
         return HC_OK;
@@ -1930,69 +2006,105 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     g.item_counts = item_counts;
     uint64_t total = 0;
     bool written = false;
-    if (prm->out_capacity > 0) {
-        // single pass into pool chunks; the slack covers every warp's last,
-        // partly filled chunk
+    if (prm->out_capacity > 0 || host) {
+        // single pass into pool chunks, in nseg search launches over
+        // consecutive item ranges, each followed by the in-place compaction
+        // of the chunks it filled; the slack covers every warp's last, partly
+        // filled chunk of every launch
         const uint64_t warps = (uint64_t)gj_grid_any(nv, shape_s, shape_o, true, threads) * (threads / 32);
-        const uint64_t n_chunks64 = (prm->out_capacity + OUT_CHUNK - 1) / OUT_CHUNK + warps;
-        if (n_chunks64 >= 0xFFFFFFFFull) return bail(fail(HC_ERR_CAPACITY, "run_join: out_capacity too large"));
+        const uint32_t nseg =
+            host ? (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(HOST_SEGMENTS, nitems / 64)) : 1u;
+        const uint64_t cap = host ? host->capacity : prm->out_capacity;
+        const uint64_t n_chunks64 = (cap + OUT_CHUNK - 1) / OUT_CHUNK + (uint64_t)nseg * warps;
+        if (n_chunks64 >= 0xFFFFFFFFull) return bail(fail(HC_ERR_CAPACITY, "run_join: output capacity too large"));
         const uint32_t n_chunks = (uint32_t)n_chunks64;
-        uint32_t *pool = nullptr, *chunk_fill;
+        uint32_t *pool = nullptr, *chunk_fill, *is_partial, *pfill, *pslot, *ptmp, *seg_ctr;
+        uint64_t *prank, *poff;
+        Seg* d_seg;
         {
             void* pp;
             if (dev_alloc(&pp, (size_t)n_chunks * OUT_CHUNK * nv * 4, s) != HC_OK) return bail(HC_ERR_OOM);
             pool = (uint32_t*)pp;
         }
-        if ((st = tmp.get(&chunk_fill, n_chunks)) != HC_OK) {
+        auto bail_pool = [&](hc_status e) {
             dev_free(pool, s);
-            return bail(st);
-        }
+            return bail(e);
+        };
+        if ((st = tmp.get(&chunk_fill, n_chunks)) != HC_OK || (st = tmp.get(&is_partial, n_chunks)) != HC_OK ||
+            (st = tmp.get(&pfill, n_chunks)) != HC_OK || (st = tmp.get(&prank, (size_t)n_chunks + 1)) != HC_OK ||
+            (st = tmp.get(&poff, (size_t)n_chunks + 1)) != HC_OK || (st = tmp.get(&pslot, warps + 1)) != HC_OK ||
+            (st = tmp.get(&ptmp, (size_t)warps * OUT_CHUNK * nv)) != HC_OK || (st = tmp.get(&d_seg, nseg)) != HC_OK ||
+            (st = tmp.get(&seg_ctr, nseg)) != HC_OK)
+            return bail_pool(st);
+        if (cudaMemsetAsync(seg_ctr, 0, nseg * sizeof(uint32_t), s) != cudaSuccess)
+            return bail_pool(cuda_fail(cudaGetLastError(), "memset"));
+        HostSegs hs;
+        if (host && (st = hs.init(nseg)) != HC_OK) return bail_pool(st);
         g.out = pool;
         g.chunk_fill = chunk_fill;
         g.n_chunks = n_chunks;
-        st = search(true);
-        if (st == HC_OK) st = read_ctl(R);
-        if (st != HC_OK) {
-            dev_free(pool, s);
-            return bail(st);
+        const unsigned cgrid = std::min<uint32_t>((n_chunks + 255) / 256, (uint32_t)num_sms() * 8);
+        const unsigned bgrid = std::min<uint32_t>(n_chunks, (uint32_t)num_sms() * 16);
+        for (uint32_t k = 0; k < nseg; ++k) {
+            g.item_lo = (uint32_t)(nitems * k / nseg);
+            g.item_hi = (uint32_t)(nitems * (k + 1) / nseg);
+            g.item_ctr = seg_ctr + k;
+            if ((st = search(true)) != HC_OK) return bail_pool(st);
+            Seg* sk = d_seg + k;
+            seg_mark_kernel<<<1, 1, 0, s>>>(ctl, n_chunks, k ? d_seg + k - 1 : nullptr, sk);
+            if (cudaError_t le = launch_check()) return bail_pool(cuda_fail(le, "seg_mark_kernel"));
+            chunk_class_kernel<<<cgrid, 256, 0, s>>>(chunk_fill, sk, is_partial, pfill);
+            if (cudaError_t le = launch_check()) return bail_pool(cuda_fail(le, "chunk_class_kernel"));
+            if ((st = exclusive_scan_u32_to_u64(is_partial, prank, n_chunks, &sk->n, &ctl->err, s)) != HC_OK ||
+                (st = exclusive_scan_u32_to_u64(pfill, poff, n_chunks, &sk->n, &ctl->err, s)) != HC_OK)
+                return bail_pool(st);
+            save_partials_kernel<<<bgrid, 256, 0, s>>>(pool, chunk_fill, sk, prank, poff, (uint32_t)nv, ptmp, pslot,
+                                                       &ctl->err);
+            if (cudaError_t le = launch_check()) return bail_pool(cuda_fail(le, "save_partials_kernel"));
+            move_donors_kernel<<<bgrid, 256, 0, s>>>(pool, chunk_fill, sk, prank, pslot, (uint32_t)nv, &ctl->err);
+            if (cudaError_t le = launch_check()) return bail_pool(cuda_fail(le, "move_donors_kernel"));
+            place_partials_kernel<<<(unsigned)num_sms() * 4, 256, 0, s>>>(pool, ptmp, sk, prank, poff, (uint32_t)nv,
+                                                                          &ctl->err);
+            if (cudaError_t le = launch_check()) return bail_pool(cuda_fail(le, "place_partials_kernel"));
+            if (host && (st = hs.mark(k, sk, s)) != HC_OK) return bail_pool(st);
         }
+        if (host) {
+            // each segment's tuples go to the host as soon as its compaction is
+            // done, on a second stream, while later segments run
+            uint64_t off = 0;
+            bool room = true;
+            for (uint32_t k = 0; k < nseg; ++k) {
+                Seg sk;
+                if ((st = hs.wait(k, &sk)) != HC_OK) return bail_pool(st);
+                if (off + sk.tuples > host->capacity) room = false;
+                if (room && sk.tuples > 0 &&
+                    cudaMemcpyAsync(host->h_tuples + off * nv, pool + (uint64_t)sk.cb * OUT_CHUNK * nv,
+                                    sk.tuples * nv * 4, cudaMemcpyDeviceToHost, hs.copy) != cudaSuccess)
+                    return bail_pool(cuda_fail(cudaGetLastError(), "result copy to host"));
+                off += sk.tuples;
+            }
+            if (cudaStreamSynchronize(hs.copy) != cudaSuccess) return bail_pool(cuda_fail(cudaGetLastError(), "copy"));
+            if ((st = read_ctl(R)) != HC_OK) return bail_pool(st);
+            *host->count_out = R->h_ctl.total;
+            dev_free(pool, s);
+            result_release(R);
+            if (!room || off != *host->count_out)
+                return fail(HC_ERR_CAPACITY, "run_join_to_host: " + std::to_string(*host->count_out) +
+                                                 " tuples do not fit a host buffer of " +
+                                                 std::to_string(host->capacity));
+            return HC_OK;
+        }
+        st = read_ctl(R);
+        if (st != HC_OK) return bail_pool(st);
         total = R->h_ctl.total;
         if (!R->h_ctl.overflow) {
-            // the pool becomes the result; compact it in place (see chunk_class_kernel)
-            R->d_tuples = pool;
-            const uint32_t n_used = std::min<uint32_t>(R->h_ctl.chunk_ctr, n_chunks);
-            if (n_used > 0) {
-                uint32_t *is_partial, *pfill, *pslot, *ptmp;
-                uint64_t *prank, *poff;
-                if ((st = tmp.get(&is_partial, n_used)) != HC_OK || (st = tmp.get(&pfill, n_used)) != HC_OK ||
-                    (st = tmp.get(&prank, (size_t)n_used + 1)) != HC_OK ||
-                    (st = tmp.get(&poff, (size_t)n_used + 1)) != HC_OK ||
-                    (st = tmp.get(&pslot, std::min<uint64_t>(n_used, warps) + 1)) != HC_OK ||
-                    (st = tmp.get(&ptmp, (size_t)std::min<uint64_t>(n_used, warps) * OUT_CHUNK * nv)) != HC_OK)
-                    return bail(st);
-                const unsigned cgrid = std::min<uint32_t>((n_used + 255) / 256, (uint32_t)num_sms() * 8);
-                chunk_class_kernel<<<cgrid, 256, 0, s>>>(chunk_fill, n_used, is_partial, pfill);
-                if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "chunk_class_kernel"));
-                if ((st = exclusive_scan_u32_to_u64(is_partial, prank, n_used, nullptr, &ctl->err, s)) != HC_OK ||
-                    (st = exclusive_scan_u32_to_u64(pfill, poff, n_used, nullptr, &ctl->err, s)) != HC_OK)
-                    return bail(st);
-                const unsigned bgrid = std::min<uint32_t>(n_used, (uint32_t)num_sms() * 16);
-                save_partials_kernel<<<bgrid, 256, 0, s>>>(pool, chunk_fill, prank, poff, n_used, (uint32_t)nv,
-                                                           ptmp, pslot, &ctl->err);
-                if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "save_partials_kernel"));
-                move_donors_kernel<<<bgrid, 256, 0, s>>>(pool, chunk_fill, prank, pslot, n_used, (uint32_t)nv,
-                                                         &ctl->err);
-                if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "move_donors_kernel"));
-                place_partials_kernel<<<(unsigned)num_sms() * 4, 256, 0, s>>>(pool, ptmp, prank, poff, n_used,
-                                                                              (uint32_t)nv, &ctl->err);
-                if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "place_partials_kernel"));
-            }
+            R->d_tuples = pool;  // compacted in place: tuples [0, total) from chunk 0
             written = true;
         } else {
+            // on overflow the item counts of the single pass place the tuples
+            // of a second, deterministic emitting pass
             dev_free(pool, s);
         }
-        // on overflow the item counts of the single pass place the tuples of a
-        // second, deterministic emitting pass
     } else {
         if ((st = search(false)) != HC_OK) return bail(st);
     }
@@ -2023,6 +2135,15 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     R->materialized = true;
     *out = R;
     return HC_OK;
+}
+
+hc_status run_join_to_host_impl(const hc_query* q, const hc_index* const* idx, const hc_join_params* prm,
+                                uint32_t* h_tuples, uint64_t capacity, uint64_t* count_out, cudaStream_t s) {
+    if (!count_out || (capacity > 0 && !h_tuples)) return fail(HC_ERR_ARG, "run_join_to_host: NULL argument");
+    *count_out = 0;
+    HostOut host{h_tuples, capacity, count_out};
+    hc_result* R = nullptr;
+    return run_join_impl(q, idx, prm, s, &R, &host);
 }
 
 // -------------------------------------------------------------- batches

@@ -1082,10 +1082,6 @@ hc_status run_kjoin_impl(const hc_kquery* q, const hc_kindex* const* idx, const 
     JoinCtl* ctl = R->d_ctl;
     if (cudaMemsetAsync(ctl, 0, sizeof(JoinCtl), s) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
     const bool timed = (dp.flags & HC_FLAG_TIME_KERNELS) != 0;
-    if (timed) {
-        for (auto& e : R->ev)
-            if (cudaEventCreate(&e) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "cudaEventCreate"));
-    }
 
     KScratch tmp(s);
     hc_status st;
@@ -1099,7 +1095,7 @@ hc_status run_kjoin_impl(const hc_kquery* q, const hc_kindex* const* idx, const 
     uint64_t* unit_off = nullptr;
     const unsigned l0_grid = (unsigned)((len0 + 255) / 256);
     auto search = [&](bool mat, uint32_t* tup, uint64_t cap) -> hc_status {
-        if (timed) cudaEventRecord(R->ev[2 * R->n_timed], s);
+        if (timed) HC_TRY(time_mark(R, false, s));
         if (nv == 1) {
             if (mat)
                 kloop0_kernel<true><<<l0_grid, 256, 0, s>>>(dP, nullptr, nullptr, ctl, tup, cap);
@@ -1111,10 +1107,7 @@ hc_status run_kjoin_impl(const hc_kquery* q, const hc_kindex* const* idx, const 
         } else {
             HC_TRY(launch_kjoin<false>((int)nv, threads, dP, entries, unit_off, ctl, dp.item_grain, nullptr, 0, s));
         }
-        if (timed) {
-            cudaEventRecord(R->ev[2 * R->n_timed + 1], s);
-            R->n_timed++;
-        }
+        if (timed) HC_TRY(time_mark(R, true, s));
         R->n_search++;
         return HC_OK;
     };
