@@ -52,14 +52,15 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--mode", choices=["materialize", "count"], default="materialize")
     ap.add_argument("--workload", choices=["triangle", "clique4", "cycle4", "batched", "serve", "build", "order",
-                                           "lw", "ct"],
+                                           "lw", "ct", "skew"],
                     default="triangle",
                     help="triangle: R-MAT triangle (default line); clique4 / cycle4: R-MAT 4-clique / 4-cycle "
                          "counts; batched: 512 triangle/4-clique queries on induced subgraphs in one launch; "
                          "serve: continuous-batching server; build: CoCo index build of R-MAT E+; "
                          "order: 4-clique under every loop order beside the cost model's choice; "
                          "lw / ct: Loomis-Whitney / Clover-Triangle counts over ST-Dense's or ST-Sparse's "
-                         "ternary relations")
+                         "ternary relations; skew: per-cell work and time of the R-MAT triangle under the "
+                         "paper's share vectors (Sec. 1, Examples 1-3)")
     ap.add_argument("--lw-n", type=int, default=512, help="lw: cube side n of ST-Dense's [n]^3 relations")
     ap.add_argument("--tensor", choices=["dense", "sparse"], default="dense",
                     help="lw / ct: ST-Dense or ST-Sparse relations")
@@ -251,7 +252,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if a.scale is None:
         a.scale = {"triangle": 22, "clique4": 20, "cycle4": 20, "batched": 21, "serve": 23, "build": 22,
-                   "order": 18, "lw": 0, "ct": 0}[a.workload]
+                   "order": 18, "lw": 0, "ct": 0, "skew": 22}[a.workload]
     if a.impl == "reference":
         return reference_arm(a, world, rank)
     if a.workload == "serve":
@@ -262,6 +263,8 @@ def main():
         return kary_workload(a, world, rank, local)
     if a.workload == "order":
         return order_workload(a, world, rank, local)
+    if a.workload == "skew":
+        return skew_workload(a, world, rank, local)
     if a.workload != "triangle":
         return other_workload(a, world, rank, local)
 
@@ -659,6 +662,12 @@ def order_workload(a, world, rank, local):
     cnt = counts.pop()
     key = "".join("XYZU"[v] for v in chosen)
     ranked = sorted(times, key=times.get)
+    # the order chosen by measurement among the cost model's best four
+    from paper_2502_06715_gb300.autotune import Tuner, ranked_orders
+
+    tuned, tuned_ms = Tuner(reps=a.steps).tune_order(q, lambda j, ao: ix[ao], top_k=4)
+    tkey = "".join("XYZU"[v] for v in tuned)
+    model_rank = ["".join("XYZU"[v] for v in o) for o in ranked_orders(q, [ix[0]] * len(q.atoms))]
     if rank == 0:
         line = {"metric": "join output tuples/s (R-MAT 4-clique, order chosen by the cost model)",
                 "value": cnt / (times[key] / 1e3), "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -667,11 +676,66 @@ def order_workload(a, world, rank, local):
                 "config": {"workload": f"4-clique on E+ of R-MAT scale {a.scale} ef {a.edge_factor}, count, shares 1, "
                                        f"every loop order (search kernel time, best of {a.steps})",
                            "tuples": cnt, "chosen_order": key, "chosen_rank": ranked.index(key) + 1,
+                           "measured_choice": {"order": tkey, "rank": ranked.index(tkey) + 1,
+                                               "ms": times[tkey],
+                                               "tried": {"".join("XYZU"[v] for v in o): round(m, 2)
+                                                         for o, m in tuned_ms.items()}},
+                           "cost_model_ranking": model_rank,
                            "orders": len(times), "best_order": ranked[0], "best_ms": times[ranked[0]],
                            "worst_order": ranked[-1], "worst_ms": times[ranked[-1]], "ms_by_order": times,
                            "generate_s": round(gen_s, 1)},
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
+
+
+def skew_workload(a, world, rank, local):
+    """The paper's share study (Sec. 1, Examples 1-3: the triangle at 4096x1x1,
+    16x16x16 and 64x64x1 cells, each cell a thread of work) on this GPU: for
+    each share vector, the search kernel's time (count mode) and, per cell,
+    its work units and the SM cycles its warps spent on it.  Skew is the
+    largest cell over the mean cell (of cycles, and of work).  One JSON line
+    per share vector."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2502_06715_gb300 as hc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ep, gen_s = make_graph(a, rank, device=f"cuda:{local}")
+    d = torch.from_numpy(ep.view(np.int32)).to(dev)
+    ix = hc.build_index(d, 0)
+    q = hc.TRIANGLE
+    knobs = {"item_grain": a.grain or 64, "merge_min": 0xFFFFFFFF, "merge_ratio": 1}
+    for sh in ([1, 1, 1], [64, 1, 1], [4096, 1, 1], [16, 16, 16], [64, 64, 1]):
+        for _ in range(max(1, a.warmup)):
+            hc.run_join(q, [ix] * 3, shares=sh, **knobs)
+        ms = []
+        for _ in range(max(1, a.steps)):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = hc.run_join(q, [ix] * 3, shares=sh, time_kernels=True, **knobs)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append((e0.elapsed_time(e1), r.ms_join_kernel))
+        prof = hc.run_join(q, [ix] * 3, shares=sh, cell_profile=True, **knobs).cell_profile.cpu().numpy()
+        work, cyc = prof[:, 0].astype(np.float64), prof[:, 1].astype(np.float64)
+        line = {"metric": "per-cell skew (triangle)", "workload": workload_name(a).replace("; materialize", ""),
+                "shares": sh, "cells": int(prof.shape[0]), "count": r.count,
+                "join_ms": round(statistics.median(m[0] for m in ms), 3),
+                "search_ms": round(statistics.median(m[1] for m in ms), 3),
+                "cycles_sum": float(cyc.sum()), "cycles_max_cell": float(cyc.max()),
+                "cycle_skew_max_over_mean": round(float(cyc.max() / max(cyc.mean(), 1.0)), 2),
+                "work_sum": float(work.sum()), "work_max_cell": float(work.max()),
+                "work_skew_max_over_mean": round(float(work.max() / max(work.mean(), 1.0)), 2),
+                "note": "cycles: SM clock cycles of the warps' work items of each cell, summed (the analogue of "
+                        "a thread's time); the join itself runs every cell's items on all SMs at once"}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
 
 
 def build_workload(a, world, rank, local):

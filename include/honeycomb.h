@@ -262,6 +262,13 @@ hc_status hc_plan_cost(const hc_query* q, const hc_index* const* idx, const uint
 #define HC_FLAG_CELL_COUNTS 1u /* also return the count of each HyperCube cell        */
 #define HC_FLAG_STATS 2u       /* also return the intersection work counter           */
 #define HC_FLAG_TIME_KERNELS 4u /* time the search kernel launches with device events  */
+/* Per-cell profile (the skew study of Sec. 1, Examples 1-3, where each
+ * HyperCube cell is a thread of work): for every cell, its work units (the
+ * HC_FLAG_STATS counter restricted to the cell's bindings) and the SM clock
+ * cycles the warps spent on its work items (clock64 spans, summed; the
+ * analogue of a thread's time).  Implies HC_FLAG_STATS (so no query
+ * rewriting); the first search pass records it. */
+#define HC_FLAG_CELL_PROFILE 16u
 /* Query rewriting (Sec. 5.1) is on by default for queries of 4+ variables
  * whose last loop has two or more lists fixed before the loop above it (the
  * 4-clique's R3[y] and R6[x] under order X,Y,Z,U): their intersection is
@@ -367,6 +374,8 @@ typedef struct {
     float ms_join_kernel;       /* with HC_FLAG_TIME_KERNELS: device time of the search */
                                 /* kernel launches (CUDA events on the join's stream)  */
     uint32_t n_join_launches;   /* search kernel launches of this join (1 or 2)         */
+    const uint64_t* d_cell_profile; /* [n_cells][2] (work units, SM cycles) with           */
+                                /* HC_FLAG_CELL_PROFILE, else NULL                      */
 } hc_result_view;
 /* Waits for the result's stream, then fills `out`. */
 hc_status hc_result_get(hc_result* r, hc_result_view* out);

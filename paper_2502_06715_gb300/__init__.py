@@ -319,6 +319,7 @@ class Result:
     n_join_launches: int = 0
     tuples: torch.Tensor | None = None
     cell_counts: torch.Tensor | None = None
+    cell_profile: torch.Tensor | None = None  # (n_cells, 2) int64: work units, SM cycles
     _handle: object = field(default=None, repr=False)
 
 
@@ -327,7 +328,7 @@ def run_join(query: Query, indexes: Sequence[Index], shares: Sequence[int] | Non
              stats: bool = False, item_grain: int = 0, block_threads: int = 0, stream=None,
              keep_device: bool = False, time_kernels: bool = False, merge_min: int = 0,
              merge_ratio: int = 0, out_capacity: int = 0, slice_grain: int = 0, lift: bool = True,
-             lift_arena: int = 0, dir_min: int = 0, pair_min: int = 0) -> Result:
+             lift_arena: int = 0, dir_min: int = 0, pair_min: int = 0, cell_profile: bool = False) -> Result:
     """Evaluate the query.  Tuples (materialize) come back as an
     (count, n_vars) int32 CUDA tensor in variable-id order (a copy, unless
     ``keep_device`` keeps an alias of library memory tied to the result).
@@ -335,6 +336,8 @@ def run_join(query: Query, indexes: Sequence[Index], shares: Sequence[int] | Non
     ``lift_arena`` sets its device scratch, in words per warp (0: default).
     ``dir_min``: list searches in runs at least this long read the run's
     bucket directory first (0: 16; 0xFFFFFFFF: plain binary search).
+    ``cell_profile``: per-cell work units and SM cycles of the warps' work on
+    the cell (the skew study of Sec. 1; implies ``stats``).
     ``pair_min``: last-loop bindings whose shorter list has at least this many
     values are searched by the whole warp (0: 32; 0xFFFFFFFF: never)."""
     if len(indexes) != len(query.atoms):
@@ -351,7 +354,8 @@ def run_join(query: Query, indexes: Sequence[Index], shares: Sequence[int] | Non
         raise ValueError("mode is 'count' or 'materialize'")
     prm.mode = _lib.HC_MODE_COUNT if mode == "count" else _lib.HC_MODE_MATERIALIZE
     prm.flags = ((_lib.HC_FLAG_CELL_COUNTS if cell_counts else 0) | (_lib.HC_FLAG_STATS if stats else 0)
-                 | (_lib.HC_FLAG_TIME_KERNELS if time_kernels else 0) | (0 if lift else _lib.HC_FLAG_NO_LIFT))
+                 | (_lib.HC_FLAG_TIME_KERNELS if time_kernels else 0) | (0 if lift else _lib.HC_FLAG_NO_LIFT)
+                 | (_lib.HC_FLAG_CELL_PROFILE if cell_profile else 0))
     prm.lift_arena = int(lift_arena)
     prm.item_grain = item_grain
     prm.block_threads = block_threads
@@ -378,6 +382,9 @@ def run_join(query: Query, indexes: Sequence[Index], shares: Sequence[int] | Non
         if v.d_cell_counts:
             c = _alias(v.d_cell_counts, (v.n_cells,), torch.int64, holder)
             res.cell_counts = c if keep_device else c.clone()
+        if v.d_cell_profile:
+            c = _alias(v.d_cell_profile, (v.n_cells, 2), torch.int64, holder)
+            res.cell_profile = c if keep_device else c.clone()
         if keep_device:
             res._handle = holder
         else:

@@ -22,6 +22,7 @@ HC_FLAG_CELL_COUNTS = 1
 HC_FLAG_STATS = 2
 HC_FLAG_TIME_KERNELS = 4
 HC_FLAG_NO_LIFT = 8
+HC_FLAG_CELL_PROFILE = 16
 HC_BUILD_CHECK_DUPLICATES = 1
 HC_BUILD_TIME_KERNELS = 2
 HC_BUILD_TEST_STALL_SORT = 0x100
@@ -68,7 +69,7 @@ class hc_result_view(ctypes.Structure):
     _fields_ = [("count", ctypes.c_uint64), ("n_tuples", ctypes.c_uint64), ("d_tuples", ctypes.c_void_p),
                 ("n_cells", ctypes.c_uint64), ("d_cell_counts", ctypes.c_void_p), ("work", ctypes.c_uint64),
                 ("n_items", ctypes.c_uint64), ("ms_join_kernel", ctypes.c_float),
-                ("n_join_launches", ctypes.c_uint32)]
+                ("n_join_launches", ctypes.c_uint32), ("d_cell_profile", ctypes.c_void_p)]
 
 
 class hc_kindex_view(ctypes.Structure):

@@ -13,6 +13,11 @@ hand and keeps the fastest configuration, searching one knob at a time
                 length ratio) or never;
   slice_grain   loop-3 candidates per slice of a hub (queries of 4+ loops).
 
+The loop order is chosen the same way (``Tuner.tune_order``): the paper's
+plan decision (Sec. 5.3) ranks orders by its cost estimate; here the cost
+model's best few orders are timed on the data at hand and the fastest kept,
+because the estimate does not see list-length skew or the GPU's search paths.
+
 Results are cached per (query shape, log2 size bucket, mode) in memory and,
 if a path is given, in a JSON file.  Tuning launches run in count mode; for
 a materializing run the merge knobs are then re-chosen with materializing
@@ -21,6 +26,7 @@ them and moves the best threshold.
 """
 from __future__ import annotations
 
+import itertools
 import json
 import math
 import os
@@ -29,7 +35,7 @@ from dataclasses import dataclass, field
 
 import torch
 
-from . import Query, choose_shares, run_join
+from . import Query, choose_shares, plan_cost, run_join
 
 MERGE_OFF = 0xFFFFFFFF
 
@@ -96,6 +102,19 @@ def share_candidates(query: Query, indexes, P_list=(64, 256, 1024), min_cells: i
     return uniq
 
 
+def ranked_orders(query: Query, indexes) -> list:
+    """Every loop order of the query, cheapest first by the Sec. 5.2 estimate
+    with all shares 1 (the sum over loops of Lemma "cost-ub"'s bound); ties
+    keep the lexicographic order.  The estimate reads only the indexes' sizes,
+    whatever their attribute order."""
+    ranked = []
+    for order in itertools.permutations(range(query.n_vars)):
+        c = plan_cost(query.with_order(order), indexes, [1] * query.n_vars)
+        ranked.append((sum(c["level_cost"]), order))
+    ranked.sort(key=lambda t: t[0])
+    return [o for _, o in ranked]
+
+
 @dataclass
 class Tuner:
     path: str | None = None
@@ -112,6 +131,27 @@ class Tuner:
             os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
             with open(self.path, "w") as f:
                 json.dump(self.cache, f, indent=1)
+
+    def tune_order(self, query: Query, index_for, top_k: int = 4, stream=None, **options) -> tuple:
+        """Loop order by measurement: the cost model's top_k orders
+        (ranked_orders), each run in count mode on the data (best of
+        self.reps launches, search kernel time); returns (order, {order:
+        ms}).  ``index_for(j, attr_order)`` gives atom j's index in that
+        attribute order; ``options`` go to run_join (shares default 1)."""
+        stream = stream or torch.cuda.current_stream()
+        base = [index_for(j, query.with_order(tuple(range(query.n_vars))).attr_order(j))
+                for j in range(len(query.atoms))]
+        times = {}
+        for order in ranked_orders(query, base)[:max(1, top_k)]:
+            qo = query.with_order(order)
+            idx = [index_for(j, qo.attr_order(j)) for j in range(len(query.atoms))]
+            best = float("inf")
+            for _ in range(self.reps):
+                r = run_join(qo, idx, stream=stream, time_kernels=True, **options)
+                best = min(best, r.ms_join_kernel)
+            times[tuple(order)] = best
+        order = min(times, key=times.get)
+        return order, times
 
     def tune(self, query: Query, indexes, P_list=(64, 256, 1024), min_cells: int = 1, stream=None,
              log=None, mode: str = "count", out_capacity: int = 0) -> Config:

@@ -135,6 +135,7 @@ struct hc_result {
     uint64_t n_cells = 0;
     hc::JoinCtl* d_ctl = nullptr;
     uint64_t* d_cell_counts = nullptr;
+    uint64_t* d_cell_prof = nullptr;  // [n_cells][2] with HC_FLAG_CELL_PROFILE
     uint32_t* d_tuples = nullptr;
     uint64_t n_tuples = 0;
     uint64_t n_items = 0;

@@ -115,7 +115,8 @@ __device__ __forceinline__ void top_range(const DAtom& a, uint32_t cell, uint32_
 
 // ------------------------------------------------------------------ loop 1
 // Per cell: length of the shortest top-level list of loop 1.
-__global__ void l0_count_kernel(const DPlan* __restrict__ gP, uint32_t* __restrict__ cand, JoinCtl* ctl, int stats) {
+__global__ void l0_count_kernel(const DPlan* __restrict__ gP, uint32_t* __restrict__ cand, JoinCtl* ctl, int stats,
+                                uint64_t* __restrict__ cprof) {
     __shared__ DPlan P;
     load_plan(P, gP);
     uint64_t work = 0;
@@ -128,6 +129,7 @@ __global__ void l0_count_kernel(const DPlan* __restrict__ gP, uint32_t* __restri
         }
         cand[c] = m;
         work += (uint64_t)P.nsrc[0] * m;
+        if (cprof) cprof[2 * (uint64_t)c] += (uint64_t)P.nsrc[0] * m;  // one thread per cell; zeroed before
     }
     if (stats) {
         work = warp_sum64(work);
@@ -319,6 +321,7 @@ struct Acc {
     JoinCtl* ctl;
     uint32_t* arena;  // the warp's arena for lifted lists (query rewriting), or NULL
     uint32_t* obuf;   // the warp's staging buffer of OBUF values (materialize), or NULL
+    uint64_t* cprof;  // per-cell profile [cells][2] (work units, SM cycles), or NULL
 };
 
 // Output slot of the lane holding rank r among the k = popc(ball) matches
@@ -1126,6 +1129,8 @@ __device__ __forceinline__ uint64_t search_item(const DPlan& P, Frame<NL, O>& F,
         E.best1 = best1;
         E.len1 = len1;
         const uint64_t before = A.count;
+        const uint64_t work0 = A.work;
+        const long long clk0 = A.cprof ? clock64() : 0;
         const uint32_t split = e_split[e];
         // units are (loop-2 candidate k, slice j) pairs, k-major; an
         // unsliced entry (split 1) is one call over its candidate range
@@ -1151,6 +1156,14 @@ __device__ __forceinline__ uint64_t search_item(const DPlan& P, Frame<NL, O>& F,
         const uint64_t got = A.count - before;
         if (pass == 0 && cell_counts && got && lane == 0)
             atomicAdd((unsigned long long*)&cell_counts[E.cell], (unsigned long long)got);
+        if (A.cprof) {  // this entry's share of its cell's work and of the warps' time on it
+            const uint64_t dw = warp_sum64(A.work - work0);
+            const unsigned long long dt = (unsigned long long)(clock64() - clk0);
+            if (lane == 0) {
+                if (dw) atomicAdd((unsigned long long*)&A.cprof[2 * (uint64_t)E.cell], (unsigned long long)dw);
+                atomicAdd((unsigned long long*)&A.cprof[2 * (uint64_t)E.cell + 1], dt);
+            }
+        }
         item_count += got;
         u0 = eb + ku1;
         ++e;
@@ -1173,7 +1186,7 @@ __global__ void __launch_bounds__(128, (NL <= 3 ? 16 : 12)) gj_kernel(const DPla
                                                     const uint64_t* __restrict__ item_base, uint32_t* __restrict__ out,
                                                     int stats, uint32_t* __restrict__ chunk_fill, uint32_t n_chunks,
                                                     uint32_t* __restrict__ arena, uint32_t item_lo, uint32_t item_hi,
-                                                    uint32_t* __restrict__ item_ctr) {
+                                                    uint32_t* __restrict__ item_ctr, uint64_t* __restrict__ cell_prof) {
     __shared__ DPlan P;
     __shared__ uint32_t s_elo[4][NL][S], s_ehi[4][NL][S];  // per warp (blocks of <= 128 threads)
     __shared__ uint32_t s_obuf[MAT ? 4 : 1][MAT ? OBUF : 1];
@@ -1200,6 +1213,7 @@ __global__ void __launch_bounds__(128, (NL <= 3 ? 16 : 12)) gj_kernel(const DPla
     A.arena = arena ? arena + (uint64_t)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * P.arena_words
                     : nullptr;
     A.obuf = MAT ? s_obuf[MAT ? (threadIdx.x >> 5) : 0] : nullptr;
+    A.cprof = pass == 0 ? cell_prof : nullptr;
     uint64_t total = 0;
     for (;;) {
         uint32_t item = 0;
@@ -1270,6 +1284,7 @@ __global__ void __launch_bounds__(128, ((NLA <= 3 && NLB <= 3) ? 16 : 12))
     A.ctl = nullptr;
     A.arena = arena ? arena + (uint64_t)(blockIdx.x * 4 + w) * arena_stride : nullptr;
     A.obuf = nullptr;
+    A.cprof = nullptr;
     for (;;) {
         uint32_t it = 0;
         if (lane == 0) it = atomicAdd(ctr, 1u);
@@ -1435,6 +1450,7 @@ struct GjArgs {
     // counter of the pass, all items)
     uint32_t item_lo = 0, item_hi = 0xFFFFFFFFu;
     uint32_t* item_ctr = nullptr;
+    uint64_t* cell_prof = nullptr;  // per-cell profile (HC_FLAG_CELL_PROFILE)
 };
 
 template <int NL, int S, int O>
@@ -1446,13 +1462,13 @@ hc_status launch_gj(bool mat, const GjArgs& g, cudaStream_t s) {
                                                              g.grain, g.ctl,
                                                              g.pass, g.cell_counts, g.item_counts, g.item_base, g.out,
                                                              g.stats, g.chunk_fill, g.n_chunks, g.arena, g.item_lo,
-                                                             g.item_hi, ctr);
+                                                             g.item_hi, ctr, g.cell_prof);
     else
         gj_kernel<NL, S, O, false><<<grid, g.threads, 0, s>>>(g.plan, g.e_cell, g.e_x, g.e_rng, g.e_split, g.uoff,
                                                               g.grain,
                                                               g.ctl, g.pass, g.cell_counts, g.item_counts, g.item_base,
                                                               g.out, g.stats, g.chunk_fill, g.n_chunks, g.arena,
-                                                              g.item_lo, g.item_hi, ctr);
+                                                              g.item_lo, g.item_hi, ctr, g.cell_prof);
     HC_CUDA_TRY(launch_check());
     return HC_OK;
 }
@@ -1531,6 +1547,7 @@ void result_release(hc_result* r) {
     for (auto* p : r->parts) partitioned_release(p, s);
     dev_free(r->d_ctl, s);
     dev_free(r->d_cell_counts, s);
+    dev_free(r->d_cell_prof, s);
     dev_free(r->d_tuples, s);
     for (auto& e : r->ev)
         if (e) cudaEventDestroy(e);
@@ -1558,6 +1575,7 @@ hc_status result_get(hc_result* R, hc_result_view* v) {
     v->d_tuples = R->materialized ? R->d_tuples : nullptr;
     v->n_cells = R->n_cells;
     v->d_cell_counts = R->d_cell_counts;
+    v->d_cell_profile = R->d_cell_prof;
     v->work = R->h_ctl.work;
     v->n_items = R->n_items;
     v->n_join_launches = (uint32_t)R->n_search;
@@ -1637,7 +1655,7 @@ hc_status plan_query(const hc_query* q, const hc_index* const* idx, const hc_joi
         return fail(HC_ERR_ARG, "run_join: block_threads must be a multiple of 32 in [32, 128]");
     out->nv = nv;
     out->ncells = ncells;
-    out->stats = (prm->flags & HC_FLAG_STATS) ? 1 : 0;
+    out->stats = (prm->flags & (HC_FLAG_STATS | HC_FLAG_CELL_PROFILE)) ? 1 : 0;
 
     DPlan& P = out->P;
     memset(&P, 0, sizeof(P));
@@ -1830,11 +1848,12 @@ hc_status alloc_level1_temp(const QueryPlan& qp, Alloc& a, Level1* L) {
 // Loop 1 of every cell (enqueued, no host waits): candidates per cell, the
 // flat probe, compaction into entries and the entries' unit offsets.  The
 // plan must already be in L.d_plan.
-hc_status enqueue_level1(const QueryPlan& qp, const Level1& L, JoinCtl* ctl, cudaStream_t s) {
+hc_status enqueue_level1(const QueryPlan& qp, const Level1& L, JoinCtl* ctl, cudaStream_t s,
+                         uint64_t* cell_prof = nullptr) {
     const int tpb = 256;
     const uint64_t ncells = qp.ncells, cb = qp.cand_bound;
     l0_count_kernel<<<(unsigned)std::min<uint64_t>((ncells + tpb - 1) / tpb, 4096), tpb, 0, s>>>(L.d_plan, L.cand, ctl,
-                                                                                                 qp.stats);
+                                                                                                 qp.stats, cell_prof);
     if (cudaError_t le = launch_check()) return cuda_fail(le, "l0_count_kernel");
     HC_TRY(exclusive_scan_u32_to_u64(L.cand, L.candoff, ncells, nullptr, &ctl->err, s));
     const unsigned pgrid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((cb + tpb - 1) / tpb, (uint64_t)num_sms() * 16));
@@ -1962,6 +1981,12 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
         R->d_cell_counts = (uint64_t*)p;
         if (cudaMemsetAsync(p, 0, ncells * 8, s) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
     }
+    if (prm->flags & HC_FLAG_CELL_PROFILE) {
+        void* p;
+        if (dev_alloc(&p, ncells * 16, s) != HC_OK) return bail(HC_ERR_OOM);
+        R->d_cell_prof = (uint64_t*)p;
+        if (cudaMemsetAsync(p, 0, ncells * 16, s) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
+    }
 
     Scratch tmp(s);
     Level1 L;
@@ -1970,7 +1995,7 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     if ((st = alloc_level1_temp(qp, tmp, &L)) != HC_OK) return bail(st);
     if (cudaMemcpyAsync(L.d_plan, &qp.P, sizeof(DPlan), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return bail(cuda_fail(cudaGetLastError(), "plan copy"));
-    if ((st = enqueue_level1(qp, L, ctl, s)) != HC_OK) return bail(st);
+    if ((st = enqueue_level1(qp, L, ctl, s, R->d_cell_prof)) != HC_OK) return bail(st);
     const uint64_t* uoff = L.uoff;
 
     GjArgs g{L.d_plan, L.e_cell, L.e_x,   L.e_rng, L.e_split, uoff,    grain,   ctl, 0, R->d_cell_counts,
@@ -1978,6 +2003,7 @@ hc_status run_join_impl(const hc_query* q, const hc_index* const* idx, const hc_
     if (const uint64_t aw = lift_arena_words(qp)) {
         if ((st = tmp.get(&g.arena, aw)) != HC_OK) return bail(st);
     }
+    g.cell_prof = R->d_cell_prof;
     const bool timed = (prm->flags & HC_FLAG_TIME_KERNELS) != 0;
     // one search launch, bracketed by events when timed
     auto search = [&](bool mat) -> hc_status {

@@ -110,3 +110,23 @@ def test_bad_arguments():
     idx = mixed_relations(q, 5)
     with pytest.raises(hc._lib.HoneycombError):
         hc.choose_plan(q, idx, 3)  # P not a power of two
+
+
+def test_ranked_orders_follow_the_estimate():
+    """The autotuner's order candidates: every loop order once, cheapest first
+    by the summed per-loop estimate that hc_plan_cost reports at shares 1."""
+    import itertools
+
+    import paper_2502_06715_gb300 as hc
+    from paper_2502_06715_gb300.autotune import ranked_orders
+
+    q = hc.FOUR_CLIQUE
+    rels = [hc.Index.from_stats(1_000_000 + 7919 * j, 40_000 + 1013 * j, 0, 2_000_000, 2_000_000)
+            for j in range(len(q.atoms))]
+    ranked = ranked_orders(q, rels)
+    assert sorted(ranked) == sorted(itertools.permutations(range(4)))
+    costs = [sum(hc.plan_cost(q.with_order(o), rels, [1] * 4)["level_cost"]) for o in ranked]
+    assert costs == sorted(costs)
+    # the plan decision's order is among the cheapest by the same estimate
+    order, _ = hc.choose_plan(q, rels, 1)
+    assert costs[ranked.index(tuple(order))] == costs[0]
