@@ -50,6 +50,9 @@ struct hc_kindex {
     // level-0 position map: pos[v] = position of v in V_0, or V1POS_NONE
     uint32_t* d_v0pos = nullptr;
     uint32_t v0pos_n = 0;
+    // bucket directory of each level's runs (level 0: one run, built when
+    // there is no position map; level d >= 1: the runs of O_{d-1})
+    uint64_t* d_g[HC_KMAX_ARITY] = {nullptr, nullptr, nullptr};
     float ms_sort = 0.f, ms_levels = 0.f;
     bool stats_only = false;  // sizes only (planning), no device arrays
 };
@@ -352,6 +355,7 @@ void kindex_release(hc_kindex* x, cudaStream_t s) {
     for (int d = 0; d < HC_KMAX_ARITY; ++d) {
         dev_free(x->d_v[d], s);
         dev_free(x->d_o[d], s);
+        dev_free(x->d_g[d], s);
     }
     dev_free(x->d_v0pos, s);
     delete x;
@@ -536,6 +540,15 @@ hc_status build_kindex_impl(const uint32_t* d_rows, uint64_t n, uint32_t k, cons
         kpos_kernel<<<grid_of(x->len[0], 256, 8), 256, 0, s>>>(x->d_v[0], x->len[0], x->d_v0pos, x->v0pos_n);
         if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "kpos_kernel"));
     }
+    // bucket directories: level 0 as one run (without a position map), and
+    // every deeper level by the runs its parent level's offsets mark
+    if (x->d_v0pos == nullptr && (st = build_directory(x->d_v[0], x->len[0], nullptr, x->len[0], nullptr, nullptr, s,
+                                                       &x->d_g[0])) != HC_OK)
+        return bail(st);
+    for (uint32_t d = 1; d < k; ++d)
+        if ((st = build_directory(x->d_v[d], x->len[d], x->d_o[d - 1], x->len[d - 1], nullptr, nullptr, s,
+                                  &x->d_g[d])) != HC_OK)
+            return bail(st);
     *out = x;
     return HC_OK;
 }
@@ -555,6 +568,7 @@ constexpr int KJ_WARPS = KJ_MAXT / 32;
 // level at its match.
 struct KSrc {
     const uint32_t* v;
+    const uint64_t* g;    // bucket directory of this level's runs, or NULL
     const uint32_t* o;
     const uint32_t* pos;  // depth 0: value -> position in V_0 (V1POS_NONE if absent), or NULL
     uint32_t pos_n;       // values covered by pos
@@ -591,8 +605,8 @@ __device__ __forceinline__ uint32_t ksearch(const KSrc& s, uint32_t lo, uint32_t
         ok = p != V1POS_NONE;
         return p;
     }
-    const uint32_t p = lower_bound_u32(s.v, lo, hi, v);
-    ok = p < hi && __ldg(s.v + p) == v;
+    uint32_t p = lo;
+    ok = dir_find(s.v, s.g, lo, hi, v, DIR_MIN, p);
     return p;
 }
 
@@ -1029,6 +1043,7 @@ hc_status make_kplan(const hc_kquery* q, const hc_kindex* const* idx, KPlan& P) 
             const int qn = P.nsrc[L]++;
             KSrc& s = P.src[L][qn];
             s.v = x->d_v[d];
+            s.g = x->d_g[d];
             s.o = d + 1 < k ? x->d_o[d] : nullptr;
             s.pos = d == 0 ? x->d_v0pos : nullptr;
             s.pos_n = d == 0 ? x->v0pos_n : 0;
