@@ -388,8 +388,11 @@ hc_status hc_result_free(hc_result* r);
  * by one atomic counter, so warps move on to whichever query still has work).
  *   qs[n], prm[n]  the queries and their parameters (mode must be COUNT);
  *   idx_flat       the indexes of query 0's atoms, then query 1's, ...;
- *   n              1..65536 queries of 3 or 4 variables, of at most two
- *                  shapes (lists and atoms per loop) per batch.
+ *   n              1..65536 queries of 3 or 4 variables, in any mix of the
+ *                  four built-in shapes (3 or 4 loops, with up to 2 or up to
+ *                  4 lists and opened atoms per loop); a batch of three or
+ *                  four shapes runs them in one launch that switches per
+ *                  query (at the occupancy of the widest shape).
  * hc_batch_create plans every query, partitions atoms whose shares need it
  * and allocates the batch's device memory (waits for the GPU once).
  * hc_batch_launch enqueues the loop-1 passes of all queries and the one

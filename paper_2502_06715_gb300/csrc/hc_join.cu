@@ -1247,7 +1247,7 @@ struct BQuery {
     const uint64_t* uoff;
     JoinCtl* ctl;
     uint32_t grain;
-    uint32_t shape;  // 0: the kernel's first shape, 1: its second
+    uint32_t shape;  // 0: the kernel's first shape, 1: its second (all-shapes kernel: the shape class)
 };
 
 __global__ void batch_items_kernel(const BQuery* __restrict__ qs, uint32_t n, uint64_t* __restrict__ items) {
@@ -1326,6 +1326,100 @@ __global__ void __launch_bounds__(128, ((NLA <= 3 && NLB <= 3) ? 16 : 12))
             c = search_item<NLB, SB, OB, false>(P, F, A, (uint32_t(*)[SB])s_e[w], (uint32_t(*)[SB])(s_e[w] + NLB * SB),
                                                 local, b.grain, E_n, U, b.e_cell, b.e_x, b.e_rng, b.e_split, b.uoff,
                                                 nullptr, 0);
+        }
+        if (lane == 0 && c) atomicAdd((unsigned long long*)&b.ctl->total, (unsigned long long)c);
+    }
+}
+
+// Batches of more than two query shapes: one launch over the four built-in
+// shape classes (3 loops with 2 or 4 lists and opened atoms per loop, 4 loops
+// likewise); each query's item runs the search compiled for its class.
+__global__ void __launch_bounds__(128, 12)
+    gj_batch_all_kernel(const BQuery* __restrict__ qs, uint32_t n, const uint64_t* __restrict__ item_off,
+                        uint32_t* __restrict__ ctr, uint32_t* __restrict__ arena, uint32_t arena_stride) {
+    __shared__ DPlan wplan[4];
+    __shared__ uint32_t s_e[4][2 * 4 * 4];
+    const uint32_t w = threadIdx.x >> 5, lane = lane_id();
+    if (dev_err_set(&qs[0].ctl->err)) return;  // the item-offset scan gave up a wait
+    const uint64_t total_items = item_off[n];
+    uint32_t cur = 0xFFFFFFFFu;
+    Acc A;
+    A.count = 0;
+    A.work = 0;
+    A.out_pos = 0;
+    A.out = nullptr;
+    A.stats = 0;
+    A.pool = 0;
+    A.chunk = NO_CHUNK;
+    A.fill = OUT_CHUNK;
+    A.n_chunks = 0;
+    A.chunk_fill = nullptr;
+    A.ctl = nullptr;
+    A.arena = arena ? arena + (uint64_t)(blockIdx.x * 4 + w) * arena_stride : nullptr;
+    A.obuf = nullptr;
+    A.cprof = nullptr;
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(ctr, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= total_items) break;
+        uint32_t lo = 0, hi = n;  // query holding item it: last q with item_off[q] <= it
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (item_off[mid] <= it)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const uint32_t q = lo;
+        const BQuery& b = qs[q];
+        if (dev_err_set(&b.ctl->err)) continue;  // a scan of this query's loop-1 pass gave up a wait
+        if (q != cur) {
+            __syncwarp();
+            const uint32_t* src = (const uint32_t*)b.plan;
+            uint32_t* dst = (uint32_t*)&wplan[w];
+            for (uint32_t i = lane; i < sizeof(DPlan) / 4; i += 32) dst[i] = src[i];
+            __syncwarp();
+            cur = q;
+        }
+        const DPlan& P = wplan[w];
+        const uint32_t E_n = b.ctl->n_entries;
+        const uint64_t U = b.uoff[E_n];
+        const uint64_t local = it - item_off[q];
+        uint64_t c = 0;
+        switch (b.shape) {
+            case 0: {
+                Frame<3, 2> F;
+                F.lifted = false;
+                c = search_item<3, 2, 2, false>(P, F, A, (uint32_t(*)[2])s_e[w], (uint32_t(*)[2])(s_e[w] + 3 * 2),
+                                                local, b.grain, E_n, U, b.e_cell, b.e_x, b.e_rng, b.e_split, b.uoff,
+                                                nullptr, 0);
+                break;
+            }
+            case 1: {
+                Frame<3, 4> F;
+                F.lifted = false;
+                c = search_item<3, 4, 4, false>(P, F, A, (uint32_t(*)[4])s_e[w], (uint32_t(*)[4])(s_e[w] + 3 * 4),
+                                                local, b.grain, E_n, U, b.e_cell, b.e_x, b.e_rng, b.e_split, b.uoff,
+                                                nullptr, 0);
+                break;
+            }
+            case 2: {
+                Frame<4, 2> F;
+                F.lifted = false;
+                c = search_item<4, 2, 2, false>(P, F, A, (uint32_t(*)[2])s_e[w], (uint32_t(*)[2])(s_e[w] + 4 * 2),
+                                                local, b.grain, E_n, U, b.e_cell, b.e_x, b.e_rng, b.e_split, b.uoff,
+                                                nullptr, 0);
+                break;
+            }
+            default: {
+                Frame<4, 4> F;
+                F.lifted = false;
+                c = search_item<4, 4, 4, false>(P, F, A, (uint32_t(*)[4])s_e[w], (uint32_t(*)[4])(s_e[w] + 4 * 4),
+                                                local, b.grain, E_n, U, b.e_cell, b.e_x, b.e_rng, b.e_split, b.uoff,
+                                                nullptr, 0);
+                break;
+            }
         }
         if (lane == 0 && c) atomicAdd((unsigned long long*)&b.ctl->total, (unsigned long long)c);
     }
@@ -2245,6 +2339,7 @@ struct hc_batch {
     uint32_t* d_ctr = nullptr;
     hc::Level1 temp;  // loop-1 temporaries shared by the queries (sized by the largest)
     int class_a = 0, class_b = 0;
+    bool all_shapes = false;  // more than two shape classes: gj_batch_all_kernel
     uint32_t* d_arena = nullptr;  // lifted lists (query rewriting), arena_stride words per warp
     uint32_t arena_stride = 0;
     cudaGraph_t graph = nullptr;
@@ -2295,7 +2390,7 @@ hc_status batch_create(const hc_query* qs, const hc_index* const* idx_flat, cons
         else if (classes[1] < 0 || classes[1] == c)
             classes[1] = c;
         else
-            return bail(fail(HC_ERR_CAPACITY, "batch: at most two query shapes per batch"));
+            B->all_shapes = true;  // three or four shape classes: the all-shapes kernel
         if ((st = alloc_level1_keep(B->plans[i], A, &B->l1[i])) != HC_OK) return bail(st);
         max_cb = std::max(max_cb, B->plans[i].cand_bound);
         max_cells = std::max(max_cells, B->plans[i].ncells);
@@ -2322,8 +2417,9 @@ hc_status batch_create(const hc_query* qs, const hc_index* const* idx_flat, cons
         return bail(st);
     for (uint32_t i = 0; i < n; ++i) {
         const Level1& L = B->l1[i];
+        const int cls = shape_class(B->plans[i]);
         hq[i] = BQuery{L.d_plan, L.e_cell, L.e_x, L.e_rng, L.e_split, L.uoff, B->d_ctl + i, B->plans[i].grain,
-                       (uint32_t)(shape_class(B->plans[i]) == B->class_a ? 0 : 1)};
+                       (uint32_t)(B->all_shapes ? cls : (cls == B->class_a ? 0 : 1))};
     }
     if (cudaMemcpy(B->d_q, hq.data(), n * sizeof(BQuery), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(cuda_fail(cudaGetLastError(), "batch table copy"));
@@ -2347,6 +2443,16 @@ static hc_status batch_enqueue(hc_batch* B, cudaStream_t s) {
     batch_items_kernel<<<(B->n + 255) / 256, 256, 0, s>>>(B->d_q, B->n, B->d_items);
     HC_CUDA_TRY(launch_check());
     HC_TRY(exclusive_scan_u64(B->d_items, B->d_item_off, B->n, nullptr, &B->d_ctl[0].err, s));
+    if (B->all_shapes) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_batch_all_kernel, 128, 0) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        gj_batch_all_kernel<<<per_sm * num_sms(), 128, 0, s>>>(B->d_q, B->n, B->d_item_off, B->d_ctr, B->d_arena,
+                                                               B->arena_stride);
+        HC_CUDA_TRY(launch_check());
+        return HC_OK;
+    }
     return launch_batch_pair(B->class_a, B->class_b, B->d_q, B->n, B->d_item_off, B->d_ctr, B->d_arena,
                              B->arena_stride, s);
 }

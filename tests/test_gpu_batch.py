@@ -62,14 +62,53 @@ def test_batch_matches_separate_and_oracle(hc, n):
     b.free()
 
 
-def test_batch_rejects_three_shapes(hc):
-    sym = datagen.random_graph(30, 0.3, 1)
+def test_batch_of_all_four_shapes(hc):
+    """Triangles (two lists per loop), triangles with a selection on y (more
+    lists at loop y), 4-cycles and 4-cliques in one batch: one launch over all
+    four shape classes; counts equal separate launches and the oracle, also
+    replayed as a CUDA graph."""
+    import torch
+
+    sym = datagen.rmat_graph(11, 8, 19)
     ep = datagen.orient_lt(sym)
+    rng = np.random.default_rng(5)
     ix = hc.build_index(dev(ep), 0)
     ixs = hc.build_index(dev(sym), 0)
-    qs = [hc.TRIANGLE, hc.FOUR_CLIQUE, hc.FOUR_CYCLE]
-    with pytest.raises(hc.HoneycombError):
-        hc.Batch(qs, [[ix] * 3, [ix] * 6, [ixs] * 4])
+    qs, lists, rels = [], [], []
+    for i in range(24):
+        kind = i % 4
+        if kind == 0:
+            qs.append(hc.TRIANGLE), lists.append([ix] * 3), rels.append([ep] * 3)
+        elif kind == 1:
+            vals = np.unique(rng.integers(0, 2048, size=400)).astype(np.uint32)
+            sel = np.stack([vals, np.zeros_like(vals)], 1)
+            q = hc.TRIANGLE.with_atoms([(1, -1), (1, -1)])
+            u = hc.build_index(dev(sel), 0)
+            qs.append(q), lists.append([ix] * 3 + [u, u]), rels.append([ep] * 3 + [sel, sel])
+        elif kind == 2:
+            qs.append(hc.FOUR_CYCLE), lists.append([ixs] * 4), rels.append([sym] * 4)
+        else:
+            qs.append(hc.FOUR_CLIQUE), lists.append([ix] * 6), rels.append([ep] * 6)
+    want = [oracle.gj_count(q.n_vars, list(q.atoms), r)[0] for q, r in zip(qs, rels)]
+    opts = [{"shares": [2] + [1] * (q.n_vars - 1)} if i % 5 == 0 else {} for i, q in enumerate(qs)]
+    assert [hc.run_join(q, l, **o).count for q, l, o in zip(qs, lists, opts)] == want
+    b = hc.Batch(qs, lists, opts)
+    b.launch()
+    assert b.counts() == want
+    s = torch.cuda.Stream()
+    b.capture(s)
+    for _ in range(2):
+        b.launch(s)
+        assert b.counts() == want
+    b.free()
+
+
+def test_batch_rejects_five_variable_queries(hc):
+    ep = datagen.orient_lt(datagen.random_graph(30, 0.3, 1))
+    ix = hc.build_index(dev(ep), 0)
+    with pytest.raises(hc.HoneycombError) as e:
+        hc.Batch([hc.TRIANGLE, hc.TWO_TRIANGLE], [[ix] * 3, [ix] * 6])
+    assert e.value.status == 5
 
 
 def test_autotuner_picks_a_valid_config(hc, tmp_path):
