@@ -86,8 +86,8 @@ struct hc_index {
     // bucket directories (search acceleration, see dir_lower_bound): d_g2
     // parallel to V2 for the runs of O1; d_g1 parallel to V1 for the single
     // run [0, l1) when there is no position map
-    uint64_t* d_g2 = nullptr;
-    uint64_t* d_g1 = nullptr;
+    uint4* d_g2 = nullptr;
+    uint4* d_g1 = nullptr;
 };
 
 struct hc_partitioned {
@@ -108,8 +108,8 @@ struct hc_partitioned {
     uint32_t v1pos_n = 0;
     // bucket directories: d_g2 parallel to V2 (runs of O1), d_g1 parallel to
     // V1 (one run per partition, lvl1_start) when there is no position map
-    uint64_t* d_g2 = nullptr;
-    uint64_t* d_g1 = nullptr;
+    uint4* d_g2 = nullptr;
+    uint4* d_g1 = nullptr;
 };
 
 namespace hc {
@@ -319,20 +319,23 @@ __device__ __forceinline__ bool find_u32(P a, uint32_t lo, uint32_t hi, uint32_t
 // The search primitive of Sec. 5 ("search(V, x)": the first position of a
 // sorted list holding a value >= x) over a run a[lo, hi) of n >= DIR_MIN
 // distinct ascending values, narrowed by a directory stored in an array g of
-// 64-bit entries parallel to a.  With vmin = a[lo], vmax = a[hi-1] the run's
+// 16-byte entries parallel to a.  With vmin = a[lo], vmax = a[hi-1] the run's
 // values fall in nb = ((vmax - vmin) >> s) + 1 buckets of width 2^s, where
 // s = dir_shift(n, vmax - vmin) makes nb at most n (one to four values a
-// bucket on average).  Entry k of the run, g[lo + k] for k < nb, holds
-// p_k = the first position in [lo, hi) whose value is in bucket k or above
-// (low 32 bits) and a[p_k] (high 32 bits); every p_k exists, since vmax lies
-// in the last bucket.  A search of x in (vmin, vmax] reads the entry of x's
-// bucket k: every value before p_k is below vmin + k 2^s <= x, so the answer
-// is p_k when a[p_k] >= x, and otherwise lies a few positions further (a
-// forward walk that stops at the latest at hi - 1, because vmax >= x).  The
-// answer is the plain binary search's.  The paper's fixed-stride
-// ("quadratic") search jumps by strides to reach the stride holding x; here
-// that stride is addressed directly, and its first value comes with it, so
-// most searches of a value that is absent end after one 8-byte read.
+// bucket on average).  Entry k of the run, g[lo + k] for k < nb, holds p_k =
+// the first position in [lo, hi) whose value is in bucket k or above, and
+// the values a[p_k], a[p_k + 1], a[p_k + 2] (~0 past the run); every p_k
+// exists, since vmax lies in the last bucket.  A search of x in [vmin, vmax]
+// reads the entry of x's bucket k: every value before p_k is below
+// vmin + k 2^s <= x, so the answer is the first of p_k, p_k + 1, p_k + 2
+// whose value is >= x, and otherwise lies further on (a forward walk that
+// stops at the latest at hi - 1, because vmax >= x).  A value of the entry
+// past the run is never consulted: it lies beyond hi - 1, where a value
+// >= x already ended the search.  The answer is the plain binary search's.
+// The paper's fixed-stride ("quadratic") search jumps by strides to reach the
+// stride holding x; here that stride is addressed directly, and its first
+// three values come with it, so a search is one 16-byte read unless x lies
+// beyond the third value of its bucket.
 constexpr uint32_t DIR_MIN = 16;  // shorter runs have no directory
 
 // Bucket width exponent for a run of n >= DIR_MIN values spanning `span`:
@@ -344,34 +347,36 @@ __device__ __forceinline__ uint32_t dir_shift(uint32_t n, uint32_t span) {
     return t ? 32u - __clz(t) : 0u;
 }
 
-__device__ __forceinline__ uint64_t dir_entry(uint32_t pos, uint32_t value) {
-    return ((uint64_t)value << 32) | pos;
-}
-
-// The answer from entry e = g[lo + k] for x in (vmin, vmax]: p_k if
-// a[p_k] >= x, else the first later position holding a value >= x.  A
-// position outside the run (a directory of unsorted input, a caller's broken
-// promise) is pulled back to hi - 1, where the walk ends.
-template <typename P>
-__device__ __forceinline__ uint32_t dir_walk(P a, uint64_t e, uint32_t hi, uint32_t x) {
-    uint32_t p = (uint32_t)e, w = (uint32_t)(e >> 32);
-    if (p >= hi) {
-        p = hi - 1;
-        w = load_ro(a + p);
-    }
-    while (w < x) w = load_ro(a + (++p));
-    return p;
-}
+__device__ __forceinline__ uint4 dir_load(const uint4* g, uint64_t i) { return __ldg(g + i); }
 
 // Membership of x in the run a[lo, hi) from the entry e of x's bucket, x in
-// (vmin, vmax]: the walk ends at the lower bound, whose value it holds.
+// [vmin, vmax]: the position of the first value >= x in pos, true when that
+// value is x.  A position outside the run (a directory of unsorted input, a
+// caller's broken promise) is pulled back to hi - 1, where the walk ends.
 template <typename P>
-__device__ __forceinline__ bool dir_walk_find(P a, uint64_t e, uint32_t hi, uint32_t x, uint32_t& pos) {
-    uint32_t p = (uint32_t)e, w = (uint32_t)(e >> 32);
+__device__ __forceinline__ bool dir_walk_find(P a, uint4 e, uint32_t hi, uint32_t x, uint32_t& pos) {
+    uint32_t p = e.x;
     if (p >= hi) {
         p = hi - 1;
-        w = load_ro(a + p);
+        uint32_t w = load_ro(a + p);
+        while (w < x) w = load_ro(a + (++p));
+        pos = p;
+        return w == x;
     }
+    if (e.y >= x) {
+        pos = p;
+        return e.y == x;
+    }
+    if (e.z >= x) {
+        pos = p + 1;
+        return e.z == x;
+    }
+    if (e.w >= x) {
+        pos = p + 2;
+        return e.w == x;
+    }
+    p += 3;
+    uint32_t w = load_ro(a + p);
     while (w < x) w = load_ro(a + (++p));
     pos = p;
     return w == x;
@@ -381,7 +386,7 @@ __device__ __forceinline__ bool dir_walk_find(P a, uint64_t e, uint32_t hi, uint
 // through the run's directory when g is given and the run has at least dmin
 // (>= DIR_MIN) values, else by find_u32.
 template <typename P>
-__device__ __forceinline__ bool dir_find(P a, const uint64_t* __restrict__ g, uint32_t lo, uint32_t hi, uint32_t x,
+__device__ __forceinline__ bool dir_find(P a, const uint4* __restrict__ g, uint32_t lo, uint32_t hi, uint32_t x,
                                          uint32_t dmin, uint32_t& pos) {
     const uint32_t n = hi - lo;
     pos = lo;
@@ -391,21 +396,7 @@ __device__ __forceinline__ bool dir_find(P a, const uint64_t* __restrict__ g, ui
     if (x <= vmin) return x == vmin;
     if (x > vmax) return false;
     const uint32_t k = (x - vmin) >> dir_shift(n, vmax - vmin);
-    return dir_walk_find(a, __ldg((const unsigned long long*)g + lo + k), hi, x, pos);
-}
-
-// lower_bound_u32 of x in the run a[lo, hi), through the run's directory when
-// g is given and the run has at least dmin (>= DIR_MIN) values.
-template <typename P>
-__device__ __forceinline__ uint32_t dir_lower_bound(P a, const uint64_t* __restrict__ g, uint32_t lo, uint32_t hi,
-                                                    uint32_t x, uint32_t dmin) {
-    const uint32_t n = hi - lo;
-    if (g == nullptr || n < dmin) return lower_bound_u32(a, lo, hi, x);
-    const uint32_t vmin = load_ro(a + lo), vmax = load_ro(a + hi - 1);
-    if (x <= vmin) return lo;
-    if (x > vmax) return hi;
-    const uint32_t k = (x - vmin) >> dir_shift(n, vmax - vmin);
-    return dir_walk(a, __ldg((const unsigned long long*)g + lo + k), hi, x);
+    return dir_walk_find(a, dir_load(g, (uint64_t)lo + k), hi, x, pos);
 }
 
 #endif  // __CUDACC__
@@ -423,12 +414,12 @@ void partitioned_release(hc_partitioned* p, cudaStream_t s);
 void index_release(hc_index* idx, cudaStream_t s);
 hc_status build_unary_impl(const uint32_t* d_values, uint64_t n, uint32_t max_value, cudaStream_t s,
                            hc_index** out);
-// Bucket directory g (parallel to a, alen 64-bit entries, allocated here) of the
+// Bucket directory g (parallel to a, alen 16-byte entries, allocated here) of the
 // runs [o[r], o[r+1]) of a, r < nruns (nruns = min(nruns_max, *d_nruns) when
 // d_nruns is given), or with o == NULL of the one run [0, nruns_max);
 // nothing is computed once *d_err is set.
 hc_status build_directory(const uint32_t* a, uint64_t alen, const uint32_t* o, uint64_t nruns_max,
-                          const uint32_t* d_nruns, const uint32_t* d_err, cudaStream_t s, uint64_t** out_g);
+                          const uint32_t* d_nruns, const uint32_t* d_err, cudaStream_t s, uint4** out_g);
 
 // Device-wide exclusive scan of counts into uint64 offsets; out[n] receives
 // the total.  n = min(n_max, *d_n) when d_n is given (a device-side count),

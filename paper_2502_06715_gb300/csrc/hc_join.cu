@@ -35,8 +35,8 @@ struct DAtom {
     const uint32_t* l1s;    // level-1 start of each partition, [np + 1]; NULL when whole
     const uint32_t* v1pos;  // value -> position in v1 (V1POS_NONE if absent), or NULL
     uint32_t v1pos_n;       // values covered by v1pos
-    const uint64_t* g1;     // bucket directory of v1's top-level runs, or NULL
-    const uint64_t* g2;     // bucket directory of v2's runs, or NULL
+    const uint4* g1;        // bucket directory of v1's top-level runs, or NULL
+    const uint4* g2;        // bucket directory of v2's runs, or NULL
     uint32_t l1_whole;
     uint32_t pb;                                     // shares of the second variable
     uint32_t stride_f, share_f, stride_s, share_s;  // cell -> partition identifiers
@@ -763,8 +763,8 @@ __device__ __forceinline__ void flush_staged(const DPlan& P, const Entry<NL, S>&
 
 template <int L, int NL, int S, int O, bool MAT, typename LP>
 __device__ __forceinline__ void probe_pair(const DPlan& P, const Entry<NL, S>& E, Acc& A, LP la,
-                                           const uint64_t* ga, uint32_t a0, uint32_t a1, LP lb,
-                                           const uint64_t* gb, uint32_t b0, uint32_t b1,
+                                           const uint4* ga, uint32_t a0, uint32_t a1, LP lb,
+                                           const uint4* gb, uint32_t b0, uint32_t b1,
                                            const uint32_t (&vals)[NL]) {
     constexpr bool VEC = std::is_same<LP, const uint32_t*>::value;  // an index list: padded, 16-byte aligned base
     const uint32_t lane = lane_id();
@@ -772,7 +772,7 @@ __device__ __forceinline__ void probe_pair(const DPlan& P, const Entry<NL, S>& E
         LP t = la;
         la = lb;
         lb = t;
-        const uint64_t* tg = ga;
+        const uint4* tg = ga;
         ga = gb;
         gb = tg;
         uint32_t u = a0;
@@ -787,7 +787,7 @@ __device__ __forceinline__ void probe_pair(const DPlan& P, const Entry<NL, S>& E
     const uint32_t vmin = load_ro(lb + b0), vmax = load_ro(lb + b1 - 1);
     const bool dir = gb != nullptr && nbv >= P.dir_min;
     const uint32_t sh = dir ? dir_shift(nbv, vmax - vmin) : 0u;
-    const unsigned long long* gd = (const unsigned long long*)gb + b0;
+    const uint4* gd = gb + b0;
     uint32_t cnt = 0;
     uint32_t staged = 0;  // values in the warp's buffer (materialize, VEC)
     if constexpr (VEC) {
@@ -797,11 +797,11 @@ __device__ __forceinline__ void probe_pair(const DPlan& P, const Entry<NL, S>& E
             if (t < a1) q4 = __ldg(reinterpret_cast<const uint4*>(la + t));
             const uint32_t vv[4] = {q4.x, q4.y, q4.z, q4.w};
             bool okv[4];
-            uint64_t ev[4];
+            uint4 ev[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 okv[j] = t + j >= a0 && t + j < a1 && vv[j] >= vmin && vv[j] <= vmax;
-                ev[j] = (okv[j] && dir) ? __ldg(gd + ((vv[j] - vmin) >> sh)) : 0ull;
+                ev[j] = (okv[j] && dir) ? dir_load(gd, (vv[j] - vmin) >> sh) : make_uint4(0u, 0u, 0u, 0u);
             }
             uint32_t mine = 0;
 #pragma unroll
@@ -835,7 +835,7 @@ __device__ __forceinline__ void probe_pair(const DPlan& P, const Entry<NL, S>& E
             bool ok = t < a1 && v >= vmin && v <= vmax;
             if (ok) {
                 uint32_t pos;
-                ok = dir ? dir_walk_find(lb, __ldg(gd + ((v - vmin) >> sh)), b1, v, pos) : find_u32(lb, b0, b1, v, pos);
+                ok = dir ? dir_walk_find(lb, dir_load(gd, (v - vmin) >> sh), b1, v, pos) : find_u32(lb, b0, b1, v, pos);
             }
             pair_match<L, NL, S, O, MAT>(P, E, A, ok, v, vals, cnt);
         }
@@ -1031,8 +1031,8 @@ __device__ __forceinline__ void run_level(const DPlan& P, Frame<NL, O>& F, const
             if (pball) {
                 const DAtom& da = P.atom[P.src_atom[L][qa]];
                 const DAtom& db = P.atom[P.src_atom[L][qb]];
-                const uint64_t* ga = qa == lift_q ? nullptr : (P.src_top[L][qa] ? da.g1 : da.g2);
-                const uint64_t* gb = qb == lift_q ? nullptr : (P.src_top[L][qb] ? db.g1 : db.g2);
+                const uint4* ga = qa == lift_q ? nullptr : (P.src_top[L][qa] ? da.g1 : da.g2);
+                const uint4* gb = qb == lift_q ? nullptr : (P.src_top[L][qb] ? db.g1 : db.g2);
                 while (pball) {
                     const uint32_t p = __ffs(pball) - 1;
                     pball &= pball - 1;
@@ -1692,6 +1692,7 @@ struct QueryPlan {
     uint32_t grain = 64;
     uint64_t ncells = 1, cand_bound = 1;
     std::vector<hc_partitioned*> parts;
+    std::vector<const hc_index*> part_src;  // the index each partitioned copy was made from
 };
 
 static void release_parts(std::vector<hc_partitioned*>& parts, cudaStream_t s) {
@@ -1796,14 +1797,26 @@ hc_status plan_query(const hc_query* q, const hc_index* const* idx, const hc_joi
             *partition_bytes += n * (8 + 8 + 4 + 4 + 4) + (np + 1) * 8 + ((n + 4095) / 4096) * 256 * 8 + 4096;
             const bool map = pb == 1 && v1pos_eligible(n, ix->max_first);
             if (map) *partition_bytes += ((uint64_t)ix->max_first + 1) * 4;
-            *partition_bytes += n * 8 * (map ? 1 : 2);  // bucket directories of V2 (and V1 without a map)
+            *partition_bytes += n * 16 * (map ? 1 : 2);  // bucket directories of V2 (and V1 without a map)
             d.l1s = nullptr;
         } else {
+            // atoms of one index with the same shares and hash seeds on both
+            // attributes (a seed is immaterial under one share) read one
+            // partitioned copy: e.g. the triangle's R(x,y) and T(x,z) on E+
+            const uint32_t seed_a = prm->seeds[first], seed_b = (unary || pb == 1) ? 0u : prm->seeds[second];
             hc_partitioned* part = nullptr;
-            const hc_status st =
-                partition_impl(ix, prm->seeds[first], pa, unary ? 0u : prm->seeds[second], pb, s, &part);
-            if (st != HC_OK) return bail(st);
-            out->parts.push_back(part);
+            for (size_t k = 0; k < out->parts.size() && !part; ++k) {
+                hc_partitioned* c = out->parts[k];
+                if (out->part_src[k] == ix && c->pa == pa && c->pb == pb && c->seed_a == seed_a &&
+                    c->seed_b == seed_b)
+                    part = c;
+            }
+            if (!part) {
+                const hc_status st = partition_impl(ix, seed_a, pa, seed_b, pb, s, &part);
+                if (st != HC_OK) return bail(st);
+                out->parts.push_back(part);
+                out->part_src.push_back(ix);
+            }
             d.v1 = part->d_v1;
             d.o1 = part->d_o1;
             d.v2 = part->d_v2;

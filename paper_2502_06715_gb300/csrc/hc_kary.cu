@@ -52,7 +52,7 @@ struct hc_kindex {
     uint32_t v0pos_n = 0;
     // bucket directory of each level's runs (level 0: one run, built when
     // there is no position map; level d >= 1: the runs of O_{d-1})
-    uint64_t* d_g[HC_KMAX_ARITY] = {nullptr, nullptr, nullptr};
+    uint4* d_g[HC_KMAX_ARITY] = {nullptr, nullptr, nullptr};
     float ms_sort = 0.f, ms_levels = 0.f;
     bool stats_only = false;  // sizes only (planning), no device arrays
 };
@@ -568,7 +568,7 @@ constexpr int KJ_WARPS = KJ_MAXT / 32;
 // level at its match.
 struct KSrc {
     const uint32_t* v;
-    const uint64_t* g;    // bucket directory of this level's runs, or NULL
+    const uint4* g;       // bucket directory of this level's runs, or NULL
     const uint32_t* o;
     const uint32_t* pos;  // depth 0: value -> position in V_0 (V1POS_NONE if absent), or NULL
     uint32_t pos_n;       // values covered by pos

@@ -480,13 +480,14 @@ __global__ void maxrun_kernel(const uint32_t* __restrict__ o1, uint64_t l1_max, 
 // and last positions, and each thread finds the run of its position by a
 // binary search of the run starts between them.  The value at position j
 // opens the buckets above its predecessor's bucket up to its own and writes
-// entry (j, a[j]) for each.  Buckets are clamped to [0, nb - 1], so unsorted
-// input (never produced by the builders here) cannot write outside the run.
+// entry (j, a[j], a[j+1], a[j+2]) for each (~0 past the run).  Buckets are
+// clamped to [0, nb - 1], so unsorted input (never produced by the builders
+// here) cannot write outside the run.
 constexpr uint32_t DIRB_TILE = 2048;
 
 __global__ void __launch_bounds__(256) dir_build_kernel(const uint32_t* __restrict__ a, const uint32_t* __restrict__ o,
                                                         uint64_t nruns_max, const uint32_t* __restrict__ d_nruns,
-                                                        uint64_t* __restrict__ g, const uint32_t* __restrict__ err) {
+                                                        uint4* __restrict__ g, const uint32_t* __restrict__ err) {
     __shared__ uint32_t s_r0, s_r1;
     if (err && dev_err_set(err)) return;
     const uint32_t nruns = o == nullptr ? 1u : (uint32_t)(d_nruns ? min(nruns_max, (uint64_t)*d_nruns) : nruns_max);
@@ -534,7 +535,7 @@ __global__ void __launch_bounds__(256) dir_build_kernel(const uint32_t* __restri
             const uint32_t v = a[j];
             const uint32_t k = min((v - vmin) >> sh, kmax);
             const uint32_t k0 = j == lo ? 0u : min((a[j - 1] - vmin) >> sh, kmax) + 1u;
-            const uint64_t e = dir_entry(j, v);
+            const uint4 e = make_uint4(j, v, j + 1 < hi ? a[j + 1] : ~0u, j + 2 < hi ? a[j + 2] : ~0u);
             for (uint32_t b = k0; b <= k; ++b) g[lo + b] = e;
         }
     }
@@ -768,20 +769,20 @@ uint32_t bits_of(uint32_t v) { return v == 0 ? 0 : 32 - __builtin_clz(v); }
 }  // namespace
 
 hc_status build_directory(const uint32_t* a, uint64_t alen, const uint32_t* o, uint64_t nruns_max,
-                          const uint32_t* d_nruns, const uint32_t* d_err, cudaStream_t s, uint64_t** out_g) {
+                          const uint32_t* d_nruns, const uint32_t* d_err, cudaStream_t s, uint4** out_g) {
     *out_g = nullptr;
     if (alen < DIR_MIN || nruns_max == 0) return HC_OK;  // no run can have a directory
     void* p = nullptr;
-    HC_TRY(dev_alloc(&p, alen * 8, s));
+    HC_TRY(dev_alloc(&p, alen * sizeof(uint4), s));
     // tiles of the level's positions, a few blocks per SM resident
     const uint64_t want = (alen + DIRB_TILE - 1) / DIRB_TILE;
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)num_sms() * 8));
-    dir_build_kernel<<<grid, 256, 0, s>>>(a, o, nruns_max, d_nruns, (uint64_t*)p, d_err);
+    dir_build_kernel<<<grid, 256, 0, s>>>(a, o, nruns_max, d_nruns, (uint4*)p, d_err);
     if (cudaError_t le = launch_check()) {
         dev_free(p, s);
         return cuda_fail(le, "dir_build_kernel");
     }
-    *out_g = (uint64_t*)p;
+    *out_g = (uint4*)p;
     return HC_OK;
 }
 

@@ -132,9 +132,9 @@ def test_position_map_never_sized_past_32_bits(lib):
     b = hc.Index.from_stats(n, n >> 1, 0, 0xFFFFFFFF, 7)
     fa = hc.join_footprint(q, [a], shares=[2, 1])
     fb = hc.join_footprint(q, [b], shares=[2, 1])
-    # (max_first + 1) map entries of 4 bytes, less the V1 directory (8 bytes a
+    # (max_first + 1) map entries of 4 bytes, less the V1 directory (16 bytes a
     # row) that a partition without a map needs
-    assert fa - fb == 4 * 0xFFFFFFFF - 8 * n
+    assert fa - fb == 4 * 0xFFFFFFFF - 16 * n
 
 
 def test_wait_limit_is_a_library_parameter(lib):
