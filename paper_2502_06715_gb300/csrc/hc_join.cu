@@ -719,11 +719,12 @@ __device__ __forceinline__ void merge_pair(const DPlan& P, const Entry<NL, S>& E
 }
 
 // Last loop, one parent whose shorter list A has many values: the warp takes
-// A's values 128 at a time, four consecutive ones per lane in one 16-byte
-// load (index lists; a list in the arena is read one value per lane), and
-// each lane searches its values in the longer list B ("search(V, x)",
-// Sec. 5) through B's bucket directory, the four directory reads issued
-// together.  B's range, bounds and bucket width are the same for every value,
+// A's values 128 at a time, lane l the values l, l + 32, l + 64, l + 96 of
+// the round (so each load instruction reads 32 consecutive values, whose
+// buckets in B lie close together), and each lane searches its values in the
+// longer list B ("search(V, x)", Sec. 5) through B's bucket directory, the
+// four directory reads issued together (index lists; a list in the arena is
+// read one value per lane).  B's range, bounds and bucket width are the same for every value,
 // so they are read once per parent.  Count mode counts per lane;
 // materialize mode writes each slot's matches in lane order.
 template <int L, int NL, int S, int O, bool MAT>
@@ -766,7 +767,7 @@ __device__ __forceinline__ void probe_pair(const DPlan& P, const Entry<NL, S>& E
                                            const uint4* ga, uint32_t a0, uint32_t a1, LP lb,
                                            const uint4* gb, uint32_t b0, uint32_t b1,
                                            const uint32_t (&vals)[NL]) {
-    constexpr bool VEC = std::is_same<LP, const uint32_t*>::value;  // an index list: padded, 16-byte aligned base
+    constexpr bool VEC = std::is_same<LP, const uint32_t*>::value;  // an index list (read-only path)
     const uint32_t lane = lane_id();
     if (a1 - a0 > b1 - b0) {  // A is the shorter list
         LP t = la;
@@ -791,18 +792,19 @@ __device__ __forceinline__ void probe_pair(const DPlan& P, const Entry<NL, S>& E
     uint32_t cnt = 0;
     uint32_t staged = 0;  // values in the warp's buffer (materialize, VEC)
     if constexpr (VEC) {
-        for (uint32_t t0 = a0 & ~3u; t0 < a1; t0 += 128) {
-            const uint32_t t = t0 + 4 * lane;
-            uint4 q4 = make_uint4(0u, 0u, 0u, 0u);
-            if (t < a1) q4 = __ldg(reinterpret_cast<const uint4*>(la + t));
-            const uint32_t vv[4] = {q4.x, q4.y, q4.z, q4.w};
+        for (uint32_t t0 = a0; t0 < a1; t0 += 128) {
+            uint32_t vv[4];
             bool okv[4];
             uint4 ev[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                okv[j] = t + j >= a0 && t + j < a1 && vv[j] >= vmin && vv[j] <= vmax;
-                ev[j] = (okv[j] && dir) ? dir_load(gd, (vv[j] - vmin) >> sh) : make_uint4(0u, 0u, 0u, 0u);
+                const uint32_t t = t0 + 32 * j + lane;
+                vv[j] = t < a1 ? load_ro(la + t) : 0u;
+                okv[j] = t < a1 && vv[j] >= vmin && vv[j] <= vmax;
             }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                ev[j] = (okv[j] && dir) ? dir_load(gd, (vv[j] - vmin) >> sh) : make_uint4(0u, 0u, 0u, 0u);
             uint32_t mine = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
