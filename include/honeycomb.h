@@ -180,9 +180,11 @@ hc_status hc_index_from_stats(uint64_t n, uint64_t l1, uint32_t attr_order, uint
  * other allocating routine; the kernel's scratch is one fixed array of
  * 32,832 bytes inside the library, held by every GPU that loads it until the
  * process exits.  The first call on a device looks up that array's device
- * address (once per device), so make it before any stream capture.  All
- * calls share the array and each call clears what it reads: calls whose
- * work overlaps on the GPU (other streams, other host threads) race. */
+ * address (once per device), so make it before any stream capture; the
+ * address is kept for the life of the process, so calls must not cross a
+ * cudaDeviceReset of that device.  All calls share the array and each call
+ * clears what it reads: calls whose work overlaps on the GPU (other streams,
+ * other host threads) race. */
 hc_status hc_coco_levels_noalloc(const uint64_t* d_sorted_keys, uint64_t n, uint32_t* d_v1, uint32_t* d_o1,
                                  uint32_t* d_v2, uint32_t* d_info, void* stream);
 
