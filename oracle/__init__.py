@@ -18,6 +18,11 @@ the passages they follow:
 * ``tuple_cells``  -- the HyperCube cell of each output tuple (Sec. 5:
   the outputs of different cells are disjoint).
 * ``share``        -- h_i(x) mod P_i, read as ((fmix32(x ^ seed) * P) >> 32).
+* ``kcoco`` / ``kpartition`` -- the k-level CoCo of a relation of arity 1..3
+  (Sec. 4, Fig. "cocoindex"), and its HyperCube partitioning (Sec. 4,
+  "Preprocessor", Example "partition"): R~, B, B^pref and one k-level CoCo
+  per partition, concatenated.
+* ``kgj``          -- Generic Join over atoms of arity 1..3 (``oracle_kary.c``).
 
 A query is ``(n_vars, atoms)`` with ``atoms`` a list of ``(var0, var1)``:
 the relation bound to atom j holds pairs whose column 0 is variable var0
@@ -231,6 +236,57 @@ def kcoco(rows, level_cols=None) -> dict:
         o = np.searchsorted(first[d + 1], first[d]).astype(np.uint32)
         O.append(np.append(o, np.uint32(first[d + 1].shape[0])))
     return {"V": V, "O": O}
+
+
+def kpartition(rows, seeds, shares, level_cols=None) -> dict:
+    """HyperCube partitioning of a relation of arity k = 1..3 and one
+    k-level CoCo per partition (Sec. 4, "Preprocessor").
+
+    Column c of a row has the partition identifier s_c = h_c(x_c) (``share``
+    with seeds[c], shares[c]); the row's partition is the mixed-radix number
+    of (s_0, .., s_{k-1}), column 0 most significant, so partitions are
+    numbered in the lexicographic order of their identifiers.  Returns
+
+    * ``B``       -- rows in each partition;
+    * ``Bpref``   -- where each partition starts in R~ (an exclusive prefix
+      of B, the reading of B^pref that the paper's example uses: the
+      partition (0,1,0) "starts at" B^pref[0,1,0]), with Bpref[np] = n;
+    * ``rt``      -- R~: the partitions concatenated in that order, each
+      partition's rows sorted in level order (columns in the input order);
+    * ``V``, ``O`` -- the levels of every partition's k-level CoCo
+      (``kcoco``), concatenated in partition order, O_d shifted to point into
+      the concatenated level d+1 (O_d[l_d] = l_{d+1});
+    * ``l0start`` -- where each partition's level 0 starts in V_0, with
+      l0start[np] = l_0."""
+    r = np.asarray(rows, dtype=np.uint32)
+    k = r.shape[1]
+    cols = list(range(k)) if level_cols is None else list(level_cols)
+    shares = [int(x) for x in shares]
+    npart = int(np.prod(shares))
+    pid = tuple_cells(r, seeds, shares).astype(np.int64) if r.shape[0] else np.zeros(0, dtype=np.int64)
+    B = np.bincount(pid, minlength=npart).astype(np.uint64)
+    Bpref = np.concatenate([[0], np.cumsum(B)]).astype(np.uint64)
+    V = [[] for _ in range(k)]
+    O = [[] for _ in range(k - 1)]
+    rt = []
+    size = [0] * k  # entries of each level before the current partition
+    l0start = [0]
+    for p in range(npart):
+        part = r[pid == p]
+        c = kcoco(part, cols)
+        if part.shape[0]:
+            lv = part[:, cols]
+            rt.append(part[np.lexsort(lv.T[::-1])])
+        for d in range(k):
+            V[d].append(c["V"][d])
+        for d in range(k - 1):
+            O[d].append(c["O"][d][:-1].astype(np.uint64) + np.uint64(size[d + 1]))
+        size = [size[d] + c["V"][d].shape[0] for d in range(k)]
+        l0start.append(size[0])
+    Vc = [np.concatenate(V[d]).astype(np.uint32) for d in range(k)]
+    Oc = [np.append(np.concatenate(O[d]), np.uint64(size[d + 1])).astype(np.uint32) for d in range(k - 1)]
+    rt = np.concatenate(rt) if rt else np.zeros((0, k), dtype=np.uint32)
+    return {"B": B, "Bpref": Bpref, "rt": rt, "V": Vc, "O": Oc, "l0start": np.array(l0start, dtype=np.uint64)}
 
 
 def gj_enumerate(n_vars: int, atoms, rels, order=None, filt=None) -> np.ndarray:

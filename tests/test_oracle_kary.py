@@ -9,6 +9,7 @@ written binary Generic Join oracle on graphs, and the paper's invariant that
 the loop order changes the work but not the result (Sec. 5).
 """
 import itertools
+import os
 
 import numpy as np
 import pytest
@@ -307,3 +308,132 @@ def test_threaded_count_equals_sequential(name, query):
         want = oracle.kgj(nv, atoms, rels, order=order, work=True)
         for t in (2, 3, 8, 64, 100):
             assert oracle.kgj(nv, atoms, rels, order=order, work=True, nthreads=t) == want, (order, t)
+
+
+# ------------------------------------------------------------- partitioning
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = [s.strip() for s in line.split("=", 1)]
+            out[k] = [[int(t) for t in r.split()] for r in v.split(";")]
+    return out
+
+
+def test_kpartition_worked_example():
+    """Sec. 4, Example "partition" on a ternary R(X,Y,Z) with shares 2x2x1:
+    partition (0,1,0) holds (0,4,1), (5,3,9), has B = 2 and starts at
+    B^pref = 3; partition (1,0,0) is empty."""
+    g = _golden("kpartition_example.txt")
+    px, py, pz = g["shares_xyz"][0]
+    grey = tuple(g["grey_partition"][0])
+    grey_tuples = [tuple(t) for t in g["grey_tuples"]]
+    sx = next(s for s in range(1, 100000) if all(oracle.share(t[0], s, px) == grey[0] for t in grey_tuples))
+    sy = next(s for s in range(1, 100000) if all(oracle.share(v, s, py) == 1 for v in g["hY_one"][0]))
+    hx = lambda v: oracle.share(v, sx, px)
+    hy = lambda v: oracle.share(v, sy, py)
+    xs0 = [v for v in range(10, 400) if hx(v) == 0][:3]
+    xs1 = [v for v in range(10, 400) if hx(v) == 1][:2]
+    ys0 = [v for v in range(10, 400) if hy(v) == 0][:3]
+    rel = [(xs0[i], ys0[i], 7 + i) for i in range(3)]   # 3 rows in (0,0,0)
+    rel += grey_tuples                                     # (0,1,0)
+    rel += [(xs1[0], 1, 2), (xs1[1], 4, 6)]                # (1,1,0); (1,0,0) left empty
+    part = oracle.kpartition(np.array(rel, dtype=np.uint32), (sx, sy, 77), (px, py, pz))
+    pid = (grey[0] * py + grey[1]) * pz + grey[2]
+    e = g["empty_partition"][0]
+    assert int(part["B"][pid]) == g["B_grey"][0][0]
+    assert int(part["Bpref"][pid]) == g["Bpref_grey"][0][0]
+    assert int(part["B"][(e[0] * py + e[1]) * pz + e[2]]) == 0
+    lo, hi = int(part["Bpref"][pid]), int(part["Bpref"][pid + 1])
+    assert sorted(map(tuple, part["rt"][lo:hi].tolist())) == sorted(grey_tuples)
+
+
+def _expand(V, O, lo, hi):
+    """Rows of the trie whose level-0 entries are [lo, hi), in level order."""
+    k = len(V)
+    rows = []
+
+    def walk(d, e, prefix):
+        t = prefix + (int(V[d][e]),)
+        if d == k - 1:
+            rows.append(t)
+            return
+        for c in range(int(O[d][e]), int(O[d][e + 1])):
+            walk(d + 1, c, t)
+
+    for e in range(lo, hi):
+        walk(0, e, ())
+    return rows
+
+
+@pytest.mark.parametrize("k,shares", [(1, (4,)), (2, (3, 2)), (3, (2, 2, 1)), (3, (1, 3, 2)), (3, (4, 1, 1)),
+                                      (3, (1, 1, 1))])
+@pytest.mark.parametrize("seed", range(3))
+def test_kpartition_definition(k, shares, seed):
+    """R~ is the input reordered (no replication); B^pref is B's exclusive
+    prefix; every row of segment p has partition identifiers whose mixed
+    radix (column 0 most significant) is p; the levels of partition p,
+    walked from its level-0 range, give back exactly its rows in level
+    order."""
+    rng = np.random.default_rng(40 + seed)
+    rel = random_rel(rng, k, {1: 60, 2: 12, 3: 6}[k], 0.4)
+    seeds = [int(x) for x in rng.integers(1, 1 << 31, size=k)]
+    for cols in itertools.permutations(range(k)):
+        part = oracle.kpartition(rel, seeds, shares, cols)
+        n = rel.shape[0]
+        rt = part["rt"]
+        assert np.array_equal(sorted_rows(rt), sorted_rows(rel))
+        pref = part["Bpref"].astype(np.int64)
+        assert pref[0] == 0 and pref[-1] == n and np.array_equal(np.diff(pref), part["B"].astype(np.int64))
+        l0 = part["l0start"].astype(np.int64)
+        assert l0[0] == 0 and l0[-1] == part["V"][0].shape[0] and np.all(np.diff(l0) >= 0)
+        assert part["V"][k - 1].shape[0] == n
+        for p in range(int(np.prod(shares))):
+            seg = rt[pref[p]:pref[p + 1]]
+            for row in seg.tolist():
+                ids = [oracle.share(row[c], seeds[c], shares[c]) for c in range(k)]
+                pid = 0
+                for c in range(k):
+                    pid = pid * shares[c] + ids[c]
+                assert pid == p
+            got = _expand(part["V"], part["O"], int(l0[p]), int(l0[p + 1]))
+            want = sorted(tuple(int(r[c]) for c in cols) for r in seg.tolist())
+            assert got == want, (cols, p)
+
+
+@pytest.mark.parametrize("vshares", [(2, 2, 1, 2), (3, 1, 2, 1), (1, 1, 1, 1), (2, 3, 2, 2)])
+def test_kpartition_cells_partition_the_join(vshares):
+    """Sec. 4-5: cell (c_X, c_Y, c_Z, c_U) joins, for each atom, the
+    partition its variables' coordinates select; the cells' outputs are
+    disjoint and cover the query's result, so the per-cell counts add up to
+    the unpartitioned count and each cell's tuples hash to that cell."""
+    nv, atoms = LW
+    rng = np.random.default_rng(77)
+    rels = [random_rel(rng, 3, 7, 0.55) for _ in atoms]
+    vseeds = [11, 22, 33, 44]
+    parts = [oracle.kpartition(r, [vseeds[v] for v in a], [vshares[v] for v in a]) for a, r in zip(atoms, rels)]
+    total = oracle.kgj(nv, atoms, rels)
+    acc = 0
+    for cell in itertools.product(*[range(s) for s in vshares]):
+        sub = []
+        for a, pt in zip(atoms, parts):
+            pid = 0
+            for v in a:
+                pid = pid * vshares[v] + cell[v]
+            lo, hi = int(pt["Bpref"][pid]), int(pt["Bpref"][pid + 1])
+            sub.append(pt["rt"][lo:hi])
+        cnt, tup = oracle.kgj(nv, atoms, sub, tuples=True)
+        acc += cnt
+        if cnt:
+            cid = 0
+            for v in range(nv):
+                cid = cid * vshares[v] + cell[v]
+            assert np.all(oracle.tuple_cells(tup, vseeds, vshares) == cid)
+    assert acc == total
