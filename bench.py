@@ -62,6 +62,9 @@ def parse_args():
                          "ternary relations; skew: per-cell work and time of the R-MAT triangle under the "
                          "paper's share vectors (Sec. 1, Examples 1-3)")
     ap.add_argument("--lw-n", type=int, default=512, help="lw: cube side n of ST-Dense's [n]^3 relations")
+    ap.add_argument("--kshares", default="",
+                    help="lw / ct: HyperCube shares of the four variables, e.g. 2,2,1,2 (Sec. 4, Example "
+                         "'partition'); the relations are partitioned when their indexes are built")
     ap.add_argument("--tensor", choices=["dense", "sparse"], default="dense",
                     help="lw / ct: ST-Dense or ST-Sparse relations")
     ap.add_argument("--ct-m", type=int, default=4096, help="ct: m of the F x [m] x [m] relations")
@@ -958,9 +961,17 @@ def kary_workload(a, world, rank, local):
     q = hc.KQuery(4, tuple(atoms))
     ixs = [hc.build_kindex(rows[j], None, stream=stream) for j in range(na)]
     q = q.with_order(hc.choose_korder(q, ixs))  # Sec. 5.2-5.3 from the built indexes' statistics
-    ixs = [ix if ix.level_cols == q.level_cols(j) else hc.build_kindex(rows[j], q.level_cols(j), stream=stream)
+    kshares = tuple(int(x) for x in a.kshares.split(",")) if a.kshares else (1, 1, 1, 1)
+    per_atom = hc.atom_shares(q, kshares)
+
+    def kbuild(j, r, **kw):
+        if kshares == (1, 1, 1, 1):
+            return hc.build_kindex(r, q.level_cols(j), stream=stream, **kw)
+        return hc.build_kindex(r, q.level_cols(j), stream=stream, seeds=per_atom[j][0], shares=per_atom[j][1], **kw)
+
+    ixs = [ix if ix.level_cols == q.level_cols(j) and kshares == (1, 1, 1, 1) else kbuild(j, rows[j])
            for j, ix in enumerate(ixs)]
-    tb = [hc.build_kindex(rows[j], q.level_cols(j), stream=stream, time_kernels=True) for j in range(na)]
+    tb = [kbuild(j, rows[j], time_kernels=True) for j in range(na)]
     build_ms = [ix.ms_sort + ix.ms_levels for ix in tb]
     del tb
     stats = hc.run_kjoin(q, ixs, stats=True, stream=stream)
@@ -1018,7 +1029,7 @@ def kary_workload(a, world, rank, local):
         def e2e_step():
             for b, h in zip(bufs, hosts):
                 b.copy_(h, non_blocking=True)
-            xs = [hc.build_kindex(bufs[j], q.level_cols(j), stream=stream) for j in range(na)]
+            xs = [kbuild(j, bufs[j]) for j in range(na)]
             c = hc.run_kjoin(q, xs, stream=stream).count
             for x in xs:
                 x.free()
@@ -1050,7 +1061,7 @@ def kary_workload(a, world, rank, local):
         t0 = time.perf_counter()
         c = oracle.kgj(4, atoms, sample, order=list(q.loop_order()), nthreads=threads)
         dt = time.perf_counter() - t0
-        sx = [hc.build_kindex(torch.from_numpy(r.view(np.int32)).to(dev), q.level_cols(j)) for j, r in enumerate(sample)]
+        sx = [kbuild(j, torch.from_numpy(r.view(np.int32)).to(dev)) for j, r in enumerate(sample)]
         got = hc.run_kjoin(q, sx).count
         if got != c:
             raise RuntimeError(f"sampled parity: GPU {got} != oracle {c}")
@@ -1066,7 +1077,8 @@ def kary_workload(a, world, rank, local):
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32",
                 "data": f"synthetic (ST-{tname} shape, seeded)",
                 "config": {"workload": desc, "rows_per_relation": [int(r.shape[0]) for r in host_rels],
-                           "order": list(q.loop_order()), "count": int(expect), "work": int(work),
+                           "order": list(q.loop_order()), "shares": list(kshares), "n_cells": int(stats.n_cells),
+                           "count": int(expect), "work": int(work),
                            "index_build_ms": [round(b, 3) for b in build_ms],
                            "l2": ("inputs larger than L2: %.0f MB of V_2 over the indexes" if v2_bytes > 129e6
                                   else "inputs within L2: %.0f MB of V_2 over the indexes") % (v2_bytes / 1e6),

@@ -45,6 +45,27 @@ typedef struct hc_kindex hc_kindex;
  * distinct; without the check flag repeated rows give wrong join results. */
 hc_status hc_build_kindex(const uint32_t* d_rows, uint64_t n, uint32_t arity, const uint8_t* level_cols,
                           uint32_t flags, void* stream, hc_kindex** out);
+
+/* ------------------------------------------------ build_kindex_partitioned
+ * The same index for a relation partitioned for HyperCube shares (Sec. 4,
+ * "Preprocessor", Example "partition"): column c of a row has the partition
+ * identifier s_c = h_c(x_c) = (fmix32(x_c ^ seeds[c]) * shares[c]) >> 32
+ * (fmix32: the MurmurHash3 32-bit finaliser), and the row's partition is
+ *    p = (..(s_0 * shares[1] + s_1) * shares[2] + s_2..)
+ * (column 0 most significant: partitions in the lexicographic order of their
+ * identifiers).  The partitions are concatenated in order of p (R~), each
+ * with its own k-level CoCo: V_d and O_d are the partitions' levels
+ * concatenated, O_d pointing into the concatenated level d+1, and the view
+ * gives each partition's first row (B^pref) and first level-0 entry.
+ *   seeds, shares  host, [arity]: per column; shares[c] >= 1 with product
+ *                  at most 65536 (HC_ERR_ARG otherwise, and when either is
+ *                  NULL).  A product of 1 builds the unpartitioned index.
+ * Other arguments and errors as hc_build_kindex.  A partitioned index keeps
+ * a level-0 position map only when the deeper levels' columns have share 1
+ * (each level-0 value then sits in one partition).  Waits for the GPU. */
+hc_status hc_build_kindex_partitioned(const uint32_t* d_rows, uint64_t n, uint32_t arity, const uint8_t* level_cols,
+                                      const uint32_t* seeds, const uint32_t* shares, uint32_t flags, void* stream,
+                                      hc_kindex** out);
 hc_status hc_kindex_free(hc_kindex* index);
 
 typedef struct {
@@ -59,6 +80,12 @@ typedef struct {
     /* filled when built with HC_BUILD_TIME_KERNELS, else 0:                         */
     float ms_sort;                /* device time of the sort stage                    */
     float ms_levels;              /* device time of the level scan                    */
+    uint32_t n_parts;             /* partitions (1: unpartitioned)                    */
+    uint32_t shares[HC_KMAX_ARITY]; /* per column (1 when unpartitioned)              */
+    uint32_t seeds[HC_KMAX_ARITY];  /* per column (0 when unpartitioned)              */
+    /* n_parts > 1, else NULL; device, [n_parts + 1], entry n_parts closes the last: */
+    const uint32_t* d_bpref;        /* B^pref: first row of each partition in R~ (n)  */
+    const uint32_t* d_level0_start; /* first level-0 entry of each partition (l_0)    */
 } hc_kindex_view;
 hc_status hc_kindex_get_view(const hc_kindex* index, hc_kindex_view* out);
 
@@ -90,28 +117,39 @@ typedef struct {
 
 typedef struct {
     uint32_t mode;          /* HC_MODE_COUNT or HC_MODE_MATERIALIZE                    */
-    uint32_t flags;         /* HC_FLAG_STATS, HC_FLAG_TIME_KERNELS                      */
+    uint32_t flags;         /* HC_FLAG_STATS, HC_FLAG_TIME_KERNELS, HC_FLAG_CELL_COUNTS */
     uint32_t item_grain;    /* loop-1 candidates per work item (0: sized from the run)  */
     uint32_t block_threads; /* threads per block of the search kernel: 32, 64, 96 or   */
                             /* 128 (0: 128)                                             */
 } hc_kjoin_params;
 
-/* Generic Join of q over k-level indexes (Sec. 5), one cell (no HyperCube
- * shares).  Loop 0 runs as a flat pass over the shortest of its lists;
- * later loops run in a persistent kernel whose warps take work items
- * (ranges of loop-1 candidates) from an atomic counter and walk the rest of
- * the loops depth first, 32 candidates at a time, each searched in the
- * loop's other lists.
+/* Generic Join of q over k-level indexes (Sec. 5) in every HyperCube cell
+ * (Sec. 4-5).  The shares come from the indexes: an index built with
+ * hc_build_kindex_partitioned partitions each variable of its atom, and
+ * every atom holding a variable must partition it with the same share and
+ * seed (share 1 everywhere for an unpartitioned variable; HC_ERR_ARG
+ * otherwise).  Cells are numbered by the mixed radix of the variables'
+ * coordinates, variable 0 most significant (at most 2^20 cells,
+ * HC_ERR_CAPACITY), and cell (c_0, ..) intersects, in each atom, the
+ * partition its variables' coordinates select; the cells' results are
+ * disjoint and their union is Q.  Loop 0 runs as a flat pass over the
+ * loop-0 candidates of all cells (in each cell, the shortest of its
+ * lists); later loops run in a persistent kernel whose warps take work
+ * items (ranges of loop-1 candidates) from an atomic counter and walk the
+ * rest of the loops depth first, 32 candidates at a time, each searched in
+ * the loop's other lists.
  *   idx[j]   index bound to atom j, of the atom's arity; its levels must
  *            hold the atom's variables in loop order (level d's variable is
  *            bound before level d+1's), else HC_ERR_ARG.
- *   Limits: at most 4 atoms hold any one variable, n_vars <= HC_KMAX_VARS
- *   (HC_ERR_CAPACITY).
+ *   Limits: at most 4 atoms hold any one variable, n_vars <= HC_KMAX_VARS,
+ *   fewer than 2^32 - 1 loop-0 candidates over all cells (HC_ERR_CAPACITY).
  * Count mode enqueues everything and returns without waiting.
  * Materialize mode counts first, waits, then writes the tuples (n_vars
  * uint32 values in variable-id order, in no fixed order).  With
  * HC_FLAG_STATS the view's `work` is the sum over loops and bindings of
- * (number of lists) * (shortest list length).  n_cells is 1 and n_items 0. */
+ * (number of lists) * (shortest list length), summed over the cells; with
+ * HC_FLAG_CELL_COUNTS the view's d_cell_counts[n_cells] holds the count of
+ * each cell.  n_items is 0. */
 hc_status hc_run_kjoin(const hc_kquery* q, const hc_kindex* const* idx, const hc_kjoin_params* params,
                        void* stream, hc_result** out);
 

@@ -549,6 +549,6 @@ class _ResultHandle:
             pass
 
 
-from .kary import CT, LW, KIndex, KQuery, build_kindex, choose_korder, kplan_cost, run_kjoin  # noqa: E402
+from .kary import CT, LW, KIndex, KQuery, atom_shares, build_kindex, choose_korder, kplan_cost, run_kjoin  # noqa: E402,E501
 
-__all__ += ["KQuery", "KIndex", "build_kindex", "run_kjoin", "choose_korder", "kplan_cost", "LW", "CT"]
+__all__ += ["KQuery", "KIndex", "build_kindex", "run_kjoin", "choose_korder", "kplan_cost", "atom_shares", "LW", "CT"]

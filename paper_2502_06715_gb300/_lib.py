@@ -76,7 +76,10 @@ class hc_kindex_view(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("arity", ctypes.c_uint32), ("level_cols", ctypes.c_uint8 * HC_KMAX_ARITY),
                 ("packed", ctypes.c_uint8), ("len", ctypes.c_uint64 * HC_KMAX_ARITY),
                 ("max_value", ctypes.c_uint32 * HC_KMAX_ARITY), ("d_v", ctypes.c_void_p * HC_KMAX_ARITY),
-                ("d_o", ctypes.c_void_p * HC_KMAX_ARITY), ("ms_sort", ctypes.c_float), ("ms_levels", ctypes.c_float)]
+                ("d_o", ctypes.c_void_p * HC_KMAX_ARITY), ("ms_sort", ctypes.c_float), ("ms_levels", ctypes.c_float),
+                ("n_parts", ctypes.c_uint32), ("shares", ctypes.c_uint32 * HC_KMAX_ARITY),
+                ("seeds", ctypes.c_uint32 * HC_KMAX_ARITY), ("d_bpref", ctypes.c_void_p),
+                ("d_level0_start", ctypes.c_void_p)]
 
 
 class hc_katom(ctypes.Structure):
@@ -138,6 +141,10 @@ SIGNATURES = {
     "hc_build_kindex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
                                        ctypes.POINTER(ctypes.c_uint8), ctypes.c_uint32, ctypes.c_void_p,
                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "hc_build_kindex_partitioned": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                                                   ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ctypes.c_uint32),
+                                                   ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32,
+                                                   ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "hc_kindex_free": (ctypes.c_int, [ctypes.c_void_p]),
     "hc_kindex_get_view": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hc_kindex_view)]),
     "hc_run_kjoin": (ctypes.c_int, [ctypes.POINTER(hc_kquery), ctypes.POINTER(ctypes.c_void_p),

@@ -53,6 +53,17 @@ struct hc_kindex {
     // bucket directory of each level's runs (level 0: one run, built when
     // there is no position map; level d >= 1: the runs of O_{d-1})
     uint4* d_g[HC_KMAX_ARITY] = {nullptr, nullptr, nullptr};
+    // HyperCube partitions (Sec. 4, "Preprocessor"): the share and seed of
+    // each column, n_parts their product.  Partitioned (n_parts > 1), the
+    // levels concatenate the partitions' tries in partition order; d_bpref[p]
+    // is partition p's first row (B^pref) and d_l0start[p] its first level-0
+    // entry, both [n_parts + 1]; h_l0start is the host copy of d_l0start.
+    uint32_t n_parts = 1;
+    uint32_t pshare[HC_KMAX_ARITY] = {1, 1, 1};
+    uint32_t pseed[HC_KMAX_ARITY] = {0, 0, 0};
+    uint32_t* d_bpref = nullptr;
+    uint32_t* d_l0start = nullptr;
+    std::vector<uint32_t> h_l0start;
     float ms_sort = 0.f, ms_levels = 0.f;
     bool stats_only = false;  // sizes only (planning), no device arrays
 };
@@ -108,6 +119,22 @@ struct KLayout {
     uint64_t mask[HC_KMAX_ARITY];
 };
 
+// Partition id of a row from its level values (Sec. 4): the mixed-radix
+// number of the columns' identifiers s_c = h_c(x_c), column 0 most
+// significant; by level d, weight[d] is the radix weight of level d's column.
+struct KPart {
+    uint32_t np;
+    uint32_t share[HC_KMAX_ARITY], seed[HC_KMAX_ARITY], weight[HC_KMAX_ARITY];
+};
+
+template <int K>
+__host__ __device__ __forceinline__ uint32_t kpid(const KPart& P, const uint32_t (&c)[K]) {
+    uint32_t p = 0;
+#pragma unroll
+    for (int d = 0; d < K; ++d) p += share_of(c[d], P.seed[d], P.share[d]) * P.weight[d];
+    return p;
+}
+
 __global__ void kcolmax_kernel(const uint32_t* __restrict__ rows, uint64_t n, uint32_t k, KBuildCtl* ctl) {
     uint32_t m[HC_KMAX_ARITY] = {0, 0, 0};
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
@@ -124,14 +151,22 @@ __global__ void kcolmax_kernel(const uint32_t* __restrict__ rows, uint64_t n, ui
     }
 }
 
-// Rows -> packed keys, stored as (high word, low word) pairs.
-__global__ void kpack_kernel(const uint32_t* __restrict__ rows, uint64_t n, KLayout L, uint2* __restrict__ out) {
+// Rows -> packed keys, stored as (high word, low word) pairs; a partitioned
+// build puts the row's partition id above the levels, at bit pid_shift.
+__global__ void kpack_kernel(const uint32_t* __restrict__ rows, uint64_t n, KLayout L, KPart Pt, uint32_t pid_shift,
+                             uint2* __restrict__ out) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t* r = rows + i * L.k;
         uint64_t key = 0;
+        uint32_t pid = 0;
 #pragma unroll
         for (int d = 0; d < HC_KMAX_ARITY; ++d)
-            if (d < (int)L.k) key |= (uint64_t)r[L.col[d]] << L.shift[d];
+            if (d < (int)L.k) {
+                const uint32_t x = r[L.col[d]];
+                key |= (uint64_t)x << L.shift[d];
+                if (Pt.np > 1) pid += share_of(x, Pt.seed[d], Pt.share[d]) * Pt.weight[d];
+            }
+        if (Pt.np > 1) key |= (uint64_t)pid << pid_shift;
         out[i] = make_uint2((uint32_t)(key >> 32), (uint32_t)key);
     }
 }
@@ -143,6 +178,20 @@ __global__ void kperm_pairs_kernel(const uint32_t* __restrict__ rows, uint64_t n
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t r = perm ? perm[i] : i;
         out[i] = make_uint2(rows[r * k + col], (uint32_t)i);
+    }
+}
+
+// Pairs (partition id of row perm[i], i): the last, most significant pass of
+// a partitioned unpacked sort.
+__global__ void kpid_pairs_kernel(const uint32_t* __restrict__ rows, uint64_t n, KLayout L, KPart Pt,
+                                  const uint32_t* __restrict__ perm, uint2* __restrict__ out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t r = perm ? perm[i] : i;
+        uint32_t pid = 0;
+#pragma unroll
+        for (int d = 0; d < HC_KMAX_ARITY; ++d)
+            if (d < (int)L.k) pid += share_of(rows[r * L.k + L.col[d]], Pt.seed[d], Pt.share[d]) * Pt.weight[d];
+        out[i] = make_uint2(pid, (uint32_t)i);
     }
 }
 
@@ -162,6 +211,9 @@ struct KSorted {
     const uint32_t* rows;
     const uint32_t* perm;
     KLayout L;
+    KPart part;        // np > 1: rows are sorted by partition first
+    uint32_t* bpref;   // partitioned: first row of each partition (others untouched)
+    uint32_t* l0start; // partitioned: first level-0 entry of each partition
 };
 
 template <int K, bool PACKED>
@@ -177,7 +229,10 @@ __device__ __forceinline__ void load_levels(const KSorted& s, uint64_t i, uint32
     }
 }
 
-// Level scan.  Rows are warp-striped as in the binary run-boundary scan:
+// Level scan.  A partitioned build (rows sorted by partition id first)
+// treats a change of partition like a change at level 0: the row opens an
+// entry of every level, and records itself as its partition's first row and
+// that entry as the partition's first level-0 entry.  Rows are warp-striped as in the binary run-boundary scan:
 // item j of lane q of warp w is row tile * KL_TILE + w * 32 * KL_ITEMS +
 // 32 j + q, so the row before a lane-0 row is lane 31's row of the previous
 // item.  fd = the first level at which a row differs from the row before
@@ -229,6 +284,10 @@ __global__ void __launch_bounds__(KL_THREADS) klevels_kernel(KSorted src, uint64
 #pragma unroll
     for (int d = 0; d < K; ++d) carry[d] = 0;
     if (lane == 0 && base > 0 && base < n) load_levels<K, PACKED>(src, base - 1, carry);
+    const bool parted = src.part.np > 1;
+    uint32_t carry_pid = 0;
+    if (parted && lane == 0) carry_pid = kpid<K>(src.part, carry);
+    uint32_t pchg = 0;  // bit j: item j's row is the first of its partition
 
     uint32_t ball[KL_ITEMS][NLA];
     uint32_t cnt[NLA];
@@ -247,6 +306,19 @@ __global__ void __launch_bounds__(KL_THREADS) klevels_kernel(KSorted src, uint64
             if (c[j][d] != prev) fd = d;
         }
         if (i == 0) fd = 0;
+        if (parted) {
+            const uint32_t pc = kpid<K>(src.part, c[j]);
+            uint32_t pp = __shfl_up_sync(FULL, pc, 1);
+            if (lane == 0) pp = carry_pid;
+            const uint32_t plast = __shfl_sync(FULL, pc, 31);
+            if (lane == 0) carry_pid = plast;
+            if (pc != pp) fd = 0;
+            if (valid && (pc != pp || i == 0)) {
+                pchg |= 1u << j;
+                src.bpref[pc] = (uint32_t)i;
+                if (K == 1) src.l0start[pc] = (uint32_t)i;
+            }
+        }
         dup |= valid && fd == K;
 #pragma unroll
         for (int d = 0; d < NL; ++d) {
@@ -296,6 +368,7 @@ __global__ void __launch_bounds__(KL_THREADS) klevels_kernel(KSorted src, uint64
             if (ball[j][d] >> lane & 1u) {  // flagged rows are valid rows
                 const uint64_t e = pos[d] + __popc(ball[j][d] & lt);
                 vv[d][e] = c[j][d];
+                if (d == 0 && (pchg >> j & 1u)) src.l0start[kpid<K>(src.part, c[j])] = (uint32_t)e;
                 const int d1 = d + 1 < NL ? d + 1 : d;
                 const uint64_t child = d + 1 < NL ? pos[d1] + __popc(ball[j][d1] & lt) : i;
                 oo[d][e] = (uint32_t)child;
@@ -358,11 +431,14 @@ void kindex_release(hc_kindex* x, cudaStream_t s) {
         dev_free(x->d_g[d], s);
     }
     dev_free(x->d_v0pos, s);
+    dev_free(x->d_bpref, s);
+    dev_free(x->d_l0start, s);
     delete x;
 }
 
 hc_status build_kindex_impl(const uint32_t* d_rows, uint64_t n, uint32_t k, const uint8_t* level_cols,
-                            uint32_t flags, cudaStream_t s, hc_kindex** out) {
+                            const uint32_t* seeds, const uint32_t* shares, uint32_t flags, cudaStream_t s,
+                            hc_kindex** out) {
     if (!out) return fail(HC_ERR_ARG, "build_kindex: out is NULL");
     *out = nullptr;
     if (k < 1 || k > HC_KMAX_ARITY) return fail(HC_ERR_ARG, "build_kindex: arity must be 1, 2 or 3");
@@ -378,15 +454,41 @@ hc_status build_kindex_impl(const uint32_t* d_rows, uint64_t n, uint32_t k, cons
             cols[d] = level_cols[d];
         }
     }
+    uint64_t np = 1;
+    if (shares) {
+        for (uint32_t c = 0; c < k; ++c) {
+            if (shares[c] == 0) return fail(HC_ERR_ARG, "build_kindex: shares must be at least 1");
+            np *= shares[c];
+            if (np > 65536) return fail(HC_ERR_ARG, "build_kindex: the shares' product must be at most 65536");
+        }
+    }
     hc_kindex* x = new hc_kindex();
     x->n = n;
     x->arity = k;
     for (uint32_t d = 0; d < k; ++d) x->level_cols[d] = cols[d];
+    x->n_parts = (uint32_t)np;
+    if (np > 1)
+        for (uint32_t c = 0; c < k; ++c) {
+            x->pshare[c] = shares[c];
+            x->pseed[c] = seeds ? seeds[c] : 0u;
+        }
     auto bail = [&](hc_status st) {
         kindex_release(x, s);
         return st;
     };
     void* p = nullptr;
+    if (np > 1) {
+        // every partition starts at 0 until the level scan says otherwise
+        if (dev_alloc(&p, (np + 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+        x->d_bpref = (uint32_t*)p;
+        if (dev_alloc(&p, (np + 1) * 4, s) != HC_OK) return bail(HC_ERR_OOM);
+        x->d_l0start = (uint32_t*)p;
+        const int fill = n == 0 ? 0x00 : 0xFF;
+        if (cudaMemsetAsync(x->d_bpref, fill, (np + 1) * 4, s) != cudaSuccess ||
+            cudaMemsetAsync(x->d_l0start, fill, (np + 1) * 4, s) != cudaSuccess)
+            return bail(cuda_fail(cudaGetLastError(), "memset"));
+        x->h_l0start.assign(np + 1, 0u);
+    }
     if (n == 0) {
         for (uint32_t d = 0; d < k; ++d) {
             if (dev_alloc(&p, 4, s) != HC_OK) return bail(HC_ERR_OOM);
@@ -428,6 +530,16 @@ hc_status build_kindex_impl(const uint32_t* d_rows, uint64_t n, uint32_t k, cons
         L.shift[d] = bits[d] ? (uint32_t)sh : 0u;  // a level of zeros takes no bits (and no shift of 64)
         sh += (int)bits[d];
     }
+    KPart Pt{};
+    Pt.np = (uint32_t)np;
+    for (uint32_t d = 0; d < k; ++d) {
+        Pt.share[d] = x->pshare[cols[d]];
+        Pt.seed[d] = x->pseed[cols[d]];
+        uint32_t w = 1;
+        for (uint32_t c = cols[d] + 1; c < k; ++c) w *= x->pshare[c];
+        Pt.weight[d] = w;
+    }
+    const uint32_t pid_bits = bit_width((uint32_t)(np - 1));
 
     const bool timed = (flags & HC_BUILD_TIME_KERNELS) != 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -447,17 +559,20 @@ hc_status build_kindex_impl(const uint32_t* d_rows, uint64_t n, uint32_t k, cons
     // ---- sort
     KSorted src{};
     src.L = L;
+    src.part = Pt;
+    src.bpref = x->d_bpref;
+    src.l0start = x->d_l0start;
     hc_index* sorted = nullptr;  // holds the packed keys, sorted
     auto bail2 = [&](hc_status e) {
         if (sorted) index_release(sorted, s);
         destroy_events();
         return bail(e);
     };
-    if (total_bits <= 64) {
+    if (total_bits + pid_bits <= 64) {
         x->packed = true;
         uint2* pk;
         if ((st = tmp.get(&pk, n)) != HC_OK) return bail2(st);
-        kpack_kernel<<<grid_of(n, 256, 8), 256, 0, s>>>(d_rows, n, L, pk);
+        kpack_kernel<<<grid_of(n, 256, 8), 256, 0, s>>>(d_rows, n, L, Pt, total_bits, pk);
         if (cudaError_t le = launch_check()) return bail2(cuda_fail(le, "kpack_kernel"));
         if ((st = build_index_impl((const uint32_t*)pk, n, 0, BUILD_NO_DIRECTORIES, s, &sorted)) != HC_OK) return bail2(st);
         src.keys = sorted->d_keys;
@@ -472,6 +587,19 @@ hc_status build_kindex_impl(const uint32_t* d_rows, uint64_t n, uint32_t k, cons
             if (cudaError_t le = launch_check()) return bail2(cuda_fail(le, "kperm_pairs_kernel"));
             hc_index* pass = nullptr;
             if ((st = build_index_impl((const uint32_t*)pairs, n, 0, BUILD_NO_DIRECTORIES, s, &pass)) != HC_OK) return bail2(st);
+            uint32_t* nxt = cur == pa ? pb : pa;
+            kperm_compose_kernel<<<grid_of(n, 256, 8), 256, 0, s>>>(pass->d_keys, cur, nxt, n);
+            cudaError_t le = launch_check();
+            index_release(pass, s);
+            if (le) return bail2(cuda_fail(le, "kperm_compose_kernel"));
+            cur = nxt;
+        }
+        if (np > 1) {  // the partition id last: the most significant key
+            kpid_pairs_kernel<<<grid_of(n, 256, 8), 256, 0, s>>>(d_rows, n, L, Pt, cur, pairs);
+            if (cudaError_t le = launch_check()) return bail2(cuda_fail(le, "kpid_pairs_kernel"));
+            hc_index* pass = nullptr;
+            if ((st = build_index_impl((const uint32_t*)pairs, n, 0, BUILD_NO_DIRECTORIES, s, &pass)) != HC_OK)
+                return bail2(st);
             uint32_t* nxt = cur == pa ? pb : pa;
             kperm_compose_kernel<<<grid_of(n, 256, 8), 256, 0, s>>>(pass->d_keys, cur, nxt, n);
             cudaError_t le = launch_check();
@@ -530,7 +658,32 @@ hc_status build_kindex_impl(const uint32_t* d_rows, uint64_t n, uint32_t k, cons
             cudaMemcpyAsync(x->d_o[d], o[d], (l + 1) * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return bail(cuda_fail(cudaGetLastError(), "build_kindex: level copy"));
     }
-    if (v1pos_eligible(n, x->maxv[0])) {
+    if (np > 1) {
+        // the starts of empty partitions were left unwritten (~0): each takes
+        // the start of the next partition, and entry np closes the last one
+        std::vector<uint32_t> hb(np + 1);
+        if (cudaMemcpyAsync(hb.data(), x->d_bpref, (np + 1) * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(x->h_l0start.data(), x->d_l0start, (np + 1) * 4, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return bail(cuda_fail(cudaGetLastError(), "build_kindex: partition starts"));
+        hb[np] = (uint32_t)n;
+        x->h_l0start[np] = (uint32_t)x->len[0];
+        for (int64_t q = (int64_t)np - 1; q >= 0; --q) {
+            if (hb[q] == 0xFFFFFFFFu) hb[q] = hb[q + 1];
+            if (x->h_l0start[q] == 0xFFFFFFFFu) x->h_l0start[q] = x->h_l0start[q + 1];
+        }
+        if (cudaMemcpyAsync(x->d_bpref, hb.data(), (np + 1) * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(x->d_l0start, x->h_l0start.data(), (np + 1) * 4, cudaMemcpyHostToDevice, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return bail(cuda_fail(cudaGetLastError(), "build_kindex: partition starts"));
+    }
+    // a level-0 position map needs each level-0 value in one partition: the
+    // deeper levels' columns unpartitioned
+    bool v0_unique = true;
+    for (uint32_t d = 1; d < k; ++d) v0_unique &= x->pshare[cols[d]] == 1;
+    if (v0_unique && v1pos_eligible(n, x->maxv[0])) {
         const uint64_t dn = (uint64_t)x->maxv[0] + 1;
         if (dev_alloc(&p, dn * 4, s) != HC_OK) return bail(HC_ERR_OOM);
         x->d_v0pos = (uint32_t*)p;
@@ -540,10 +693,12 @@ hc_status build_kindex_impl(const uint32_t* d_rows, uint64_t n, uint32_t k, cons
         kpos_kernel<<<grid_of(x->len[0], 256, 8), 256, 0, s>>>(x->d_v[0], x->len[0], x->d_v0pos, x->v0pos_n);
         if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "kpos_kernel"));
     }
-    // bucket directories: level 0 as one run (without a position map), and
-    // every deeper level by the runs its parent level's offsets mark
-    if (x->d_v0pos == nullptr && (st = build_directory(x->d_v[0], x->len[0], nullptr, x->len[0], nullptr, nullptr, s,
-                                                       &x->d_g[0])) != HC_OK)
+    // bucket directories: level 0 as one run per partition (without a
+    // position map), and every deeper level by the runs its parent level's
+    // offsets mark
+    if (x->d_v0pos == nullptr &&
+        (st = build_directory(x->d_v[0], x->len[0], np > 1 ? x->d_l0start : nullptr, np > 1 ? np : x->len[0],
+                              nullptr, nullptr, s, &x->d_g[0])) != HC_OK)
         return bail(st);
     for (uint32_t d = 1; d < k; ++d)
         if ((st = build_directory(x->d_v[d], x->len[d], x->d_o[d - 1], x->len[d - 1], nullptr, nullptr, s,
@@ -558,6 +713,7 @@ hc_status build_kindex_impl(const uint32_t* d_rows, uint64_t n, uint32_t k, cons
 namespace {
 
 constexpr int KMAXS = 4;          // lists intersected by one loop
+constexpr uint64_t KMAX_CELLS = 1ull << 20;
 constexpr int KJ_MAXT = 128;      // threads per block of the search kernel, at most
 constexpr int KJ_WARPS = KJ_MAXT / 32;
 
@@ -571,24 +727,40 @@ struct KSrc {
     const uint4* g;       // bucket directory of this level's runs, or NULL
     const uint32_t* o;
     const uint32_t* pos;  // depth 0: value -> position in V_0 (V1POS_NONE if absent), or NULL
+    const uint32_t* l0s;  // depth 0 of a partitioned atom: first level-0 entry of each partition, else NULL
     uint32_t pos_n;       // values covered by pos
     uint32_t top_len;     // l_0 of the atom
+    uint32_t pw[HC_KMAX_ARITY];  // radix weight of each column of the atom in its partition id
+    uint8_t pv[HC_KMAX_ARITY];   // variable of each column of the atom
+    uint8_t pk;                  // the atom's arity
     int32_t depth;
     int32_t from_loop, from_src;
 };
 
+// HyperCube cells (Sec. 4-5): cell id = mixed radix of the variables'
+// coordinates, variable 0 most significant; coordinate of variable v in
+// cell c = (c / vstride[v]) % vshare[v].
 struct KPlan {
-    int32_t nv, drv0, stats, pad;
+    int32_t nv, stats;
+    uint32_t n_cells;
     int32_t nsrc[HC_KMAX_VARS];
     int32_t var_of_loop[HC_KMAX_VARS];
+    uint32_t vshare[HC_KMAX_VARS], vstride[HC_KMAX_VARS];
     KSrc src[HC_KMAX_VARS][KMAXS];
 };
 
-// A loop-0 binding: its value and, per loop-0 list that opens a level, the
-// range of its children there.
+// A loop-0 binding: its cell, its value and, per loop-0 list that opens a
+// level, the range of its children there.
 struct KEntry {
+    uint32_t cell;
     uint32_t val;
     uint32_t lo[KMAXS], hi[KMAXS];
+};
+
+// A cell with loop-0 candidates: its shortest loop-0 list (drv) and that
+// list's range [lo, lo + len) in V_0.
+struct KCell {
+    uint32_t cell, drv, lo, len;
 };
 
 __device__ __forceinline__ void load_kplan(KPlan& dst, const KPlan* __restrict__ src) {
@@ -598,11 +770,32 @@ __device__ __forceinline__ void load_kplan(KPlan& dst, const KPlan* __restrict__
     __syncthreads();
 }
 
+// The range of a top-level list in a cell: the level 0 of the partition
+// that the cell's coordinates select in the list's atom (Sec. 4-5), or all
+// of V_0 for an unpartitioned atom.
+__device__ __forceinline__ void ktop(const KPlan& P, const KSrc& s, uint32_t cell, uint32_t& lo, uint32_t& hi) {
+    if (s.l0s == nullptr) {
+        lo = 0;
+        hi = s.top_len;
+        return;
+    }
+    uint32_t pid = 0;
+#pragma unroll
+    for (int c = 0; c < HC_KMAX_ARITY; ++c) {
+        if (c < (int)s.pk) {
+            const uint32_t v = s.pv[c];
+            pid += (cell / P.vstride[v]) % P.vshare[v] * s.pw[c];
+        }
+    }
+    lo = __ldg(s.l0s + pid);
+    hi = __ldg(s.l0s + pid + 1);
+}
+
 // search(V, x) of Sec. 5 within [lo, hi): the position of v, found or not.
 __device__ __forceinline__ uint32_t ksearch(const KSrc& s, uint32_t lo, uint32_t hi, uint32_t v, bool& ok) {
     if (s.depth == 0 && s.pos != nullptr) {
         const uint32_t p = v < s.pos_n ? __ldg(s.pos + v) : V1POS_NONE;
-        ok = p != V1POS_NONE;
+        ok = p != V1POS_NONE && p >= lo && p < hi;
         return p;
     }
     uint32_t p = lo;
@@ -611,40 +804,61 @@ __device__ __forceinline__ uint32_t ksearch(const KSrc& s, uint32_t lo, uint32_t
 }
 
 // ----------------------------------------------------------------- loop 0
-// Thread t takes value t of the shortest loop-0 list and searches it in the
-// others.  n_vars == 1: matches are the result (counted, or written with
-// MAT).  Otherwise a match with loop-1 candidates becomes an entry.
+// The loop-0 candidates of all cells, concatenated: thread t takes
+// candidate t, a value of its cell's shortest loop-0 list, and searches it
+// in the cell's other loop-0 lists.  n_vars == 1: matches are the result
+// (counted, or written with MAT).  Otherwise a match with loop-1 candidates
+// becomes an entry.
 template <bool MAT>
-__global__ void __launch_bounds__(256) kloop0_kernel(const KPlan* __restrict__ gP, KEntry* __restrict__ entries,
-                                                     uint32_t* __restrict__ units, JoinCtl* ctl,
-                                                     uint32_t* __restrict__ out, uint64_t cap) {
+__global__ void __launch_bounds__(256) kloop0_kernel(const KPlan* __restrict__ gP, const KCell* __restrict__ cells,
+                                                     const uint64_t* __restrict__ cell_pref, uint32_t ncell,
+                                                     KEntry* __restrict__ entries, uint32_t* __restrict__ units,
+                                                     JoinCtl* ctl, uint32_t* __restrict__ out, uint64_t cap,
+                                                     uint64_t* __restrict__ cell_counts) {
     __shared__ KPlan P;
     load_kplan(P, gP);
     const uint32_t lane = lane_id();
-    const KSrc& s0 = P.src[0][P.drv0];
     const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    const bool valid = t < s0.top_len;
+    const bool valid = t < cell_pref[ncell];
+    KCell C{0, 0, 0, 0};
+    uint32_t off = 0;
+    if (valid) {
+        uint32_t lo = 0, hi = ncell;  // the last cell whose first candidate is <= t
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (cell_pref[mid] <= t)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        C = cells[lo];
+        off = (uint32_t)(t - cell_pref[lo]);
+    }
     uint32_t v = 0;
     bool ok = valid;
     uint32_t pq[KMAXS];
-    if (valid) v = __ldg(s0.v + t);
+    if (valid) v = __ldg(P.src[0][C.drv].v + C.lo + off);
 #pragma unroll
     for (int q = 0; q < KMAXS; ++q) {
         pq[q] = 0;
         if (q < P.nsrc[0]) {
-            if (q == P.drv0) {
-                pq[q] = (uint32_t)t;
+            if (q == (int)C.drv) {
+                pq[q] = C.lo + off;
             } else if (ok) {
                 const KSrc& s = P.src[0][q];
-                pq[q] = ksearch(s, 0, s.top_len, v, ok);
+                uint32_t lo, hi;
+                ktop(P, s, C.cell, lo, hi);
+                pq[q] = ksearch(s, lo, hi, v, ok);
             }
         }
     }
-    if (!MAT && P.stats && t == 0) atomicAdd((unsigned long long*)&ctl->work, (unsigned long long)P.nsrc[0] * s0.top_len);
+    if (!MAT && P.stats && valid && off == 0)
+        atomicAdd((unsigned long long*)&ctl->work, (unsigned long long)P.nsrc[0] * C.len);
     if (P.nv == 1) {
         const uint32_t m = __ballot_sync(FULL, ok);
         if (!MAT) {
             if (lane == 0 && m) atomicAdd((unsigned long long*)&ctl->total, (unsigned long long)__popc(m));
+            if (cell_counts && ok) atomicAdd((unsigned long long*)&cell_counts[C.cell], 1ull);
             return;
         }
         unsigned long long b = 0;
@@ -677,8 +891,12 @@ __global__ void __launch_bounds__(256) kloop0_kernel(const KPlan* __restrict__ g
         for (int q = 0; q < KMAXS; ++q) {
             if (q < P.nsrc[1]) {
                 const KSrc& s = P.src[1][q];
-                uint32_t len = s.top_len;
-                if (s.depth > 0) {
+                uint32_t len = 0;
+                if (s.depth == 0) {
+                    uint32_t lo, hi;
+                    ktop(P, s, C.cell, lo, hi);
+                    len = hi - lo;
+                } else {
 #pragma unroll
                     for (int r = 0; r < KMAXS; ++r)
                         if (r == s.from_src) len = hi[r] - lo[r];
@@ -699,6 +917,7 @@ __global__ void __launch_bounds__(256) kloop0_kernel(const KPlan* __restrict__ g
     if (ok) {
         const uint32_t slot = b + __popc(m & lanemask_lt());
         KEntry e;
+        e.cell = C.cell;
         e.val = v;
 #pragma unroll
         for (int q = 0; q < KMAXS; ++q) {
@@ -725,8 +944,10 @@ struct KWarp {
     uint32_t rlo[NF][KMAXS][32];
     uint32_t rhi[NF][KMAXS][32];
     uint32_t dlo[NV - 1][32];
+    uint32_t tlo[NV - 1][KMAXS], thi[NV - 1][KMAXS];  // top-level lists of loops 1.. in the entry's cell
     uint32_t e_lo[KMAXS], e_hi[KMAXS];
     uint32_t e_val;
+    uint64_t c0[32];  // each lane's count when the entry started (per-cell counts)
     uint8_t par[NF][32];
     uint8_t drv[NV - 1][32];
 };
@@ -738,8 +959,8 @@ __device__ __forceinline__ void krange(const KPlan& P, const KWarp<NV>& S, int L
                                        uint32_t& hi) {
     const KSrc& s = P.src[L][q];
     if (s.depth == 0) {
-        lo = 0;
-        hi = s.top_len;
+        lo = S.tlo[L - 1][q];
+        hi = S.thi[L - 1][q];
         return;
     }
     const int f = s.from_loop, r = s.from_src;
@@ -905,12 +1126,16 @@ __device__ void kwalk(const KPlan& P, KWarp<NV>& S, uint32_t t0, uint32_t t1, ui
 
 // Persistent search kernel: warps take work items of `grain` loop-1
 // candidates (0: sized so that each warp gets about 8 items) from an atomic
-// counter, over the concatenation of all entries' candidates.
+// counter, over the concatenation of all entries' candidates.  Bounded to
+// 40 registers (12 blocks of 128 threads per SM): the per-cell setup at an
+// entry's start would otherwise lift the whole kernel to 48 and cost 5% on
+// LW over [256]^3.
 template <int NV, bool MAT>
-__global__ void __launch_bounds__(KJ_MAXT) kjoin_kernel(const KPlan* __restrict__ gP,
+__global__ void __launch_bounds__(KJ_MAXT, 12) kjoin_kernel(const KPlan* __restrict__ gP,
                                                         const KEntry* __restrict__ entries,
                                                         const uint64_t* __restrict__ unit_off, JoinCtl* ctl,
-                                                        uint32_t grain_in, uint32_t* __restrict__ out, uint64_t cap) {
+                                                        uint32_t grain_in, uint32_t* __restrict__ out, uint64_t cap,
+                                                        uint64_t* __restrict__ cell_counts) {
     __shared__ KPlan P;
     __shared__ KWarp<NV> WS[KJ_WARPS];
     load_kplan(P, gP);
@@ -956,9 +1181,20 @@ __global__ void __launch_bounds__(KJ_MAXT) kjoin_kernel(const KPlan* __restrict_
                         S.e_hi[q] = en.hi[q];
                     }
                 }
+                if (lane < (uint32_t)((NV - 1) * KMAXS)) {
+                    const int L = 1 + (int)lane / KMAXS, q = (int)lane % KMAXS;
+                    if (q < P.nsrc[L] && P.src[L][q].depth == 0)
+                        ktop(P, P.src[L][q], entries[e].cell, S.tlo[L - 1][q], S.thi[L - 1][q]);
+                }
                 __syncwarp();
                 const uint64_t u_end = u1 < ee ? u1 : ee;
+                if (!MAT && cell_counts) S.c0[lane] = cnt;
                 kwalk<NV, MAT>(P, S, (uint32_t)(u0 - eb), (uint32_t)(u_end - eb), cnt, work, ctl, out, cap);
+                if (!MAT && cell_counts) {
+                    const uint64_t dc = warp_sum64(cnt - S.c0[lane]);
+                    if (lane == 0 && dc)
+                        atomicAdd((unsigned long long*)&cell_counts[entries[e].cell], (unsigned long long)dc);
+                }
                 u0 = u_end;
             }
             ++e;
@@ -976,24 +1212,24 @@ __global__ void __launch_bounds__(KJ_MAXT) kjoin_kernel(const KPlan* __restrict_
 
 template <int NV, bool MAT>
 hc_status launch_kjoin_t(int threads, const KPlan* P, const KEntry* entries, const uint64_t* unit_off, JoinCtl* ctl,
-                         uint32_t grain, uint32_t* out, uint64_t cap, cudaStream_t s) {
+                         uint32_t grain, uint32_t* out, uint64_t cap, uint64_t* cell_counts, cudaStream_t s) {
     int per_sm = 0;
     HC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kjoin_kernel<NV, MAT>, threads, 0));
     const int grid = num_sms() * std::max(1, per_sm);
-    kjoin_kernel<NV, MAT><<<grid, threads, 0, s>>>(P, entries, unit_off, ctl, grain, out, cap);
+    kjoin_kernel<NV, MAT><<<grid, threads, 0, s>>>(P, entries, unit_off, ctl, grain, out, cap, cell_counts);
     HC_CUDA_TRY(launch_check());
     return HC_OK;
 }
 
 template <bool MAT>
 hc_status launch_kjoin(int nv, int threads, const KPlan* P, const KEntry* entries, const uint64_t* unit_off,
-                       JoinCtl* ctl, uint32_t grain, uint32_t* out, uint64_t cap, cudaStream_t s) {
+                       JoinCtl* ctl, uint32_t grain, uint32_t* out, uint64_t cap, uint64_t* cc, cudaStream_t s) {
     switch (nv) {
-        case 2: return launch_kjoin_t<2, MAT>(threads, P, entries, unit_off, ctl, grain, out, cap, s);
-        case 3: return launch_kjoin_t<3, MAT>(threads, P, entries, unit_off, ctl, grain, out, cap, s);
-        case 4: return launch_kjoin_t<4, MAT>(threads, P, entries, unit_off, ctl, grain, out, cap, s);
-        case 5: return launch_kjoin_t<5, MAT>(threads, P, entries, unit_off, ctl, grain, out, cap, s);
-        case 6: return launch_kjoin_t<6, MAT>(threads, P, entries, unit_off, ctl, grain, out, cap, s);
+        case 2: return launch_kjoin_t<2, MAT>(threads, P, entries, unit_off, ctl, grain, out, cap, cc, s);
+        case 3: return launch_kjoin_t<3, MAT>(threads, P, entries, unit_off, ctl, grain, out, cap, cc, s);
+        case 4: return launch_kjoin_t<4, MAT>(threads, P, entries, unit_off, ctl, grain, out, cap, cc, s);
+        case 5: return launch_kjoin_t<5, MAT>(threads, P, entries, unit_off, ctl, grain, out, cap, cc, s);
+        case 6: return launch_kjoin_t<6, MAT>(threads, P, entries, unit_off, ctl, grain, out, cap, cc, s);
         default: return fail(HC_ERR_CAPACITY, "run_kjoin: unsupported number of variables");
     }
 }
@@ -1022,6 +1258,7 @@ hc_status make_kplan(const hc_kquery* q, const hc_kindex* const* idx, KPlan& P) 
         P.var_of_loop[i] = (int32_t)v;
     }
     P.nv = (int32_t)nv;
+    uint32_t vseed[HC_KMAX_VARS] = {0};
     for (uint32_t j = 0; j < na; ++j) {
         const hc_katom& a = q->atoms[j];
         const uint32_t k = a.arity;
@@ -1034,6 +1271,19 @@ hc_status make_kplan(const hc_kquery* q, const hc_kindex* const* idx, KPlan& P) 
         const hc_kindex* x = idx[j];
         if (!x) return fail(HC_ERR_ARG, "run_kjoin: index is NULL");
         if (x->arity != k) return fail(HC_ERR_ARG, "run_kjoin: index arity differs from the atom's");
+        // every atom holding a variable partitions it with the same share
+        // and seed, so the cells' coordinates select one partition per atom
+        uint32_t pw[HC_KMAX_ARITY] = {1, 1, 1};
+        for (int c = (int)k - 2; c >= 0; --c) pw[c] = pw[c + 1] * x->pshare[c + 1];
+        for (uint32_t c = 0; c < k; ++c) {
+            const uint32_t v = a.var[c], sh = x->pshare[c], sd = sh > 1 ? x->pseed[c] : 0u;
+            if (P.vshare[v] == 0) {
+                P.vshare[v] = sh;
+                vseed[v] = sd;
+            } else if (P.vshare[v] != sh || vseed[v] != sd) {
+                return fail(HC_ERR_ARG, "run_kjoin: atoms partition a variable with different shares or seeds");
+            }
+        }
         int prev_loop = -1, prev_src = -1;
         for (uint32_t d = 0; d < k; ++d) {
             const int L = rank[a.var[x->level_cols[d]]];
@@ -1048,6 +1298,12 @@ hc_status make_kplan(const hc_kquery* q, const hc_kindex* const* idx, KPlan& P) 
             s.pos = d == 0 ? x->d_v0pos : nullptr;
             s.pos_n = d == 0 ? x->v0pos_n : 0;
             s.top_len = (uint32_t)x->len[0];
+            s.l0s = d == 0 && x->n_parts > 1 ? x->d_l0start : nullptr;
+            s.pk = (uint8_t)k;
+            for (uint32_t c = 0; c < k; ++c) {
+                s.pv[c] = a.var[c];
+                s.pw[c] = pw[c];
+            }
             s.depth = (int32_t)d;
             s.from_loop = prev_loop;
             s.from_src = prev_src;
@@ -1059,10 +1315,46 @@ hc_status make_kplan(const hc_kquery* q, const hc_kindex* const* idx, KPlan& P) 
         if (P.nsrc[i] == 0) return fail(HC_ERR_ARG, "run_kjoin: every variable must occur in some atom");
     for (uint32_t j = 0; j < na; ++j)
         if (idx[j]->stats_only) return fail(HC_ERR_ARG, "run_kjoin: a statistics-only index has no data");
-    P.drv0 = 0;
-    for (int qn = 1; qn < P.nsrc[0]; ++qn)
-        if (P.src[0][qn].top_len < P.src[0][P.drv0].top_len) P.drv0 = qn;
+    uint64_t cells = 1;
+    for (int v = (int)nv - 1; v >= 0; --v) {
+        P.vstride[v] = (uint32_t)cells;
+        cells *= P.vshare[v];
+        if (cells > KMAX_CELLS) return fail(HC_ERR_CAPACITY, "run_kjoin: more than 2^20 HyperCube cells");
+    }
+    P.n_cells = (uint32_t)cells;
     return HC_OK;
+}
+
+// Loop-0 candidates of every cell (host, from the indexes' partition
+// starts): per cell, its shortest loop-0 list and that list's range; cells
+// with an empty loop-0 list are left out.  pref receives the prefix of the
+// candidate counts (size cells.size() + 1).
+void kcell_table(const KPlan& P, const hc_kquery* q, const hc_kindex* const* idx, std::vector<KCell>& cells,
+                 std::vector<uint64_t>& pref) {
+    // the atom behind each loop-0 list
+    const hc_kindex* xs[KMAXS] = {nullptr, nullptr, nullptr, nullptr};
+    for (int qn = 0; qn < P.nsrc[0]; ++qn)
+        for (uint32_t j = 0; j < q->n_atoms; ++j)
+            if (idx[j]->d_v[0] == P.src[0][qn].v) xs[qn] = idx[j];
+    cells.clear();
+    pref.assign(1, 0);
+    for (uint32_t c = 0; c < P.n_cells; ++c) {
+        KCell best{c, 0, 0, 0xFFFFFFFFu};
+        for (int qn = 0; qn < P.nsrc[0]; ++qn) {
+            const KSrc& s = P.src[0][qn];
+            uint32_t lo = 0, hi = s.top_len;
+            if (s.l0s != nullptr) {
+                uint32_t pid = 0;
+                for (uint32_t k = 0; k < s.pk; ++k) pid += (c / P.vstride[s.pv[k]]) % P.vshare[s.pv[k]] * s.pw[k];
+                lo = xs[qn]->h_l0start[pid];
+                hi = xs[qn]->h_l0start[pid + 1];
+            }
+            if (hi - lo < best.len) best = KCell{c, (uint32_t)qn, lo, hi - lo};
+        }
+        if (best.len == 0) continue;
+        cells.push_back(best);
+        pref.push_back(pref.back() + best.len);
+    }
 }
 
 }  // namespace
@@ -1083,10 +1375,16 @@ hc_status run_kjoin_impl(const hc_kquery* q, const hc_kindex* const* idx, const 
     P.stats = (dp.flags & HC_FLAG_STATS) ? 1 : 0;
     const uint32_t nv = q->n_vars;
 
+    std::vector<KCell> hcells;
+    std::vector<uint64_t> hpref;
+    kcell_table(P, q, idx, hcells, hpref);
+    const uint64_t len0 = hpref.back();  // loop-0 candidates over all cells
+    if (len0 >= 0xFFFFFFFFull) return fail(HC_ERR_CAPACITY, "run_kjoin: 2^32 - 1 or more loop-0 candidates");
+
     hc_result* R = new hc_result();
     R->stream = s;
     R->n_vars = nv;
-    R->n_cells = 1;
+    R->n_cells = P.n_cells;
     auto bail = [&](hc_status st) {
         result_release(R);
         return st;
@@ -1096,6 +1394,13 @@ hc_status run_kjoin_impl(const hc_kquery* q, const hc_kindex* const* idx, const 
     R->d_ctl = (JoinCtl*)p;
     JoinCtl* ctl = R->d_ctl;
     if (cudaMemsetAsync(ctl, 0, sizeof(JoinCtl), s) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
+    if (dp.flags & HC_FLAG_CELL_COUNTS) {
+        if (dev_alloc(&p, (uint64_t)P.n_cells * 8, s) != HC_OK) return bail(HC_ERR_OOM);
+        R->d_cell_counts = (uint64_t*)p;
+        if (cudaMemsetAsync(R->d_cell_counts, 0, (uint64_t)P.n_cells * 8, s) != cudaSuccess)
+            return bail(cuda_fail(cudaGetLastError(), "memset"));
+    }
+    uint64_t* cc = R->d_cell_counts;
     const bool timed = (dp.flags & HC_FLAG_TIME_KERNELS) != 0;
 
     KScratch tmp(s);
@@ -1104,7 +1409,16 @@ hc_status run_kjoin_impl(const hc_kquery* q, const hc_kindex* const* idx, const 
     if ((st = tmp.get(&dP, 1)) != HC_OK) return bail(st);
     if (cudaMemcpyAsync(dP, &P, sizeof(KPlan), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return bail(cuda_fail(cudaGetLastError(), "plan copy"));
-    const uint32_t len0 = P.src[0][P.drv0].top_len;
+    const uint32_t ncell = (uint32_t)hcells.size();
+    KCell* dcells;
+    uint64_t* dpref;
+    if ((st = tmp.get(&dcells, ncell)) != HC_OK || (st = tmp.get(&dpref, (size_t)ncell + 1)) != HC_OK)
+        return bail(st);
+    if ((ncell && cudaMemcpyAsync(dcells, hcells.data(), ncell * sizeof(KCell), cudaMemcpyHostToDevice, s) !=
+                      cudaSuccess) ||
+        cudaMemcpyAsync(dpref, hpref.data(), (ncell + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "cell table copy"));
     KEntry* entries = nullptr;
     uint32_t* units = nullptr;
     uint64_t* unit_off = nullptr;
@@ -1113,14 +1427,18 @@ hc_status run_kjoin_impl(const hc_kquery* q, const hc_kindex* const* idx, const 
         if (timed) HC_TRY(time_mark(R, false, s));
         if (nv == 1) {
             if (mat)
-                kloop0_kernel<true><<<l0_grid, 256, 0, s>>>(dP, nullptr, nullptr, ctl, tup, cap);
+                kloop0_kernel<true><<<l0_grid, 256, 0, s>>>(dP, dcells, dpref, ncell, nullptr, nullptr, ctl, tup, cap,
+                                                            nullptr);
             else
-                kloop0_kernel<false><<<l0_grid, 256, 0, s>>>(dP, nullptr, nullptr, ctl, nullptr, 0);
+                kloop0_kernel<false><<<l0_grid, 256, 0, s>>>(dP, dcells, dpref, ncell, nullptr, nullptr, ctl, nullptr,
+                                                             0, cc);
             HC_CUDA_TRY(launch_check());
         } else if (mat) {
-            HC_TRY(launch_kjoin<true>((int)nv, threads, dP, entries, unit_off, ctl, dp.item_grain, tup, cap, s));
+            HC_TRY(launch_kjoin<true>((int)nv, threads, dP, entries, unit_off, ctl, dp.item_grain, tup, cap, nullptr,
+                                      s));
         } else {
-            HC_TRY(launch_kjoin<false>((int)nv, threads, dP, entries, unit_off, ctl, dp.item_grain, nullptr, 0, s));
+            HC_TRY(
+                launch_kjoin<false>((int)nv, threads, dP, entries, unit_off, ctl, dp.item_grain, nullptr, 0, cc, s));
         }
         if (timed) HC_TRY(time_mark(R, true, s));
         R->n_search++;
@@ -1131,7 +1449,8 @@ hc_status run_kjoin_impl(const hc_kquery* q, const hc_kindex* const* idx, const 
             if ((st = tmp.get(&entries, len0)) != HC_OK || (st = tmp.get(&units, len0)) != HC_OK ||
                 (st = tmp.get(&unit_off, (size_t)len0 + 1)) != HC_OK)
                 return bail(st);
-            kloop0_kernel<false><<<l0_grid, 256, 0, s>>>(dP, entries, units, ctl, nullptr, 0);
+            kloop0_kernel<false><<<l0_grid, 256, 0, s>>>(dP, dcells, dpref, ncell, entries, units, ctl, nullptr, 0,
+                                                         nullptr);
             if (cudaError_t le = launch_check()) return bail(cuda_fail(le, "kloop0_kernel"));
             if ((st = exclusive_scan_u32_to_u64(units, unit_off, len0, &ctl->n_entries, &ctl->err, s)) != HC_OK)
                 return bail(st);
@@ -1261,7 +1580,17 @@ extern "C" {
 
 hc_status hc_build_kindex(const uint32_t* d_rows, uint64_t n, uint32_t arity, const uint8_t* level_cols,
                           uint32_t flags, void* stream, hc_kindex** out) {
-    return hc::build_kindex_impl(d_rows, n, arity, level_cols, flags, (cudaStream_t)stream, out);
+    return hc::build_kindex_impl(d_rows, n, arity, level_cols, nullptr, nullptr, flags, (cudaStream_t)stream, out);
+}
+
+hc_status hc_build_kindex_partitioned(const uint32_t* d_rows, uint64_t n, uint32_t arity, const uint8_t* level_cols,
+                                      const uint32_t* seeds, const uint32_t* shares, uint32_t flags, void* stream,
+                                      hc_kindex** out) {
+    if (!shares || !seeds) {
+        if (out) *out = nullptr;
+        return hc::fail(HC_ERR_ARG, "build_kindex_partitioned: seeds and shares are required");
+    }
+    return hc::build_kindex_impl(d_rows, n, arity, level_cols, seeds, shares, flags, (cudaStream_t)stream, out);
 }
 
 hc_status hc_kindex_free(hc_kindex* index) {
@@ -1284,6 +1613,13 @@ hc_status hc_kindex_get_view(const hc_kindex* x, hc_kindex_view* v) {
     }
     v->ms_sort = x->ms_sort;
     v->ms_levels = x->ms_levels;
+    v->n_parts = x->n_parts;
+    for (int c = 0; c < HC_KMAX_ARITY; ++c) {
+        v->shares[c] = (uint32_t)c < x->arity ? x->pshare[c] : 0u;
+        v->seeds[c] = (uint32_t)c < x->arity ? x->pseed[c] : 0u;
+    }
+    v->d_bpref = x->d_bpref;
+    v->d_level0_start = x->d_l0start;
     return HC_OK;
 }
 

@@ -5,8 +5,10 @@ such as the paper's Loomis-Whitney (LW) and Clover-Triangle (CT) queries
 library's CUDA kernels.
 
     build_kindex(rows, level_cols)     sort + k-level CoCo
+    build_kindex(.., seeds, shares)    the same per HyperCube partition (Sec. 4)
     choose_korder(query, indexes)      Sec. 5.2-5.3: loop order of least estimated cost
-    run_kjoin(query, indexes, mode)    Generic Join (one cell)
+    run_kjoin(query, indexes, mode)    Generic Join in every HyperCube cell
+    atom_shares(query, shares, seeds)  per atom, the seeds and shares of its columns
 """
 from __future__ import annotations
 
@@ -73,6 +75,9 @@ class KIndex:
         self.len = tuple(int(v.len[d]) for d in range(v.arity))
         self.max_value = tuple(int(v.max_value[d]) for d in range(v.arity))
         self.ms_sort, self.ms_levels = v.ms_sort, v.ms_levels
+        self.n_parts = int(v.n_parts) if v.n_parts else 1
+        self.shares = tuple(int(v.shares[c]) for c in range(v.arity))
+        self.seeds = tuple(int(v.seeds[c]) for c in range(v.arity))
         self._view = v
 
     @classmethod
@@ -104,6 +109,20 @@ class KIndex:
             raise IndexError("the last level has no offsets")
         return _alias(self._view.d_o[d], (self.len[d] + 1,), torch.int32, self)
 
+    def bpref(self) -> torch.Tensor | None:
+        """B^pref (first row of each partition, [n_parts + 1]), or None when
+        unpartitioned."""
+        if not self._view.d_bpref:
+            return None
+        return _alias(self._view.d_bpref, (self.n_parts + 1,), torch.int32, self)
+
+    def level0_start(self) -> torch.Tensor | None:
+        """First level-0 entry of each partition ([n_parts + 1]), or None
+        when unpartitioned."""
+        if not self._view.d_level0_start:
+            return None
+        return _alias(self._view.d_level0_start, (self.n_parts + 1,), torch.int32, self)
+
     def free(self) -> None:
         if self._h is not None:
             _lib.load().hc_kindex_free(self._h)
@@ -117,9 +136,13 @@ class KIndex:
 
 
 def build_kindex(rows: torch.Tensor, level_cols: Sequence[int] | None = None, check_duplicates: bool = False,
-                 stream=None, time_kernels: bool = False) -> KIndex:
+                 stream=None, time_kernels: bool = False, seeds: Sequence[int] | None = None,
+                 shares: Sequence[int] | None = None) -> KIndex:
     """k-level CoCo of a relation given as an (n, k) 32-bit CUDA tensor, k = 1..3,
-    with level d holding column level_cols[d] (default 0, 1, ..)."""
+    with level d holding column level_cols[d] (default 0, 1, ..).  With
+    ``shares`` (and ``seeds``), one per column, the relation is partitioned
+    for HyperCube shares first (Sec. 4) and each partition gets its own
+    trie."""
     if not isinstance(rows, torch.Tensor) or not rows.is_cuda or rows.dim() != 2 or rows.element_size() != 4:
         raise TypeError("rows must be an (n, k) 32-bit CUDA tensor")
     r = rows.contiguous()
@@ -130,10 +153,32 @@ def build_kindex(rows: torch.Tensor, level_cols: Sequence[int] | None = None, ch
     flags = (_lib.HC_BUILD_CHECK_DUPLICATES if check_duplicates else 0) | (
         _lib.HC_BUILD_TIME_KERNELS if time_kernels else 0)
     out = ctypes.c_void_p()
-    st = _lib.load().hc_build_kindex(ctypes.c_void_p(r.data_ptr() if r.numel() else 0), r.shape[0], k, cols, flags,
-                                     ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(out))
-    _lib.check(st, "hc_build_kindex")
+    ptr = ctypes.c_void_p(r.data_ptr() if r.numel() else 0)
+    if shares is None:
+        st = _lib.load().hc_build_kindex(ptr, r.shape[0], k, cols, flags, ctypes.c_void_p(_stream_ptr(stream)),
+                                         ctypes.byref(out))
+        _lib.check(st, "hc_build_kindex")
+    else:
+        if len(shares) != k:
+            raise ValueError("one share per column")
+        sd = list(seeds) if seeds is not None else [0] * k
+        if len(sd) != k:
+            raise ValueError("one seed per column")
+        sh = (ctypes.c_uint32 * 3)(*([int(x) for x in shares] + [1] * (3 - k)))
+        se = (ctypes.c_uint32 * 3)(*([int(x) & 0xFFFFFFFF for x in sd] + [0] * (3 - k)))
+        st = _lib.load().hc_build_kindex_partitioned(ptr, r.shape[0], k, cols, se, sh, flags,
+                                                     ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(out))
+        _lib.check(st, "hc_build_kindex_partitioned")
     return KIndex(out.value)
+
+
+def atom_shares(query: KQuery, shares: Sequence[int], seeds: Sequence[int] | None = None) -> list:
+    """Per atom j, (seeds, shares) of its columns for variable shares
+    ``shares[v]`` and seeds ``seeds[v]`` (default v + 1): the arguments of
+    build_kindex that partition atom j for the HyperCube cells of these
+    shares."""
+    sd = list(seeds) if seeds is not None else [v + 1 for v in range(query.n_vars)]
+    return [(tuple(sd[v] for v in a), tuple(int(shares[v]) for v in a)) for a in query.atoms]
 
 
 def _kindex_array(indexes):
@@ -161,9 +206,14 @@ def choose_korder(query: KQuery, indexes: Sequence[KIndex]) -> tuple:
 
 
 def run_kjoin(query: KQuery, indexes: Sequence[KIndex], mode: str = "count", stats: bool = False,
-              item_grain: int = 0, block_threads: int = 0, time_kernels: bool = False, stream=None) -> Result:
-    """Generic Join of a k-ary query; tuples (materialize) come back as a
-    (count, n_vars) int32 CUDA tensor in variable-id order, in no fixed order."""
+              item_grain: int = 0, block_threads: int = 0, time_kernels: bool = False, stream=None,
+              cell_counts: bool = False) -> Result:
+    """Generic Join of a k-ary query in every HyperCube cell (the shares
+    come from the indexes, see build_kindex); tuples (materialize) come back
+    as a (count, n_vars) int32 CUDA tensor in variable-id order, in no fixed
+    order; ``cell_counts`` adds the count of each cell (int64, cell id = the
+    mixed radix of the variables' coordinates, variable 0 most
+    significant)."""
     if len(indexes) != len(query.atoms):
         raise ValueError("one index per atom")
     if mode not in ("count", "materialize"):
@@ -172,7 +222,8 @@ def run_kjoin(query: KQuery, indexes: Sequence[KIndex], mode: str = "count", sta
     arr = (ctypes.c_void_p * len(indexes))(*[ix.handle.value for ix in indexes])
     prm = _lib.hc_kjoin_params()
     prm.mode = _lib.HC_MODE_COUNT if mode == "count" else _lib.HC_MODE_MATERIALIZE
-    prm.flags = (_lib.HC_FLAG_STATS if stats else 0) | (_lib.HC_FLAG_TIME_KERNELS if time_kernels else 0)
+    prm.flags = ((_lib.HC_FLAG_STATS if stats else 0) | (_lib.HC_FLAG_TIME_KERNELS if time_kernels else 0)
+                 | (_lib.HC_FLAG_CELL_COUNTS if cell_counts else 0))
     prm.item_grain = item_grain
     prm.block_threads = block_threads
     lib = _lib.load()
@@ -185,6 +236,8 @@ def run_kjoin(query: KQuery, indexes: Sequence[KIndex], mode: str = "count", sta
     _lib.check(lib.hc_result_get(ctypes.c_void_p(holder.h), ctypes.byref(v)), "hc_result_get")
     res = Result(count=v.count, n_cells=v.n_cells, work=v.work, n_items=v.n_items,
                  ms_join_kernel=v.ms_join_kernel, n_join_launches=v.n_join_launches)
+    if v.d_cell_counts:
+        res.cell_counts = _alias(v.d_cell_counts, (v.n_cells,), torch.int64, holder).clone()
     if v.d_tuples:
         res.tuples = _alias(v.d_tuples, (v.n_tuples, query.n_vars), torch.int32, holder).clone()
     elif mode == "materialize":
