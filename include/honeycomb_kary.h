@@ -121,6 +121,9 @@ typedef struct {
     uint32_t item_grain;    /* loop-1 candidates per work item (0: sized from the run)  */
     uint32_t block_threads; /* threads per block of the search kernel: 32, 64, 96 or   */
                             /* 128 (0: 128)                                             */
+    uint32_t pair_min;      /* last loop: a binding with at least this many candidates  */
+                            /* is searched by the whole warp, 128 candidates at a time  */
+                            /* (0: 32; 0xFFFFFFFF: never)                               */
 } hc_kjoin_params;
 
 /* Generic Join of q over k-level indexes (Sec. 5) in every HyperCube cell

@@ -93,7 +93,7 @@ class hc_kquery(ctypes.Structure):
 
 class hc_kjoin_params(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("item_grain", ctypes.c_uint32),
-                ("block_threads", ctypes.c_uint32)]
+                ("block_threads", ctypes.c_uint32), ("pair_min", ctypes.c_uint32)]
 
 
 # name -> (restype, argtypes)

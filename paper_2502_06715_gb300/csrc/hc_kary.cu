@@ -14,21 +14,32 @@
 // sorts (level value, position in the previous order) pairs, which orders
 // by the level value and keeps the previous order among equal values.
 //
+// Partitioning (Sec. 4, "Preprocessor").  With HyperCube shares the rows
+// are sorted by partition id first (the mixed radix of the columns' hash
+// identifiers), and a change of partition opens an entry of every level, so
+// the levels are the partitions' tries concatenated; the scan records where
+// each partition starts in the rows (B^pref) and in level 0.
+//
 // Join.  Loop 0 intersects the top levels of the atoms holding its variable
-// in a flat pass, one thread per value of the shortest list; every match
-// ("entry") records the level-1 ranges of the atoms it opens and its number
-// of loop-1 candidates.  The later loops run in a persistent kernel: a warp
-// takes a work item (a range of loop-1 candidates, over consecutive
-// entries) from an atomic counter and walks the remaining loops depth
-// first.  At each loop it holds up to 32 parent bindings and flattens their
-// candidates over its lanes, 32 a round; a candidate is an element of its
-// parent's shortest list (Sec. 5.2: iterate the smallest set, search the
-// others) and is searched in the parent's other lists by binary search (or
-// a direct position map of a top level); matches are compacted into the
-// next loop's bindings.  A binding keeps, for each list it matched that
-// has a deeper level, the range of its children there (the level
-// restriction of Sec. 5), and the index of its parent, so that a later
-// loop finds the range an earlier loop opened by walking up the parents.
+// in a flat pass over the loop-0 candidates of all HyperCube cells (in each
+// cell the shortest list of the partitions its coordinates select), one
+// thread per candidate; every match ("entry") records its cell, the
+// level-1 ranges of the atoms it opens and its number of loop-1
+// candidates.  The later loops run in a persistent kernel: a warp takes a
+// work item (a range of loop-1 candidates, over consecutive entries) from
+// an atomic counter and walks the remaining loops depth first.  At each
+// loop it holds up to 32 parent bindings and flattens their candidates
+// over its lanes, 32 a round; a candidate is an element of its parent's
+// shortest list (Sec. 5.2: iterate the smallest set, search the others)
+// and is searched in the parent's other lists through their bucket
+// directories (or a direct position map of a top level); matches are
+// compacted into the next loop's bindings.  At the last loop a parent with
+// many candidates is searched by the whole warp instead, 128 candidates an
+// iteration with its lists' bounds read once (kpair).  A binding keeps, for
+// each list it matched that has a deeper level, the range of its children
+// there (the level restriction of Sec. 5), and the index of its parent, so
+// that a later loop finds the range an earlier loop opened by walking up
+// the parents.
 #include <math.h>
 #include <string.h>
 
@@ -714,6 +725,7 @@ namespace {
 
 constexpr int KMAXS = 4;          // lists intersected by one loop
 constexpr uint64_t KMAX_CELLS = 1ull << 20;
+constexpr uint32_t KPAIR_MIN = 32;  // default per-binding threshold of the last loop
 constexpr int KJ_MAXT = 128;      // threads per block of the search kernel, at most
 constexpr int KJ_WARPS = KJ_MAXT / 32;
 
@@ -743,6 +755,7 @@ struct KSrc {
 struct KPlan {
     int32_t nv, stats;
     uint32_t n_cells;
+    uint32_t pair_min;  // last-loop parents with at least this many candidates take the per-binding path
     int32_t nsrc[HC_KMAX_VARS];
     int32_t var_of_loop[HC_KMAX_VARS];
     uint32_t vshare[HC_KMAX_VARS], vstride[HC_KMAX_VARS];
@@ -947,7 +960,10 @@ struct KWarp {
     uint32_t tlo[NV - 1][KMAXS], thi[NV - 1][KMAXS];  // top-level lists of loops 1.. in the entry's cell
     uint32_t e_lo[KMAXS], e_hi[KMAXS];
     uint32_t e_val;
-    uint64_t c0[32];  // each lane's count when the entry started (per-cell counts)
+    uint64_t c0[32];    // each lane's count when the entry started (per-cell counts)
+    uint32_t llen[32];  // candidates of each last-loop parent on the per-binding path
+    uint32_t lmask;     // those parents
+    uint32_t pl[KMAXS][5];  // kpair: each list's lo, hi, vmin, vmax, bucket shift (| 0x100: directory)
     uint8_t par[NF][32];
     uint8_t drv[NV - 1][32];
 };
@@ -1004,6 +1020,16 @@ __device__ __forceinline__ void kinit_level(const KPlan& P, KWarp<NV>& S, int L,
             if (P.stats) work += (uint64_t)P.nsrc[L] * best;
         }
     }
+    // last loop: a parent with many candidates leaves the flattened rounds
+    // for the per-binding path (kpair)
+    bool lng = false;
+    if (L == NV - 1 && lane < nb && c >= P.pair_min) {
+        lng = true;
+        S.llen[lane] = (uint32_t)c;
+        c = 0;
+    }
+    const uint32_t lm = __ballot_sync(FULL, lng);
+    if (lane == 0 && L == NV - 1) S.lmask = lm;
     const uint64_t incl = warp_incl_scan64(c);
     __syncwarp();
     S.pref[li][lane + 1] = incl;
@@ -1019,6 +1045,113 @@ __device__ __forceinline__ void kinit_level(const KPlan& P, KWarp<NV>& S, int L,
     __syncwarp();
 }
 
+// The per-binding path of the last loop: parent b's candidates, the
+// elements of its shortest list, 128 per iteration (lane l takes the
+// elements l, l + 32, l + 64, l + 96 of each block), searched in each other
+// list in turn with the four directory reads of a lane issued together.  A
+// list's range, bounds and bucket width are the same for every candidate,
+// so they are read once.  The last loop's lists are the atoms' last levels
+// (no positions are needed).
+template <int NV, bool MAT>
+__device__ __forceinline__ void kpair(const KPlan& P, KWarp<NV>& S, uint32_t b, uint64_t& cnt, JoinCtl* ctl,
+                                      uint32_t* __restrict__ out, uint64_t cap) {
+    constexpr int L = NV - 1, li = NV - 2;
+    const uint32_t lane = lane_id();
+    const uint32_t d = S.drv[li][b];
+    const uint32_t a0 = S.dlo[li][b], a1 = a0 + S.llen[b];
+    const uint32_t* __restrict__ va = P.src[L][d].v;
+    const int ns = P.nsrc[L];
+    if (ns == 1 && !MAT) {  // nothing to search: every candidate is a result
+        if (lane == 0) cnt += a1 - a0;
+        return;
+    }
+    // lane q sets up list q once for the whole parent
+    __syncwarp();
+    if (lane < (uint32_t)ns && lane != d) {
+        const KSrc& sq = P.src[L][lane];
+        uint32_t lo, hi;
+        krange<NV>(P, S, L, (int)lane, b, lo, hi);
+        S.pl[lane][0] = lo;
+        S.pl[lane][1] = hi;
+        if (!(sq.depth == 0 && sq.pos != nullptr)) {
+            const uint32_t vmin = __ldg(sq.v + lo), vmax = __ldg(sq.v + hi - 1);
+            const bool dir = sq.g != nullptr && hi - lo >= DIR_MIN;
+            S.pl[lane][2] = vmin;
+            S.pl[lane][3] = vmax;
+            S.pl[lane][4] = dir ? (0x100u | dir_shift(hi - lo, vmax - vmin)) : 0u;
+        }
+    }
+    __syncwarp();
+    for (uint32_t t0 = a0; t0 < a1; t0 += 128) {
+        uint32_t vv[4];
+        bool ok[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t t = t0 + 32 * j + lane;
+            ok[j] = t < a1;
+            vv[j] = ok[j] ? __ldg(va + t) : 0u;
+        }
+        for (int q = 0; q < ns; ++q) {
+            if (q == (int)d) continue;
+            const KSrc& sq = P.src[L][q];
+            const uint32_t lo = S.pl[q][0], hi = S.pl[q][1];
+            if (sq.depth == 0 && sq.pos != nullptr) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t p = ok[j] && vv[j] < sq.pos_n ? __ldg(sq.pos + vv[j]) : V1POS_NONE;
+                    ok[j] = p != V1POS_NONE && p >= lo && p < hi;
+                }
+                continue;
+            }
+            const uint32_t vmin = S.pl[q][2], vmax = S.pl[q][3], sd = S.pl[q][4];
+            const bool dir = sd != 0;
+            const uint4* __restrict__ gq = sq.g + lo;
+            uint4 ev[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                ok[j] = ok[j] && vv[j] >= vmin && vv[j] <= vmax;
+                ev[j] = (ok[j] && dir) ? dir_load(gq, (vv[j] - vmin) >> (sd & 0xFFu)) : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                uint32_t pos;
+                if (ok[j]) ok[j] = dir ? dir_walk_find(sq.v, ev[j], hi, vv[j], pos) : find_u32(sq.v, lo, hi, vv[j], pos);
+            }
+        }
+        uint32_t mine = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mine += ok[j] ? 1u : 0u;
+        if (!MAT) {
+            cnt += mine;
+            continue;
+        }
+        const uint32_t incl = warp_incl_scan(mine);
+        const uint32_t k = __shfl_sync(FULL, incl, 31);
+        if (k == 0) continue;
+        unsigned long long base = 0;
+        if (lane == 31) base = atomicAdd((unsigned long long*)&ctl->written, (unsigned long long)k);
+        base = __shfl_sync(FULL, base, 31);
+        uint64_t idx = base + incl - mine;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!ok[j]) continue;
+            if (idx < cap) {
+                uint32_t* t = out + idx * (uint64_t)P.nv;
+                t[P.var_of_loop[NV - 1]] = vv[j];
+                t[P.var_of_loop[0]] = S.e_val;
+                uint32_t a = b;
+                for (int l = NV - 2; l >= 1; --l) {
+                    t[P.var_of_loop[l]] = S.val[l - 1][a];
+                    a = S.par[l - 1][a];
+                }
+            } else {
+                atomicOr(&ctl->overflow, 1u);
+            }
+            ++idx;
+        }
+    }
+}
+
 // Walk loops 1..NV-1 below the entry in S, loop 1 over candidates [t0, t1).
 template <int NV, bool MAT>
 __device__ void kwalk(const KPlan& P, KWarp<NV>& S, uint32_t t0, uint32_t t1, uint64_t& cnt, uint64_t& work,
@@ -1032,6 +1165,14 @@ __device__ void kwalk(const KPlan& P, KWarp<NV>& S, uint32_t t0, uint32_t t1, ui
         const uint64_t r = S.round[li], tot = S.total[li];
         __syncwarp();
         if (r * 32 >= tot) {
+            if (L == NV - 1) {  // the last loop's long parents, one at a time
+                uint32_t lm = S.lmask;
+                while (lm) {
+                    const uint32_t b = __ffs(lm) - 1;
+                    lm &= lm - 1;
+                    kpair<NV, MAT>(P, S, b, cnt, ctl, out, cap);
+                }
+            }
             if (L == 1) break;
             --L;
             continue;
@@ -1126,12 +1267,9 @@ __device__ void kwalk(const KPlan& P, KWarp<NV>& S, uint32_t t0, uint32_t t1, ui
 
 // Persistent search kernel: warps take work items of `grain` loop-1
 // candidates (0: sized so that each warp gets about 8 items) from an atomic
-// counter, over the concatenation of all entries' candidates.  Bounded to
-// 40 registers (12 blocks of 128 threads per SM): the per-cell setup at an
-// entry's start would otherwise lift the whole kernel to 48 and cost 5% on
-// LW over [256]^3.
+// counter, over the concatenation of all entries' candidates.
 template <int NV, bool MAT>
-__global__ void __launch_bounds__(KJ_MAXT, 12) kjoin_kernel(const KPlan* __restrict__ gP,
+__global__ void __launch_bounds__(KJ_MAXT) kjoin_kernel(const KPlan* __restrict__ gP,
                                                         const KEntry* __restrict__ entries,
                                                         const uint64_t* __restrict__ unit_off, JoinCtl* ctl,
                                                         uint32_t grain_in, uint32_t* __restrict__ out, uint64_t cap,
@@ -1373,6 +1511,7 @@ hc_status run_kjoin_impl(const hc_kquery* q, const hc_kindex* const* idx, const 
     KPlan P;
     HC_TRY(make_kplan(q, idx, P));
     P.stats = (dp.flags & HC_FLAG_STATS) ? 1 : 0;
+    P.pair_min = dp.pair_min ? dp.pair_min : KPAIR_MIN;
     const uint32_t nv = q->n_vars;
 
     std::vector<KCell> hcells;

@@ -207,13 +207,15 @@ def choose_korder(query: KQuery, indexes: Sequence[KIndex]) -> tuple:
 
 def run_kjoin(query: KQuery, indexes: Sequence[KIndex], mode: str = "count", stats: bool = False,
               item_grain: int = 0, block_threads: int = 0, time_kernels: bool = False, stream=None,
-              cell_counts: bool = False) -> Result:
+              cell_counts: bool = False, pair_min: int = 0) -> Result:
     """Generic Join of a k-ary query in every HyperCube cell (the shares
     come from the indexes, see build_kindex); tuples (materialize) come back
     as a (count, n_vars) int32 CUDA tensor in variable-id order, in no fixed
     order; ``cell_counts`` adds the count of each cell (int64, cell id = the
     mixed radix of the variables' coordinates, variable 0 most
-    significant)."""
+    significant); ``pair_min``: last-loop bindings with at least this many
+    candidates are searched warp-wide (0: the library's 32, 0xFFFFFFFF:
+    never)."""
     if len(indexes) != len(query.atoms):
         raise ValueError("one index per atom")
     if mode not in ("count", "materialize"):
@@ -226,6 +228,7 @@ def run_kjoin(query: KQuery, indexes: Sequence[KIndex], mode: str = "count", sta
                  | (_lib.HC_FLAG_CELL_COUNTS if cell_counts else 0))
     prm.item_grain = item_grain
     prm.block_threads = block_threads
+    prm.pair_min = pair_min
     lib = _lib.load()
     out = ctypes.c_void_p()
     _lib.check(lib.hc_run_kjoin(ctypes.byref(q), ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)),

@@ -279,3 +279,32 @@ def test_six_variables(hc, seed):
     rels = [distinct_rows(rng, {1: 5, 2: 30, 3: 200}[len(a)], len(a), dom) for a in atoms]
     for order in ((0, 1, 2, 3, 4, 5), (5, 3, 1, 4, 0, 2)):
         run_both(hc, 6, atoms, rels, order)
+
+
+@pytest.mark.parametrize("pair_min", [1, 4, 0xFFFFFFFF])
+def test_last_loop_paths_agree(hc, pair_min):
+    """The last loop's per-binding path (warp-wide, 128 candidates an
+    iteration) against the flattened one: pair_min 1 sends every last-loop
+    binding through it, 0xFFFFFFFF none; counts, work and sorted tuples
+    equal the oracle's for LW, CT, mixed arities (a last loop with one list,
+    and a top-level list with a position map), two and six variables, and a
+    cube whose bindings span several 128-candidate blocks."""
+    rng = np.random.default_rng(123)
+    rels = [distinct_rows(rng, 1500, 3, 14) for _ in LW_ATOMS]
+    run_both(hc, 4, LW_ATOMS, rels, (0, 1, 2, 3), pair_min=pair_min)
+    run_both(hc, 4, LW_ATOMS, rels, (3, 1, 0, 2), pair_min=pair_min)
+    run_both(hc, 4, CT_ATOMS, rels[:3], (1, 0, 2, 3), pair_min=pair_min)
+    atoms = [(2, 0, 4), (3, 1), (4,), (1, 2, 0), (3, 4)]
+    mixed = [distinct_rows(rng, {1: 6, 2: 50, 3: 350}[len(a)], len(a), 9) for a in atoms]
+    run_both(hc, 5, atoms, mixed, (0, 1, 2, 3, 4), pair_min=pair_min)
+    run_both(hc, 5, atoms, mixed, (4, 3, 2, 1, 0), pair_min=pair_min)
+    r = distinct_rows(rng, 4000, 2, 300)
+    s = distinct_rows(rng, 120, 1, 300)
+    run_both(hc, 2, [(0, 1), (1,)], [r, s], pair_min=pair_min)
+    run_both(hc, 2, [(0, 1)], [r], pair_min=pair_min)
+    six = [(0, 1, 2), (2, 3, 4), (4, 5), (5, 0), (1, 3), (3,)]
+    rels6 = [distinct_rows(rng, {1: 5, 2: 30, 3: 200}[len(a)], len(a), 7) for a in six]
+    run_both(hc, 6, six, rels6, (5, 3, 1, 4, 0, 2), pair_min=pair_min)
+    cube = datagen.full_cube(40)
+    sparse = [cube[rng.random(cube.shape[0]) < 0.7] for _ in LW_ATOMS]
+    run_both(hc, 4, LW_ATOMS, sparse, pair_min=pair_min)
