@@ -1103,19 +1103,40 @@ __device__ __forceinline__ void kpair(const KPlan& P, KWarp<NV>& S, uint32_t b, 
                 }
                 continue;
             }
-            const uint32_t vmin = S.pl[q][2], vmax = S.pl[q][3], sd = S.pl[q][4];
-            const bool dir = sd != 0;
+            const uint32_t vmin = S.pl[q][2], span = S.pl[q][3] - vmin, sd = S.pl[q][4];
+            if (sd == 0) {  // a short list: binary search
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    uint32_t pos;
+                    if (ok[j]) ok[j] = vv[j] - vmin <= span && find_u32(sq.v, lo, hi, vv[j], pos);
+                }
+                continue;
+            }
             const uint4* __restrict__ gq = sq.g + lo;
             uint4 ev[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                ok[j] = ok[j] && vv[j] >= vmin && vv[j] <= vmax;
-                ev[j] = (ok[j] && dir) ? dir_load(gq, (vv[j] - vmin) >> (sd & 0xFFu)) : make_uint4(0u, 0u, 0u, 0u);
+                const uint32_t dx = vv[j] - vmin;  // x in [vmin, vmax] <=> x - vmin <= vmax - vmin
+                ok[j] = ok[j] && dx <= span;
+                ev[j] = ok[j] ? dir_load(gq, dx >> (sd & 0xFFu)) : make_uint4(0u, 0u, 0u, 0u);
             }
+            // the entry's three values decide, unless x lies beyond them
+            // (then the walk of dir_walk_find, which also pulls a position
+            // outside the run back to it)
+            uint32_t slow = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                uint32_t pos;
-                if (ok[j]) ok[j] = dir ? dir_walk_find(sq.v, ev[j], hi, vv[j], pos) : find_u32(sq.v, lo, hi, vv[j], pos);
+                const uint4 e = ev[j];
+                const bool hit = (e.y == vv[j]) | (e.z == vv[j]) | (e.w == vv[j]);
+                slow |= (ok[j] && vv[j] > e.w ? 1u : 0u) << j;
+                ok[j] = ok[j] && hit;
+            }
+            if (slow) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    uint32_t pos;
+                    if (slow >> j & 1u) ok[j] = dir_walk_find(sq.v, ev[j], hi, vv[j], pos);
+                }
             }
         }
         uint32_t mine = 0;
