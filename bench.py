@@ -92,6 +92,9 @@ def parse_args():
                     help="materialize output pool: 'plan' = 1.25 x the planning run's count (one pass), "
                          "'0' = counting pass + emitting pass")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-select", choices=["all", "rmat"], default="all",
+                    help="serve: restrict every request to a vertex sample (all), or only those with an R-MAT "
+                         "atom (rmat; the others join the uniform relations unrestricted)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-edges", default="1e4,8e6",
                     help="batched: range of the log-uniform subgraph edge counts")
@@ -1125,6 +1128,9 @@ def serve_workload(a, world, rank, local):
         rel_names = tuple(names[k] for k in rng.integers(0, len(names), size=len(base.atoms)))
         size = int(np.exp(rng.uniform(np.log(4096), np.log(131072))))
         f = np.unique(pool[rng.integers(0, pool.shape[0], size=size)])
+        if a.serve_select == "rmat" and "rmat23" not in rel_names:
+            reqs.append(Request(i, base, rel_names, None))  # the uniform relations as they are
+            continue
         q = base.with_atoms([(v, None) for v in range(base.n_vars)])
         reqs.append(Request(i, q, rel_names, f))
     srv = Server(idx, budget_bytes=120 << 30, max_inflight=8, device=dev)
@@ -1160,9 +1166,13 @@ def serve_workload(a, world, rank, local):
             "ms_per_step": 1e3 * serial_s / n, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic (seeded R-MAT + uniform relations)",
             "config": {"workload": "10,000 Poisson requests, 60% Q1 / 30% Q2 / 10% Q6 over R-MAT scale 23 ef 16 "
-                                   "(symmetric) + uniform 50M/10M/1M pairs on 2^24 vertices; every variable "
-                                   "restricted to a request vertex sample (4096..131072 vertices of R-MAT "
-                                   "degree <= 64)",
+                                   "(symmetric) + uniform 50M/10M/1M pairs on 2^24 vertices; " + (
+                                       "every variable restricted to a request vertex sample (4096..131072 "
+                                       "vertices of R-MAT degree <= 64)" if a.serve_select == "all" else
+                                       "requests with an R-MAT atom restricted to a request vertex sample "
+                                       "(4096..131072 vertices of R-MAT degree <= 64), the others over the "
+                                       "uniform relations as they are"),
+                       "unrestricted_requests": sum(1 for r in reqs if r.restrict is None),
                        "rows": {k: int(v.shape[0]) for k, v in rels.items()}, "max_inflight": 8,
                        "hbm_budget_gb": 120, "serial_throughput_per_s": mu, "rates": rates,
                        "counts_equal_alone": True, "generate_s": round(gen_s, 1)},

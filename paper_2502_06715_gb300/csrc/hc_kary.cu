@@ -726,6 +726,11 @@ namespace {
 constexpr int KMAXS = 4;          // lists intersected by one loop
 constexpr uint64_t KMAX_CELLS = 1ull << 20;
 constexpr uint32_t KPAIR_MIN = 32;  // default per-binding threshold of the last loop
+// How kpair searches a list: a run holding every integer of [vmin, vmax]
+// addresses itself (x can only sit at lo + x - vmin: one 4-byte read);
+// else through its bucket directory (low byte: the bucket shift), else, a
+// run shorter than DIR_MIN, by binary search.
+constexpr uint32_t KP_DIRECT = 0x200u, KP_DIR = 0x100u;
 constexpr int KJ_MAXT = 128;      // threads per block of the search kernel, at most
 constexpr int KJ_WARPS = KJ_MAXT / 32;
 
@@ -963,7 +968,7 @@ struct KWarp {
     uint64_t c0[32];    // each lane's count when the entry started (per-cell counts)
     uint32_t llen[32];  // candidates of each last-loop parent on the per-binding path
     uint32_t lmask;     // those parents
-    uint32_t pl[KMAXS][5];  // kpair: each list's lo, hi, vmin, vmax, bucket shift (| 0x100: directory)
+    uint32_t pl[KMAXS][5];  // kpair: each list's lo, hi, vmin, vmax, search (KP_* | bucket shift)
     uint8_t par[NF][32];
     uint8_t drv[NV - 1][32];
 };
@@ -1078,7 +1083,10 @@ __device__ __forceinline__ void kpair(const KPlan& P, KWarp<NV>& S, uint32_t b, 
             const bool dir = sq.g != nullptr && hi - lo >= DIR_MIN;
             S.pl[lane][2] = vmin;
             S.pl[lane][3] = vmax;
-            S.pl[lane][4] = dir ? (0x100u | dir_shift(hi - lo, vmax - vmin)) : 0u;
+            // distinct ascending values with vmax - vmin = n - 1 are every integer between
+            S.pl[lane][4] = vmax - vmin == hi - lo - 1 ? KP_DIRECT
+                            : dir                      ? (KP_DIR | dir_shift(hi - lo, vmax - vmin))
+                                                       : 0u;
         }
     }
     __syncwarp();
@@ -1104,6 +1112,16 @@ __device__ __forceinline__ void kpair(const KPlan& P, KWarp<NV>& S, uint32_t b, 
                 continue;
             }
             const uint32_t vmin = S.pl[q][2], span = S.pl[q][3] - vmin, sd = S.pl[q][4];
+            if (sd == KP_DIRECT) {  // x can only be at lo + (x - vmin): read that value
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t dx = vv[j] - vmin;
+                    ok[j] = ok[j] && dx <= span;
+                    const uint32_t w = ok[j] ? __ldg(sq.v + lo + dx) : 0u;
+                    ok[j] = ok[j] && w == vv[j];
+                }
+                continue;
+            }
             if (sd == 0) {  // a short list: binary search
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {

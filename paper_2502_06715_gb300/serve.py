@@ -1,9 +1,9 @@
 """Continuous-batching join server over device-resident indexes.
 
 Relations are indexed once and stay in HBM.  A request names a query, the
-relation bound to each of its atoms and the values its first variable is
-restricted to (a unary atom, i.e. a selection pushed into the query,
-Sec. 2).  The loop admits queued requests while a stream slot is free and
+relation bound to each of its binary atoms and, optionally, the values its
+unary atoms restrict variables to (a selection pushed into the query,
+Sec. 2); a request without a selection joins the relations as they are.  The loop admits queued requests while a stream slot is free and
 the request's device footprint (``join_footprint``) fits in what is left of
 the HBM budget; admitted requests run concurrently, one CUDA stream each, so
 their kernels overlap on the device; a finished request frees its slot and
@@ -30,7 +30,7 @@ class Request:
     rid: int
     query: Query            # binary atoms first, then unary atoms over `restrict`
     relations: tuple        # relation name per binary atom
-    restrict: np.ndarray    # values the unary atoms allow (sorted, distinct, uint32)
+    restrict: np.ndarray | None  # values the unary atoms allow; None: no unary atoms
     arrival: float = 0.0    # seconds from the start of the run
 
 
@@ -54,9 +54,11 @@ def _selection_values(values) -> np.ndarray:
     return np.unique(np.asarray(values, dtype=np.uint32))
 
 
-def _unary_index(values: np.ndarray, device, stream) -> Index:
+def _unary_index(values: np.ndarray | None, device, stream) -> Index | None:
     """The request's selection as a unary index, built on `stream` without
-    waiting for the GPU."""
+    waiting for the GPU (None without a selection)."""
+    if values is None:
+        return None
     v = _selection_values(values)
     d = torch.from_numpy(v.view(np.int32)).to(device)
     return build_unary_index(d, int(v[-1]) if v.shape[0] else 0, stream=stream)
@@ -71,9 +73,11 @@ class Server:
     options: dict = field(default_factory=dict)
     _fp: dict = field(default_factory=dict, repr=False)  # footprint cache
 
-    def _indexes(self, req: Request, unary: Index) -> list:
+    def _indexes(self, req: Request, unary: Index | None) -> list:
         # every atom after the binary ones is a unary atom over the request's values
         extra = len(req.query.atoms) - len(req.relations)
+        if extra and unary is None:
+            raise ValueError("a request with unary atoms needs its selection")
         return [self.indexes[n] for n in req.relations] + [unary] * extra
 
     def footprint(self, req: Request) -> int:
@@ -81,13 +85,16 @@ class Server:
         size class of the selection): the class's largest selection (the next
         power of two, values up to the next power of two) stands in for the
         request's own, so the cached figure bounds every request of the class."""
-        n = max(1, int(req.restrict.shape[0]))
-        top = int(req.restrict.max()) if req.restrict.shape[0] else 0
-        cn, cv = 1 << (n - 1).bit_length(), (1 << max(1, top.bit_length())) - 1
+        if req.restrict is None:
+            cn = cv = -1
+        else:
+            n = max(1, int(req.restrict.shape[0]))
+            top = int(req.restrict.max()) if req.restrict.shape[0] else 0
+            cn, cv = 1 << (n - 1).bit_length(), (1 << max(1, top.bit_length())) - 1
         key = (req.query.n_vars, tuple(req.query.atoms), req.query.order, tuple(req.relations), cn, cv)
         fp = self._fp.get(key)
         if fp is None:
-            stand_in = Index.from_stats(cn, cn, 0, cv, 0)
+            stand_in = None if req.restrict is None else Index.from_stats(cn, cn, 0, cv, 0)
             fp = join_footprint(req.query, self._indexes(req, stand_in), **self.options)
             self._fp[key] = fp
         return fp
@@ -128,7 +135,8 @@ class Server:
                 req, s, unary, pend, ev, fp, t_adm = item
                 if ev.query():
                     c = pend.count()
-                    unary.free()
+                    if unary is not None:
+                        unary.free()
                     out.append(Outcome(req.rid, c, req.arrival, t_adm, time.perf_counter() - t0))
                     budget += fp
                     streams.append(s)
@@ -150,7 +158,8 @@ def serve_serial(server: Server, requests: list) -> list:
         with torch.cuda.stream(s):
             unary = _unary_index(req.restrict, server.device, s)
             c = run_join(req.query, server._indexes(req, unary), stream=s, **server.options).count
-            unary.free()
+            if unary is not None:
+                unary.free()
         s.synchronize()
         out.append(Outcome(req.rid, c, 0.0, t, time.perf_counter()))
     return out

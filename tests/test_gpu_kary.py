@@ -308,3 +308,21 @@ def test_last_loop_paths_agree(hc, pair_min):
     cube = datagen.full_cube(40)
     sparse = [cube[rng.random(cube.shape[0]) < 0.7] for _ in LW_ATOMS]
     run_both(hc, 4, LW_ATOMS, sparse, pair_min=pair_min)
+
+
+@pytest.mark.parametrize("pair_min", [0, 1, 0xFFFFFFFF])
+def test_dense_runs(hc, pair_min):
+    """Lists that hold every integer of their range (ST-Dense cubes, here
+    offset by 1000 so that no range starts at 0) are searched by reading the
+    one position a value can take; mixed with lists that have gaps, runs of
+    exactly 32 values (the per-binding threshold), and materialize mode,
+    all against the oracle."""
+    rng = np.random.default_rng(321)
+    cube = datagen.full_cube(12).astype(np.uint32) + np.uint32(1000)
+    holes = cube[rng.random(cube.shape[0]) < 0.8]
+    run_both(hc, 4, LW_ATOMS, [cube] * 4, pair_min=pair_min)
+    run_both(hc, 4, LW_ATOMS, [cube, holes, cube, holes], pair_min=pair_min)
+    run_both(hc, 4, LW_ATOMS, [holes, cube, cube, cube], (2, 0, 3, 1), pair_min=pair_min)
+    c32 = np.array(list(itertools.product(range(3), range(3), range(32))), dtype=np.uint32)
+    run_both(hc, 4, LW_ATOMS, [c32, c32, c32, c32], pair_min=pair_min)
+    run_both(hc, 4, CT_ATOMS, [cube, holes, cube], pair_min=pair_min)

@@ -81,3 +81,31 @@ def test_admission_respects_budget(hc):
     spans = sorted((o.admitted, o.done) for o in out)
     for (a0, d0), (a1, d1) in zip(spans, spans[1:]):
         assert a1 >= d0 - 1e-3  # never two in flight
+
+
+def test_unrestricted_requests_served(hc):
+    """Requests without a selection (the uniform relations joined as they
+    are) beside restricted ones: served counts equal the same requests run
+    alone, and the unrestricted ones equal the oracle over the relations."""
+    import torch
+
+    from paper_2502_06715_gb300.serve import Request, Server, serve_serial
+
+    nv = 1 << 12
+    rels = {"rmat": datagen.rmat_graph(12, 8, 5),
+            "u20k": datagen.uniform_relation(20000, nv, 6),
+            "u5k": datagen.uniform_relation(5000, nv, 7)}
+    idx = {k: hc.build_index(torch.from_numpy(v.view(np.int32)).cuda(), 0) for k, v in rels.items()}
+    reqs = make_requests(hc, rels, 30, 11, nv)
+    rng = np.random.default_rng(12)
+    for i in range(30, 50):
+        base = (hc.TRIANGLE, hc.FOUR_CYCLE, hc.FOUR_CLIQUE)[i % 3]
+        names = tuple(("u20k", "u5k")[k] for k in rng.integers(0, 2, size=len(base.atoms)))
+        reqs.append(Request(i, base, names, None, arrival=0.0002 * i))
+    srv = Server(idx, budget_bytes=1 << 30, max_inflight=4)
+    alone = {o.rid: o.count for o in serve_serial(srv, reqs)}
+    mixed = {o.rid: o.count for o in srv.run(reqs)}
+    assert mixed == alone
+    for r in reqs[30:]:
+        want = oracle.gj_count(r.query.n_vars, list(r.query.atoms), [rels[n] for n in r.relations])[0]
+        assert alone[r.rid] == want, r.rid

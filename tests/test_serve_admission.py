@@ -42,3 +42,21 @@ def test_cached_footprint_bounds_every_request():
         assert cached >= exact, (i, cached, exact)
     # the cache is keyed by size class: far fewer entries than requests
     assert len(server._fp) < 120
+
+
+def test_unrestricted_requests_footprint():
+    """A request without a selection joins the resident relations as they
+    are: its footprint is the query's over those indexes alone, and asking
+    for unary atoms without a selection is refused."""
+    from paper_2502_06715_gb300.serve import Request, Server
+
+    nv = 1 << 24
+    rels = {"u10M": hc.Index.from_stats(10_000_000, 7_000_000, 0, nv - 1, nv - 1),
+            "u1M": hc.Index.from_stats(1_000_000, 950_000, 0, nv - 1, nv - 1)}
+    server = Server(rels)
+    req = Request(0, hc.TRIANGLE, ("u10M", "u1M", "u10M"), None)
+    want = hc.join_footprint(hc.TRIANGLE, [rels["u10M"], rels["u1M"], rels["u10M"]])
+    assert server.footprint(req) == want
+    bad = Request(1, hc.TRIANGLE.with_atoms([(0, -1)]), ("u10M", "u1M", "u10M"), None)
+    with pytest.raises(ValueError):
+        server.footprint(bad)
