@@ -39,6 +39,7 @@ METRIC = "join output tuples/s (R-MAT triangle)"
 UNIT = "tuples/s"
 PROFILE_NOTE = os.path.join(ROOT, "profiles", "gj_search_kernel_rmat22.md")
 BUILD_PROFILE_NOTE = os.path.join(ROOT, "profiles", "radix_pass_rmat22_build.md")
+KJOIN_PROFILE_NOTE = os.path.join(ROOT, "profiles", "kjoin_kernel_lw.md")  # LW over [512]^3, one cell
 
 
 def parse_args():
@@ -1018,10 +1019,13 @@ def kary_workload(a, world, rank, local):
     kms = kern_ms / a.steps
     metric = "LW results/s (count)" if a.workload == "lw" else "CT results/s (count)"
     achieved = 4.0 * work / (kms / 1e3) / 1e9
+    # the committed capture covers LW over ST-Dense's [512]^3 cubes in one cell
+    profiled = (a.workload == "lw" and a.lw_n == 512 and a.tensor == "dense" and kshares == (1, 1, 1, 1))
     roofline = {"bound": "hbm", "kernel": "kjoin_kernel<4> (k-ary search)", "achieved": round(achieved, 1),
                 "launches_per_step": 1,
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "alg_bytes_per_launch": 4 * work, "avg_launch_ms": round(kms, 3),
+                "traffic": profiled_traffic(KJOIN_PROFILE_NOTE, ("hc_kary.cu", "hc_internal.cuh")) if profiled else None,
+                "alg_bytes_per_launch": 4 * work, "avg_launch_ms": round(kms, 3),
                 "note": "work measure x 4 B; short lists are L1/L2-resident, so this can exceed what DRAM moves"}
 
     e2e = None
