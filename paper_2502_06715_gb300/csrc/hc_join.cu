@@ -800,7 +800,7 @@ __device__ __forceinline__ void probe_pair(const DPlan& P, const Entry<NL, S>& E
             for (int j = 0; j < 4; ++j) {
                 const uint32_t t = t0 + 32 * j + lane;
                 vv[j] = t < a1 ? load_ro(la + t) : 0u;
-                okv[j] = t < a1 && vv[j] >= vmin && vv[j] <= vmax;
+                okv[j] = t < a1 && vv[j] - vmin <= vmax - vmin;  // x in [vmin, vmax], one compare
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j)

@@ -730,7 +730,7 @@ constexpr uint32_t KPAIR_MIN = 32;  // default per-binding threshold of the last
 // addresses itself (x can only sit at lo + x - vmin: one 4-byte read);
 // else through its bucket directory (low byte: the bucket shift), else, a
 // run shorter than DIR_MIN, by binary search.
-constexpr uint32_t KP_DIRECT = 0x200u, KP_DIR = 0x100u;
+constexpr uint32_t KP_DIRECT = 0x200u, KP_DIR = 0x100u, KP_POS = 0x400u;  // KP_POS: a top level's position map
 constexpr int KJ_MAXT = 128;      // threads per block of the search kernel, at most
 constexpr int KJ_WARPS = KJ_MAXT / 32;
 
@@ -968,7 +968,13 @@ struct KWarp {
     uint64_t c0[32];    // each lane's count when the entry started (per-cell counts)
     uint32_t llen[32];  // candidates of each last-loop parent on the per-binding path
     uint32_t lmask;     // those parents
-    uint32_t pl[KMAXS][5];  // kpair: each list's lo, hi, vmin, vmax, search (KP_* | bucket shift)
+    // kpair, per list of the parent: (lo, span or hi, vmin or pos_n, search kind KP_* | bucket
+    // shift), the array it reads (the values from lo for KP_DIRECT, the position map for KP_POS),
+    // the directory from lo, and hi
+    uint4 prec[KMAXS];
+    const uint32_t* pptr[KMAXS];
+    const uint4* pdir[KMAXS];
+    uint32_t phi[KMAXS];
     uint8_t par[NF][32];
     uint8_t drv[NV - 1][32];
 };
@@ -1076,17 +1082,19 @@ __device__ __forceinline__ void kpair(const KPlan& P, KWarp<NV>& S, uint32_t b, 
         const KSrc& sq = P.src[L][lane];
         uint32_t lo, hi;
         krange<NV>(P, S, L, (int)lane, b, lo, hi);
-        S.pl[lane][0] = lo;
-        S.pl[lane][1] = hi;
-        if (!(sq.depth == 0 && sq.pos != nullptr)) {
+        S.phi[lane] = hi;
+        if (sq.depth == 0 && sq.pos != nullptr) {
+            S.prec[lane] = make_uint4(lo, hi, sq.pos_n, KP_POS);
+            S.pptr[lane] = sq.pos;
+        } else {
             const uint32_t vmin = __ldg(sq.v + lo), vmax = __ldg(sq.v + hi - 1);
             const bool dir = sq.g != nullptr && hi - lo >= DIR_MIN;
-            S.pl[lane][2] = vmin;
-            S.pl[lane][3] = vmax;
             // distinct ascending values with vmax - vmin = n - 1 are every integer between
-            S.pl[lane][4] = vmax - vmin == hi - lo - 1 ? KP_DIRECT
-                            : dir                      ? (KP_DIR | dir_shift(hi - lo, vmax - vmin))
-                                                       : 0u;
+            const bool direct = vmax - vmin == hi - lo - 1;
+            S.prec[lane] = make_uint4(lo, vmax - vmin, vmin,
+                                      direct ? KP_DIRECT : dir ? (KP_DIR | dir_shift(hi - lo, vmax - vmin)) : 0u);
+            S.pptr[lane] = direct ? sq.v + lo : sq.v;
+            S.pdir[lane] = dir ? sq.g + lo : nullptr;
         }
     }
     __syncwarp();
@@ -1101,42 +1109,42 @@ __device__ __forceinline__ void kpair(const KPlan& P, KWarp<NV>& S, uint32_t b, 
         }
         for (int q = 0; q < ns; ++q) {
             if (q == (int)d) continue;
-            const KSrc& sq = P.src[L][q];
-            const uint32_t lo = S.pl[q][0], hi = S.pl[q][1];
-            if (sq.depth == 0 && sq.pos != nullptr) {
+            const uint4 r = S.prec[q];
+            const uint32_t* __restrict__ pq = S.pptr[q];
+            if (r.w == KP_DIRECT) {  // x can only be at lo + (x - vmin): read that value
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const uint32_t p = ok[j] && vv[j] < sq.pos_n ? __ldg(sq.pos + vv[j]) : V1POS_NONE;
-                    ok[j] = p != V1POS_NONE && p >= lo && p < hi;
-                }
-                continue;
-            }
-            const uint32_t vmin = S.pl[q][2], span = S.pl[q][3] - vmin, sd = S.pl[q][4];
-            if (sd == KP_DIRECT) {  // x can only be at lo + (x - vmin): read that value
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const uint32_t dx = vv[j] - vmin;
-                    ok[j] = ok[j] && dx <= span;
-                    const uint32_t w = ok[j] ? __ldg(sq.v + lo + dx) : 0u;
+                    const uint32_t dx = vv[j] - r.z;
+                    ok[j] = ok[j] && dx <= r.y;
+                    const uint32_t w = ok[j] ? __ldg(pq + dx) : 0u;
                     ok[j] = ok[j] && w == vv[j];
                 }
                 continue;
             }
-            if (sd == 0) {  // a short list: binary search
+            if (r.w == KP_POS) {  // a top level's position map, checked against the cell's range
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    uint32_t pos;
-                    if (ok[j]) ok[j] = vv[j] - vmin <= span && find_u32(sq.v, lo, hi, vv[j], pos);
+                    const uint32_t p = ok[j] && vv[j] < r.z ? __ldg(pq + vv[j]) : V1POS_NONE;
+                    ok[j] = p != V1POS_NONE && p >= r.x && p < r.y;
                 }
                 continue;
             }
-            const uint4* __restrict__ gq = sq.g + lo;
+            const uint32_t lo = r.x, span = r.y, vmin = r.z, hi = S.phi[q];
+            if (r.w == 0) {  // a short list: binary search
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    uint32_t pos;
+                    if (ok[j]) ok[j] = vv[j] - vmin <= span && find_u32(pq, lo, hi, vv[j], pos);
+                }
+                continue;
+            }
+            const uint4* __restrict__ gq = S.pdir[q];
             uint4 ev[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const uint32_t dx = vv[j] - vmin;  // x in [vmin, vmax] <=> x - vmin <= vmax - vmin
                 ok[j] = ok[j] && dx <= span;
-                ev[j] = ok[j] ? dir_load(gq, dx >> (sd & 0xFFu)) : make_uint4(0u, 0u, 0u, 0u);
+                ev[j] = ok[j] ? dir_load(gq, dx >> (r.w & 0xFFu)) : make_uint4(0u, 0u, 0u, 0u);
             }
             // the entry's three values decide, unless x lies beyond them
             // (then the walk of dir_walk_find, which also pulls a position
@@ -1153,7 +1161,7 @@ __device__ __forceinline__ void kpair(const KPlan& P, KWarp<NV>& S, uint32_t b, 
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     uint32_t pos;
-                    if (slow >> j & 1u) ok[j] = dir_walk_find(sq.v, ev[j], hi, vv[j], pos);
+                    if (slow >> j & 1u) ok[j] = dir_walk_find(pq, ev[j], hi, vv[j], pos);
                 }
             }
         }
