@@ -157,3 +157,21 @@ def test_serving_selection_is_sorted_and_distinct():
     v = _selection_values([9, 3, 3, 0xFFFFFFFF, 0, 9])
     assert v.dtype == np.uint32 and v.tolist() == [0, 3, 9, 0xFFFFFFFF]
     assert _selection_values([]).shape == (0,)
+
+
+def test_partitioned_kindex_argument_checks(lib):
+    """hc_build_kindex_partitioned refuses bad shares and missing seeds,
+    shares or rows before any device work."""
+    import ctypes
+
+    out = ctypes.c_void_p()
+    seeds = (ctypes.c_uint32 * 3)(1, 2, 3)
+    for sh in ((2, 0, 1), (256, 256, 2)):  # a zero share; a product above 65536
+        shares = (ctypes.c_uint32 * 3)(*sh)
+        assert lib.hc_build_kindex_partitioned(None, 0, 3, None, seeds, shares, 0, None, ctypes.byref(out)) == 1
+        assert not out.value
+    good = (ctypes.c_uint32 * 3)(2, 2, 1)
+    assert lib.hc_build_kindex_partitioned(None, 0, 3, None, None, good, 0, None, ctypes.byref(out)) == 1
+    assert lib.hc_build_kindex_partitioned(None, 0, 3, None, seeds, None, 0, None, ctypes.byref(out)) == 1
+    assert lib.hc_build_kindex_partitioned(None, 10, 3, None, seeds, good, 0, None, ctypes.byref(out)) == 1
+    assert lib.hc_build_kindex_partitioned(None, 0, 4, None, seeds, good, 0, None, ctypes.byref(out)) == 1
