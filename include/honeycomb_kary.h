@@ -168,7 +168,9 @@ hc_status hc_run_kjoin(const hc_kquery* q, const hc_kindex* const* idx, const hc
  * variable v (the least single-column count among its atoms).  For binary
  * atoms these are hc_plan_cost's level costs without query rewriting.  Host
  * only; statistics-only indexes serve; the indexes' level orders need not
- * match q->order. */
+ * match q->order.  The level sizes of a partitioned index count a prefix
+ * once per partition that holds it, so estimates are best taken from the
+ * unpartitioned indexes. */
 hc_status hc_kplan_cost(const hc_kquery* q, const hc_kindex* const* idx, double level_cost[HC_MAX_VARS],
                         double dom_out[HC_MAX_VARS]);
 /* Loop order of least estimated cost (the sum of hc_kplan_cost's level
