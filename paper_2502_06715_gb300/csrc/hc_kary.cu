@@ -1059,10 +1059,10 @@ __device__ __forceinline__ void kinit_level(const KPlan& P, KWarp<NV>& S, int L,
 // The per-binding path of the last loop: parent b's candidates, the
 // elements of its shortest list, 128 per iteration (lane l takes the
 // elements l, l + 32, l + 64, l + 96 of each block), searched in each other
-// list in turn with the four directory reads of a lane issued together.  A
-// list's range, bounds and bucket width are the same for every candidate,
-// so they are read once.  The last loop's lists are the atoms' last levels
-// (no positions are needed).
+// list in turn with the four reads of a lane issued together.  A list's
+// range, bounds and search kind (KP_*) are the same for every candidate, so
+// one lane per list sets them up once, in one shared-memory record.  The
+// last loop's lists are the atoms' last levels (no positions are needed).
 template <int NV, bool MAT>
 __device__ __forceinline__ void kpair(const KPlan& P, KWarp<NV>& S, uint32_t b, uint64_t& cnt, JoinCtl* ctl,
                                       uint32_t* __restrict__ out, uint64_t cap) {
