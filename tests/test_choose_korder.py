@@ -143,3 +143,15 @@ def test_argument_checks_without_device_work():
     assert e.value.status == 5
     with pytest.raises(hc.HoneycombError):
         hc.kplan_cost(hc.KQuery(4, ((0, 1, 2),)), [r3])  # U in no atom
+
+
+def test_atom_shares_maps_variable_shares_to_columns():
+    """Each atom's columns take their variables' shares and seeds (the
+    arguments of a partitioned build), default seeds v + 1."""
+    import paper_2502_06715_gb300 as hc
+
+    per_atom = hc.atom_shares(hc.LW, (2, 3, 1, 5))
+    assert per_atom == [((1, 2, 3), (2, 3, 1)), ((1, 2, 4), (2, 3, 5)), ((1, 3, 4), (2, 1, 5)),
+                        ((2, 3, 4), (3, 1, 5))]
+    ct = hc.atom_shares(hc.CT, (4, 1, 2, 1), seeds=(9, 8, 7, 6))
+    assert ct == [((9, 8, 7), (4, 1, 2)), ((9, 8, 6), (4, 1, 1)), ((9, 7, 6), (4, 2, 1))]
